@@ -1,0 +1,442 @@
+/*
+ * Plain CPU oracle for the segment x depth-label matching-cost volume, the per-segment temporal
+ * consistency test and the winner-take-all readout of Mieloch, Stankiewicz and Domanski,
+ * "Depth Map Estimation for Free-Viewpoint Television" (arXiv:1909.02294).
+ *
+ * TEST INFRASTRUCTURE ONLY. The library under test never links, loads or calls this file; only the
+ * tests, the smoke check and the benchmark's CPU-baseline leg do. It shares no code, header, table
+ * or constant with the CUDA library: it is written from the paper and from the arithmetic contract
+ * stated below, and it is deliberately slow and direct (single thread, no blocking, no reordering).
+ *
+ * Arithmetic contract (the paper leaves the numerics open; this is the reading both sides follow):
+ *  - Candidate depths are uniform in 1/z between z_far (label 0) and z_near (label L-1), on planes
+ *    parallel to the reference camera's image plane (Sec. IV-A), or to the centre camera's image
+ *    plane when depths are measured from the centre camera (Sec. III-B).
+ *  - The transform T[.] of Eq. 4 for plane n^T X_r = delta is the plane homography
+ *    H = K_v (R_v R_r^T + (t_v - R_v R_r^T t_r) n^T / delta) K_r^-1, formed in FP64 in a fixed
+ *    operation order (or_homography_f64) and rounded once per entry to FP32.
+ *  - A reference pixel (x, y) maps to X = fma(h0,x,fma(h1,y,h2)), Y = fma(h3,x,fma(h4,y,h5)),
+ *    Wz = fma(h6,x,fma(h7,y,h8)) in FP32; it is out of the view unless Wz > 0; otherwise
+ *    r = 1/Wz, u = X*r, v = Y*r (each IEEE FP32 round-to-nearest), and the nearest sample is
+ *    (floor(u + 0.5), floor(v + 0.5)), which must lie inside the view.
+ *  - The sample cost is the L1 distance of the integer (Y, Cb, Cr) vectors (Eq. 4 with a one-pixel
+ *    window and without the 1/size(W) scaling), or a fixed penalty when the sample is out of view.
+ *  - Per pixel the costs of the neighbouring views are combined by their minimum (or their sum, the
+ *    shape of the sum over c' in Eq. 1), and the segment's cost is the int32 sum over its pixels.
+ *  - Temporal test (Sec. III-E): a segment keeps the previous P frame's depth when every compared
+ *    component of its mean colour moved by less than T_P, else the I frame's depth when every
+ *    component moved by less than T_I, else it is re-estimated. With n pixels and channel sums S,
+ *    |S_cur - S_ref| < T * n is the same test on means, evaluated exactly in integers.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    double K[9], R[9], t[3];
+    int32_t width, height;
+} or_camera;
+
+typedef struct {
+    const void* Y;
+    const void* U;
+    const void* V;
+    int64_t pitch; /* row pitch in samples (same for the three planes) */
+} or_image;
+
+/* ------------------------------------------------------------------------------------ depths */
+
+/* Candidate inverse depths, uniform in 1/z, label 0 = far (Sec. IV-A: planes parallel to the camera). */
+int or_label_inv_depths(int L, double z_near, double z_far, double* iz) {
+    if (L < 1 || !(z_near > 0) || !(z_far > z_near) || !iz) return 1;
+    double a = 1.0 / z_far;
+    double b = 1.0 / z_near;
+    if (L == 1) {
+        iz[0] = a;
+        return 0;
+    }
+    double step = (b - a) / (double)(L - 1);
+    for (int d = 0; d < L; d++) iz[d] = a + (double)d * step;
+    return 0;
+}
+
+/* --------------------------------------------------------------------------------- geometry */
+
+static int k_ok(const double* K) {
+    return K[3] == 0.0 && K[6] == 0.0 && K[7] == 0.0 && K[8] == 1.0 && K[0] != 0.0 && K[4] != 0.0;
+}
+
+/* Inverse of an upper-triangular intrinsic matrix K = [[fx, s, cx], [0, fy, cy], [0, 0, 1]]. */
+static void k_inverse(const double* K, double* Ki) {
+    double fx = K[0], s = K[1], cx = K[2], fy = K[4], cy = K[5];
+    double fxfy = fx * fy;
+    Ki[0] = 1.0 / fx;
+    Ki[1] = -s / fxfy;
+    Ki[2] = (s * cy - cx * fy) / fxfy;
+    Ki[3] = 0.0;
+    Ki[4] = 1.0 / fy;
+    Ki[5] = -cy / fy;
+    Ki[6] = 0.0;
+    Ki[7] = 0.0;
+    Ki[8] = 1.0;
+}
+
+/* c = a * b for row-major 3x3, each entry summed left to right */
+static void mat3_mul(const double* a, const double* b, double* c) {
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++)
+            c[i * 3 + j] = (a[i * 3 + 0] * b[0 * 3 + j] + a[i * 3 + 1] * b[1 * 3 + j]) + a[i * 3 + 2] * b[2 * 3 + j];
+}
+
+/*
+ * FP64 plane homography of Eq. 4's transform T[.] from reference camera cr into view cv for the
+ * candidate plane with inverse depth iz (Sec. IV-A). With cc == NULL the plane is parallel to the
+ * reference image plane at depth 1/iz: n = (0,0,1), delta = 1/iz. With a centre camera cc
+ * (Sec. III-B) the plane is parallel to cc's image plane at depth 1/iz from it, written in the
+ * reference frame as n = R_r R_c^T (0,0,1), delta = (1/iz - t_c[2]) + n . t_r.
+ * Operation order: A = R_v R_r^T; b = t_v - A t_r; M = A + (b n^T) w with w = iz or 1/delta;
+ * H = K_v (M K_r^-1).
+ */
+int or_homography_f64(const or_camera* cr, const or_camera* cv, const or_camera* cc, double iz, double* H) {
+    if (!cr || !cv || !H || !k_ok(cr->K) || !k_ok(cv->K)) return 1;
+    double A[9], b[3], n[3], w, M[9], Ki[9], T[9];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++)
+            A[i * 3 + j] = (cv->R[i * 3 + 0] * cr->R[j * 3 + 0] + cv->R[i * 3 + 1] * cr->R[j * 3 + 1]) +
+                           cv->R[i * 3 + 2] * cr->R[j * 3 + 2];
+    for (int i = 0; i < 3; i++)
+        b[i] = cv->t[i] - ((A[i * 3 + 0] * cr->t[0] + A[i * 3 + 1] * cr->t[1]) + A[i * 3 + 2] * cr->t[2]);
+    if (cc == NULL) {
+        n[0] = 0.0;
+        n[1] = 0.0;
+        n[2] = 1.0;
+        w = iz;
+    } else {
+        for (int j = 0; j < 3; j++)
+            n[j] = (cr->R[j * 3 + 0] * cc->R[2 * 3 + 0] + cr->R[j * 3 + 1] * cc->R[2 * 3 + 1]) +
+                   cr->R[j * 3 + 2] * cc->R[2 * 3 + 2];
+        double z = 1.0 / iz;
+        double delta = (z - cc->t[2]) + ((n[0] * cr->t[0] + n[1] * cr->t[1]) + n[2] * cr->t[2]);
+        if (!(fabs(delta) > 1e-12)) return 2;
+        w = 1.0 / delta;
+    }
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) M[i * 3 + j] = A[i * 3 + j] + (b[i] * n[j]) * w;
+    k_inverse(cr->K, Ki);
+    mat3_mul(M, Ki, T);
+    mat3_mul(cv->K, T, H);
+    return 0;
+}
+
+/* FP32 table [n_nbrs][L][9] for one reference view. plane_mode 0 = reference planes, 1 = centre. */
+int or_homography_table(const or_camera* cams, int n_views, int ref, int n_nbrs, const int32_t* nbrs, int L,
+                        double z_near, double z_far, int plane_mode, int centre, float* out) {
+    if (!cams || ref < 0 || ref >= n_views || n_nbrs < 0 || L < 1 || !out) return 1;
+    if (plane_mode == 1 && (centre < 0 || centre >= n_views)) return 1;
+    double* iz = (double*)malloc(sizeof(double) * (size_t)L);
+    if (!iz) return 1;
+    if (or_label_inv_depths(L, z_near, z_far, iz)) { free(iz); return 1; }
+    for (int k = 0; k < n_nbrs; k++) {
+        int v = nbrs[k];
+        if (v < 0 || v >= n_views) { free(iz); return 1; }
+        for (int d = 0; d < L; d++) {
+            double H[9];
+            int rc = or_homography_f64(&cams[ref], &cams[v], plane_mode == 1 ? &cams[centre] : NULL, iz[d], H);
+            if (rc) { free(iz); return rc; }
+            for (int e = 0; e < 9; e++) out[((size_t)k * L + d) * 9 + e] = (float)H[e];
+        }
+    }
+    free(iz);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ samples */
+
+static int sample_at(const or_image* im, int sample_bytes, int c, int x, int y) {
+    const void* p = c == 0 ? im->Y : (c == 1 ? im->U : im->V);
+    size_t i = (size_t)y * (size_t)im->pitch + (size_t)x;
+    return sample_bytes == 1 ? (int)((const uint8_t*)p)[i] : (int)((const uint16_t*)p)[i];
+}
+
+/* Nearest-sample position of reference pixel (x, y) in a view under FP32 homography h; returns 1 and
+ * the integer position when the sample lies inside the Wv x Hv view, 0 when it is out of view. */
+static int project_f32(const float* h, int x, int y, int Wv, int Hv, int* ui, int* vi) {
+    float fx = (float)x, fy = (float)y;
+    float X = fmaf(h[0], fx, fmaf(h[1], fy, h[2]));
+    float Yh = fmaf(h[3], fx, fmaf(h[4], fy, h[5]));
+    float Wz = fmaf(h[6], fx, fmaf(h[7], fy, h[8]));
+    if (!(Wz > 0.0f)) return 0;
+    float r = 1.0f / Wz;
+    float u = X * r;
+    float v = Yh * r;
+    float fu = floorf(u + 0.5f);
+    float fv = floorf(v + 0.5f);
+    if (!(fu >= 0.0f && fu <= (float)(Wv - 1) && fv >= 0.0f && fv <= (float)(Hv - 1))) return 0;
+    *ui = (int)fu;
+    *vi = (int)fv;
+    return 1;
+}
+
+/* Same decision in FP64 with the unrounded homography: used only to measure how often the FP32
+ * contract picks a different sample than exact-ish arithmetic would. */
+static int project_f64(const double* h, int x, int y, int Wv, int Hv, long* ui, long* vi) {
+    double X = h[0] * x + h[1] * y + h[2];
+    double Yh = h[3] * x + h[4] * y + h[5];
+    double Wz = h[6] * x + h[7] * y + h[8];
+    if (!(Wz > 0.0)) return 0;
+    double fu = floor(X / Wz + 0.5), fv = floor(Yh / Wz + 0.5);
+    if (!(fu >= 0.0 && fu <= (double)(Wv - 1) && fv >= 0.0 && fv <= (double)(Hv - 1))) return 0;
+    *ui = (long)fu;
+    *vi = (long)fv;
+    return 1;
+}
+
+/* Eq. 4 with a one-pixel window: L1 distance of (Y, Cb, Cr) at reference pixel (x, y) and at the
+ * corresponding sample of view v, or the out-of-view penalty. */
+static int view_cost(const or_image* ref_im, const or_image* v_im, int sample_bytes, const float* h, int x, int y,
+                     int Wv, int Hv, int penalty) {
+    int ui, vi;
+    if (!project_f32(h, x, y, Wv, Hv, &ui, &vi)) return penalty;
+    int c = 0;
+    for (int ch = 0; ch < 3; ch++) {
+        int a = sample_at(ref_im, sample_bytes, ch, x, y);
+        int b = sample_at(v_im, sample_bytes, ch, ui, vi);
+        c += a > b ? a - b : b - a;
+    }
+    return c;
+}
+
+/* Per-pixel combination over the neighbouring views: minimum (combine 0) or sum (combine 1). */
+static int pixel_cost(const or_camera* cams, const or_image* imgs, int sample_bytes, int ref, int n_nbrs,
+                      const int32_t* nbrs, const float* H, int L, int d, int x, int y, int penalty, int combine) {
+    int acc = combine == 0 ? INT32_MAX : 0;
+    for (int k = 0; k < n_nbrs; k++) {
+        int v = nbrs[k];
+        const float* h = H + ((size_t)k * L + d) * 9;
+        int c = view_cost(&imgs[ref], &imgs[v], sample_bytes, h, x, y, cams[v].width, cams[v].height, penalty);
+        if (combine == 0) acc = c < acc ? c : acc;
+        else acc += c;
+    }
+    if (n_nbrs == 0) acc = 0;
+    return acc;
+}
+
+/* Pixels of every segment in raster order: offsets[S+1], pix[n] (y * W + x). Labels outside [0, S)
+ * make the call fail. */
+static int segment_lists(const int32_t* labels, int W, int H, int S, int32_t** offs_out, int32_t** pix_out) {
+    size_t P = (size_t)W * (size_t)H;
+    int32_t* offs = (int32_t*)calloc((size_t)S + 1, sizeof(int32_t));
+    int32_t* pix = (int32_t*)malloc(sizeof(int32_t) * (P ? P : 1));
+    int32_t* fill = (int32_t*)calloc((size_t)S + 1, sizeof(int32_t));
+    if (!offs || !pix || !fill) { free(offs); free(pix); free(fill); return 1; }
+    for (size_t p = 0; p < P; p++) {
+        int s = labels[p];
+        if (s < 0 || s >= S) { free(offs); free(pix); free(fill); return 2; }
+        offs[s + 1]++;
+    }
+    for (int s = 0; s < S; s++) offs[s + 1] += offs[s];
+    for (size_t p = 0; p < P; p++) {
+        int s = labels[p];
+        pix[offs[s] + fill[s]++] = (int32_t)p;
+    }
+    free(fill);
+    *offs_out = offs;
+    *pix_out = pix;
+    return 0;
+}
+
+/*
+ * Cost volume of one reference view: cost[s][d] for every listed segment s (all segments when
+ * seg_list is NULL) and every label d; rows of unlisted segments are not written. H is the
+ * reference's FP32 table [n_nbrs][L][9] (or_homography_table). Sums are exact int64 and the call
+ * fails with 3 if one does not fit in int32.
+ */
+int or_cost_volume(const or_camera* cams, int n_views, const or_image* imgs, int sample_bytes, int ref, int n_nbrs,
+                   const int32_t* nbrs, const float* H, int L, const int32_t* labels, int S, int penalty,
+                   int combine, const int32_t* seg_list, int n_list, int32_t* cost) {
+    if (!cams || !imgs || ref < 0 || ref >= n_views || L < 1 || S < 0 || !labels || !cost) return 1;
+    if (sample_bytes != 1 && sample_bytes != 2) return 1;
+    int W = cams[ref].width, Hh = cams[ref].height;
+    int32_t *offs, *pix;
+    int rc = segment_lists(labels, W, Hh, S, &offs, &pix);
+    if (rc) return rc;
+    int n = seg_list ? n_list : S;
+    for (int i = 0; i < n; i++) {
+        int s = seg_list ? seg_list[i] : i;
+        if (s < 0 || s >= S) { rc = 1; break; }
+        for (int d = 0; d < L; d++) {
+            int64_t sum = 0;
+            for (int32_t q = offs[s]; q < offs[s + 1]; q++) {
+                int x = pix[q] % W, y = pix[q] / W;
+                sum += pixel_cost(cams, imgs, sample_bytes, ref, n_nbrs, nbrs, H, L, d, x, y, penalty, combine);
+            }
+            if (sum > INT32_MAX) rc = 3;
+            cost[(size_t)s * L + d] = (int32_t)sum;
+        }
+    }
+    free(offs);
+    free(pix);
+    return rc;
+}
+
+/* Selected entries cost[seg[i]][lab[i]] of the same volume, each computed on its own. */
+int or_cost_entries(const or_camera* cams, int n_views, const or_image* imgs, int sample_bytes, int ref, int n_nbrs,
+                    const int32_t* nbrs, const float* H, int L, const int32_t* labels, int S, int penalty,
+                    int combine, int n_entries, const int32_t* seg, const int32_t* lab, int32_t* out) {
+    if (!cams || !imgs || ref < 0 || ref >= n_views || !labels || !out) return 1;
+    int W = cams[ref].width, Hh = cams[ref].height;
+    int32_t *offs, *pix;
+    int rc = segment_lists(labels, W, Hh, S, &offs, &pix);
+    if (rc) return rc;
+    for (int i = 0; i < n_entries; i++) {
+        int s = seg[i], d = lab[i];
+        if (s < 0 || s >= S || d < 0 || d >= L) { rc = 1; break; }
+        int64_t sum = 0;
+        for (int32_t q = offs[s]; q < offs[s + 1]; q++) {
+            int x = pix[q] % W, y = pix[q] / W;
+            sum += pixel_cost(cams, imgs, sample_bytes, ref, n_nbrs, nbrs, H, L, d, x, y, penalty, combine);
+        }
+        if (sum > INT32_MAX) rc = 3;
+        out[i] = (int32_t)sum;
+    }
+    free(offs);
+    free(pix);
+    return rc;
+}
+
+/*
+ * Rounding-precision check: over the listed reference pixels (pix[i] = y * W + x, all pixels when
+ * NULL), every label and every neighbour, count evaluations whose FP32 sample position or in/out
+ * decision differs from the FP64 projection with the unrounded homography. Returns counts in
+ * out[0] (mismatches) and out[1] (evaluations).
+ */
+int or_fp64_mismatch(const or_camera* cams, int n_views, int ref, int n_nbrs, const int32_t* nbrs, int L,
+                     double z_near, double z_far, int plane_mode, int centre, int n_pix, const int32_t* pix,
+                     int64_t* out) {
+    if (!cams || ref < 0 || ref >= n_views || !out) return 1;
+    double* iz = (double*)malloc(sizeof(double) * (size_t)L);
+    if (!iz || or_label_inv_depths(L, z_near, z_far, iz)) { free(iz); return 1; }
+    int W = cams[ref].width, Hh = cams[ref].height;
+    int64_t n_eval = 0, n_bad = 0;
+    int np = pix ? n_pix : W * Hh;
+    for (int k = 0; k < n_nbrs; k++) {
+        int v = nbrs[k];
+        for (int d = 0; d < L; d++) {
+            double Hd[9];
+            float Hf[9];
+            int rc = or_homography_f64(&cams[ref], &cams[v], plane_mode == 1 ? &cams[centre] : NULL, iz[d], Hd);
+            if (rc) { free(iz); return rc; }
+            for (int e = 0; e < 9; e++) Hf[e] = (float)Hd[e];
+            for (int i = 0; i < np; i++) {
+                int p = pix ? pix[i] : i;
+                int x = p % W, y = p / W;
+                int ui = 0, vi = 0;
+                long uj = 0, vj = 0;
+                int a = project_f32(Hf, x, y, cams[v].width, cams[v].height, &ui, &vi);
+                int b = project_f64(Hd, x, y, cams[v].width, cams[v].height, &uj, &vj);
+                n_eval++;
+                if (a != b || (a && (ui != uj || vi != vj))) n_bad++;
+            }
+        }
+    }
+    free(iz);
+    out[0] = n_bad;
+    out[1] = n_eval;
+    return 0;
+}
+
+/* -------------------------------------------------------------------------------- temporal */
+
+/*
+ * Temporal consistency test of Sec. III-E for one view with the current frame's label map: for every
+ * segment, the per-channel sums of the current frame over the segment's pixels are compared with the
+ * sums of the previous frame and of the I frame over the same pixels. mode 0 compares Y only, mode 1
+ * compares Y, Cb and Cr. mask[s] = 1 (adopt previous depth) if every compared channel satisfies
+ * |S_cur - S_prev| < t_p * n, else 2 (adopt I-frame depth) if iframe is given and every channel
+ * satisfies |S_cur - S_I| < t_i * n, else 0 (estimate again). Empty segments are 0. changed_list
+ * receives the segments with mask 0 in increasing order and *n_changed their count.
+ */
+int or_temporal_mask(int W, int Hh, const int32_t* labels, int S, const or_image* cur, const or_image* prev,
+                     const or_image* iframe, int sample_bytes, int t_p, int t_i, int mode, uint8_t* mask,
+                     int32_t* changed_list, int32_t* n_changed) {
+    if (!labels || S < 0 || !cur || !prev || !mask) return 1;
+    int nch = mode == 1 ? 3 : 1;
+    int64_t* n = (int64_t*)calloc((size_t)S + 1, sizeof(int64_t));
+    int64_t* dp = (int64_t*)calloc((size_t)S * 3 + 1, sizeof(int64_t));
+    int64_t* di = (int64_t*)calloc((size_t)S * 3 + 1, sizeof(int64_t));
+    if (!n || !dp || !di) { free(n); free(dp); free(di); return 1; }
+    for (int y = 0; y < Hh; y++)
+        for (int x = 0; x < W; x++) {
+            int s = labels[(size_t)y * W + x];
+            if (s < 0 || s >= S) { free(n); free(dp); free(di); return 2; }
+            n[s]++;
+            for (int c = 0; c < nch; c++) {
+                int a = sample_at(cur, sample_bytes, c, x, y);
+                dp[(size_t)s * 3 + c] += a - sample_at(prev, sample_bytes, c, x, y);
+                if (iframe) di[(size_t)s * 3 + c] += a - sample_at(iframe, sample_bytes, c, x, y);
+            }
+        }
+    int32_t cnt = 0;
+    for (int s = 0; s < S; s++) {
+        int m = 0;
+        if (n[s] > 0) {
+            int okp = 1, oki = iframe != NULL;
+            for (int c = 0; c < nch; c++) {
+                int64_t a = dp[(size_t)s * 3 + c], b = di[(size_t)s * 3 + c];
+                if (!((a < 0 ? -a : a) < (int64_t)t_p * n[s])) okp = 0;
+                if (!((b < 0 ? -b : b) < (int64_t)t_i * n[s])) oki = 0;
+            }
+            m = okp ? 1 : (oki ? 2 : 0);
+        }
+        mask[s] = (uint8_t)m;
+        if (m == 0) {
+            if (changed_list) changed_list[cnt] = s;
+            cnt++;
+        }
+    }
+    if (n_changed) *n_changed = cnt;
+    free(n);
+    free(dp);
+    free(di);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------- WTA */
+
+/*
+ * Winner-take-all readout: for each listed segment (all when seg_list is NULL) out[s] is the label
+ * with the smallest cost, the smallest label on ties; with a mask, segments marked 1 take
+ * prev_label[s] and segments marked 2 take iframe_label[s] instead (Sec. III-E adoption).
+ */
+int or_wta(const int32_t* cost, int S, int L, const uint8_t* mask, const uint16_t* prev_label,
+           const uint16_t* iframe_label, const int32_t* seg_list, int n_list, uint16_t* out) {
+    if (!cost || S < 0 || L < 1 || !out) return 1;
+    int n = seg_list ? n_list : S;
+    for (int i = 0; i < n; i++) {
+        int s = seg_list ? seg_list[i] : i;
+        if (s < 0 || s >= S) return 1;
+        int m = mask ? mask[s] : 0;
+        if (m == 1 && prev_label) { out[s] = prev_label[s]; continue; }
+        if (m == 2 && iframe_label) { out[s] = iframe_label[s]; continue; }
+        int best = 0;
+        for (int d = 1; d < L; d++)
+            if (cost[(size_t)s * L + d] < cost[(size_t)s * L + best]) best = d;
+        out[s] = (uint16_t)best;
+    }
+    return 0;
+}
+
+/* Per-pixel depth map from per-segment labels: depth[p] = z of label[labels[p]] (FP64 1/iz rounded). */
+int or_depth_map(int W, int Hh, const int32_t* labels, int S, const uint16_t* seg_label, int L, double z_near,
+                 double z_far, float* depth) {
+    double* iz = (double*)malloc(sizeof(double) * (size_t)L);
+    if (!iz || or_label_inv_depths(L, z_near, z_far, iz)) { free(iz); return 1; }
+    for (size_t p = 0; p < (size_t)W * Hh; p++) {
+        int s = labels[p];
+        if (s < 0 || s >= S || seg_label[s] >= L) { free(iz); return 2; }
+        depth[p] = (float)(1.0 / iz[seg_label[s]]);
+    }
+    free(iz);
+    return 0;
+}
