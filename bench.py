@@ -1,0 +1,351 @@
+"""Benchmark: segment x label cost volumes + winner-take-all depth for every reference view.
+
+One step = one pass of the hot path over one synthetic frame of the 1920x1080 8-view workload: pack
+the 8 views, build the 8 segment indexes, the 8 cost volumes (20736 segments x 250 labels, min over
+the 7 other views, 2.90e10 pixel x label x view evaluations) and the 8 winner-take-all depth maps.
+`value` = evaluations / s with inputs resident in HBM; `e2e` = the same metric through the C ABI
+with the inputs copied from pinned host memory and the depth labels read back inside the timed
+region. The L2 is flushed (256 MB write) before every timed step.
+
+--impl reference times the CPU oracle as it stands on a bounded sample of the same workload.
+Multi-GPU (torchrun): every rank runs an independent replica (the work shards by frames/jobs; there is
+no exchange step), rank 0 prints the whole-job throughput from the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pixel·label·view evals/s"
+UNIT = "evals/s"
+WORKLOAD = "hd8"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _workload_desc(wl):
+    S = wl.labels(wl.ref_views[0])[1]
+    c = wl.cams[0]
+    return (f"{wl.name}: {wl.n_views} views {c.width}x{c.height} {wl.bit_depth}-bit 4:4:4 (4:2:0 upsampled), "
+            f"{S} segments/view, {wl.n_labels} labels, {len(wl.ref_views)} references, "
+            f"{len(wl.neighbours(wl.ref_views[0]))} neighbours, min over views")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _traffic_for_current_kernel(workload_key: str):
+    """DRAM bytes per cost-kernel launch from the committed ncu summary, if it was taken on the current
+    kernel source (hash match); otherwise None."""
+    path = os.path.join(ROOT, "profiles", "cost_kernel_traffic.txt")
+    src = os.path.join(ROOT, "paper_1909_02294_gb300", "csrc", "ftv_cost.cu")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == workload_key and parts[1] == h:
+            return float(parts[2])
+    return None
+
+
+def algorithmic_bytes(wl) -> tuple[int, int]:
+    """Per cost-volume launch: (evaluation bytes, compulsory bytes). One evaluation reads one 3-sample
+    texel of the neighbour view (3 x sample_bytes); compulsory streams are every packed view read once,
+    each reference pixel's index record and reference texel, and the int32 volume written once."""
+    sb = wl.sample_bytes
+    evals = wl.evaluations()
+    comp = 0
+    for v in range(wl.n_views):
+        c = wl.cams[v]
+        comp += c.width * c.height * 4
+    for r in wl.ref_views:
+        c = wl.cams[r]
+        S = wl.labels(r)[1]
+        comp += c.width * c.height * 8 + S * wl.n_labels * 4
+    return evals * 3 * sb, comp
+
+
+def cpu_baseline(wl, budget_s: float = 12.0, min_rows: int = 4):
+    """Time the oracle as it stands on the first k segments of reference 0 (whole label rows), k chosen
+    so the run takes about budget_s seconds. Returns (evals/s, sample description)."""
+    import oracle
+    r = wl.ref_views[0]
+    lab, S = wl.labels(r)
+    nb = wl.neighbours(r)
+    H = oracle.homography_table(wl.cams, r, nb, wl.n_labels, wl.z_near, wl.z_far)
+    views = wl.views()
+    sizes = np.bincount(lab.ravel(), minlength=S)
+    out = np.zeros((S, wl.n_labels), np.int32)
+
+    def run(k):
+        lst = np.arange(k, dtype=np.int32)
+        t = time.perf_counter()
+        oracle.cost_volume(wl.cams, views, wl.sample_bytes, r, nb, H, wl.n_labels, lab, S, wl.oob_penalty,
+                           wl.combine, seg_list=lst, out=out)
+        dt = time.perf_counter() - t
+        return int(sizes[:k].sum()) * wl.n_labels * len(nb), dt
+
+    ev, dt = run(min_rows)
+    k = int(min(S, max(min_rows, min_rows * budget_s / max(dt, 1e-3))))
+    ev, dt = run(k)
+    return ev / dt, f"oracle, 1 thread: cost rows of segments 0..{k - 1} of reference {r} ({ev:.3e} evaluations)", k
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import synth
+    wl = synth.make_workload(WORKLOAD)
+    _ = cpu_baseline(wl, budget_s=2.0)  # warm caches / size the sample
+    rate, desc, k = cpu_baseline(wl, budget_s=8.0)
+    times, evals = [], 0
+    import oracle
+    lab_cache = {}
+    for it in range(args.warmup + args.steps):
+        r = wl.ref_views[it % len(wl.ref_views)]
+        if r not in lab_cache:
+            lab_cache[r] = wl.labels(r)
+        lab, S = lab_cache[r]
+        nb = wl.neighbours(r)
+        H = oracle.homography_table(wl.cams, r, nb, wl.n_labels, wl.z_near, wl.z_far)
+        lst = np.arange(min(k, S), dtype=np.int32)
+        sizes = np.bincount(lab.ravel(), minlength=S)
+        out = np.zeros((S, wl.n_labels), np.int32)
+        t = time.perf_counter()
+        oracle.cost_volume(wl.cams, wl.views(), wl.sample_bytes, r, nb, H, wl.n_labels, lab, S, wl.oob_penalty,
+                           wl.combine, seg_list=lst, out=out)
+        dt = time.perf_counter() - t
+        if it >= args.warmup:
+            times.append(dt)
+            evals += int(sizes[: len(lst)].sum()) * wl.n_labels * len(nb)
+    total = sum(times)
+    value = evals / total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+i32", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": _workload_desc(wl), "sample": f"cost rows of {len(lst)} segments per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"cost rows of the first {k} segments of one reference per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_1909_02294_gb300 as ftv
+    import synth
+
+    wl = synth.make_workload(WORKLOAD)
+    dev = torch.device("cuda", local)
+    R, L = len(wl.ref_views), wl.n_labels
+    S = [wl.labels(r)[1] for r in wl.ref_views]
+    ctx = ftv.ftv_depth_init(wl.cams, wl.ref_views, L, wl.z_near, wl.z_far, sample_bytes=wl.sample_bytes,
+                             bit_depth=wl.bit_depth, oob_penalty=wl.oob_penalty, max_segments=max(S))
+    host_views = wl.views()
+    host_planes = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (v.Y, v.U, v.V)]
+                   for v in host_views]
+    host_labels = [torch.from_numpy(wl.labels(r)[0]).pin_memory() for r in wl.ref_views]
+    planes = [[t.to(dev) for t in trip] for trip in host_planes]
+    labels = [t.to(dev) for t in host_labels]
+    costs = [torch.empty((s, L), dtype=torch.int32, device=dev) for s in S]
+    wins = [torch.empty(s, dtype=torch.int16, device=dev) for s in S]
+    host_wins = [torch.empty(s, dtype=torch.int16).pin_memory() for s in S]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        ftv.ftv_cost_volume(ctx, planes, labels, S, costs)
+        for i in range(R):
+            ftv.ftv_wta_depth(ctx, i, costs[i], S[i], wins[i])
+
+    for _ in range(args.warmup):
+        step()
+    st = ftv.ftv_check(ctx)
+    if st != 0:
+        raise RuntimeError(f"device status {ftv.ftv_status_str(st)}")
+
+    ftv.ftv_set_profiling(ctx, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kernel_ms = []
+    launches0 = ftv.ftv_launch_count(ctx)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            kernel_ms.append(ftv.ftv_last_kernel_ms(ctx))
+        torch.cuda.synchronize()
+    launches = ftv.ftv_launch_count(ctx) - launches0
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1000.0
+    if world > 1:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    evals = wl.evaluations()
+    value = world * evals * args.steps / total_s
+    st = ftv.ftv_check(ctx)
+    if st != 0:
+        raise RuntimeError(f"device status {ftv.ftv_status_str(st)}")
+
+    # end to end through the C ABI: pinned host -> device, the step, depth labels -> host
+    ftv.ftv_set_profiling(ctx, False)
+    h2d = sum(t.numel() * t.element_size() for trip in host_planes for t in trip)
+    h2d += sum(t.numel() * t.element_size() for t in host_labels)
+    d2h = sum(t.numel() * t.element_size() for t in host_wins)
+    e2e_ev = []
+    torch.cuda.synchronize()
+    for k in range(max(3, args.steps // 2)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for trip_h, trip_d in zip(host_planes, planes):
+            for th, td in zip(trip_h, trip_d):
+                td.copy_(th, non_blocking=True)
+        for th, td in zip(host_labels, labels):
+            td.copy_(th, non_blocking=True)
+        step()
+        for th, td in zip(host_wins, wins):
+            th.copy_(td, non_blocking=True)
+        b.record(stream)
+        e2e_ev.append((a, b))
+    torch.cuda.synchronize()
+    e2e_s = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1000.0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * evals * len(e2e_ev) / e2e_s
+
+    if rank == 0:
+        peak, peak_kind = _peaks()
+        ev_bytes, comp_bytes = algorithmic_bytes(wl)
+        kms = statistics.mean(kernel_ms)
+        achieved = (ev_bytes + comp_bytes) / (kms / 1000.0) / 1e9
+        traffic = _traffic_for_current_kernel(WORKLOAD)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+i32", "data": "synthetic",
+            "config": {"workload": _workload_desc(wl), "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "depth_maps_per_s": world * R * args.steps / total_s,
+                       "cost_kernel_ms": kms, "evaluations_per_step": evals},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": ev_bytes + comp_bytes,
+                         "kernel": "cost_kernel<FMT_P10, MIN>"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clocks.summary(),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            rate, desc, _ = cpu_baseline(wl)
+            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

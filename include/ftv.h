@@ -1,0 +1,240 @@
+/*
+ * ftv.h - C ABI of a GB300 (sm_103a) library for the data-parallel hot path of the segment-based
+ * multiview depth estimator of Mieloch, Stankiewicz and Domanski, "Depth Map Estimation for
+ * Free-Viewpoint Television" (arXiv:1909.02294):
+ *   - the segment x depth-label matching-cost volume (Eq. 4 summed over every segment pixel,
+ *     combined over the neighbouring views of Eq. 1),
+ *   - the per-segment temporal consistency test of Sec. III-E,
+ *   - a winner-take-all readout of the volume (a stand-in for the paper's graph cut, Sec. IV-B),
+ *   - a batched form that runs many such jobs in one persistent launch.
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named d_* are CUDA device pointers owned by the caller; host_* / plain pointers are
+ *     host memory owned by the caller. The library never frees caller memory. An ftv_ctx owns its
+ *     own device scratch (homography table, segment index, packed views) for its lifetime.
+ *   - ftv_stream is a cudaStream_t (NULL = the legacy default stream). Entry points that take a
+ *     stream only enqueue work on it and return without waiting.
+ *   - Argument errors are detected on the host before anything is enqueued and returned at once.
+ *     Errors found by kernels (a label outside [0, S), a sample above 2^bit_depth - 1, a segment
+ *     sum that could overflow int32) set a status word in the context; ftv_check() waits for the
+ *     stream and returns and clears it. Kernels never trap.
+ *   - An ftv_ctx may be used from one host thread and one stream at a time.
+ *   - Arithmetic contract: the homographies are formed in FP64 on the host and rounded once to FP32;
+ *     the projection, reciprocal and rounding on the device are the FP32 round-to-nearest sequence
+ *     documented at ftv_cost_volume; all costs are exact integers, so results do not depend on the
+ *     order of summation, tiling or batching.
+ */
+#ifndef FTV_H
+#define FTV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define FTV_API __attribute__((visibility("default")))
+#else
+#define FTV_API
+#endif
+
+typedef enum ftv_status {
+    FTV_OK = 0,
+    FTV_ERR_INVALID_ARG = 1,   /* bad argument, or a kernel found an invalid label or sample */
+    FTV_ERR_OUT_OF_MEMORY = 2, /* device allocation failed */
+    FTV_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    FTV_ERR_OVERFLOW = 4,      /* a segment is large enough that its int32 cost sum could overflow */
+    FTV_ERR_TIMEOUT = 5,       /* reserved: a bounded device wait gave up */
+    FTV_ERR_BUSY = 6,          /* batch admission refused: over the HBM budget or out of slots */
+    FTV_ERR_STATE = 7          /* call out of order (e.g. no segment index built yet) */
+} ftv_status;
+
+typedef void* ftv_stream; /* cudaStream_t */
+typedef struct ftv_ctx ftv_ctx;
+
+/* Pinhole camera: X_cam = R * X_world + t; K upper triangular with K[8] == 1 (row-major).
+ * Pixel centres sit at integer coordinates. */
+typedef struct ftv_camera {
+    double K[9];
+    double R[9];
+    double t[3];
+    int32_t width;
+    int32_t height;
+} ftv_camera;
+
+enum { FTV_PLANES_REF = 0, FTV_PLANES_CENTRE = 1 };
+enum { FTV_COMBINE_MIN = 0, FTV_COMBINE_SUM = 1 };
+enum { FTV_TM_Y_ONLY = 0, FTV_TM_ALL_YUV = 1 };
+enum { FTV_MASK_CHANGED = 0, FTV_MASK_REUSE_P = 1, FTV_MASK_REUSE_I = 2 };
+
+#define FTV_MAX_VIEWS 64
+#define FTV_MAX_NBRS 32
+#define FTV_MAX_LABELS 4096
+#define FTV_MAX_DIM 32767
+
+/*
+ * Depth-estimation configuration (one rig, one set of candidate depths).
+ *   n_views, cams        all cameras of the rig (cams[n_views], host memory, copied at init)
+ *   n_refs, ref_views    views for which cost volumes are produced (Sec. III-A: all views at once)
+ *   nbr_offsets/views    CSR neighbour lists per reference (nbr_offsets[n_refs+1]); NULL = every other
+ *                        view. Sec. III-B's set D (nearest left and right view) is one such list.
+ *   n_labels, z_near,    candidate depths uniform in 1/z, label 0 = z_far, label n_labels-1 = z_near
+ *   z_far                (Sec. IV-A: depth levels are planes parallel to the camera plane)
+ *   plane_mode           FTV_PLANES_REF: planes parallel to each reference camera; FTV_PLANES_CENTRE:
+ *                        planes parallel to the centre camera `centre_view` and depth measured from it
+ *                        (Sec. III-B, for non-parallel optical axes)
+ *   sample_bytes         1 (uint8 samples) or 2 (uint16 samples)
+ *   bit_depth            significant bits per sample (<= 8 for 1 byte, <= 16 for 2 bytes)
+ *   oob_penalty          cost of a sample that falls outside a view; < 0 selects 3 * (2^bit_depth - 1)
+ *   combine              per-pixel combination over neighbours: FTV_COMBINE_MIN or FTV_COMBINE_SUM
+ *   max_segments         capacity: largest segment count any reference label map will use
+ */
+typedef struct ftv_config {
+    int32_t n_views;
+    const ftv_camera* cams;
+    int32_t n_refs;
+    const int32_t* ref_views;
+    const int32_t* nbr_offsets;
+    const int32_t* nbr_views;
+    int32_t n_labels;
+    double z_near;
+    double z_far;
+    int32_t plane_mode;
+    int32_t centre_view;
+    int32_t sample_bytes;
+    int32_t bit_depth;
+    int32_t oob_penalty;
+    int32_t combine;
+    int32_t max_segments;
+} ftv_config;
+
+/*
+ * Create a context: validates the configuration, forms every homography (below), allocates the
+ * device scratch and uploads the table. Synchronous. On success *out receives the context.
+ *
+ * Candidate inverse depths (Sec. IV-A): a = 1/z_far, b = 1/z_near, step = (b - a)/(L - 1),
+ * iz_d = a + d * step (FP64). Plane homography of Eq. 4's transform T[.] from reference r into view v
+ * for candidate d, in FP64 and in this order:
+ *   A = R_v R_r^T;  b = t_v - A t_r;
+ *   reference planes: n = (0,0,1), w = iz_d;
+ *   centre planes:    n = R_r R_c^T (0,0,1), delta = (1/iz_d - t_c[2]) + n . t_r, w = 1/delta;
+ *   M = A + (b n^T) w;  H = K_v (M K_r^-1)  with the closed-form upper-triangular K_r^-1
+ *   [[1/fx, -s/(fx fy), (s cy - cx fy)/(fx fy)], [0, 1/fy, -cy/fy], [0, 0, 1]];
+ *   every 3-term dot product summed left to right; each entry rounded once to FP32.
+ * Errors: FTV_ERR_INVALID_ARG (bad sizes, K not upper triangular, z range, a degenerate centre
+ * plane), FTV_ERR_OUT_OF_MEMORY, FTV_ERR_CUDA.
+ */
+FTV_API ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out);
+
+/* Host-only: the FP32 homography table that ftv_depth_init would form for reference ref_index of cfg,
+ * laid out [n_nbrs][n_labels][9] into host_out (same arithmetic, no device needed). */
+FTV_API ftv_status ftv_compute_homographies(const ftv_config* cfg, int32_t ref_index, float* host_out);
+
+/* Release a context and its device scratch. Waits for the device. NULL is accepted. */
+FTV_API ftv_status ftv_depth_destroy(ftv_ctx* ctx);
+
+/* Copy the FP32 homography table of reference ref_index (0 <= ref_index < n_refs) into host_out,
+ * laid out [n_nbrs][n_labels][9] row-major, neighbours in list order. */
+FTV_API ftv_status ftv_get_homographies(const ftv_ctx* ctx, int32_t ref_index, float* host_out);
+
+/* Number of neighbours of reference ref_index, and the views they are, in table order
+ * (host_views may be NULL; else it receives n entries). */
+FTV_API ftv_status ftv_get_neighbours(const ftv_ctx* ctx, int32_t ref_index, int32_t* n, int32_t* host_views);
+
+/* Candidate depths z_d = 1/iz_d in FP64 rounded to FP32, host_out[n_labels]. */
+FTV_API ftv_status ftv_get_label_depths(const ftv_ctx* ctx, float* host_out);
+
+/*
+ * Build and cache the segment index of reference ref_index from its label map: d_labels is int32
+ * [height][width] of that reference camera (row pitch = width), values in [0, n_segments),
+ * n_segments <= max_segments. Segments are the estimation units (Sec. III-A: depth per segment;
+ * Sec. IV-C: any superpixel segmentation). A label outside the range sets FTV_ERR_INVALID_ARG in
+ * the status word and that pixel is left out. A segment whose pixel count times the largest per-pixel
+ * cost exceeds INT32_MAX sets FTV_ERR_OVERFLOW. Asynchronous on `stream`.
+ */
+FTV_API ftv_status ftv_segment_index(ftv_ctx* ctx, int32_t ref_index, const int32_t* d_labels,
+                                     int32_t n_segments, ftv_stream stream);
+
+/*
+ * Segment x label matching-cost volumes of every reference (Eq. 4 per pixel, Eq. 1's combination over
+ * neighbours, summed over each segment's pixels).
+ *
+ *   d_planes[3*v + c], pitch_bytes[3*v + c]  (host arrays of n_views*3 entries) sample plane c
+ *       (0 = Y, 1 = Cb, 2 = Cr, 4:4:4) of view v, `sample_bytes` per sample, rows pitch_bytes apart.
+ *   d_labels[r]   label map of reference r, or NULL to reuse the index cached by ftv_segment_index
+ *                 (FTV_ERR_STATE if none); d_labels itself may be NULL (all cached).
+ *   n_segments[r] segment count of reference r (ignored when the cached index is used).
+ *   d_seg_list[r], d_n_listed[r]  optional device list of segments to evaluate and a device pointer to
+ *                 its length (e.g. the changed list of ftv_temporal_mask); NULL = all segments.
+ *                 Rows of segments that are not listed are left untouched.
+ *   d_cost[r]     int32 [n_segments][n_labels] output of reference r (label-contiguous rows).
+ *
+ * For each listed segment s and label d: cost[s][d] = sum over pixels (x, y) of s of
+ * comb over neighbours v of c_v(x, y, d), comb = min or sum, where with h = H[r][v][d] (FP32):
+ *   X = fma(h0, x, fma(h1, y, h2)); Y = fma(h3, x, fma(h4, y, h5)); Wz = fma(h6, x, fma(h7, y, h8));
+ *   out of view unless Wz > 0; r = 1/Wz; u = X * r; v = Y * r (all IEEE FP32 round-to-nearest);
+ *   (ui, vi) = (floor(u + 0.5), floor(v + 0.5)) must satisfy 0 <= ui <= W_v - 1, 0 <= vi <= H_v - 1;
+ *   c_v = |Y_r - Y_v| + |Cb_r - Cb_v| + |Cr_r - Cr_v| at (x, y) and (ui, vi) (integer samples), else the
+ *   out-of-view penalty. Eq. 4's 1/size(W) factor is dropped (the sum is an argmin-preserving scale).
+ * Asynchronous on `stream`.
+ */
+FTV_API ftv_status ftv_cost_volume(ftv_ctx* ctx, const void* const* d_planes, const int64_t* pitch_bytes,
+                                   const int32_t* const* d_labels, const int32_t* n_segments,
+                                   const int32_t* const* d_seg_list, const int32_t* const* d_n_listed,
+                                   int32_t* const* d_cost, ftv_stream stream);
+
+/*
+ * Temporal consistency test of Sec. III-E for reference ref_index with the current label map d_labels
+ * ([height][width] int32 of that camera, n_segments segments). d_cur/d_prev/d_iframe are 3-entry host
+ * arrays of device plane pointers (Y, Cb, Cr; Cb/Cr may be NULL in FTV_TM_Y_ONLY mode) with
+ * pitches in bytes; d_iframe may be NULL (no I-frame test). For each segment with n pixels and
+ * per-channel sums S over its pixels, mask = FTV_MASK_REUSE_P when every compared channel has
+ * |S_cur - S_prev| < t_p * n; else FTV_MASK_REUSE_I when an I frame is given and every channel has
+ * |S_cur - S_I| < t_i * n; else FTV_MASK_CHANGED (also for empty segments). This is the paper's test
+ * on segment means (mean change < T) in exact integers. d_mask[n_segments] receives the mask,
+ * d_changed_list the changed segments in increasing order and *d_n_changed their count (device).
+ * The paper's thresholds are T_P = 3 and T_I = 1 for 8-bit samples. Asynchronous.
+ */
+FTV_API ftv_status ftv_temporal_mask(ftv_ctx* ctx, int32_t ref_index, const void* const* d_cur,
+                                     const int64_t* cur_pitch, const void* const* d_prev, const int64_t* prev_pitch,
+                                     const void* const* d_iframe, const int64_t* iframe_pitch,
+                                     const int32_t* d_labels, int32_t n_segments, int32_t t_p, int32_t t_i,
+                                     int32_t mode, uint8_t* d_mask, int32_t* d_changed_list,
+                                     int32_t* d_n_changed, ftv_stream stream);
+
+/*
+ * Winner-take-all readout of one cost volume d_cost [n_segments][n_labels]: d_label_out[s] = the label
+ * of least cost, the smallest such label on ties. With d_mask (from ftv_temporal_mask), segments
+ * marked FTV_MASK_REUSE_P take d_prev_label[s] and FTV_MASK_REUSE_I take d_iframe_label[s]
+ * (Sec. III-E adoption). With d_seg_list/d_n_listed only listed segments are written. With d_labels_pix
+ * (the reference label map) and d_depth_map, also writes the per-pixel depth z of each pixel's segment
+ * label (float [height][width]) for reference ref_index. Asynchronous.
+ */
+FTV_API ftv_status ftv_wta_depth(ftv_ctx* ctx, int32_t ref_index, const int32_t* d_cost, int32_t n_segments,
+                                 const uint8_t* d_mask, const uint16_t* d_prev_label,
+                                 const uint16_t* d_iframe_label, const int32_t* d_seg_list,
+                                 const int32_t* d_n_listed, uint16_t* d_label_out, const int32_t* d_labels_pix,
+                                 float* d_depth_map, ftv_stream stream);
+
+/* Wait for `stream`, then return and clear the context's device status word (FTV_OK if clean). */
+FTV_API ftv_status ftv_check(ftv_ctx* ctx, ftv_stream stream);
+
+/* Timing of the dominant kernel: with enable != 0, every ftv_cost_volume call records a pair of CUDA
+ * events on its stream immediately around its cost-kernel launch (the events belong to the context). */
+FTV_API ftv_status ftv_set_profiling(ftv_ctx* ctx, int32_t enable);
+
+/* Elapsed milliseconds between the events of the most recent timed cost-kernel launch; waits for the
+ * stop event. FTV_ERR_STATE if no timed launch happened. */
+FTV_API ftv_status ftv_last_kernel_ms(ftv_ctx* ctx, float* ms);
+
+/* Kernel launches this context has enqueued since creation (for accounting). */
+FTV_API int64_t ftv_launch_count(const ftv_ctx* ctx);
+
+/* Human-readable name of a status code (static storage). */
+FTV_API const char* ftv_status_str(ftv_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FTV_H */

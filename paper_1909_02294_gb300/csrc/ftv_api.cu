@@ -1,0 +1,476 @@
+// C ABI entry points: argument validation, context set-up and launch sequencing.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ftv_internal.h"
+
+using namespace ftv;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+bool valid_camera(const ftv_camera& c) {
+    if (c.width < 1 || c.height < 1 || c.width > FTV_MAX_DIM || c.height > FTV_MAX_DIM) return false;
+    if (c.K[3] != 0.0 || c.K[6] != 0.0 || c.K[7] != 0.0 || c.K[8] != 1.0 || c.K[0] == 0.0 || c.K[4] == 0.0) return false;
+    for (double v : c.K) if (!(v == v)) return false;
+    for (double v : c.R) if (!(v == v)) return false;
+    for (double v : c.t) if (!(v == v)) return false;
+    return true;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+    return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (count ? count : 1));
+}
+
+void free_ctx(ftv_ctx* c) {
+    if (!c) return;
+    for (auto& r : c->refs) {
+        cudaFree(r.d_H);
+        cudaFree(r.d_nbrs);
+        cudaFree(r.d_offs);
+        cudaFree(r.d_cursor);
+        cudaFree(r.d_woffs);
+        cudaFree(r.d_pix);
+    }
+    cudaFree(c->d_packed);
+    cudaFree(c->d_status);
+    cudaFree(c->d_jobs);
+    cudaFree(c->d_plan);
+    cudaFree(c->d_tstats);
+    cudaFree(c->d_label_z);
+    if (c->ev_start) cudaEventDestroy(c->ev_start);
+    if (c->ev_stop) cudaEventDestroy(c->ev_stop);
+    delete c;
+}
+
+int64_t max_sample_cost(const ftv_ctx* c) { return 3LL * ((1LL << c->bit_depth) - 1); }
+
+int64_t max_pixel_cost(const ftv_ctx* c, int n_nbrs) {
+    const int64_t one = std::max<int64_t>(c->penalty, max_sample_cost(c));
+    return c->combine == FTV_COMBINE_MIN ? one : one * std::max(1, n_nbrs);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ftv_status_str(ftv_status s) {
+    switch (s) {
+        case FTV_OK: return "ok";
+        case FTV_ERR_INVALID_ARG: return "invalid argument";
+        case FTV_ERR_OUT_OF_MEMORY: return "out of device memory";
+        case FTV_ERR_CUDA: return "CUDA error";
+        case FTV_ERR_OVERFLOW: return "segment cost may overflow int32";
+        case FTV_ERR_TIMEOUT: return "device wait timed out";
+        case FTV_ERR_BUSY: return "busy: admission refused";
+        case FTV_ERR_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out) {
+    if (!cfg || !out) return FTV_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (cfg->n_views < 1 || cfg->n_views > FTV_MAX_VIEWS || !cfg->cams) return FTV_ERR_INVALID_ARG;
+    if (cfg->n_refs < 1 || cfg->n_refs > cfg->n_views || !cfg->ref_views) return FTV_ERR_INVALID_ARG;
+    if (cfg->n_labels < 1 || cfg->n_labels > FTV_MAX_LABELS) return FTV_ERR_INVALID_ARG;
+    if (!(cfg->z_near > 0.0) || !(cfg->z_far > cfg->z_near)) return FTV_ERR_INVALID_ARG;
+    if (cfg->plane_mode != FTV_PLANES_REF && cfg->plane_mode != FTV_PLANES_CENTRE) return FTV_ERR_INVALID_ARG;
+    if (cfg->plane_mode == FTV_PLANES_CENTRE && (cfg->centre_view < 0 || cfg->centre_view >= cfg->n_views))
+        return FTV_ERR_INVALID_ARG;
+    if (cfg->sample_bytes != 1 && cfg->sample_bytes != 2) return FTV_ERR_INVALID_ARG;
+    if (cfg->bit_depth < 1 || cfg->bit_depth > 8 * cfg->sample_bytes) return FTV_ERR_INVALID_ARG;
+    if (cfg->combine != FTV_COMBINE_MIN && cfg->combine != FTV_COMBINE_SUM) return FTV_ERR_INVALID_ARG;
+    if (cfg->max_segments < 1) return FTV_ERR_INVALID_ARG;
+    for (int v = 0; v < cfg->n_views; ++v)
+        if (!valid_camera(cfg->cams[v])) return FTV_ERR_INVALID_ARG;
+
+    ftv_ctx* c = new (std::nothrow) ftv_ctx();
+    if (!c) return FTV_ERR_OUT_OF_MEMORY;
+    c->n_views = cfg->n_views;
+    c->n_refs = cfg->n_refs;
+    c->L = cfg->n_labels;
+    c->plane_mode = cfg->plane_mode;
+    c->centre = cfg->centre_view;
+    c->sample_bytes = cfg->sample_bytes;
+    c->bit_depth = cfg->bit_depth;
+    c->combine = cfg->combine;
+    c->max_segments = cfg->max_segments;
+    c->z_near = cfg->z_near;
+    c->z_far = cfg->z_far;
+    c->penalty = cfg->oob_penalty >= 0 ? cfg->oob_penalty : (int32_t)(3 * ((1LL << cfg->bit_depth) - 1));
+    c->fmt = cfg->sample_bytes == 1 ? FMT_U8X4 : (cfg->bit_depth <= 10 ? FMT_P10 : FMT_U16X4);
+    c->texel_bytes = c->fmt == FMT_U16X4 ? 8 : 4;
+    c->cams.assign(cfg->cams, cfg->cams + cfg->n_views);
+
+    std::vector<double> iz;
+    if (!label_inv_depths(c->L, c->z_near, c->z_far, iz)) { delete c; return FTV_ERR_INVALID_ARG; }
+    c->label_z.resize(c->L);
+    for (int d = 0; d < c->L; ++d) c->label_z[d] = (float)(1.0 / iz[d]);
+
+    // references and their neighbour lists
+    std::vector<char> seen(c->n_views, 0);
+    int max_n = 0;
+    c->refs.resize(c->n_refs);
+    for (int i = 0; i < c->n_refs; ++i) {
+        RefState& r = c->refs[i];
+        r.view = cfg->ref_views[i];
+        if (r.view < 0 || r.view >= c->n_views || seen[r.view]) { free_ctx(c); return FTV_ERR_INVALID_ARG; }
+        seen[r.view] = 1;
+        r.W = c->cams[r.view].width;
+        r.H = c->cams[r.view].height;
+        if (cfg->nbr_offsets) {
+            const int b = cfg->nbr_offsets[i], e = cfg->nbr_offsets[i + 1];
+            if (b < 0 || e < b || !cfg->nbr_views) { free_ctx(c); return FTV_ERR_INVALID_ARG; }
+            for (int k = b; k < e; ++k) r.nbrs.push_back(cfg->nbr_views[k]);
+        } else {
+            for (int v = 0; v < c->n_views; ++v)
+                if (v != r.view) r.nbrs.push_back(v);
+        }
+        r.n_nbrs = (int)r.nbrs.size();
+        if (r.n_nbrs > FTV_MAX_NBRS) { free_ctx(c); return FTV_ERR_INVALID_ARG; }
+        for (int v : r.nbrs)
+            if (v < 0 || v >= c->n_views || v == r.view) { free_ctx(c); return FTV_ERR_INVALID_ARG; }
+        max_n = std::max(max_n, r.n_nbrs);
+    }
+
+    // label blocking: N x LB x 9 homography floats must fit the kernel's shared-memory stage
+    int lb_max = std::min(kMaxLB, kHFloats / (9 * std::max(1, max_n)));
+    lb_max = std::max(1, std::min(lb_max, c->L));
+    c->nLB = (c->L + lb_max - 1) / lb_max;
+    c->LB = (c->L + c->nLB - 1) / c->nLB;
+
+    // homographies (FP64 -> FP32)
+    const ftv_camera* cc = c->plane_mode == FTV_PLANES_CENTRE ? &c->cams[c->centre] : nullptr;
+    for (auto& r : c->refs) {
+        r.h_H.resize((size_t)r.n_nbrs * c->L * 9);
+        for (int k = 0; k < r.n_nbrs; ++k)
+            for (int d = 0; d < c->L; ++d) {
+                double H[9];
+                if (plane_homography(c->cams[r.view], c->cams[r.nbrs[k]], cc, iz[d], H) != 0) {
+                    free_ctx(c);
+                    return FTV_ERR_INVALID_ARG;
+                }
+                for (int e = 0; e < 9; ++e) r.h_H[((size_t)k * c->L + d) * 9 + e] = (float)H[e];
+            }
+    }
+
+    // device scratch (all host-side validation is done by now)
+    if (cudaGetDevice(&c->device) != cudaSuccess) { free_ctx(c); return FTV_ERR_CUDA; }
+    cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
+    size_t packed = 0;
+    c->view_offset_bytes.resize(c->n_views);
+    for (int v = 0; v < c->n_views; ++v) {
+        c->view_offset_bytes[v] = packed;
+        const size_t bytes = (size_t)c->cams[v].width * c->cams[v].height * c->texel_bytes;
+        packed += (bytes + 255) & ~(size_t)255;
+    }
+    bool ok = dalloc(reinterpret_cast<char**>(&c->d_packed), packed) == cudaSuccess;
+    ok = ok && dalloc(&c->d_status, 1) == cudaSuccess;
+    ok = ok && dalloc(&c->d_jobs, kMaxUnits) == cudaSuccess;
+    ok = ok && dalloc(&c->d_plan, 1) == cudaSuccess;
+    ok = ok && dalloc(&c->d_tstats, (size_t)c->max_segments * 8) == cudaSuccess;
+    ok = ok && dalloc(&c->d_label_z, (size_t)c->L) == cudaSuccess;
+    for (auto& r : c->refs) {
+        ok = ok && dalloc(&r.d_H, r.h_H.size()) == cudaSuccess;
+        ok = ok && dalloc(&r.d_nbrs, (size_t)r.n_nbrs) == cudaSuccess;
+        ok = ok && dalloc(&r.d_offs, (size_t)c->max_segments + 1) == cudaSuccess;
+        ok = ok && dalloc(&r.d_cursor, (size_t)c->max_segments) == cudaSuccess;
+        ok = ok && dalloc(&r.d_woffs, (size_t)c->max_segments + 1) == cudaSuccess;
+        ok = ok && dalloc(&r.d_pix, (size_t)r.W * r.H) == cudaSuccess;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        free_ctx(c);
+        return FTV_ERR_OUT_OF_MEMORY;
+    }
+    ok = cudaMemset(c->d_status, 0, sizeof(uint32_t)) == cudaSuccess;
+    ok = ok && cudaMemcpy(c->d_label_z, c->label_z.data(), sizeof(float) * c->L, cudaMemcpyHostToDevice) == cudaSuccess;
+    for (auto& r : c->refs) {
+        std::vector<NbrView> nv(r.n_nbrs);
+        for (int k = 0; k < r.n_nbrs; ++k) {
+            const int v = r.nbrs[k];
+            nv[k].texels = static_cast<char*>(c->d_packed) + c->view_offset_bytes[v];
+            nv[k].w = c->cams[v].width;
+            nv[k].h = c->cams[v].height;
+            nv[k].pitch = c->cams[v].width;
+            nv[k].pad = 0;
+        }
+        ok = ok && cudaMemcpy(r.d_H, r.h_H.data(), sizeof(float) * r.h_H.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+        if (r.n_nbrs)
+            ok = ok && cudaMemcpy(r.d_nbrs, nv.data(), sizeof(NbrView) * nv.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    c->cost_blocks_per_sm = cost_blocks_per_sm(c->fmt, c->combine);
+    if (!ok) {
+        free_ctx(c);
+        return FTV_ERR_CUDA;
+    }
+    *out = c;
+    return FTV_OK;
+}
+
+ftv_status ftv_compute_homographies(const ftv_config* cfg, int32_t ref_index, float* host_out) {
+    if (!cfg || !host_out || !cfg->cams || !cfg->ref_views) return FTV_ERR_INVALID_ARG;
+    if (cfg->n_views < 1 || cfg->n_views > FTV_MAX_VIEWS || ref_index < 0 || ref_index >= cfg->n_refs)
+        return FTV_ERR_INVALID_ARG;
+    if (cfg->plane_mode == FTV_PLANES_CENTRE && (cfg->centre_view < 0 || cfg->centre_view >= cfg->n_views))
+        return FTV_ERR_INVALID_ARG;
+    std::vector<double> iz;
+    if (!label_inv_depths(cfg->n_labels, cfg->z_near, cfg->z_far, iz)) return FTV_ERR_INVALID_ARG;
+    const int ref = cfg->ref_views[ref_index];
+    if (ref < 0 || ref >= cfg->n_views) return FTV_ERR_INVALID_ARG;
+    std::vector<int> nbrs;
+    if (cfg->nbr_offsets) {
+        for (int k = cfg->nbr_offsets[ref_index]; k < cfg->nbr_offsets[ref_index + 1]; ++k) nbrs.push_back(cfg->nbr_views[k]);
+    } else {
+        for (int v = 0; v < cfg->n_views; ++v)
+            if (v != ref) nbrs.push_back(v);
+    }
+    const ftv_camera* cc = cfg->plane_mode == FTV_PLANES_CENTRE ? &cfg->cams[cfg->centre_view] : nullptr;
+    for (size_t k = 0; k < nbrs.size(); ++k) {
+        if (nbrs[k] < 0 || nbrs[k] >= cfg->n_views) return FTV_ERR_INVALID_ARG;
+        for (int d = 0; d < cfg->n_labels; ++d) {
+            double H[9];
+            if (plane_homography(cfg->cams[ref], cfg->cams[nbrs[k]], cc, iz[d], H) != 0) return FTV_ERR_INVALID_ARG;
+            for (int e = 0; e < 9; ++e) host_out[(k * cfg->n_labels + d) * 9 + e] = (float)H[e];
+        }
+    }
+    return FTV_OK;
+}
+
+ftv_status ftv_depth_destroy(ftv_ctx* ctx) {
+    if (!ctx) return FTV_OK;
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    free_ctx(ctx);
+    return FTV_OK;
+}
+
+ftv_status ftv_get_homographies(const ftv_ctx* ctx, int32_t ref_index, float* host_out) {
+    if (!ctx || !host_out || ref_index < 0 || ref_index >= ctx->n_refs) return FTV_ERR_INVALID_ARG;
+    const auto& r = ctx->refs[ref_index];
+    std::memcpy(host_out, r.h_H.data(), sizeof(float) * r.h_H.size());
+    return FTV_OK;
+}
+
+ftv_status ftv_get_neighbours(const ftv_ctx* ctx, int32_t ref_index, int32_t* n, int32_t* host_views) {
+    if (!ctx || !n || ref_index < 0 || ref_index >= ctx->n_refs) return FTV_ERR_INVALID_ARG;
+    const auto& r = ctx->refs[ref_index];
+    *n = r.n_nbrs;
+    if (host_views) std::copy(r.nbrs.begin(), r.nbrs.end(), host_views);
+    return FTV_OK;
+}
+
+ftv_status ftv_get_label_depths(const ftv_ctx* ctx, float* host_out) {
+    if (!ctx || !host_out) return FTV_ERR_INVALID_ARG;
+    std::copy(ctx->label_z.begin(), ctx->label_z.end(), host_out);
+    return FTV_OK;
+}
+
+ftv_status ftv_segment_index(ftv_ctx* ctx, int32_t ref_index, const int32_t* d_labels, int32_t n_segments,
+                             ftv_stream stream) {
+    if (!ctx || !d_labels || ref_index < 0 || ref_index >= ctx->n_refs) return FTV_ERR_INVALID_ARG;
+    if (n_segments < 0 || n_segments > ctx->max_segments) return FTV_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    RefState& r = ctx->refs[ref_index];
+    const cudaError_t e = launch_segment_index(d_labels, r.W, r.H, n_segments, max_pixel_cost(ctx, r.n_nbrs), r.d_offs,
+                                               r.d_cursor, r.d_pix, ctx->d_status, (cudaStream_t)stream,
+                                               &ctx->launches);
+    if (e != cudaSuccess) return FTV_ERR_CUDA;
+    r.S_indexed = n_segments;
+    return FTV_OK;
+}
+
+ftv_status ftv_cost_volume(ftv_ctx* ctx, const void* const* d_planes, const int64_t* pitch_bytes,
+                           const int32_t* const* d_labels, const int32_t* n_segments,
+                           const int32_t* const* d_seg_list, const int32_t* const* d_n_listed, int32_t* const* d_cost,
+                           ftv_stream stream) {
+    if (!ctx || !d_planes || !pitch_bytes || !d_cost) return FTV_ERR_INVALID_ARG;
+    if (ctx->n_refs > kMaxUnits) return FTV_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    // which views are read
+    std::vector<char> used(ctx->n_views, 0);
+    for (const auto& r : ctx->refs) {
+        used[r.view] = 1;
+        for (int v : r.nbrs) used[v] = 1;
+    }
+    for (int v = 0; v < ctx->n_views; ++v) {
+        if (!used[v]) continue;
+        for (int ch = 0; ch < 3; ++ch) {
+            if (!d_planes[3 * v + ch]) return FTV_ERR_INVALID_ARG;
+            if (pitch_bytes[3 * v + ch] < (int64_t)ctx->cams[v].width * ctx->sample_bytes) return FTV_ERR_INVALID_ARG;
+        }
+    }
+    for (int i = 0; i < ctx->n_refs; ++i) {
+        const RefState& r = ctx->refs[i];
+        const bool fresh = d_labels && d_labels[i];
+        if (fresh && (!n_segments || n_segments[i] < 0 || n_segments[i] > ctx->max_segments)) return FTV_ERR_INVALID_ARG;
+        if (!fresh && r.S_indexed < 0) return FTV_ERR_STATE;
+        if (!d_cost[i]) return FTV_ERR_INVALID_ARG;
+        if (d_seg_list && d_seg_list[i] && (!d_n_listed || !d_n_listed[i])) return FTV_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; v < ctx->n_views && e == cudaSuccess; ++v) {
+        if (!used[v]) continue;
+        e = launch_pack(d_planes + 3 * v, pitch_bytes + 3 * v, ctx->sample_bytes, ctx->bit_depth, ctx->fmt,
+                        ctx->cams[v].width, ctx->cams[v].height,
+                        static_cast<char*>(ctx->d_packed) + ctx->view_offset_bytes[v], ctx->d_status, s);
+        ctx->launches++;
+    }
+    std::vector<RefJob> jobs(ctx->n_refs);
+    for (int i = 0; i < ctx->n_refs && e == cudaSuccess; ++i) {
+        RefState& r = ctx->refs[i];
+        if (d_labels && d_labels[i]) {
+            e = launch_segment_index(d_labels[i], r.W, r.H, n_segments[i], max_pixel_cost(ctx, r.n_nbrs), r.d_offs,
+                                     r.d_cursor, r.d_pix, ctx->d_status, s, &ctx->launches);
+            r.S_indexed = n_segments[i];
+        }
+        const int S = r.S_indexed;
+        const int32_t* list = d_seg_list ? d_seg_list[i] : nullptr;
+        const int32_t* nl = list ? d_n_listed[i] : nullptr;
+        if (e == cudaSuccess) {
+            if (list) {
+                e = launch_zero_rows(d_cost[i], ctx->L, S, list, nl, s);
+                ctx->launches++;
+            } else {
+                e = cudaMemsetAsync(d_cost[i], 0, sizeof(int32_t) * (size_t)S * ctx->L, s);
+            }
+        }
+        RefJob& J = jobs[i];
+        std::memset(&J, 0, sizeof(J));
+        J.ref_texels = static_cast<char*>(ctx->d_packed) + ctx->view_offset_bytes[r.view];
+        J.pix = r.d_pix;
+        J.offs = r.d_offs;
+        J.list = list;
+        J.n_listed = nl;
+        J.woffs = r.d_woffs;
+        J.H = r.d_H;
+        J.nbrs = r.d_nbrs;
+        J.cost = d_cost[i];
+        J.W = r.W;
+        J.S = S;
+        J.N = r.n_nbrs;
+        J.L = ctx->L;
+        J.LB = ctx->LB;
+        J.nLB = ctx->nLB;
+        J.penalty = ctx->penalty;
+        J.fmt = ctx->fmt;
+    }
+    if (e == cudaSuccess) {
+        e = launch_plan(jobs.data(), ctx->n_refs, ctx->d_jobs, ctx->d_plan, s);
+        ctx->launches++;
+    }
+    if (e == cudaSuccess && ctx->profiling) e = cudaEventRecord(ctx->ev_start, s);
+    if (e == cudaSuccess) {
+        e = launch_cost(ctx->d_jobs, ctx->n_refs, ctx->d_plan, ctx->fmt, ctx->combine,
+                        ctx->n_sm * ctx->cost_blocks_per_sm, s);
+        ctx->launches++;
+    }
+    if (e == cudaSuccess && ctx->profiling) {
+        e = cudaEventRecord(ctx->ev_stop, s);
+        ctx->timed = e == cudaSuccess;
+    }
+    return e == cudaSuccess ? FTV_OK : FTV_ERR_CUDA;
+}
+
+ftv_status ftv_temporal_mask(ftv_ctx* ctx, int32_t ref_index, const void* const* d_cur, const int64_t* cur_pitch,
+                             const void* const* d_prev, const int64_t* prev_pitch, const void* const* d_iframe,
+                             const int64_t* iframe_pitch, const int32_t* d_labels, int32_t n_segments, int32_t t_p,
+                             int32_t t_i, int32_t mode, uint8_t* d_mask, int32_t* d_changed_list,
+                             int32_t* d_n_changed, ftv_stream stream) {
+    if (!ctx || ref_index < 0 || ref_index >= ctx->n_refs || !d_cur || !cur_pitch || !d_prev || !prev_pitch)
+        return FTV_ERR_INVALID_ARG;
+    if (!d_labels || !d_mask || !d_changed_list || !d_n_changed) return FTV_ERR_INVALID_ARG;
+    if (n_segments < 0 || n_segments > ctx->max_segments || t_p < 0 || t_i < 0) return FTV_ERR_INVALID_ARG;
+    if (mode != FTV_TM_Y_ONLY && mode != FTV_TM_ALL_YUV) return FTV_ERR_INVALID_ARG;
+    if (d_iframe && !iframe_pitch) return FTV_ERR_INVALID_ARG;
+    const RefState& r = ctx->refs[ref_index];
+    const int nch = mode == FTV_TM_ALL_YUV ? 3 : 1;
+    const int64_t row = (int64_t)r.W * ctx->sample_bytes;
+    for (int c = 0; c < nch; ++c) {
+        if (!d_cur[c] || !d_prev[c] || cur_pitch[c] < row || prev_pitch[c] < row) return FTV_ERR_INVALID_ARG;
+        if (d_iframe && (!d_iframe[c] || iframe_pitch[c] < row)) return FTV_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    const cudaError_t e =
+        launch_temporal(d_cur, cur_pitch, d_prev, prev_pitch, d_iframe, iframe_pitch, ctx->sample_bytes, d_labels, r.W,
+                        r.H, n_segments, t_p, t_i, mode, ctx->d_tstats, d_mask, d_changed_list, d_n_changed,
+                        ctx->d_status, (cudaStream_t)stream, &ctx->launches);
+    return e == cudaSuccess ? FTV_OK : FTV_ERR_CUDA;
+}
+
+ftv_status ftv_wta_depth(ftv_ctx* ctx, int32_t ref_index, const int32_t* d_cost, int32_t n_segments,
+                         const uint8_t* d_mask, const uint16_t* d_prev_label, const uint16_t* d_iframe_label,
+                         const int32_t* d_seg_list, const int32_t* d_n_listed, uint16_t* d_label_out,
+                         const int32_t* d_labels_pix, float* d_depth_map, ftv_stream stream) {
+    if (!ctx || !d_cost || !d_label_out || n_segments < 0 || n_segments > ctx->max_segments) return FTV_ERR_INVALID_ARG;
+    if (ref_index < 0 || ref_index >= ctx->n_refs) return FTV_ERR_INVALID_ARG;
+    if (d_seg_list && !d_n_listed) return FTV_ERR_INVALID_ARG;
+    if ((d_labels_pix == nullptr) != (d_depth_map == nullptr)) return FTV_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = launch_wta(d_cost, n_segments, ctx->L, d_mask, d_prev_label, d_iframe_label, d_seg_list,
+                               d_n_listed, d_label_out, s);
+    ctx->launches++;
+    if (e == cudaSuccess && d_depth_map) {
+        const RefState& r = ctx->refs[ref_index];
+        e = launch_depth_map(d_labels_pix, r.W, r.H, n_segments, d_label_out, ctx->d_label_z, ctx->L, d_depth_map,
+                             ctx->d_status, s);
+        ctx->launches++;
+    }
+    return e == cudaSuccess ? FTV_OK : FTV_ERR_CUDA;
+}
+
+ftv_status ftv_check(ftv_ctx* ctx, ftv_stream stream) {
+    if (!ctx) return FTV_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return FTV_ERR_CUDA;
+    uint32_t st = 0;
+    if (cudaMemcpy(&st, ctx->d_status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return FTV_ERR_CUDA;
+    if (st && cudaMemset(ctx->d_status, 0, sizeof(st)) != cudaSuccess) return FTV_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return FTV_ERR_CUDA;
+    if (st & (ST_BAD_LABEL | ST_BAD_SAMPLE)) return FTV_ERR_INVALID_ARG;
+    if (st & ST_OVERFLOW) return FTV_ERR_OVERFLOW;
+    return FTV_OK;
+}
+
+int64_t ftv_launch_count(const ftv_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+ftv_status ftv_set_profiling(ftv_ctx* ctx, int32_t enable) {
+    if (!ctx) return FTV_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (enable && !ctx->ev_start) {
+        if (cudaEventCreate(&ctx->ev_start) != cudaSuccess || cudaEventCreate(&ctx->ev_stop) != cudaSuccess)
+            return FTV_ERR_CUDA;
+    }
+    ctx->profiling = enable != 0;
+    return FTV_OK;
+}
+
+ftv_status ftv_last_kernel_ms(ftv_ctx* ctx, float* ms) {
+    if (!ctx || !ms) return FTV_ERR_INVALID_ARG;
+    if (!ctx->timed) return FTV_ERR_STATE;
+    DeviceGuard g(ctx->device);
+    if (cudaEventSynchronize(ctx->ev_stop) != cudaSuccess) return FTV_ERR_CUDA;
+    if (cudaEventElapsedTime(ms, ctx->ev_start, ctx->ev_stop) != cudaSuccess) return FTV_ERR_CUDA;
+    return FTV_OK;
+}
+
+}  // extern "C"

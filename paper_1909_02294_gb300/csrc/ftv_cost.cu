@@ -1,0 +1,314 @@
+// Segment x depth-label matching-cost volume: the persistent cost kernel.
+//
+// Paper: Eq. 4 (L1 distance of Y, Cb, Cr between a reference point and its transform T[.] into a
+// neighbouring view for the considered depth), Eq. 1 (costs of the neighbouring views c' in D are
+// combined for every segment of every view), Sec. III-A (segments are the units; depth per segment).
+// Here every pixel of a segment is a sample point (window of one pixel), the per-pixel costs of the
+// neighbours are combined by min or sum, and the segment's cost is the int32 sum over its pixels.
+//
+// Work decomposition (GB300 design, not the paper's CPU threading of Sec. IV-A): a work item is one
+// tile of kTile consecutive pixels of the listed segments (segments in list order, each segment's
+// pixels contiguous) times one block of LB consecutive labels of one (job, reference) unit. Resident
+// CTAs take items from a global counter in increasing order, so CTAs that run together work on
+// neighbouring tiles and label blocks and share their neighbour-view footprints in L2. Per item:
+//   - the N x LB homographies and the neighbour geometry are staged in shared memory;
+//   - each thread owns kPPT pixels (x, y and the reference samples in registers);
+//   - for each label, for each neighbour: FP32 projection, one packed-texel gather, |dY|+|dCb|+|dCr|,
+//     running min/sum per pixel in registers;
+//   - per label, warp reductions over runs of equal segment collapse the per-pixel costs, one shared
+//     atomic per run, and at the end of the item each segment's row slice is written: plain stores
+//     for segments wholly inside the tile, global atomics for segments cut by a tile boundary.
+// All arithmetic that decides a sample position is explicit round-to-nearest FP32 (no contraction
+// freedom is left to the compiler), so the result is bit-identical to any implementation of the same
+// sequence; costs are integers, so summation order does not matter.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <climits>
+
+#include "ftv_internal.h"
+
+namespace ftv {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kSentinel = INT_MAX;
+constexpr int kLocCache = kTile + 1;
+
+template <int FMT>
+struct TexelOps;
+
+template <>
+struct TexelOps<FMT_U8X4> {
+    static __device__ __forceinline__ void unpack_ref(const void* base, int64_t i, int& a, int& b, int& c) {
+        const uint32_t t = __ldg(static_cast<const uint32_t*>(base) + i);
+        a = t & 0xff;
+        b = (t >> 8) & 0xff;
+        c = t >> 16;
+    }
+    static __device__ __forceinline__ int cost(const void* base, int i, int a, int b, int c) {
+        const uint32_t t = __ldg(static_cast<const uint32_t*>(base) + i);
+        return abs((int)(t & 0xff) - a) + abs((int)((t >> 8) & 0xff) - b) + abs((int)(t >> 16) - c);
+    }
+};
+
+template <>
+struct TexelOps<FMT_P10> {
+    static __device__ __forceinline__ void unpack_ref(const void* base, int64_t i, int& a, int& b, int& c) {
+        const uint32_t t = __ldg(static_cast<const uint32_t*>(base) + i);
+        a = t & 0x3ff;
+        b = (t >> 10) & 0x3ff;
+        c = t >> 20;
+    }
+    static __device__ __forceinline__ int cost(const void* base, int i, int a, int b, int c) {
+        const uint32_t t = __ldg(static_cast<const uint32_t*>(base) + i);
+        return abs((int)(t & 0x3ff) - a) + abs((int)((t >> 10) & 0x3ff) - b) + abs((int)(t >> 20) - c);
+    }
+};
+
+template <>
+struct TexelOps<FMT_U16X4> {
+    static __device__ __forceinline__ void unpack_ref(const void* base, int64_t i, int& a, int& b, int& c) {
+        const uint2 t = __ldg(static_cast<const uint2*>(base) + i);
+        a = t.x & 0xffff;
+        b = t.x >> 16;
+        c = t.y;
+    }
+    static __device__ __forceinline__ int cost(const void* base, int i, int a, int b, int c) {
+        const uint2 t = __ldg(static_cast<const uint2*>(base) + i);
+        return abs((int)(t.x & 0xffff) - a) + abs((int)(t.x >> 16) - b) + abs((int)t.y - c);
+    }
+};
+
+// Cost of one sample: reference pixel (x, y) through homography h into one neighbour view.
+template <int FMT>
+__device__ __forceinline__ int sample_cost(const float (&h)[9], float x, float y, int a, int b, int c,
+                                           const void* tex, int pitch, float wm1, float hm1, int penalty) {
+    const float X = __fmaf_rn(h[0], x, __fmaf_rn(h[1], y, h[2]));
+    const float Yh = __fmaf_rn(h[3], x, __fmaf_rn(h[4], y, h[5]));
+    const float Wz = __fmaf_rn(h[6], x, __fmaf_rn(h[7], y, h[8]));
+    int cst = penalty;
+    if (Wz > 0.0f) {
+        const float r = __frcp_rn(Wz);
+        const float fu = floorf(__fadd_rn(__fmul_rn(X, r), 0.5f));
+        const float fv = floorf(__fadd_rn(__fmul_rn(Yh, r), 0.5f));
+        if (fu >= 0.0f && fu <= wm1 && fv >= 0.0f && fv <= hm1) {
+            cst = TexelOps<FMT>::cost(tex, (int)fv * pitch + (int)fu, a, b, c);
+        }
+    }
+    return cst;
+}
+
+__device__ __forceinline__ int find_job(const RefJob* __restrict__ jobs, int n_jobs, int item) {
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&jobs[mid].item_base) <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Largest k in [lo, hi) with a[k] <= w (a nondecreasing, a[lo] <= w).
+__device__ __forceinline__ int upper_index(const int32_t* a, int lo, int hi, int w) {
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] <= w) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int FMT, int COMB>
+__global__ void __launch_bounds__(kThreads) cost_kernel(const RefJob* __restrict__ jobs, int n_jobs,
+                                                        Plan* __restrict__ plan) {
+    __shared__ float sH[kHFloats];
+    __shared__ NbrView sNbr[FTV_MAX_NBRS];
+    __shared__ int sAcc[kSegAcc * kMaxLB];
+    __shared__ int sWoffs[kLocCache + 1];
+    __shared__ int s_item, s_k0, s_k1;
+
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int total = *reinterpret_cast<volatile int*>(&plan->total_items);
+    for (int i = tid; i < kSegAcc * kMaxLB; i += kThreads) sAcc[i] = 0;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = atomicAdd(&plan->counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) break;
+
+        const RefJob* Jp = &jobs[find_job(jobs, n_jobs, item)];
+        const int q = item - Jp->item_base;
+        const int nLB = Jp->nLB, L = Jp->L, N = Jp->N, W = Jp->W, penalty = Jp->penalty;
+        const int tile = q / nLB, lb = q - tile * nLB;
+        const int d0 = lb * Jp->LB;
+        const int LBa = min(Jp->LB, L - d0);
+        const int n_rec = Jp->n_rec, n_work = Jp->n_work;
+        const int32_t* __restrict__ woffs = Jp->woffs;
+        const int32_t* __restrict__ list = Jp->list;
+        const int32_t* __restrict__ offs = Jp->offs;
+        const uint32_t* __restrict__ pix = Jp->pix;
+        const void* ref_tex = Jp->ref_texels;
+        int32_t* __restrict__ cost = Jp->cost;
+        const int w0 = tile * kTile;
+        const int w1 = min(w0 + kTile, n_rec);
+
+        // stage homographies [N][LBa][9] and neighbour geometry
+        const float* __restrict__ Hg = Jp->H;
+        const int nh = N * LBa * 9;
+        for (int i = tid; i < nh; i += kThreads) {
+            const int n = i / (LBa * 9), rem = i - n * (LBa * 9);
+            sH[i] = __ldg(&Hg[((int64_t)n * L + d0) * 9 + rem]);
+        }
+        for (int i = tid; i < N; i += kThreads) sNbr[i] = Jp->nbrs[i];
+        if (tid == 0) {
+            s_k0 = upper_index(woffs, 0, n_work + 1, w0);
+            s_k1 = upper_index(woffs, 0, n_work + 1, w1 - 1);
+        }
+        __syncthreads();
+        const int k0 = s_k0, k1 = s_k1;
+        const int nk = k1 - k0 + 1;
+        const bool cached = nk + 1 <= kLocCache;
+        if (cached)
+            for (int i = tid; i <= nk; i += kThreads) sWoffs[i] = woffs[k0 + i];
+        __syncthreads();
+
+        // this thread's pixels
+        float px[kPPT], py[kPPT];
+        int ra[kPPT], rb[kPPT], rc[kPPT], key[kPPT];
+#pragma unroll
+        for (int j = 0; j < kPPT; ++j) {
+            const int w = w0 + j * kThreads + tid;
+            key[j] = kSentinel;
+            px[j] = py[j] = 0.0f;
+            ra[j] = rb[j] = rc[j] = 0;
+            if (w < w1) {
+                int k;
+                if (cached) k = k0 + upper_index(sWoffs, 0, nk + 1, w);
+                else k = upper_index(woffs, k0, k1 + 1, w);
+                const int s = list ? list[k] : k;
+                const int base = cached ? sWoffs[k - k0] : woffs[k];
+                const uint32_t xy = pix[offs[s] + (w - base)];
+                const int x = xy & 0xffff, y = xy >> 16;
+                px[j] = (float)x;
+                py[j] = (float)y;
+                TexelOps<FMT>::unpack_ref(ref_tex, (int64_t)y * W + x, ra[j], rb[j], rc[j]);
+                key[j] = k - k0;
+            }
+        }
+
+        for (int l = 0; l < LBa; ++l) {
+            int m[kPPT];
+#pragma unroll
+            for (int j = 0; j < kPPT; ++j) m[j] = (COMB == FTV_COMBINE_MIN && N > 0) ? INT_MAX : 0;
+            for (int n = 0; n < N; ++n) {
+                float h[9];
+                const float* hs = &sH[(n * LBa + l) * 9];
+#pragma unroll
+                for (int e = 0; e < 9; ++e) h[e] = hs[e];
+                const NbrView nv = sNbr[n];
+                const float wm1 = (float)(nv.w - 1), hm1 = (float)(nv.h - 1);
+#pragma unroll
+                for (int j = 0; j < kPPT; ++j) {
+                    if (key[j] != kSentinel) {
+                        const int c = sample_cost<FMT>(h, px[j], py[j], ra[j], rb[j], rc[j], nv.texels, nv.pitch,
+                                                       wm1, hm1, penalty);
+                        m[j] = (COMB == FTV_COMBINE_MIN) ? min(m[j], c) : m[j] + c;
+                    }
+                }
+            }
+            // segmented warp reduction: keys are nondecreasing along the lanes
+#pragma unroll
+            for (int j = 0; j < kPPT; ++j) {
+                const int v = key[j] != kSentinel ? m[j] : 0;
+                const int kfirst = __shfl_sync(kFull, key[j], 0);
+                const int klast = __shfl_sync(kFull, key[j], 31);
+                if (kfirst == klast) {
+                    if (kfirst != kSentinel) {
+                        const int sum = __reduce_add_sync(kFull, v);
+                        if (lane == 0) {
+                            if (kfirst < kSegAcc) atomicAdd(&sAcc[kfirst * kMaxLB + l], sum);
+                            else {
+                                const int s = list ? list[k0 + kfirst] : k0 + kfirst;
+                                atomicAdd(&cost[(int64_t)s * L + d0 + l], sum);
+                            }
+                        }
+                    }
+                } else {
+                    unsigned rem = kFull;
+                    while (rem) {
+                        const int leader = __ffs(rem) - 1;
+                        const int kk = __shfl_sync(kFull, key[j], leader);
+                        const unsigned grp = __ballot_sync(kFull, key[j] == kk);
+                        const int sum = __reduce_add_sync(kFull, key[j] == kk ? v : 0);
+                        if (lane == leader && kk != kSentinel) {
+                            if (kk < kSegAcc) atomicAdd(&sAcc[kk * kMaxLB + l], sum);
+                            else {
+                                const int s = list ? list[k0 + kk] : k0 + kk;
+                                atomicAdd(&cost[(int64_t)s * L + d0 + l], sum);
+                            }
+                        }
+                        rem &= ~grp;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+
+        // write the row slices of this tile's segments
+        const int nacc = min(nk, kSegAcc);
+        for (int i = tid; i < nacc * LBa; i += kThreads) {
+            const int loc = i / LBa, l = i - loc * LBa;
+            const int k = k0 + loc;
+            const int s = list ? list[k] : k;
+            const int v = sAcc[loc * kMaxLB + l];
+            sAcc[loc * kMaxLB + l] = 0;
+            if ((unsigned)s >= (unsigned)Jp->S) continue;  // an invalid list entry owns no pixels
+            const int a = cached ? sWoffs[loc] : woffs[k];
+            const int b = cached ? sWoffs[loc + 1] : woffs[k + 1];
+            int32_t* dst = &cost[(int64_t)s * L + d0 + l];
+            if (a >= w0 && b <= w0 + kTile) *dst = v;
+            else atomicAdd(dst, v);
+        }
+    }
+}
+
+template <int FMT, int COMB>
+int blocks_per_sm_for() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cost_kernel<FMT, COMB>, kThreads, 0) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+}  // namespace
+
+int cost_blocks_per_sm(int fmt, int combine) {
+    if (fmt == FMT_U8X4) return combine == FTV_COMBINE_MIN ? blocks_per_sm_for<FMT_U8X4, FTV_COMBINE_MIN>()
+                                                           : blocks_per_sm_for<FMT_U8X4, FTV_COMBINE_SUM>();
+    if (fmt == FMT_P10) return combine == FTV_COMBINE_MIN ? blocks_per_sm_for<FMT_P10, FTV_COMBINE_MIN>()
+                                                          : blocks_per_sm_for<FMT_P10, FTV_COMBINE_SUM>();
+    return combine == FTV_COMBINE_MIN ? blocks_per_sm_for<FMT_U16X4, FTV_COMBINE_MIN>()
+                                      : blocks_per_sm_for<FMT_U16X4, FTV_COMBINE_SUM>();
+}
+
+cudaError_t launch_cost(const RefJob* jobs, int n_jobs, const Plan* plan, int fmt, int combine, int grid,
+                        cudaStream_t s) {
+    Plan* p = const_cast<Plan*>(plan);
+#define FTV_LAUNCH(F, C) cost_kernel<F, C><<<grid, kThreads, 0, s>>>(jobs, n_jobs, p)
+    if (fmt == FMT_U8X4) {
+        if (combine == FTV_COMBINE_MIN) FTV_LAUNCH(FMT_U8X4, FTV_COMBINE_MIN);
+        else FTV_LAUNCH(FMT_U8X4, FTV_COMBINE_SUM);
+    } else if (fmt == FMT_P10) {
+        if (combine == FTV_COMBINE_MIN) FTV_LAUNCH(FMT_P10, FTV_COMBINE_MIN);
+        else FTV_LAUNCH(FMT_P10, FTV_COMBINE_SUM);
+    } else {
+        if (combine == FTV_COMBINE_MIN) FTV_LAUNCH(FMT_U16X4, FTV_COMBINE_MIN);
+        else FTV_LAUNCH(FMT_U16X4, FTV_COMBINE_SUM);
+    }
+#undef FTV_LAUNCH
+    return cudaGetLastError();
+}
+
+}  // namespace ftv

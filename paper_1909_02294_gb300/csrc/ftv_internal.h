@@ -1,0 +1,140 @@
+// Internal declarations shared by the library's translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/ftv.h"
+
+namespace ftv {
+
+// Packed texel formats: one load fetches the three samples of a pixel.
+enum TexelFormat : int32_t {
+    FMT_U8X4 = 0,   // uint32: Y | Cb << 8 | Cr << 16          (8-bit samples)
+    FMT_P10 = 1,    // uint32: Y | Cb << 10 | Cr << 20         (samples of at most 10 bits)
+    FMT_U16X4 = 2,  // uint2 : (Y | Cb << 16, Cr)              (samples of 11 to 16 bits)
+};
+
+// Device status bits (OR-ed by kernels, read and cleared by ftv_check).
+enum StatusBits : uint32_t { ST_BAD_LABEL = 1u, ST_BAD_SAMPLE = 2u, ST_OVERFLOW = 4u };
+
+// Cost-kernel tiling: each work item is one tile of kTile consecutive segment pixels (in listed-segment
+// order) times one block of consecutive labels. kThreads threads own kPPT pixels each.
+constexpr int kThreads = 256;
+constexpr int kPPT = 4;
+constexpr int kTile = kThreads * kPPT;
+constexpr int kMaxLB = 64;          // labels per block
+constexpr int kHFloats = 4608;      // shared-memory capacity for N x LB x 9 homography floats
+constexpr int kSegAcc = 64;         // per-tile segment accumulators in shared memory
+
+// Geometry of a neighbour view as the cost kernel sees it.
+struct NbrView {
+    const void* texels;  // packed view, row pitch `pitch` texels
+    int32_t w, h, pitch, pad;
+};
+
+// One (job, reference) unit of the persistent cost kernel. Plan fields are written on the device.
+struct RefJob {
+    const void* ref_texels;    // packed reference view (row pitch = W texels)
+    const uint32_t* pix;       // segment index records: (y << 16) | x, grouped by segment
+    const int32_t* offs;       // segment index offsets [S + 1]
+    const int32_t* list;       // listed segments or nullptr (all)
+    const int32_t* n_listed;   // device length of `list` (nullptr with list == nullptr)
+    int32_t* woffs;            // scratch [S + 1]: prefix of listed segment sizes (written by plan)
+    const float* H;            // [N][L][9]
+    const NbrView* nbrs;       // [N]
+    int32_t* cost;             // [S][L]
+    int32_t W, S, N, L, LB, nLB, penalty, fmt;
+    // plan outputs
+    int32_t n_work;            // listed segments
+    int32_t n_rec;             // listed pixels
+    int32_t n_items;           // tiles * nLB
+    int32_t item_base;         // first item of this unit in the launch
+};
+
+struct Plan {
+    int32_t total_items;
+    int32_t counter;           // next item to take (persistent CTAs)
+    int32_t pad[2];
+};
+
+struct RefState {
+    int32_t view;              // camera index
+    int32_t W, H;
+    int32_t n_nbrs;
+    std::vector<int32_t> nbrs;
+    float* d_H = nullptr;      // [N][L][9]
+    NbrView* d_nbrs = nullptr; // [N]
+    int32_t* d_offs = nullptr;   // [max_segments + 1]
+    int32_t* d_cursor = nullptr; // [max_segments]
+    int32_t* d_woffs = nullptr;  // [max_segments + 1]
+    uint32_t* d_pix = nullptr;   // [W * H]
+    int32_t S_indexed = -1;      // segment count of the cached index (-1: none)
+    std::vector<float> h_H;      // host copy of the table
+};
+
+}  // namespace ftv
+
+struct ftv_ctx {
+    int device = 0;
+    int n_sm = 0;
+    int cost_blocks_per_sm = 0;
+    int32_t n_views = 0, n_refs = 0, L = 0, plane_mode = 0, centre = 0;
+    int32_t sample_bytes = 1, bit_depth = 8, penalty = 0, combine = 0, max_segments = 0, fmt = 0;
+    int32_t LB = 0, nLB = 0;
+    double z_near = 0, z_far = 0;
+    std::vector<ftv_camera> cams;
+    std::vector<ftv::RefState> refs;
+    std::vector<float> label_z;
+    // device scratch
+    void* d_packed = nullptr;                 // all views, packed texels
+    std::vector<size_t> view_offset_bytes;    // byte offset of each packed view
+    size_t texel_bytes = 4;
+    uint32_t* d_status = nullptr;
+    ftv::RefJob* d_jobs = nullptr;            // [n_refs]
+    ftv::Plan* d_plan = nullptr;
+    int64_t* d_tstats = nullptr;              // temporal accumulators [max_segments][7]
+    float* d_label_z = nullptr;               // [L]
+    int64_t launches = 0;
+    bool profiling = false;
+    bool timed = false;
+    cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
+};
+
+namespace ftv {
+
+// Host geometry (ftv_geometry.cpp)
+bool label_inv_depths(int L, double z_near, double z_far, std::vector<double>& iz);
+int plane_homography(const ftv_camera& cr, const ftv_camera& cv, const ftv_camera* cc, double iz, double H[9]);
+
+// Launchers (ftv_index.cu)
+cudaError_t launch_pack(const void* const* planes, const int64_t* pitch, int sample_bytes, int bit_depth, int fmt,
+                        int W, int H, void* out, uint32_t* status, cudaStream_t s);
+cudaError_t launch_segment_index(const int32_t* labels, int W, int H, int S, int64_t max_pix_cost, int32_t* offs,
+                                 int32_t* cursor, uint32_t* pix, uint32_t* status, cudaStream_t s, int64_t* launches);
+// Descriptors travel as kernel parameters (graph-capturable, no host staging buffer to race on).
+constexpr int kMaxUnits = 240;  // (job, reference) units per launch
+cudaError_t launch_plan(const RefJob* host_jobs, int n_jobs, RefJob* d_jobs, Plan* plan, cudaStream_t s);
+cudaError_t launch_zero_rows(int32_t* cost, int L, int S, const int32_t* list, const int32_t* n_listed,
+                             cudaStream_t s);
+
+// Cost kernel (ftv_cost.cu)
+int cost_blocks_per_sm(int fmt, int combine);
+cudaError_t launch_cost(const RefJob* jobs, int n_jobs, const Plan* plan, int fmt, int combine, int grid,
+                        cudaStream_t s);
+
+// Temporal / WTA (ftv_temporal.cu)
+cudaError_t launch_temporal(const void* const* cur, const int64_t* cur_pitch, const void* const* prev,
+                            const int64_t* prev_pitch, const void* const* ifr, const int64_t* ifr_pitch,
+                            int sample_bytes, const int32_t* labels, int W, int H, int S, int t_p, int t_i,
+                            int mode, int64_t* stats, uint8_t* mask, int32_t* changed, int32_t* n_changed,
+                            uint32_t* status, cudaStream_t s, int64_t* launches);
+cudaError_t launch_wta(const int32_t* cost, int S, int L, const uint8_t* mask, const uint16_t* prev_label,
+                       const uint16_t* ifr_label, const int32_t* list, const int32_t* n_listed, uint16_t* out,
+                       cudaStream_t s);
+cudaError_t launch_depth_map(const int32_t* labels, int W, int H, int S, const uint16_t* seg_label,
+                             const float* label_z, int L, float* depth, uint32_t* status, cudaStream_t s);
+
+}  // namespace ftv

@@ -1,0 +1,296 @@
+"""Thin Python binding of the C ABI in include/ftv.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does nothing but convert
+arguments: torch CUDA tensors become device pointers, the current torch stream becomes the
+ftv_stream, and non-zero status codes become FtvError. All computation happens in libftv.so's CUDA
+kernels; if the shared library is missing this module raises at import, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libftv.so")
+
+FTV_OK = 0
+FTV_ERR_INVALID_ARG, FTV_ERR_OUT_OF_MEMORY, FTV_ERR_CUDA, FTV_ERR_OVERFLOW = 1, 2, 3, 4
+FTV_ERR_TIMEOUT, FTV_ERR_BUSY, FTV_ERR_STATE = 5, 6, 7
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
+          4: "segment cost may overflow int32", 5: "device wait timed out", 6: "busy", 7: "call out of order"}
+FTV_PLANES_REF, FTV_PLANES_CENTRE = 0, 1
+FTV_COMBINE_MIN, FTV_COMBINE_SUM = 0, 1
+FTV_TM_Y_ONLY, FTV_TM_ALL_YUV = 0, 1
+FTV_MASK_CHANGED, FTV_MASK_REUSE_P, FTV_MASK_REUSE_I = 0, 1, 2
+
+
+class FtvError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({code})")
+        self.code = code
+
+
+class ftv_camera(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_double * 9), ("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class ftv_config(ctypes.Structure):
+    _fields_ = [("n_views", ctypes.c_int32), ("cams", ctypes.POINTER(ftv_camera)),
+                ("n_refs", ctypes.c_int32), ("ref_views", ctypes.POINTER(ctypes.c_int32)),
+                ("nbr_offsets", ctypes.POINTER(ctypes.c_int32)), ("nbr_views", ctypes.POINTER(ctypes.c_int32)),
+                ("n_labels", ctypes.c_int32), ("z_near", ctypes.c_double), ("z_far", ctypes.c_double),
+                ("plane_mode", ctypes.c_int32), ("centre_view", ctypes.c_int32),
+                ("sample_bytes", ctypes.c_int32), ("bit_depth", ctypes.c_int32),
+                ("oob_penalty", ctypes.c_int32), ("combine", ctypes.c_int32),
+                ("max_segments", ctypes.c_int32)]
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run __graft_entry__.build() (nvcc, sm_103a)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "ftv_depth_init": [ctypes.POINTER(ftv_config), ctypes.POINTER(vp)],
+        "ftv_depth_destroy": [vp],
+        "ftv_get_homographies": [vp, i32, vp],
+        "ftv_compute_homographies": [ctypes.POINTER(ftv_config), i32, vp],
+        "ftv_get_neighbours": [vp, i32, vp, vp],
+        "ftv_get_label_depths": [vp, vp],
+        "ftv_segment_index": [vp, i32, vp, i32, vp],
+        "ftv_cost_volume": [vp, vp, vp, vp, vp, vp, vp, vp, vp],
+        "ftv_temporal_mask": [vp, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp],
+        "ftv_wta_depth": [vp, i32, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp],
+        "ftv_check": [vp, vp],
+        "ftv_set_profiling": [vp, i32],
+        "ftv_last_kernel_ms": [vp, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.ftv_launch_count.argtypes = [vp]
+    lib.ftv_launch_count.restype = i64
+    lib.ftv_status_str.argtypes = [ctypes.c_int]
+    lib.ftv_status_str.restype = ctypes.c_char_p
+    return lib
+
+
+lib = _load()
+
+EXPORTED = ["ftv_depth_init", "ftv_depth_destroy", "ftv_compute_homographies", "ftv_get_homographies", "ftv_get_neighbours",
+            "ftv_get_label_depths", "ftv_segment_index", "ftv_cost_volume", "ftv_temporal_mask",
+            "ftv_wta_depth", "ftv_check", "ftv_launch_count", "ftv_status_str", "ftv_set_profiling",
+            "ftv_last_kernel_ms"]
+
+
+def _ok(code: int, where: str) -> None:
+    if code != FTV_OK:
+        raise FtvError(code, where)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _arr(ctype, values):
+    values = list(values)
+    return (ctype * max(1, len(values)))(*values)
+
+
+def camera_struct(cam) -> ftv_camera:
+    c = ftv_camera()
+    c.K[:] = [float(v) for v in np.asarray(cam.K, np.float64).ravel()]
+    c.R[:] = [float(v) for v in np.asarray(cam.R, np.float64).ravel()]
+    c.t[:] = [float(v) for v in np.asarray(cam.t, np.float64).ravel()]
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+@dataclass
+class Context:
+    """Owns an ftv_ctx handle (ftv_depth_destroy on close)."""
+    handle: int
+    n_refs: int
+    n_labels: int
+    ref_views: list
+
+    def close(self) -> None:
+        if self.handle:
+            ftv_depth_destroy(self)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _config(cams, ref_views, n_labels, z_near, z_far, nbr_lists, plane_mode, centre_view, sample_bytes,
+            bit_depth, oob_penalty, combine, max_segments):
+    cam_arr = (ftv_camera * len(cams))(*[camera_struct(c) for c in cams])
+    refs = _arr(ctypes.c_int32, ref_views)
+    cfg = ftv_config()
+    cfg.n_views, cfg.cams = len(cams), ctypes.cast(cam_arr, ctypes.POINTER(ftv_camera))
+    cfg.n_refs, cfg.ref_views = len(ref_views), ctypes.cast(refs, ctypes.POINTER(ctypes.c_int32))
+    keep = [cam_arr, refs]
+    if nbr_lists is not None:
+        offs = [0]
+        flat = []
+        for lst in nbr_lists:
+            flat += list(lst)
+            offs.append(len(flat))
+        o, f = _arr(ctypes.c_int32, offs), _arr(ctypes.c_int32, flat)
+        keep += [o, f]
+        cfg.nbr_offsets = ctypes.cast(o, ctypes.POINTER(ctypes.c_int32))
+        cfg.nbr_views = ctypes.cast(f, ctypes.POINTER(ctypes.c_int32))
+    cfg.n_labels, cfg.z_near, cfg.z_far = n_labels, z_near, z_far
+    cfg.plane_mode, cfg.centre_view = plane_mode, centre_view
+    cfg.sample_bytes, cfg.bit_depth, cfg.oob_penalty = sample_bytes, bit_depth, oob_penalty
+    cfg.combine, cfg.max_segments = combine, max_segments
+    return cfg, keep
+
+
+def ftv_depth_init(cams, ref_views, n_labels: int, z_near: float, z_far: float, *, nbr_lists=None,
+                   plane_mode: int = FTV_PLANES_REF, centre_view: int = 0, sample_bytes: int = 1,
+                   bit_depth: int = 8, oob_penalty: int = -1, combine: int = FTV_COMBINE_MIN,
+                   max_segments: int = 1) -> Context:
+    cfg, keep = _config(cams, ref_views, n_labels, z_near, z_far, nbr_lists, plane_mode, centre_view, sample_bytes,
+                        bit_depth, oob_penalty, combine, max_segments)
+    h = ctypes.c_void_p()
+    _ok(lib.ftv_depth_init(ctypes.byref(cfg), ctypes.byref(h)), "ftv_depth_init")
+    return Context(h.value, len(ref_views), n_labels, list(ref_views))
+
+
+def ftv_compute_homographies(cams, ref_views, ref_index: int, n_labels: int, z_near: float, z_far: float, *,
+                             nbr_lists=None, plane_mode: int = FTV_PLANES_REF, centre_view: int = 0) -> np.ndarray:
+    """Host-only FP32 homography table [n_nbrs][n_labels][9] of reference ref_index."""
+    cfg, keep = _config(cams, ref_views, n_labels, z_near, z_far, nbr_lists, plane_mode, centre_view, 1, 8, -1,
+                        FTV_COMBINE_MIN, 1)
+    ref = ref_views[ref_index]
+    n = len(nbr_lists[ref_index]) if nbr_lists is not None else len(cams) - 1
+    out = np.empty((n, n_labels, 9), np.float32)
+    _ok(lib.ftv_compute_homographies(ctypes.byref(cfg), ref_index, out.ctypes.data), "ftv_compute_homographies")
+    return out
+
+
+def ftv_depth_destroy(ctx: Context) -> None:
+    _ok(lib.ftv_depth_destroy(ctx.handle), "ftv_depth_destroy")
+
+
+def ftv_get_homographies(ctx: Context, ref_index: int) -> np.ndarray:
+    n = ctypes.c_int32()
+    _ok(lib.ftv_get_neighbours(ctx.handle, ref_index, ctypes.byref(n), None), "ftv_get_neighbours")
+    out = np.empty((n.value, ctx.n_labels, 9), np.float32)
+    _ok(lib.ftv_get_homographies(ctx.handle, ref_index, out.ctypes.data), "ftv_get_homographies")
+    return out
+
+
+def ftv_get_neighbours(ctx: Context, ref_index: int) -> list[int]:
+    n = ctypes.c_int32()
+    _ok(lib.ftv_get_neighbours(ctx.handle, ref_index, ctypes.byref(n), None), "ftv_get_neighbours")
+    out = np.empty(max(1, n.value), np.int32)
+    _ok(lib.ftv_get_neighbours(ctx.handle, ref_index, ctypes.byref(n), out.ctypes.data), "ftv_get_neighbours")
+    return [int(v) for v in out[: n.value]]
+
+
+def ftv_get_label_depths(ctx: Context) -> np.ndarray:
+    out = np.empty(ctx.n_labels, np.float32)
+    _ok(lib.ftv_get_label_depths(ctx.handle, out.ctypes.data), "ftv_get_label_depths")
+    return out
+
+
+def ftv_segment_index(ctx: Context, ref_index: int, labels, n_segments: int, stream=None) -> None:
+    _ok(lib.ftv_segment_index(ctx.handle, ref_index, _ptr(labels), n_segments, _stream(stream)),
+        "ftv_segment_index")
+
+
+def ftv_cost_volume(ctx: Context, planes, labels, n_segments, costs, seg_lists=None, n_listed=None,
+                    stream=None) -> None:
+    """planes: per view a (Y, Cb, Cr) triple of 2-D CUDA tensors (uint8 or uint16, any row pitch);
+    labels: per reference an int32 [H][W] tensor or None (reuse the cached index);
+    costs: per reference an int32 [S][L] tensor; seg_lists/n_listed: optional per-reference device
+    list and one-element int32 length tensor."""
+    ptrs, pitches = [], []
+    for trip in planes:
+        for t in trip:
+            ptrs.append(_ptr(t))
+            pitches.append(int(t.stride(0)) * t.element_size())
+    R = ctx.n_refs
+    p_arr = _arr(ctypes.c_void_p, ptrs)
+    pitch_arr = _arr(ctypes.c_int64, pitches)
+    lab_arr = _arr(ctypes.c_void_p, [_ptr(l) if l is not None else None for l in labels]) if labels is not None else None
+    nseg = _arr(ctypes.c_int32, n_segments) if n_segments is not None else None
+    sl = _arr(ctypes.c_void_p, [_ptr(x) for x in seg_lists]) if seg_lists is not None else None
+    nl = _arr(ctypes.c_void_p, [_ptr(x) for x in n_listed]) if n_listed is not None else None
+    c_arr = _arr(ctypes.c_void_p, [_ptr(c) for c in costs])
+    assert len(costs) == R
+    _ok(lib.ftv_cost_volume(ctx.handle, p_arr, pitch_arr, lab_arr, nseg, sl, nl, c_arr, _stream(stream)),
+        "ftv_cost_volume")
+
+
+def _trip(planes):
+    if planes is None:
+        return None, None
+    ptrs = _arr(ctypes.c_void_p, [_ptr(t) for t in planes])
+    pitches = _arr(ctypes.c_int64, [int(t.stride(0)) * t.element_size() if t is not None else 0 for t in planes])
+    return ptrs, pitches
+
+
+def ftv_temporal_mask(ctx: Context, ref_index: int, cur, prev, iframe, labels, n_segments: int, t_p: int, t_i: int,
+                      mode: int, mask, changed_list, n_changed, stream=None) -> None:
+    cp, cpi = _trip(cur)
+    pp, ppi = _trip(prev)
+    ip, ipi = _trip(iframe)
+    _ok(lib.ftv_temporal_mask(ctx.handle, ref_index, cp, cpi, pp, ppi, ip, ipi, _ptr(labels), n_segments, t_p, t_i,
+                              mode, _ptr(mask), _ptr(changed_list), _ptr(n_changed), _stream(stream)),
+        "ftv_temporal_mask")
+
+
+def ftv_wta_depth(ctx: Context, ref_index: int, cost, n_segments: int, label_out, *, mask=None, prev_label=None,
+                  iframe_label=None, seg_list=None, n_listed=None, labels_pix=None, depth_map=None,
+                  stream=None) -> None:
+    _ok(lib.ftv_wta_depth(ctx.handle, ref_index, _ptr(cost), n_segments, _ptr(mask), _ptr(prev_label),
+                          _ptr(iframe_label), _ptr(seg_list), _ptr(n_listed), _ptr(label_out), _ptr(labels_pix),
+                          _ptr(depth_map), _stream(stream)), "ftv_wta_depth")
+
+
+def ftv_check(ctx: Context, stream=None) -> int:
+    """Wait for the stream and return the context's device status code (0 = clean)."""
+    return int(lib.ftv_check(ctx.handle, _stream(stream)))
+
+
+def ftv_launch_count(ctx: Context) -> int:
+    return int(lib.ftv_launch_count(ctx.handle))
+
+
+def ftv_status_str(code: int) -> str:
+    return lib.ftv_status_str(code).decode()
+
+
+def ftv_set_profiling(ctx: Context, enable: bool) -> None:
+    _ok(lib.ftv_set_profiling(ctx.handle, 1 if enable else 0), "ftv_set_profiling")
+
+
+def ftv_last_kernel_ms(ctx: Context) -> float:
+    ms = ctypes.c_float()
+    _ok(lib.ftv_last_kernel_ms(ctx.handle, ctypes.byref(ms)), "ftv_last_kernel_ms")
+    return float(ms.value)

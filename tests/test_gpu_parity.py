@@ -1,0 +1,286 @@
+"""GPU parity: the CUDA cost volume, temporal mask and winner-take-all against the CPU oracle.
+
+Integer outputs, so the bar is bit-exact everywhere. Small and reduced workloads are compared entry
+by entry over whole volumes (they span many 1024-pixel tiles, several label blocks and a ragged last
+tile); the full-size workloads, run in the launch configuration the benchmark times, are compared on
+seeded samples of (segment, label) entries that the oracle computes one by one.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import oracle_runs
+import synth
+from synth.configs import make_workload
+
+pytestmark = pytest.mark.gpu
+
+ftv = pytest.importorskip("paper_1909_02294_gb300")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from gpu_runs import Run, dev  # noqa: E402
+
+
+def _oracle_all(wl, combine=None, plane_mode=0, centre=0, nbr_lists=None, frame=0):
+    out = []
+    for i, r in enumerate(wl.ref_views):
+        lab, S = wl.labels(r)
+        nb = nbr_lists[i] if nbr_lists is not None else wl.neighbours(r)
+        H = oracle.homography_table(wl.cams, r, nb, wl.n_labels, wl.z_near, wl.z_far, plane_mode=plane_mode,
+                                    centre=centre)
+        out.append(oracle.cost_volume(wl.cams, wl.views(frame), wl.sample_bytes, r, nb, H, wl.n_labels, lab, S,
+                                      wl.oob_penalty, combine or wl.combine))
+    return out
+
+
+def _assert_equal(got, ref, what):
+    got = got.cpu().numpy() if isinstance(got, torch.Tensor) else got
+    bad = int((got != ref).sum())
+    assert bad == 0, f"{what}: {bad} of {ref.size} entries differ"
+
+
+@pytest.mark.parametrize("combine", ["min", "sum"])
+def test_tiny_volume_wta_and_depth_bit_exact(combine):
+    wl = make_workload("tiny")
+    run = Run(wl, combine=combine)
+    costs = run.volumes()
+    assert run.check() == 0
+    ref = _oracle_all(wl, combine)
+    _assert_equal(costs[0], ref[0], "tiny volume")
+    S = run.S[0]
+    win = torch.empty(S, dtype=torch.int16, device="cuda")
+    depth = torch.empty((270, 480), dtype=torch.float32, device="cuda")
+    ftv.ftv_wta_depth(run.ctx, 0, costs[0], S, win, labels_pix=run.labels[0], depth_map=depth)
+    assert run.check() == 0
+    w_ref = oracle.wta(ref[0])
+    assert np.array_equal(win.cpu().numpy().view(np.uint16), w_ref)
+    d_ref = oracle.depth_map(wl.labels(1)[0], S, w_ref, wl.n_labels, wl.z_near, wl.z_far)
+    assert np.array_equal(depth.cpu().numpy(), d_ref)
+    run.close()
+
+
+@pytest.mark.parametrize("name", ["hd8", "uhd15", "temporal"])
+def test_reduced_workloads_bit_exact(name):
+    wl = make_workload(name, reduced=True)
+    run = Run(wl)
+    costs = run.volumes()
+    assert run.check() == 0
+    for c, ref, r in zip(costs, _oracle_all(wl), wl.ref_views):
+        _assert_equal(c, ref, f"{wl.name} ref {r}")
+    run.close()
+
+
+def test_serving_small_shape_bit_exact():
+    wl = make_workload("serving_small")
+    run = Run(wl)
+    costs = run.volumes()
+    assert run.check() == 0
+    for c, ref in zip(costs, _oracle_all(wl)):
+        _assert_equal(c, ref, "serving_small")
+    run.close()
+
+
+def test_sixteen_bit_samples_use_wide_texels():
+    wl = make_workload("hd8", reduced=True)
+    wl.bit_depth = 12  # 12-bit samples: packed as 16-bit fields
+    wl.ref_views = [0, 5]
+    run = Run(wl)
+    costs = run.volumes()
+    assert run.check() == 0
+    for c, ref in zip(costs, _oracle_all(wl)):
+        _assert_equal(c, ref, "12-bit")
+    run.close()
+
+
+def test_centre_planes_and_nearest_neighbour_views():
+    wl = make_workload("uhd15", reduced=True)
+    lists = [[1], [6, 8], [13]]  # the paper's set D: nearest left and right (one at the ends)
+    run = Run(wl, plane_mode=1, centre=7, nbr_lists=lists)
+    costs = run.volumes()
+    assert run.check() == 0
+    for c, ref in zip(costs, _oracle_all(wl, plane_mode=1, centre=7, nbr_lists=lists)):
+        _assert_equal(c, ref, "centre planes")
+    run.close()
+
+
+def test_listed_segments_leave_other_rows_untouched():
+    wl = make_workload("hd8", reduced=True)
+    run = Run(wl)
+    rng = np.random.default_rng(3)
+    lists, counts, host_lists = [], [], []
+    for S in run.S:
+        lst = np.sort(rng.choice(S, size=S // 7, replace=False)).astype(np.int32)
+        host_lists.append(lst)
+        pad = np.concatenate([lst, np.full(5, -1, np.int32)])  # capacity beyond the count is ignored
+        lists.append(dev(pad))
+        counts.append(dev(np.array([len(lst)], np.int32)))
+    costs = run.volumes(seg_lists=lists, n_listed=counts, fill=-7)
+    assert run.check() == 0
+    full = _oracle_all(wl)
+    for c, ref, lst in zip(costs, full, host_lists):
+        got = c.cpu().numpy()
+        _assert_equal(got[lst], ref[lst], "listed rows")
+        rest = np.setdiff1d(np.arange(ref.shape[0]), lst)
+        assert np.all(got[rest] == -7)
+    run.close()
+
+
+def test_cached_segment_index_and_determinism():
+    wl = make_workload("hd8", reduced=True)
+    run = Run(wl)
+    a = [c.cpu().numpy() for c in run.volumes()]
+    for i in range(len(wl.ref_views)):
+        ftv.ftv_segment_index(run.ctx, i, run.labels[i], run.S[i])
+    b = [c.cpu().numpy() for c in run.volumes(use_cache=True)]
+    assert run.check() == 0
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    run.close()
+
+
+def _tiny_with_labels(lab, S):
+    wl = make_workload("tiny")
+    wl._labels[1] = (np.ascontiguousarray(lab, np.int32), S)
+    return wl
+
+
+@pytest.mark.parametrize("case", ["one_segment", "pixel_segments", "empty_segments", "stripes"])
+def test_degenerate_segmentations(case):
+    H, W = 270, 480
+    if case == "one_segment":
+        lab, S = np.zeros((H, W), np.int32), 1
+    elif case == "pixel_segments":
+        lab = np.empty((H, W), np.int32)
+        lab[:, :64] = np.arange(H * 64).reshape(H, 64)  # one-pixel segments
+        lab[:, 64:] = H * 64 + np.arange(H * (W - 64)).reshape(H, W - 64) // 37  # 37-pixel runs
+        S = int(lab.max()) + 1
+    elif case == "empty_segments":
+        lab, S0 = synth.grid_labels(W, H, 16, 3, 11)
+        lab = lab * 3  # only every third id is used
+        S = 3 * S0 + 5
+    else:  # one segment per row: segments cut by every tile boundary
+        lab, S = np.repeat(np.arange(H, dtype=np.int32)[:, None], W, 1), H
+    wl = _tiny_with_labels(lab, S)
+    run = Run(wl)
+    costs = run.volumes()
+    assert run.check() == 0
+    _assert_equal(costs[0], _oracle_all(wl)[0], case)
+    run.close()
+
+
+def test_single_neighbour_and_single_label():
+    wl = make_workload("tiny")
+    wl.n_labels = 1
+    run = Run(wl, nbr_lists=[[2]])
+    costs = run.volumes()
+    assert run.check() == 0
+    ref = _oracle_all(wl, nbr_lists=[[2]])
+    _assert_equal(costs[0], ref[0], "L=1, N=1")
+    run.close()
+
+
+def test_invalid_labels_and_overflow_are_reported_not_trapped():
+    wl = make_workload("tiny")
+    lab, S = wl.labels(1)
+    bad = lab.copy()
+    bad[5, 7] = S  # out of range
+    bad[6, 8] = -1
+    wl2 = _tiny_with_labels(bad, S)
+    run = Run(wl2)
+    run.volumes()
+    assert run.check() == ftv.FTV_ERR_INVALID_ARG
+    # the context stays usable and clean afterwards
+    run.labels = [dev(lab)]
+    c = run.volumes()
+    assert run.check() == 0
+    _assert_equal(c[0], _oracle_all(make_workload("tiny"))[0], "after invalid labels")
+    run.close()
+    # one segment of 129600 pixels with a penalty of 2^20 could overflow int32
+    wl3 = _tiny_with_labels(np.zeros((270, 480), np.int32), 1)
+    run = Run(wl3, penalty=1 << 20)
+    run.volumes()
+    assert run.check() == ftv.FTV_ERR_OVERFLOW
+    run.close()
+
+
+def test_samples_above_bit_depth_are_reported():
+    wl = make_workload("tiny")
+    wl.bit_depth = 7
+    run = Run(wl)
+    run.volumes()
+    assert run.check() == ftv.FTV_ERR_INVALID_ARG
+    run.close()
+
+
+# ------------------------------------------------------------------------------------------ temporal
+
+def test_temporal_mask_and_adoption_bit_exact():
+    wl = make_workload("temporal", reduced=True)
+    run = Run(wl)
+    r = wl.ref_views[2]
+    lab, S = wl.labels(r)
+    labels = dev(lab)
+    frames = [run.planes(f)[r] for f in range(3)]
+    host = [wl.view(r, f) for f in range(3)]
+    for mode in (0, 1):
+        for cur, prev, ifr in [(1, 0, None), (2, 1, 0), (1, 1, None)]:
+            mask = torch.empty(S, dtype=torch.uint8, device="cuda")
+            changed = torch.empty(S, dtype=torch.int32, device="cuda")
+            n = torch.empty(1, dtype=torch.int32, device="cuda")
+            ftv.ftv_temporal_mask(run.ctx, 2, frames[cur], frames[prev], frames[ifr] if ifr is not None else None,
+                                  labels, S, 12, 4, mode, mask, changed, n)
+            assert run.check() == 0
+            m_ref, ch_ref, n_ref = oracle.temporal_mask(lab, S, host[cur], host[prev],
+                                                        host[ifr] if ifr is not None else None, 2, 12, 4, mode)
+            assert np.array_equal(mask.cpu().numpy(), m_ref)
+            assert int(n.item()) == n_ref
+            assert np.array_equal(changed.cpu().numpy()[:n_ref], ch_ref)
+    # masked WTA: listed (changed) segments get the argmin, others adopt
+    mask = torch.empty(S, dtype=torch.uint8, device="cuda")
+    changed = torch.empty(S, dtype=torch.int32, device="cuda")
+    n = torch.empty(1, dtype=torch.int32, device="cuda")
+    ftv.ftv_temporal_mask(run.ctx, 2, frames[1], frames[0], frames[0], labels, S, 12, 4, 0, mask, changed, n)
+    costs = run.volumes(frame=1, seg_lists=[changed if i == 2 else None for i in range(len(wl.ref_views))],
+                        n_listed=[n if i == 2 else None for i in range(len(wl.ref_views))], fill=0)
+    prev_l = dev(np.arange(S, dtype=np.uint16) % wl.n_labels)
+    ifr_l = dev((np.arange(S, dtype=np.uint16) * 3) % wl.n_labels)
+    out = torch.full((S,), 999, dtype=torch.int16, device="cuda")
+    ftv.ftv_wta_depth(run.ctx, 2, costs[2], S, out, mask=mask, prev_label=prev_l, iframe_label=ifr_l)
+    assert run.check() == 0
+    m_host = mask.cpu().numpy()
+    vol_ref = np.zeros((S, wl.n_labels), np.int32)
+    ch = changed.cpu().numpy()[: int(n.item())]
+    if len(ch):
+        vol_ref = oracle_runs.volume(wl, r, frame=1, seg_list=ch, out=vol_ref)
+    w_ref = oracle.wta(vol_ref, m_host, prev_l.cpu().numpy(), ifr_l.cpu().numpy())
+    assert np.array_equal(out.cpu().numpy().view(np.uint16), w_ref)
+    run.close()
+
+
+# ------------------------------------------------------------------------------------ full size, sampled
+
+@pytest.mark.parametrize("name", ["hd8", "uhd15"])
+def test_full_size_sampled_entries(name):
+    wl = make_workload(name)
+    run = Run(wl)
+    costs = run.volumes()
+    assert run.check() == 0
+    rng = np.random.default_rng(7)
+    for i, r in enumerate(wl.ref_views[:: 3 if name == "uhd15" else 2]):
+        idx = wl.ref_views.index(r)
+        S = run.S[idx]
+        seg = rng.integers(0, S, 24).astype(np.int32)
+        lab = rng.integers(0, wl.n_labels, 24).astype(np.int32)
+        got = costs[idx][torch.from_numpy(seg).long().cuda(), torch.from_numpy(lab).long().cuda()].cpu().numpy()
+        ref = oracle_runs.entries(wl, r, seg, lab)
+        assert np.array_equal(got, ref), (name, r, got, ref)
+        # the winner of sampled rows equals the argmin of the GPU's own full rows, checked on the host
+        win = torch.empty(S, dtype=torch.int16, device="cuda")
+        ftv.ftv_wta_depth(run.ctx, idx, costs[idx], S, win)
+        rows = costs[idx][torch.from_numpy(seg).long().cuda()].cpu().numpy()
+        assert np.array_equal(win.cpu().numpy().view(np.uint16)[seg], rows.argmin(1).astype(np.uint16))
+    run.close()

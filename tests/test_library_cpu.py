@@ -1,0 +1,89 @@
+"""CPU-side checks of the C-ABI library: it loads, exports what include/ftv.h declares, forms the same
+FP32 homography table as the oracle bit for bit, and rejects bad arguments before touching a device."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth.configs import make_workload
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ftv():
+    import __graft_entry__
+    __graft_entry__._load_builder().build()
+    import paper_1909_02294_gb300 as ftv
+    return ftv
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"FTV_API\s+[\w\s\*]+?\b(ftv_\w+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol(ftv):
+    names = _declared()
+    assert {"ftv_depth_init", "ftv_cost_volume", "ftv_temporal_mask", "ftv_wta_depth"} <= names
+    lib = ctypes.CDLL(ftv.ftv.LIB_PATH)
+    for n in sorted(names):
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+    assert set(ftv.ftv.EXPORTED) <= names
+
+
+@pytest.mark.parametrize("name,reduced", [("tiny", False), ("hd8", False), ("uhd15", False), ("uhd15", True),
+                                          ("serving_small", False)])
+def test_homography_table_bit_identical_to_oracle(ftv, name, reduced):
+    wl = make_workload(name, reduced=reduced)
+    for i, r in enumerate(wl.ref_views[:4]):
+        mine = ftv.ftv_compute_homographies(wl.cams, wl.ref_views, i, wl.n_labels, wl.z_near, wl.z_far)
+        ref = oracle.homography_table(wl.cams, r, wl.neighbours(r), wl.n_labels, wl.z_near, wl.z_far)
+        assert mine.shape == ref.shape
+        assert np.array_equal(mine.view(np.uint32), ref.view(np.uint32))
+
+
+def test_homography_table_centre_planes_and_neighbour_lists(ftv):
+    wl = make_workload("uhd15", reduced=True)
+    lists = [[1, 2], [6, 8, 0], [13]]
+    for i, r in enumerate(wl.ref_views):
+        mine = ftv.ftv_compute_homographies(wl.cams, wl.ref_views, i, 33, 0.8, 15.0, nbr_lists=lists,
+                                            plane_mode=ftv.FTV_PLANES_CENTRE, centre_view=7)
+        ref = oracle.homography_table(wl.cams, r, lists[i], 33, 0.8, 15.0, plane_mode=1, centre=7)
+        assert np.array_equal(mine.view(np.uint32), ref.view(np.uint32))
+
+
+def test_init_rejects_bad_arguments_before_any_device_call(ftv):
+    wl = make_workload("tiny")
+    good = dict(sample_bytes=1, bit_depth=8, max_segments=600)
+    bad_cases = [
+        dict(n_labels=0), dict(z_near=0.0), dict(z_far=0.4), dict(sample_bytes=3), dict(bit_depth=9),
+        dict(max_segments=0), dict(plane_mode=1, centre_view=7), dict(combine=5), dict(ref_views=[1, 1]),
+        dict(nbr_lists=[[1]]),
+    ]
+    for case in bad_cases:
+        kw = dict(good)
+        args = dict(cams=wl.cams, ref_views=[1], n_labels=64, z_near=0.5, z_far=10.0)
+        for k in list(case):
+            if k in args:
+                args[k] = case.pop(k)
+        kw.update(case)
+        with pytest.raises(ftv.FtvError) as e:
+            ftv.ftv_depth_init(args["cams"], args["ref_views"], args["n_labels"], args["z_near"], args["z_far"], **kw)
+        assert e.value.code == 1, case
+    bad_cam = synth.Camera(wl.cams[0].K.copy(), wl.cams[0].R, wl.cams[0].t, 480, 270)
+    bad_cam.K[2, 0] = 0.1
+    with pytest.raises(ftv.FtvError) as e:
+        ftv.ftv_depth_init([bad_cam] + wl.cams[1:], [1], 64, 0.5, 10.0, **good)
+    assert e.value.code == 1
+    assert ftv.ftv_status_str(4).startswith("segment cost")
