@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -151,7 +152,7 @@ ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out) {
     }
 
     // label blocking: N x LB x 9 homography floats must fit the kernel's shared-memory stage
-    int lb_max = std::min(kMaxLB, kHFloats / (9 * std::max(1, max_n)));
+    int lb_max = std::min(kMaxLB, kHEntries / std::max(1, max_n));
     lb_max = std::max(1, std::min(lb_max, c->L));
     c->nLB = (c->L + lb_max - 1) / lb_max;
     c->LB = (c->L + c->nLB - 1) / c->nLB;
@@ -167,7 +168,15 @@ ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out) {
                     free_ctx(c);
                     return FTV_ERR_INVALID_ARG;
                 }
-                for (int e = 0; e < 9; ++e) r.h_H[((size_t)k * c->L + d) * 9 + e] = (float)H[e];
+                for (int e = 0; e < 9; ++e) {
+                    const float f = (float)H[e];
+                    // the device's exact in-view test relies on |h| <= 2^100 (finite projections)
+                    if (!(std::fabs(f) <= 0x1p100f)) {
+                        free_ctx(c);
+                        return FTV_ERR_INVALID_ARG;
+                    }
+                    r.h_H[((size_t)k * c->L + d) * 9 + e] = f;
+                }
             }
     }
 

@@ -80,22 +80,32 @@ struct TexelOps<FMT_U16X4> {
     }
 };
 
-// Cost of one sample: reference pixel (x, y) through homography h into one neighbour view.
+// Staged per-(neighbour, label) entry: the FP32 homography and the neighbour's geometry, 48 bytes so
+// that a thread fetches it with three 128-bit shared loads.
+struct __align__(16) HEntry {
+    float h[9];
+    uint32_t w, h_, pitch;
+};
+
+// Cost of one sample: reference pixel (x, y) through homography e.h into one neighbour view.
+// Equivalent to the contract's float test (Wz > 0, 0 <= floor(u + 0.5) <= W - 1, ...): the host
+// guarantees |h| <= 2^100, so X and Y are finite; r = 1/Wz is then finite and positive exactly when
+// Wz > 0 and 1/Wz does not overflow (if it does, u is +-inf or NaN and the contract says "out");
+// with finite positive r, u + 0.5 is finite or +-inf, and floor-to-int with saturation followed by an
+// unsigned range test decides "in view" exactly as the float compares do.
 template <int FMT>
-__device__ __forceinline__ int sample_cost(const float (&h)[9], float x, float y, int a, int b, int c,
-                                           const void* tex, int pitch, float wm1, float hm1, int penalty) {
-    const float X = __fmaf_rn(h[0], x, __fmaf_rn(h[1], y, h[2]));
-    const float Yh = __fmaf_rn(h[3], x, __fmaf_rn(h[4], y, h[5]));
-    const float Wz = __fmaf_rn(h[6], x, __fmaf_rn(h[7], y, h[8]));
+__device__ __forceinline__ int sample_cost(const float4& a, const float4& b, const float4& c, float x, float y,
+                                           int ra, int rb, int rc, const void* tex, int penalty) {
+    const float X = __fmaf_rn(a.x, x, __fmaf_rn(a.y, y, a.z));
+    const float Yh = __fmaf_rn(a.w, x, __fmaf_rn(b.x, y, b.y));
+    const float Wz = __fmaf_rn(b.z, x, __fmaf_rn(b.w, y, c.x));
+    const float r = __frcp_rn(Wz);
+    const int ui = __float2int_rd(__fadd_rn(__fmul_rn(X, r), 0.5f));
+    const int vi = __float2int_rd(__fadd_rn(__fmul_rn(Yh, r), 0.5f));
+    const bool ok = ((unsigned)(__float_as_int(r) - 1) < 0x7f7fffffu) & ((unsigned)ui < __float_as_uint(c.y)) &
+                    ((unsigned)vi < __float_as_uint(c.z));
     int cst = penalty;
-    if (Wz > 0.0f) {
-        const float r = __frcp_rn(Wz);
-        const float fu = floorf(__fadd_rn(__fmul_rn(X, r), 0.5f));
-        const float fv = floorf(__fadd_rn(__fmul_rn(Yh, r), 0.5f));
-        if (fu >= 0.0f && fu <= wm1 && fv >= 0.0f && fv <= hm1) {
-            cst = TexelOps<FMT>::cost(tex, (int)fv * pitch + (int)fu, a, b, c);
-        }
-    }
+    if (ok) cst = TexelOps<FMT>::cost(tex, vi * (int)__float_as_uint(c.w) + ui, ra, rb, rc);
     return cst;
 }
 
@@ -120,10 +130,10 @@ __device__ __forceinline__ int upper_index(const int32_t* a, int lo, int hi, int
 }
 
 template <int FMT, int COMB>
-__global__ void __launch_bounds__(kThreads) cost_kernel(const RefJob* __restrict__ jobs, int n_jobs,
+__global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob* __restrict__ jobs, int n_jobs,
                                                         Plan* __restrict__ plan) {
-    __shared__ float sH[kHFloats];
-    __shared__ NbrView sNbr[FTV_MAX_NBRS];
+    __shared__ HEntry sH[kHEntries];
+    __shared__ const void* sBase[FTV_MAX_NBRS];
     __shared__ int sAcc[kSegAcc * kMaxLB];
     __shared__ int sWoffs[kLocCache + 1];
     __shared__ int s_item, s_k0, s_k1;
@@ -155,14 +165,21 @@ __global__ void __launch_bounds__(kThreads) cost_kernel(const RefJob* __restrict
         const int w0 = tile * kTile;
         const int w1 = min(w0 + kTile, n_rec);
 
-        // stage homographies [N][LBa][9] and neighbour geometry
+        // stage homographies and neighbour geometry: entry (n, l) for n < N, l < LBa
         const float* __restrict__ Hg = Jp->H;
-        const int nh = N * LBa * 9;
-        for (int i = tid; i < nh; i += kThreads) {
-            const int n = i / (LBa * 9), rem = i - n * (LBa * 9);
-            sH[i] = __ldg(&Hg[((int64_t)n * L + d0) * 9 + rem]);
+        const NbrView* __restrict__ nbrs = Jp->nbrs;
+        const int nh = N * LBa;
+        for (int i = tid; i < nh * 12; i += kThreads) {
+            const int e = i / 12, f = i - e * 12;
+            const int n = e / LBa, l = e - n * LBa;
+            uint32_t v;
+            if (f < 9) v = __float_as_uint(__ldg(&Hg[((int64_t)n * L + d0 + l) * 9 + f]));
+            else if (f == 9) v = (uint32_t)nbrs[n].w;
+            else if (f == 10) v = (uint32_t)nbrs[n].h;
+            else v = (uint32_t)nbrs[n].pitch;
+            reinterpret_cast<uint32_t*>(sH)[i] = v;
         }
-        for (int i = tid; i < N; i += kThreads) sNbr[i] = Jp->nbrs[i];
+        for (int i = tid; i < N; i += kThreads) sBase[i] = nbrs[i].texels;
         if (tid == 0) {
             s_k0 = upper_index(woffs, 0, n_work + 1, w0);
             s_k1 = upper_index(woffs, 0, n_work + 1, w1 - 1);
@@ -204,19 +221,13 @@ __global__ void __launch_bounds__(kThreads) cost_kernel(const RefJob* __restrict
 #pragma unroll
             for (int j = 0; j < kPPT; ++j) m[j] = (COMB == FTV_COMBINE_MIN && N > 0) ? INT_MAX : 0;
             for (int n = 0; n < N; ++n) {
-                float h[9];
-                const float* hs = &sH[(n * LBa + l) * 9];
-#pragma unroll
-                for (int e = 0; e < 9; ++e) h[e] = hs[e];
-                const NbrView nv = sNbr[n];
-                const float wm1 = (float)(nv.w - 1), hm1 = (float)(nv.h - 1);
+                const float4* e4 = reinterpret_cast<const float4*>(&sH[n * LBa + l]);
+                const float4 ha = e4[0], hb = e4[1], hc = e4[2];
+                const void* tex = sBase[n];
 #pragma unroll
                 for (int j = 0; j < kPPT; ++j) {
-                    if (key[j] != kSentinel) {
-                        const int c = sample_cost<FMT>(h, px[j], py[j], ra[j], rb[j], rc[j], nv.texels, nv.pitch,
-                                                       wm1, hm1, penalty);
-                        m[j] = (COMB == FTV_COMBINE_MIN) ? min(m[j], c) : m[j] + c;
-                    }
+                    const int c = sample_cost<FMT>(ha, hb, hc, px[j], py[j], ra[j], rb[j], rc[j], tex, penalty);
+                    m[j] = (COMB == FTV_COMBINE_MIN) ? min(m[j], c) : m[j] + c;
                 }
             }
             // segmented warp reduction: keys are nondecreasing along the lanes

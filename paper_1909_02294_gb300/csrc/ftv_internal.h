@@ -22,11 +22,21 @@ enum StatusBits : uint32_t { ST_BAD_LABEL = 1u, ST_BAD_SAMPLE = 2u, ST_OVERFLOW 
 
 // Cost-kernel tiling: each work item is one tile of kTile consecutive segment pixels (in listed-segment
 // order) times one block of consecutive labels. kThreads threads own kPPT pixels each.
-constexpr int kThreads = 256;
-constexpr int kPPT = 4;
+#ifndef FTV_THREADS
+#define FTV_THREADS 256
+#endif
+#ifndef FTV_PPT
+#define FTV_PPT 4
+#endif
+#ifndef FTV_MINB
+#define FTV_MINB 4
+#endif
+constexpr int kThreads = FTV_THREADS;
+constexpr int kPPT = FTV_PPT;
+constexpr int kMinBlocks = FTV_MINB;  // resident CTAs per SM the register budget is sized for
 constexpr int kTile = kThreads * kPPT;
 constexpr int kMaxLB = 64;          // labels per block
-constexpr int kHFloats = 4608;      // shared-memory capacity for N x LB x 9 homography floats
+constexpr int kHEntries = 512;      // shared-memory capacity for N x LB staged homographies
 constexpr int kSegAcc = 64;         // per-tile segment accumulators in shared memory
 
 // Geometry of a neighbour view as the cost kernel sees it.

@@ -14,7 +14,7 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libftv.so")
+LIB_PATH = os.environ.get("FTV_LIBRARY") or os.path.join(_HERE, "libftv.so")
 
 FTV_OK = 0
 FTV_ERR_INVALID_ARG, FTV_ERR_OUT_OF_MEMORY, FTV_ERR_CUDA, FTV_ERR_OVERFLOW = 1, 2, 3, 4

@@ -209,7 +209,8 @@ def test_invalid_labels_and_overflow_are_reported_not_trapped():
 
 def test_samples_above_bit_depth_are_reported():
     wl = make_workload("tiny")
-    wl.bit_depth = 7
+    wl.views()  # rendered with 8-bit samples ...
+    wl.bit_depth = 7  # ... then declared as 7-bit: samples above 127 must be reported
     run = Run(wl)
     run.volumes()
     assert run.check() == ftv.FTV_ERR_INVALID_ARG
