@@ -81,11 +81,25 @@ struct TexelOps<FMT_U16X4> {
 };
 
 // Staged per-(neighbour, label) entry: the FP32 homography and the neighbour's geometry, 48 bytes so
-// that a thread fetches it with three 128-bit shared loads.
+// that a thread fetches it with three 128-bit shared loads. `pm` holds the row pitch (low 28 bits)
+// and the entry's evaluation mode (high bits):
+//   kGeneral  projective homography, evaluated as written in the contract;
+//   kAffine   h6 == h7 == 0: Wz = fma(h6, x, fma(h7, y, h8)) is exactly h8 for every pixel, so
+//             r = 1/h8 is computed once at staging time and stored in place of h6;
+//   kUnit     affine with r == 1: u = X * 1 is exactly X, the multiplications are skipped;
+//   kOut      affine with 1/h8 not finite and positive: every sample is out of view.
+// All four give bit-identical results to the general sequence; they only skip work whose result is
+// known exactly.
 struct __align__(16) HEntry {
     float h[9];
-    uint32_t w, h_, pitch;
+    uint32_t w, h_, pm;
 };
+enum : uint32_t { kGeneral = 0, kAffine = 1, kUnit = 2, kOut = 3 };
+constexpr uint32_t kPitchMask = (1u << 28) - 1u;
+
+__device__ __forceinline__ bool finite_positive(float r) {
+    return (unsigned)(__float_as_int(r) - 1) < 0x7f7fffffu;
+}
 
 // Cost of one sample: reference pixel (x, y) through homography e.h into one neighbour view.
 // Equivalent to the contract's float test (Wz > 0, 0 <= floor(u + 0.5) <= W - 1, ...): the host
@@ -94,18 +108,34 @@ struct __align__(16) HEntry {
 // with finite positive r, u + 0.5 is finite or +-inf, and floor-to-int with saturation followed by an
 // unsigned range test decides "in view" exactly as the float compares do.
 template <int FMT>
-__device__ __forceinline__ int sample_cost(const float4& a, const float4& b, const float4& c, float x, float y,
-                                           int ra, int rb, int rc, const void* tex, int penalty) {
+__device__ __forceinline__ int sample_cost(const float4& a, const float4& b, const float4& c, int pitch, float x,
+                                           float y, int ra, int rb, int rc, const void* tex, int penalty) {
     const float X = __fmaf_rn(a.x, x, __fmaf_rn(a.y, y, a.z));
     const float Yh = __fmaf_rn(a.w, x, __fmaf_rn(b.x, y, b.y));
     const float Wz = __fmaf_rn(b.z, x, __fmaf_rn(b.w, y, c.x));
     const float r = __frcp_rn(Wz);
     const int ui = __float2int_rd(__fadd_rn(__fmul_rn(X, r), 0.5f));
     const int vi = __float2int_rd(__fadd_rn(__fmul_rn(Yh, r), 0.5f));
-    const bool ok = ((unsigned)(__float_as_int(r) - 1) < 0x7f7fffffu) & ((unsigned)ui < __float_as_uint(c.y)) &
-                    ((unsigned)vi < __float_as_uint(c.z));
+    const bool ok = finite_positive(r) & ((unsigned)ui < __float_as_uint(c.y)) & ((unsigned)vi < __float_as_uint(c.z));
     int cst = penalty;
-    if (ok) cst = TexelOps<FMT>::cost(tex, vi * (int)__float_as_uint(c.w) + ui, ra, rb, rc);
+    if (ok) cst = TexelOps<FMT>::cost(tex, vi * pitch + ui, ra, rb, rc);
+    return cst;
+}
+
+// Affine entries: r (finite, positive) was hoisted out of the pixel loop; UNIT means r == 1.
+template <int FMT, bool UNIT>
+__device__ __forceinline__ int sample_cost_affine(const float4& a, const float4& b, const float4& c, float r,
+                                                  int pitch, float x, float y, int ra, int rb, int rc,
+                                                  const void* tex, int penalty) {
+    const float X = __fmaf_rn(a.x, x, __fmaf_rn(a.y, y, a.z));
+    const float Yh = __fmaf_rn(a.w, x, __fmaf_rn(b.x, y, b.y));
+    const float u = UNIT ? X : __fmul_rn(X, r);
+    const float v = UNIT ? Yh : __fmul_rn(Yh, r);
+    const int ui = __float2int_rd(__fadd_rn(u, 0.5f));
+    const int vi = __float2int_rd(__fadd_rn(v, 0.5f));
+    const bool ok = ((unsigned)ui < __float_as_uint(c.y)) & ((unsigned)vi < __float_as_uint(c.z));
+    int cst = penalty;
+    if (ok) cst = TexelOps<FMT>::cost(tex, vi * pitch + ui, ra, rb, rc);
     return cst;
 }
 
@@ -169,15 +199,21 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
         const float* __restrict__ Hg = Jp->H;
         const NbrView* __restrict__ nbrs = Jp->nbrs;
         const int nh = N * LBa;
-        for (int i = tid; i < nh * 12; i += kThreads) {
-            const int e = i / 12, f = i - e * 12;
+        for (int e = tid; e < nh; e += kThreads) {
             const int n = e / LBa, l = e - n * LBa;
-            uint32_t v;
-            if (f < 9) v = __float_as_uint(__ldg(&Hg[((int64_t)n * L + d0 + l) * 9 + f]));
-            else if (f == 9) v = (uint32_t)nbrs[n].w;
-            else if (f == 10) v = (uint32_t)nbrs[n].h;
-            else v = (uint32_t)nbrs[n].pitch;
-            reinterpret_cast<uint32_t*>(sH)[i] = v;
+            const float* src = &Hg[((int64_t)n * L + d0 + l) * 9];
+            HEntry& E = sH[e];
+#pragma unroll
+            for (int f = 0; f < 9; ++f) E.h[f] = __ldg(&src[f]);
+            uint32_t mode = kGeneral;
+            if (E.h[6] == 0.0f && E.h[7] == 0.0f) {
+                const float r = __frcp_rn(E.h[8]);
+                mode = !finite_positive(r) ? kOut : (r == 1.0f ? kUnit : kAffine);
+                E.h[6] = r;
+            }
+            E.w = (uint32_t)nbrs[n].w;
+            E.h_ = (uint32_t)nbrs[n].h;
+            E.pm = (uint32_t)nbrs[n].pitch | (mode << 28);
         }
         for (int i = tid; i < N; i += kThreads) sBase[i] = nbrs[i].texels;
         if (tid == 0) {
@@ -224,10 +260,33 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                 const float4* e4 = reinterpret_cast<const float4*>(&sH[n * LBa + l]);
                 const float4 ha = e4[0], hb = e4[1], hc = e4[2];
                 const void* tex = sBase[n];
+                const uint32_t pm = __float_as_uint(hc.w);
+                const uint32_t mode = pm >> 28;
+                const int pitch = (int)(pm & kPitchMask);
+                if (mode == kGeneral) {
 #pragma unroll
-                for (int j = 0; j < kPPT; ++j) {
-                    const int c = sample_cost<FMT>(ha, hb, hc, px[j], py[j], ra[j], rb[j], rc[j], tex, penalty);
-                    m[j] = (COMB == FTV_COMBINE_MIN) ? min(m[j], c) : m[j] + c;
+                    for (int j = 0; j < kPPT; ++j) {
+                        const int c = sample_cost<FMT>(ha, hb, hc, pitch, px[j], py[j], ra[j], rb[j], rc[j], tex,
+                                                       penalty);
+                        m[j] = (COMB == FTV_COMBINE_MIN) ? min(m[j], c) : m[j] + c;
+                    }
+                } else if (mode == kUnit) {
+#pragma unroll
+                    for (int j = 0; j < kPPT; ++j) {
+                        const int c = sample_cost_affine<FMT, true>(ha, hb, hc, 1.0f, pitch, px[j], py[j], ra[j],
+                                                                    rb[j], rc[j], tex, penalty);
+                        m[j] = (COMB == FTV_COMBINE_MIN) ? min(m[j], c) : m[j] + c;
+                    }
+                } else if (mode == kAffine) {
+#pragma unroll
+                    for (int j = 0; j < kPPT; ++j) {
+                        const int c = sample_cost_affine<FMT, false>(ha, hb, hc, hb.z, pitch, px[j], py[j], ra[j],
+                                                                     rb[j], rc[j], tex, penalty);
+                        m[j] = (COMB == FTV_COMBINE_MIN) ? min(m[j], c) : m[j] + c;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < kPPT; ++j) m[j] = (COMB == FTV_COMBINE_MIN) ? min(m[j], penalty) : m[j] + penalty;
                 }
             }
             // segmented warp reduction: keys are nondecreasing along the lanes

@@ -107,6 +107,29 @@ def test_centre_planes_and_nearest_neighbour_views():
     run.close()
 
 
+def test_affine_and_out_of_view_homography_modes():
+    """Cameras displaced along the optical axis give homographies with h6 = h7 = 0 and h8 != 1 (and
+    h8 <= 0 for candidate planes behind the displaced camera): the kernel's affine and all-out paths."""
+    wl = make_workload("tiny")
+    base = wl.cams[1]
+    for C in ([0.0, 0.0, 0.3], [0.02, 0.0, 1.0]):
+        R = np.eye(3)
+        wl.cams.append(synth.Camera(base.K.copy(), R, -R @ np.array(C), base.width, base.height))
+    wl.nbr_views = {1: [0, 3, 4]}
+    run = Run(wl, nbr_lists=[[0, 3, 4]])
+    for combine in ("min", "sum"):
+        run.close()
+        run = Run(wl, nbr_lists=[[0, 3, 4]], combine=combine)
+        costs = run.volumes()
+        assert run.check() == 0
+        ref = _oracle_all(wl, combine=combine, nbr_lists=[[0, 3, 4]])
+        _assert_equal(costs[0], ref[0], f"affine modes ({combine})")
+    H = oracle.homography_table(wl.cams, 1, [3, 4], wl.n_labels, wl.z_near, wl.z_far)
+    assert np.all(H[:, :, 6] == 0) and np.all(H[:, :, 7] == 0)
+    assert np.any(H[0, :, 8] != 1.0) and np.any(H[1, :, 8] <= 0) and np.any(H[1, :, 8] > 0)
+    run.close()
+
+
 def test_listed_segments_leave_other_rows_untouched():
     wl = make_workload("hd8", reduced=True)
     run = Run(wl)
