@@ -166,9 +166,9 @@ def run_reference(args, rank):
     if rank != 0:
         return
     import synth
-    wl = synth.make_workload(WORKLOAD)
-    _ = cpu_baseline(wl, budget_s=2.0)  # warm caches / size the sample
-    rate, desc, k = cpu_baseline(wl, budget_s=8.0)
+    wl = synth.make_workload(args.workload)
+    per_step = max(0.5, min(8.0, 90.0 / (args.steps + args.warmup)))  # whole run within a few minutes
+    rate, desc, k = cpu_baseline(wl, budget_s=per_step)
     times, evals = [], 0
     import oracle
     lab_cache = {}
@@ -209,6 +209,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="synthetic workload (default: the 1920x1080 8-view configuration; others for profiling)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -228,7 +230,7 @@ def main():
     import paper_1909_02294_gb300 as ftv
     import synth
 
-    wl = synth.make_workload(WORKLOAD)
+    wl = synth.make_workload(args.workload)
     dev = torch.device("cuda", local)
     R, L = len(wl.ref_views), wl.n_labels
     S = [wl.labels(r)[1] for r in wl.ref_views]
@@ -321,7 +323,7 @@ def main():
         ev_bytes, comp_bytes = algorithmic_bytes(wl)
         kms = statistics.mean(kernel_ms)
         achieved = (ev_bytes + comp_bytes) / (kms / 1000.0) / 1e9
-        traffic = _traffic_for_current_kernel(WORKLOAD)
+        traffic = _traffic_for_current_kernel(args.workload)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,

@@ -214,6 +214,8 @@ def make_workload(name: str, reduced: bool = False, painted: bool = False) -> Wo
         if reduced:
             return _hd8(seed, W=244, H=138, f=190.0, L=40, name="hd8_reduced")
         return _hd8(seed)
+    if name == "uhd15_half":  # the uhd15 rig and scene at 1920x1080 (profiling-sized)
+        return _uhd15(BASE_SEED + 2, W=1920, H=1080, f=1500.0, cell=13, name="uhd15_half")
     if name == "uhd15":
         if reduced:
             return _uhd15(seed, W=390, H=218, f=304.0, L=48, refs=[0, 7, 14], cell=7, name="uhd15_reduced")
