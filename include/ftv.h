@@ -204,6 +204,33 @@ FTV_API ftv_status ftv_temporal_mask(ftv_ctx* ctx, int32_t ref_index, const void
                                      int32_t* d_n_changed, ftv_stream stream);
 
 /*
+ * ftv_temporal_mask_static - the temporal test of ftv_temporal_mask without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that cannot call cudaMalloc,
+ * e.g. a process whose device memory is fully reserved up front under a fixed budget, or a
+ * latency-critical loop that must not take cudaMalloc's implicit device-wide synchronisation. It needs
+ * no ftv_ctx (creating one allocates): the caller passes the geometry (width, height, sample_bytes of
+ * the frames and label map) plus the same inputs and outputs as ftv_temporal_mask, and gets the same
+ * results. Device-found errors (a label outside [0, n_segments)) are OR-ed into *d_status when
+ * d_status (a caller-owned device word) is not NULL; such pixels are left out.
+ *
+ * Scratch: the per-segment accumulators live in one statically sized device array inside this library
+ * (FTV_STATIC_MAX_SEGMENTS x 64 bytes = 4 MiB), which every GPU that loads the library holds until the
+ * process exits. n_segments above FTV_STATIC_MAX_SEGMENTS is rejected with FTV_ERR_INVALID_ARG.
+ * The first call on a device looks up the array's device address (once per device, with that device
+ * current); make that first call before any stream capture. Every call on a device shares the same
+ * array and clears it on its stream before use: calls whose work overlaps on the GPU (different
+ * streams without ordering between them) race and give wrong results. Asynchronous on `stream`.
+ */
+#define FTV_STATIC_MAX_SEGMENTS 65536
+FTV_API ftv_status ftv_temporal_mask_static(int32_t width, int32_t height, int32_t sample_bytes,
+                                            const void* const* d_cur, const int64_t* cur_pitch,
+                                            const void* const* d_prev, const int64_t* prev_pitch,
+                                            const void* const* d_iframe, const int64_t* iframe_pitch,
+                                            const int32_t* d_labels, int32_t n_segments, int32_t t_p, int32_t t_i,
+                                            int32_t mode, uint8_t* d_mask, int32_t* d_changed_list,
+                                            int32_t* d_n_changed, uint32_t* d_status, ftv_stream stream);
+
+/*
  * Winner-take-all readout of one cost volume d_cost [n_segments][n_labels]: d_label_out[s] = the label
  * of least cost, the smallest such label on ties. With d_mask (from ftv_temporal_mask), segments
  * marked FTV_MASK_REUSE_P take d_prev_label[s] and FTV_MASK_REUSE_I take d_iframe_label[s]

@@ -67,6 +67,8 @@ def _load() -> ctypes.CDLL:
         "ftv_wta_depth": [vp, i32, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp],
         "ftv_check": [vp, vp],
         "ftv_set_profiling": [vp, i32],
+        "ftv_temporal_mask_static": [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp,
+                                     vp],
         "ftv_last_kernel_ms": [vp, vp],
     }
     for name, args in sig.items():
@@ -85,7 +87,7 @@ lib = _load()
 EXPORTED = ["ftv_depth_init", "ftv_depth_destroy", "ftv_compute_homographies", "ftv_get_homographies", "ftv_get_neighbours",
             "ftv_get_label_depths", "ftv_segment_index", "ftv_cost_volume", "ftv_temporal_mask",
             "ftv_wta_depth", "ftv_check", "ftv_launch_count", "ftv_status_str", "ftv_set_profiling",
-            "ftv_last_kernel_ms"]
+            "ftv_last_kernel_ms", "ftv_temporal_mask_static"]
 
 
 def _ok(code: int, where: str) -> None:
@@ -294,3 +296,19 @@ def ftv_last_kernel_ms(ctx: Context) -> float:
     ms = ctypes.c_float()
     _ok(lib.ftv_last_kernel_ms(ctx.handle, ctypes.byref(ms)), "ftv_last_kernel_ms")
     return float(ms.value)
+
+
+FTV_STATIC_MAX_SEGMENTS = 65536
+
+
+def ftv_temporal_mask_static(width: int, height: int, sample_bytes: int, cur, prev, iframe, labels, n_segments: int,
+                             t_p: int, t_i: int, mode: int, mask, changed_list, n_changed, status=None,
+                             stream=None) -> None:
+    """The temporal test without a context and without any device allocation (statically sized scratch
+    inside the library, at most FTV_STATIC_MAX_SEGMENTS segments)."""
+    cp, cpi = _trip(cur)
+    pp, ppi = _trip(prev)
+    ip, ipi = _trip(iframe)
+    _ok(lib.ftv_temporal_mask_static(width, height, sample_bytes, cp, cpi, pp, ppi, ip, ipi, _ptr(labels), n_segments,
+                                     t_p, t_i, mode, _ptr(mask), _ptr(changed_list), _ptr(n_changed), _ptr(status),
+                                     _stream(stream)), "ftv_temporal_mask_static")
