@@ -136,6 +136,20 @@ def algorithmic_bytes(wl) -> tuple[int, int]:
     return evals * 3 * sb, comp
 
 
+# Operations the cost contract performs per pixel x label x neighbour evaluation (the kernel may skip
+# some of them when their result is known exactly): 6 FMA (projection), 1 reciprocal, 2 multiplies,
+# 2 adds (+0.5), 2 floors, 5 compares (Wz > 0 and the two-sided range tests), 1 address multiply-add,
+# 1 gather, 8 for |dY|+|dCb|+|dCr| (3 subtracts, 3 absolute values, 2 adds), 1 min over views.
+OPS_PER_EVAL = 29
+# ... plus one add per pixel x label for the segment sum.
+OPS_PER_PIXEL_LABEL = 1
+
+
+def algorithmic_ops(wl) -> int:
+    px_labels = sum(wl.cams[r].width * wl.cams[r].height * wl.n_labels for r in wl.ref_views)
+    return wl.evaluations() * OPS_PER_EVAL + px_labels * OPS_PER_PIXEL_LABEL
+
+
 def cpu_baseline(wl, budget_s: float = 12.0, min_rows: int = 4):
     """Time the oracle as it stands on the first k segments of reference 0 (whole label rows), k chosen
     so the run takes about budget_s seconds. Returns (evals/s, sample description)."""
@@ -324,6 +338,11 @@ def main():
         kms = statistics.mean(kernel_ms)
         achieved = (ev_bytes + comp_bytes) / (kms / 1000.0) / 1e9
         traffic = _traffic_for_current_kernel(args.workload)
+        clk = clocks.summary()
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        sm_mhz = clk["sm_mhz"] if clk else 2070.0
+        alu_peak = n_sm * 128 * sm_mhz * 1e6 / 1e12  # lane operations per second, Tops/s
+        alu_achieved = algorithmic_ops(wl) / (kms / 1000.0) / 1e12
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
@@ -332,13 +351,19 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "depth_maps_per_s": world * R * args.steps / total_s,
                        "cost_kernel_ms": kms, "evaluations_per_step": evals},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "algorithmic_bytes_per_launch": ev_bytes + comp_bytes,
+            "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Tops/s",
+                         "frac": alu_achieved / alu_peak, "traffic": traffic,
+                         "peak_kind": f"{n_sm} SMs x 128 lanes x {sm_mhz:.0f} MHz (median sampled SM clock)",
+                         "algorithmic_ops_per_launch": algorithmic_ops(wl), "ops_per_evaluation": OPS_PER_EVAL,
                          "kernel": "cost_kernel<FMT_P10, MIN>"},
+            "hbm_roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "peak_kind": peak_kind,
+                             "algorithmic_bytes_per_launch": ev_bytes + comp_bytes,
+                             "definition": "one 3-sample texel (3 x sample bytes) per evaluation + compulsory "
+                                           "streams, over the cost kernel's event-timed duration"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
-            "clocks": clocks.summary(),
+            "clocks": clk,
         }
         if world == 1 and not args.no_cpu_baseline:
             rate, desc, _ = cpu_baseline(wl)
