@@ -244,6 +244,75 @@ FTV_API ftv_status ftv_wta_depth(ftv_ctx* ctx, int32_t ref_index, const int32_t*
                                  const int32_t* d_n_listed, uint16_t* d_label_out, const int32_t* d_labels_pix,
                                  float* d_depth_map, ftv_stream stream);
 
+/* ------------------------------------------------------------------ batched and served forms -----
+ * A camera stream is one ftv_ctx with resident state (ftv_stream_init): its static label maps and
+ * segment indexes, a ring of three packed frames (current, previous P, I) and per-segment labels of
+ * the previous and the I frame (Sec. III-E: I-type and P-type depth frames). A batch runs one frame
+ * of each of many streams (any mix of shapes, view, segment and label counts that share sample
+ * format and combination rule) as one fixed launch sequence: pack, temporal test, one persistent cost
+ * kernel over the flat (job, reference, tile, label block) queue, winner-take-all with adoption. */
+
+enum { FTV_FRAME_I = 0, FTV_FRAME_P = 1 };
+typedef struct ftv_batch ftv_batch;
+
+/* One frame of one stream. d_planes/pitch_bytes as in ftv_cost_volume (3 entries per view, host
+ * arrays of device pointers); frame_type FTV_FRAME_I (every segment is estimated; the frame becomes the
+ * stream's I frame) or FTV_FRAME_P (only segments that fail the temporal test are estimated; the others
+ * adopt the previous or the I frame's label). d_label_out[r] (optional, uint16 [S_r]) receives the
+ * labels; d_depth_out[r] (optional, float [H][W]) the per-pixel depth; either array may be NULL. */
+typedef struct ftv_frame_job {
+    ftv_ctx* ctx;
+    const void* const* d_planes;
+    const int64_t* pitch_bytes;
+    int32_t frame_type;
+    uint16_t* const* d_label_out;
+    float* const* d_depth_out;
+} ftv_frame_job;
+
+/* Make ctx a stream: copies the label maps d_labels[r] (int32 [H][W], n_segments[r] segments each, kept
+ * for the stream's life), builds their segment indexes and allocates the resident state. t_p, t_i,
+ * mode: the temporal test of ftv_temporal_mask. The first frame of a stream must be FTV_FRAME_I.
+ * Asynchronous on `stream` apart from the allocations. */
+FTV_API ftv_status ftv_stream_init(ftv_ctx* ctx, const int32_t* const* d_labels, const int32_t* n_segments,
+                                   int32_t t_p, int32_t t_i, int32_t mode, ftv_stream stream);
+
+/* Device bytes of a stream's resident state for segment counts n_segments[n_refs] (for admission by
+ * HBM footprint; the context's own scratch is allocated at ftv_depth_init). */
+FTV_API ftv_status ftv_stream_footprint(const ftv_ctx* ctx, const int32_t* n_segments, int64_t* bytes);
+
+/* Device pointer to a stream's current per-segment labels of reference ref_index (uint16 [S]). */
+FTV_API ftv_status ftv_stream_labels(const ftv_ctx* ctx, int32_t ref_index, const uint16_t** d_labels_out);
+
+/* A batch executor with room for max_jobs frames, max_units (job, reference) units (<= 240) and
+ * max_views views in total; owns a device descriptor block and a pinned staging copy of it. */
+FTV_API ftv_status ftv_batch_create(int32_t max_jobs, int32_t max_units, int32_t max_views, ftv_batch** out);
+FTV_API ftv_status ftv_batch_destroy(ftv_batch* b);
+
+/* Host side of one batch: validates the jobs (one frame per stream, same sample format and combination
+ * rule, capacity), writes their descriptors into the pinned staging block and advances each stream's
+ * ring. Must be followed by exactly one ftv_batch_launch or ftv_batch_replay. Returns FTV_ERR_BUSY
+ * while the previous launch of this batch object is still pending (the staging block is in use).
+ * A stream may have at most one frame in flight: submit its next frame after this batch completes. */
+FTV_API ftv_status ftv_batch_prepare(ftv_batch* b, const ftv_frame_job* jobs, int32_t n_jobs);
+
+/* Enqueue the prepared batch on `stream` (one H2D copy of the descriptor block + 9 kernels). */
+FTV_API ftv_status ftv_batch_launch(ftv_batch* b, ftv_stream stream);
+
+/* Same work as ftv_batch_launch through a CUDA graph of the launch sequence, captured on the first
+ * call (and again if the sample format or combination rule changes) and replayed afterwards: the
+ * descriptor block is re-read from the staging copy at every replay, so any batch composition
+ * within capacity replays the same graph. */
+FTV_API ftv_status ftv_batch_replay(ftv_batch* b, ftv_stream stream);
+
+/* Non-blocking completion test of the last launch: FTV_OK when done, FTV_ERR_BUSY while running. */
+FTV_API ftv_status ftv_batch_query(ftv_batch* b);
+
+/* Wait for the last launch; returns and clears device-found errors of the batch. */
+FTV_API ftv_status ftv_batch_wait(ftv_batch* b);
+
+/* Kernel launches this batch object has enqueued (for accounting). */
+FTV_API int64_t ftv_batch_launch_count(const ftv_batch* b);
+
 /* Wait for `stream`, then return and clear the context's device status word (FTV_OK if clean). */
 FTV_API ftv_status ftv_check(ftv_ctx* ctx, ftv_stream stream);
 

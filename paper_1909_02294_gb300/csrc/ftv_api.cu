@@ -41,6 +41,7 @@ cudaError_t dalloc(T** p, size_t count) {
 
 void free_ctx(ftv_ctx* c) {
     if (!c) return;
+    free_stream_state(c);
     for (auto& r : c->refs) {
         cudaFree(r.d_H);
         cudaFree(r.d_nbrs);
@@ -388,8 +389,7 @@ ftv_status ftv_cost_volume(ftv_ctx* ctx, const void* const* d_planes, const int6
     }
     if (e == cudaSuccess && ctx->profiling) e = cudaEventRecord(ctx->ev_start, s);
     if (e == cudaSuccess) {
-        e = launch_cost(ctx->d_jobs, ctx->n_refs, ctx->d_plan, ctx->fmt, ctx->combine,
-                        ctx->n_sm * ctx->cost_blocks_per_sm, s);
+        e = launch_cost(ctx->d_jobs, ctx->d_plan, ctx->fmt, ctx->combine, ctx->n_sm * ctx->cost_blocks_per_sm, s);
         ctx->launches++;
     }
     if (e == cudaSuccess && ctx->profiling) {

@@ -1,0 +1,813 @@
+// Batched and served forms: per-stream resident state and one launch sequence for many jobs.
+//
+// Paper: Sec. III-E keeps an I-type and the preceding P-type depth frame per view and re-estimates only
+// segments whose colour changed. Here every camera stream keeps that state on the device (a ring of
+// three packed frames: current, previous P, I; per-segment labels of the previous and the I frame), and
+// a batch runs the whole hot path for many jobs (frames of different streams, shapes, view, segment and
+// label counts) with one fixed sequence of launches:
+//   H2D descriptor copy -> pack (all views of all jobs) -> temporal statistics -> masks + changed lists
+//   -> zero changed cost rows -> plan -> persistent cost kernel over the flat (job, reference, tile,
+//   label block) queue -> winner-take-all with adoption and label-state update -> optional depth maps.
+// Every kernel reads its work from the descriptor block and sizes its loop from it, with grids fixed
+// at creation, so one captured CUDA graph of the sequence replays for any batch composition (the host
+// rewrites the pinned descriptor block between replays).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ftv_internal.h"
+
+using namespace ftv;
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kStat = 8;
+
+struct PackTask {
+    const void* planes[3];
+    int64_t pitch[3];
+    void* out;
+    int32_t W, H, sb, fmt;
+    uint32_t maxv;
+    int32_t row_base;  // first row of this task in the flattened row space
+};
+
+struct TempUnit {
+    const void* cur;
+    const void* prev;
+    const void* ifr;
+    const int32_t* labels;
+    int64_t* stats;
+    uint8_t* mask;
+    int32_t* changed;
+    int32_t* n_changed;
+    int32_t W, H, S, t_p, t_i, nch, fmt, is_i;
+    int32_t row_base;   // rows of P-frame units, flattened (I-frame units have no rows)
+    int32_t stat_base;  // stats words of P-frame units, flattened
+};
+
+struct WtaUnit {
+    const int32_t* cost;
+    const uint8_t* mask;
+    uint16_t* prev_label;
+    uint16_t* i_label;
+    uint16_t* out;
+    const int32_t* labels;
+    float* depth;
+    const float* label_z;
+    int32_t S, L, W, H, is_i;
+    int32_t seg_base;    // segments, flattened
+    int32_t depth_base;  // rows of units with depth maps, flattened (units without depth own no rows)
+};
+
+struct Header {
+    int32_t n_pack, n_units, fmt, combine;
+    int32_t pack_rows, temp_rows, temp_stats, wta_segs, depth_rows, pad[3];
+};
+
+struct BatchLayout {
+    size_t header, pack, temp, jobs, wta, total;
+};
+
+BatchLayout layout(int max_views, int max_units) {
+    BatchLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += (bytes + 255) & ~(size_t)255;
+        return at;
+    };
+    L.header = take(sizeof(Header));
+    L.pack = take(sizeof(PackTask) * max_views);
+    L.temp = take(sizeof(TempUnit) * max_units);
+    L.jobs = take(sizeof(RefJob) * max_units);
+    L.wta = take(sizeof(WtaUnit) * max_units);
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ int find_base(const int32_t* base_field_of, int stride_bytes, int n, int v) {
+    // largest i in [0, n) with base(i) <= v, where base(i) is an int at byte offset i * stride
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int b = *reinterpret_cast<const int32_t*>(reinterpret_cast<const char*>(base_field_of) +
+                                                         (size_t)mid * stride_bytes);
+        if (b <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// --------------------------------------------------------------------------------------------- pack
+
+__device__ __forceinline__ uint32_t load_plane(const void* plane, int64_t pitch, int sb, int x, int y) {
+    const char* row = static_cast<const char*>(plane) + (int64_t)y * pitch;
+    return sb == 1 ? (uint32_t)reinterpret_cast<const uint8_t*>(row)[x] : (uint32_t)reinterpret_cast<const uint16_t*>(row)[x];
+}
+
+__global__ void pack_multi_kernel(const Header* __restrict__ hdr, const PackTask* __restrict__ tasks, uint32_t* status) {
+    const int rows = hdr->pack_rows, n = hdr->n_pack;
+    for (int g = blockIdx.x; g < rows; g += gridDim.x) {
+        const int t = find_base(&tasks[0].row_base, sizeof(PackTask), n, g);
+        const PackTask& T = tasks[t];
+        const int y = g - T.row_base;
+        for (int x = threadIdx.x; x < T.W; x += blockDim.x) {
+            uint32_t a = load_plane(T.planes[0], T.pitch[0], T.sb, x, y);
+            uint32_t b = load_plane(T.planes[1], T.pitch[1], T.sb, x, y);
+            uint32_t c = load_plane(T.planes[2], T.pitch[2], T.sb, x, y);
+            if (a > T.maxv || b > T.maxv || c > T.maxv) {
+                atomicOr(status, ST_BAD_SAMPLE);
+                a = min(a, T.maxv);
+                b = min(b, T.maxv);
+                c = min(c, T.maxv);
+            }
+            const int64_t i = (int64_t)y * T.W + x;
+            if (T.fmt == FMT_U8X4) static_cast<uint32_t*>(T.out)[i] = a | (b << 8) | (c << 16);
+            else if (T.fmt == FMT_P10) static_cast<uint32_t*>(T.out)[i] = a | (b << 10) | (c << 20);
+            else static_cast<uint2*>(T.out)[i] = make_uint2(a | (b << 16), c);
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------------------- temporal
+
+__device__ __forceinline__ void texel_fields(const void* base, int fmt, int64_t i, int* v) {
+    if (fmt == FMT_U16X4) {
+        const uint2 t = static_cast<const uint2*>(base)[i];
+        v[0] = t.x & 0xffff;
+        v[1] = t.x >> 16;
+        v[2] = t.y;
+    } else {
+        const uint32_t t = static_cast<const uint32_t*>(base)[i];
+        const int sh = fmt == FMT_P10 ? 10 : 8;
+        const uint32_t m = (1u << sh) - 1u;
+        v[0] = t & m;
+        v[1] = (t >> sh) & m;
+        v[2] = t >> (2 * sh);
+    }
+}
+
+__global__ void temporal_zero_multi_kernel(const Header* __restrict__ hdr, const TempUnit* __restrict__ units) {
+    const int total = hdr->temp_stats, n = hdr->n_units;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+        const int u = find_base(&units[0].stat_base, sizeof(TempUnit), n, g);
+        units[u].stats[g - units[u].stat_base] = 0;
+    }
+}
+
+// Per-segment sums of cur - prev and cur - I (rows of P-frame units flattened; one block per row at a
+// time). Lanes with the same label are reduced in the warp first.
+__global__ void temporal_accumulate_multi_kernel(const Header* __restrict__ hdr, const TempUnit* __restrict__ units,
+                                                 uint32_t* status) {
+    const int rows = hdr->temp_rows, n = hdr->n_units;
+    const int lane = threadIdx.x & 31;
+    for (int g = blockIdx.x; g < rows; g += gridDim.x) {
+        const int u = find_base(&units[0].row_base, sizeof(TempUnit), n, g);
+        const TempUnit& T = units[u];
+        const int y = g - T.row_base;
+        for (int x0 = 0; x0 < T.W; x0 += blockDim.x) {
+            const int x = x0 + threadIdx.x;
+            const bool in = x < T.W;
+            const int l = in ? T.labels[(int64_t)y * T.W + x] : -1;
+            const bool ok = in && (unsigned)l < (unsigned)T.S;
+            if (in && !ok) atomicOr(status, ST_BAD_LABEL);
+            int dp[3] = {0, 0, 0}, di[3] = {0, 0, 0};
+            if (ok) {
+                int a[3], b[3], c[3];
+                const int64_t i = (int64_t)y * T.W + x;
+                texel_fields(T.cur, T.fmt, i, a);
+                texel_fields(T.prev, T.fmt, i, b);
+                texel_fields(T.ifr, T.fmt, i, c);
+                for (int k = 0; k < 3; ++k) {
+                    dp[k] = k < T.nch ? a[k] - b[k] : 0;
+                    di[k] = k < T.nch ? a[k] - c[k] : 0;
+                }
+            }
+            const int key = ok ? l : -1;
+            unsigned rem = __ballot_sync(kFull, ok);
+            while (rem) {
+                const int leader = __ffs(rem) - 1;
+                const int kk = __shfl_sync(kFull, key, leader);
+                const bool mine = key == kk;
+                const unsigned grp = __ballot_sync(kFull, mine);
+                int sums[7];
+                sums[0] = __popc(grp);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    sums[1 + k] = __reduce_add_sync(kFull, mine ? dp[k] : 0);
+                    sums[4 + k] = __reduce_add_sync(kFull, mine ? di[k] : 0);
+                }
+                if (lane == leader) {
+                    unsigned long long* st = reinterpret_cast<unsigned long long*>(T.stats + (int64_t)kk * kStat);
+#pragma unroll
+                    for (int k = 0; k < 7; ++k)
+                        if (sums[k]) atomicAdd(&st[k], (unsigned long long)(long long)sums[k]);
+                }
+                rem &= ~grp;
+            }
+        }
+    }
+}
+
+__device__ int block_scan_1024(int v, int* total) {
+    __shared__ int warp_sums[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int s = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, s, o);
+            if (lane >= o) s += t;
+        }
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const int base = warp > 0 ? warp_sums[warp - 1] : 0;
+    *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return base + incl - v;
+}
+
+__device__ __forceinline__ int64_t iabs64(int64_t v) { return v < 0 ? -v : v; }
+
+// One block of 1024 threads per unit: masks and the ordered changed list. I-frame units list every
+// segment (Sec. III-E: all segments of an I-type frame are estimated).
+__global__ void temporal_finalize_multi_kernel(const Header* __restrict__ hdr, const TempUnit* __restrict__ units) {
+    for (int u = blockIdx.x; u < hdr->n_units; u += gridDim.x) {
+        const TempUnit& T = units[u];
+        const int S = T.S;
+        const int per = (S + blockDim.x - 1) / blockDim.x;
+        const int b = threadIdx.x * per, e = min(S, b + per);
+        int cnt = 0;
+        for (int s = b; s < e; ++s) {
+            int m = FTV_MASK_CHANGED;
+            if (!T.is_i) {
+                const int64_t* st = T.stats + (int64_t)s * kStat;
+                const int64_t n = st[0];
+                if (n > 0) {
+                    bool okp = true, oki = true;
+                    for (int c = 0; c < T.nch; ++c) {
+                        okp = okp && iabs64(st[1 + c]) < (int64_t)T.t_p * n;
+                        oki = oki && iabs64(st[4 + c]) < (int64_t)T.t_i * n;
+                    }
+                    m = okp ? FTV_MASK_REUSE_P : (oki ? FTV_MASK_REUSE_I : FTV_MASK_CHANGED);
+                }
+            }
+            T.mask[s] = (uint8_t)m;
+            cnt += m == FTV_MASK_CHANGED;
+        }
+        int total;
+        int run = block_scan_1024(cnt, &total);
+        for (int s = b; s < e; ++s)
+            if (T.mask[s] == FTV_MASK_CHANGED) T.changed[run++] = s;
+        if (threadIdx.x == 0) *T.n_changed = total;
+        __syncthreads();
+    }
+}
+
+// Zero the cost rows of each unit's changed segments (blockIdx.y = unit).
+__global__ void zero_changed_rows_kernel(const Header* __restrict__ hdr, const RefJob* __restrict__ jobs) {
+    for (int u = blockIdx.y; u < hdr->n_units; u += gridDim.y) {
+        const RefJob& J = jobs[u];
+        const int n = min(max(*J.n_listed, 0), J.S);
+        const int64_t total = (int64_t)n * J.L;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+            const int k = (int)(i / J.L), d = (int)(i - (int64_t)k * J.L);
+            const int s = J.list[k];
+            if ((unsigned)s < (unsigned)J.S) J.cost[(int64_t)s * J.L + d] = 0;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------ WTA etc.
+
+// One warp per segment over all units: argmin for changed segments (smallest label on ties), adoption
+// for reused ones; the result updates the stream's label state and is copied to the caller's output.
+__global__ void wta_multi_kernel(const Header* __restrict__ hdr, const WtaUnit* __restrict__ units) {
+    const int lane = threadIdx.x & 31;
+    const int total = hdr->wta_segs, n = hdr->n_units;
+    for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < total; g += (gridDim.x * blockDim.x) >> 5) {
+        const int u = find_base(&units[0].seg_base, sizeof(WtaUnit), n, g);
+        const WtaUnit& T = units[u];
+        const int s = g - T.seg_base;
+        const int m = T.mask[s];
+        uint16_t label;
+        if (m == FTV_MASK_REUSE_P) {
+            label = T.prev_label[s];
+        } else if (m == FTV_MASK_REUSE_I) {
+            label = T.i_label[s];
+        } else {
+            unsigned long long best = ~0ull;
+            const int32_t* row = T.cost + (int64_t)s * T.L;
+            for (int d = lane; d < T.L; d += 32) {
+                const unsigned long long k = ((unsigned long long)((uint32_t)row[d] ^ 0x80000000u) << 32) | (unsigned)d;
+                best = k < best ? k : best;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long t = __shfl_xor_sync(kFull, best, o);
+                best = t < best ? t : best;
+            }
+            label = (uint16_t)(best & 0xffffu);
+        }
+        if (lane == 0) {
+            T.prev_label[s] = label;
+            if (T.is_i) T.i_label[s] = label;
+            if (T.out) T.out[s] = label;
+        }
+    }
+}
+
+__global__ void depth_multi_kernel(const Header* __restrict__ hdr, const WtaUnit* __restrict__ units, uint32_t* status) {
+    const int rows = hdr->depth_rows, n = hdr->n_units;
+    for (int g = blockIdx.x; g < rows; g += gridDim.x) {
+        const int u = find_base(&units[0].depth_base, sizeof(WtaUnit), n, g);
+        const WtaUnit& T = units[u];
+        const int y = g - T.depth_base;
+        for (int x = threadIdx.x; x < T.W; x += blockDim.x) {
+            const int64_t p = (int64_t)y * T.W + x;
+            const int s = T.labels[p];
+            float z = 0.0f;
+            if ((unsigned)s < (unsigned)T.S && T.prev_label[s] < T.L) z = T.label_z[T.prev_label[s]];
+            else atomicOr(status, ST_BAD_LABEL);
+            T.depth[p] = z;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+    return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (count ? count : 1));
+}
+
+}  // namespace
+
+struct ftv_batch {
+    int device = 0;
+    int n_sm = 0;
+    int32_t max_jobs = 0, max_units = 0, max_views = 0;
+    BatchLayout lay{};
+    char* d_desc = nullptr;     // device descriptor block
+    char* h_stage = nullptr;    // pinned staging copy
+    ftv::Plan* d_plan = nullptr;
+    uint32_t* d_status = nullptr;
+    int32_t fmt = -1, combine = -1;
+    int32_t prepared_units = 0;
+    int cost_grid = 0;
+    cudaEvent_t done = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_fmt = -1, graph_combine = -1;
+    int64_t launches = 0;
+};
+
+namespace ftv {
+
+void free_stream_state(ftv_ctx* c) {
+    StreamState& st = c->stream;
+    for (auto& r : st.refs) {
+        cudaFree(r.d_prev_label);
+        cudaFree(r.d_i_label);
+        cudaFree(r.d_mask);
+        cudaFree(r.d_changed);
+        cudaFree(r.d_n_changed);
+        cudaFree(r.d_stats);
+        cudaFree(r.d_cost);
+        cudaFree(r.d_labels);
+        for (auto* p : r.d_nbrs_ring) cudaFree(p);
+    }
+    st.refs.clear();
+    for (auto& p : st.d_ring) {
+        cudaFree(p);
+        p = nullptr;
+    }
+    st.ready = false;
+}
+
+}  // namespace ftv
+
+namespace {
+
+int64_t stream_bytes(const ftv_ctx* c, const int32_t* n_segments) {
+    int64_t b = 0;
+    size_t packed = 0;
+    for (int v = 0; v < c->n_views; ++v)
+        packed += (((size_t)c->cams[v].width * c->cams[v].height * c->texel_bytes) + 255) & ~(size_t)255;
+    b += 3 * (int64_t)packed;
+    for (int i = 0; i < c->n_refs; ++i) {
+        const int64_t S = n_segments[i];
+        const auto& r = c->refs[i];
+        b += S * (2 + 2 + 1 + 4 + 64) + S * c->L * 4 + (int64_t)r.W * r.H * 4 + 3 * (int64_t)r.n_nbrs * sizeof(NbrView);
+    }
+    return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+ftv_status ftv_stream_init(ftv_ctx* ctx, const int32_t* const* d_labels, const int32_t* n_segments, int32_t t_p,
+                           int32_t t_i, int32_t mode, ftv_stream stream) {
+    if (!ctx || !d_labels || !n_segments || t_p < 0 || t_i < 0) return FTV_ERR_INVALID_ARG;
+    if (mode != FTV_TM_Y_ONLY && mode != FTV_TM_ALL_YUV) return FTV_ERR_INVALID_ARG;
+    for (int i = 0; i < ctx->n_refs; ++i)
+        if (!d_labels[i] || n_segments[i] < 0 || n_segments[i] > ctx->max_segments) return FTV_ERR_INVALID_ARG;
+    int prev_dev = -1;
+    cudaGetDevice(&prev_dev);
+    if (prev_dev != ctx->device) cudaSetDevice(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    free_stream_state(ctx);
+    StreamState& st = ctx->stream;
+    st.t_p = t_p;
+    st.t_i = t_i;
+    st.mode = mode;
+    st.prev = st.iframe = -1;
+    st.frames = 0;
+    size_t packed = 0;
+    for (int v = 0; v < ctx->n_views; ++v)
+        packed += (((size_t)ctx->cams[v].width * ctx->cams[v].height * ctx->texel_bytes) + 255) & ~(size_t)255;
+    bool ok = true;
+    for (auto& p : st.d_ring) ok = ok && cudaMalloc(&p, packed) == cudaSuccess;
+    st.refs.resize(ctx->n_refs);
+    for (int i = 0; i < ctx->n_refs && ok; ++i) {
+        StreamRef& R = st.refs[i];
+        const RefState& r = ctx->refs[i];
+        R.S = n_segments[i];
+        const size_t S = (size_t)R.S;
+        ok = ok && dalloc(&R.d_prev_label, S) == cudaSuccess && dalloc(&R.d_i_label, S) == cudaSuccess;
+        ok = ok && dalloc(&R.d_mask, S) == cudaSuccess && dalloc(&R.d_changed, S) == cudaSuccess;
+        ok = ok && dalloc(&R.d_n_changed, 1) == cudaSuccess && dalloc(&R.d_stats, S * kStat) == cudaSuccess;
+        ok = ok && dalloc(&R.d_cost, S * ctx->L) == cudaSuccess;
+        ok = ok && dalloc(&R.d_labels, (size_t)r.W * r.H) == cudaSuccess;
+        for (int b = 0; b < 3 && ok; ++b) {
+            ok = dalloc(&R.d_nbrs_ring[b], (size_t)r.n_nbrs) == cudaSuccess;
+            std::vector<NbrView> nv(r.n_nbrs);
+            for (int k = 0; k < r.n_nbrs; ++k) {
+                const int v = r.nbrs[k];
+                nv[k].texels = static_cast<char*>(st.d_ring[b]) + ctx->view_offset_bytes[v];
+                nv[k].w = ctx->cams[v].width;
+                nv[k].h = ctx->cams[v].height;
+                nv[k].pitch = ctx->cams[v].width;
+                nv[k].pad = 0;
+            }
+            if (ok && r.n_nbrs)
+                ok = cudaMemcpy(R.d_nbrs_ring[b], nv.data(), sizeof(NbrView) * nv.size(), cudaMemcpyHostToDevice) ==
+                     cudaSuccess;
+        }
+        if (ok) ok = cudaMemsetAsync(R.d_prev_label, 0, sizeof(uint16_t) * std::max<size_t>(S, 1), s) == cudaSuccess;
+        if (ok) ok = cudaMemsetAsync(R.d_i_label, 0, sizeof(uint16_t) * std::max<size_t>(S, 1), s) == cudaSuccess;
+        if (ok)
+            ok = cudaMemcpyAsync(R.d_labels, d_labels[i], sizeof(int32_t) * (size_t)r.W * r.H, cudaMemcpyDeviceToDevice,
+                                 s) == cudaSuccess;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        free_stream_state(ctx);
+        if (prev_dev >= 0 && prev_dev != ctx->device) cudaSetDevice(prev_dev);
+        return FTV_ERR_OUT_OF_MEMORY;
+    }
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < ctx->n_refs && e == cudaSuccess; ++i) {
+        // the stream's label map is static: its segment index is built once here (with the same int32
+        // overflow check as ftv_segment_index) and reused by every frame
+        RefState& r = ctx->refs[i];
+        const int64_t one = std::max<int64_t>(ctx->penalty, 3LL * ((1LL << ctx->bit_depth) - 1));
+        const int64_t mpc = ctx->combine == FTV_COMBINE_MIN ? one : one * std::max(1, r.n_nbrs);
+        e = launch_segment_index(st.refs[i].d_labels, r.W, r.H, n_segments[i], mpc, r.d_offs, r.d_cursor, r.d_pix,
+                                 ctx->d_status, s, &ctx->launches);
+        r.S_indexed = n_segments[i];
+    }
+    if (prev_dev >= 0 && prev_dev != ctx->device) cudaSetDevice(prev_dev);
+    if (e != cudaSuccess) return FTV_ERR_CUDA;
+    st.ready = true;
+    return FTV_OK;
+}
+
+ftv_status ftv_stream_footprint(const ftv_ctx* ctx, const int32_t* n_segments, int64_t* bytes) {
+    if (!ctx || !n_segments || !bytes) return FTV_ERR_INVALID_ARG;
+    *bytes = stream_bytes(ctx, n_segments);
+    return FTV_OK;
+}
+
+ftv_status ftv_stream_labels(const ftv_ctx* ctx, int32_t ref_index, const uint16_t** d_labels_out) {
+    if (!ctx || !d_labels_out || !ctx->stream.ready || ref_index < 0 || ref_index >= ctx->n_refs)
+        return FTV_ERR_INVALID_ARG;
+    *d_labels_out = ctx->stream.refs[ref_index].d_prev_label;
+    return FTV_OK;
+}
+
+ftv_status ftv_batch_create(int32_t max_jobs, int32_t max_units, int32_t max_views, ftv_batch** out) {
+    if (!out || max_jobs < 1 || max_units < 1 || max_views < 1 || max_units > kMaxUnits) return FTV_ERR_INVALID_ARG;
+    *out = nullptr;
+    ftv_batch* b = new (std::nothrow) ftv_batch();
+    if (!b) return FTV_ERR_OUT_OF_MEMORY;
+    if (cudaGetDevice(&b->device) != cudaSuccess) {
+        delete b;
+        return FTV_ERR_CUDA;
+    }
+    cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, b->device);
+    b->max_jobs = max_jobs;
+    b->max_units = max_units;
+    b->max_views = max_views;
+    b->lay = layout(max_views, max_units);
+    bool ok = cudaMalloc(reinterpret_cast<void**>(&b->d_desc), b->lay.total) == cudaSuccess;
+    ok = ok && cudaMallocHost(reinterpret_cast<void**>(&b->h_stage), b->lay.total) == cudaSuccess;
+    ok = ok && cudaMalloc(reinterpret_cast<void**>(&b->d_plan), sizeof(Plan)) == cudaSuccess;
+    ok = ok && cudaMalloc(reinterpret_cast<void**>(&b->d_status), sizeof(uint32_t)) == cudaSuccess;
+    ok = ok && cudaMemset(b->d_status, 0, sizeof(uint32_t)) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) std::memset(b->h_stage, 0, b->lay.total);
+    if (!ok) {
+        cudaGetLastError();
+        cudaFree(b->d_desc);
+        cudaFreeHost(b->h_stage);
+        cudaFree(b->d_plan);
+        cudaFree(b->d_status);
+        if (b->done) cudaEventDestroy(b->done);
+        delete b;
+        return FTV_ERR_OUT_OF_MEMORY;
+    }
+    *out = b;
+    return FTV_OK;
+}
+
+ftv_status ftv_batch_destroy(ftv_batch* b) {
+    if (!b) return FTV_OK;
+    cudaEventSynchronize(b->done);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->d_desc);
+    cudaFreeHost(b->h_stage);
+    cudaFree(b->d_plan);
+    cudaFree(b->d_status);
+    cudaEventDestroy(b->done);
+    delete b;
+    return FTV_OK;
+}
+
+ftv_status ftv_batch_prepare(ftv_batch* b, const ftv_frame_job* jobs, int32_t n_jobs) {
+    if (!b || (!jobs && n_jobs > 0) || n_jobs < 0 || n_jobs > b->max_jobs) return FTV_ERR_INVALID_ARG;
+    // the staging block must not be rewritten while a launch that reads it is pending
+    if (cudaEventQuery(b->done) == cudaErrorNotReady) return FTV_ERR_BUSY;
+    cudaGetLastError();
+    int n_views = 0, n_units = 0, fmt = -1, combine = -1;
+    for (int j = 0; j < n_jobs; ++j) {
+        const ftv_frame_job& J = jobs[j];
+        if (!J.ctx || !J.ctx->stream.ready || !J.d_planes || !J.pitch_bytes) return FTV_ERR_INVALID_ARG;
+        if (J.frame_type != FTV_FRAME_I && J.frame_type != FTV_FRAME_P) return FTV_ERR_INVALID_ARG;
+        if (J.frame_type == FTV_FRAME_P && J.ctx->stream.prev < 0) return FTV_ERR_STATE;
+        if (J.ctx->device != b->device) return FTV_ERR_INVALID_ARG;
+        for (int k = 0; k < j; ++k)
+            if (jobs[k].ctx == J.ctx) return FTV_ERR_INVALID_ARG;  // one frame per stream per batch
+        if (fmt >= 0 && (J.ctx->fmt != fmt || J.ctx->combine != combine)) return FTV_ERR_INVALID_ARG;
+        fmt = J.ctx->fmt;
+        combine = J.ctx->combine;
+        n_views += J.ctx->n_views;
+        n_units += J.ctx->n_refs;
+        for (int v = 0; v < J.ctx->n_views; ++v)
+            for (int c = 0; c < 3; ++c) {
+                if (!J.d_planes[3 * v + c]) return FTV_ERR_INVALID_ARG;
+                if (J.pitch_bytes[3 * v + c] < (int64_t)J.ctx->cams[v].width * J.ctx->sample_bytes) return FTV_ERR_INVALID_ARG;
+            }
+    }
+    if (n_views > b->max_views || n_units > b->max_units) return FTV_ERR_BUSY;
+
+    char* h = b->h_stage;
+    Header& H = *reinterpret_cast<Header*>(h + b->lay.header);
+    PackTask* P = reinterpret_cast<PackTask*>(h + b->lay.pack);
+    TempUnit* T = reinterpret_cast<TempUnit*>(h + b->lay.temp);
+    RefJob* R = reinterpret_cast<RefJob*>(h + b->lay.jobs);
+    WtaUnit* Wt = reinterpret_cast<WtaUnit*>(h + b->lay.wta);
+    std::memset(&H, 0, sizeof(H));
+    int pv = 0, pu = 0, pack_rows = 0, temp_rows = 0, temp_stats = 0, wta_segs = 0, depth_rows = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        const ftv_frame_job& J = jobs[j];
+        ftv_ctx* c = J.ctx;
+        StreamState& st = c->stream;
+        const bool is_i = J.frame_type == FTV_FRAME_I;
+        int cur = 0;
+        while (cur == st.prev || (!is_i && cur == st.iframe)) ++cur;  // a ring slot that is neither prev nor I
+        const int prev = is_i ? cur : st.prev;
+        const int ifr = is_i ? cur : st.iframe;
+        const uint32_t maxv = c->bit_depth >= 32 ? 0xffffffffu : ((1u << c->bit_depth) - 1u);
+        for (int v = 0; v < c->n_views; ++v) {
+            PackTask& t = P[pv++];
+            for (int k = 0; k < 3; ++k) {
+                t.planes[k] = J.d_planes[3 * v + k];
+                t.pitch[k] = J.pitch_bytes[3 * v + k];
+            }
+            t.out = static_cast<char*>(st.d_ring[cur]) + c->view_offset_bytes[v];
+            t.W = c->cams[v].width;
+            t.H = c->cams[v].height;
+            t.sb = c->sample_bytes;
+            t.fmt = c->fmt;
+            t.maxv = maxv;
+            t.row_base = pack_rows;
+            pack_rows += t.H;
+        }
+        for (int i = 0; i < c->n_refs; ++i) {
+            const RefState& r = c->refs[i];
+            StreamRef& S = st.refs[i];
+            const size_t ref_off = c->view_offset_bytes[r.view];
+            TempUnit& t = T[pu];
+            t.cur = static_cast<char*>(st.d_ring[cur]) + ref_off;
+            t.prev = static_cast<char*>(st.d_ring[prev]) + ref_off;
+            t.ifr = static_cast<char*>(st.d_ring[ifr]) + ref_off;
+            t.labels = S.d_labels;
+            t.stats = S.d_stats;
+            t.mask = S.d_mask;
+            t.changed = S.d_changed;
+            t.n_changed = S.d_n_changed;
+            t.W = r.W;
+            t.H = is_i ? 0 : r.H;
+            t.S = S.S;
+            t.t_p = st.t_p;
+            t.t_i = st.t_i;
+            t.nch = st.mode == FTV_TM_ALL_YUV ? 3 : 1;
+            t.fmt = c->fmt;
+            t.is_i = is_i;
+            t.row_base = temp_rows;
+            t.stat_base = temp_stats;
+            if (!is_i) {
+                temp_rows += r.H;
+                temp_stats += S.S * kStat;
+            }
+            RefJob& q = R[pu];
+            std::memset(&q, 0, sizeof(q));
+            q.ref_texels = t.cur;
+            q.pix = r.d_pix;
+            q.offs = r.d_offs;
+            q.list = S.d_changed;
+            q.n_listed = S.d_n_changed;
+            q.woffs = r.d_woffs;
+            q.H = r.d_H;
+            q.nbrs = S.d_nbrs_ring[cur];
+            q.cost = S.d_cost;
+            q.W = r.W;
+            q.S = S.S;
+            q.N = r.n_nbrs;
+            q.L = c->L;
+            q.LB = c->LB;
+            q.nLB = c->nLB;
+            q.penalty = c->penalty;
+            q.fmt = c->fmt;
+            WtaUnit& w = Wt[pu];
+            w.cost = S.d_cost;
+            w.mask = S.d_mask;
+            w.prev_label = S.d_prev_label;
+            w.i_label = S.d_i_label;
+            w.out = J.d_label_out ? J.d_label_out[i] : nullptr;
+            w.labels = S.d_labels;
+            w.depth = J.d_depth_out ? J.d_depth_out[i] : nullptr;
+            w.label_z = c->d_label_z;
+            w.S = S.S;
+            w.L = c->L;
+            w.W = r.W;
+            w.H = r.H;
+            w.is_i = is_i;
+            w.seg_base = wta_segs;
+            wta_segs += S.S;
+            ++pu;
+        }
+        st.prev = cur;
+        if (is_i) st.iframe = cur;
+        st.frames++;
+    }
+    // Depth rows flattened over the units that asked for depth maps. Units without one own no rows:
+    // they share their base with the next unit, and find_base (largest index whose base is <= row)
+    // always resolves a row to the unit that owns it. The temporal row/stat bases of I-frame units
+    // and the segment bases of empty units follow the same rule.
+    {
+        int next = 0;
+        for (int u = 0; u < pu; ++u) {
+            Wt[u].depth_base = next;
+            if (Wt[u].depth) next += Wt[u].H;
+        }
+        depth_rows = next;
+    }
+    H.n_pack = pv;
+    H.n_units = pu;
+    H.fmt = fmt;
+    H.combine = combine;
+    H.pack_rows = pack_rows;
+    H.temp_rows = temp_rows;
+    H.temp_stats = temp_stats;
+    H.wta_segs = wta_segs;
+    H.depth_rows = depth_rows;
+    if (fmt >= 0 && (fmt != b->fmt || combine != b->combine)) b->cost_grid = b->n_sm * cost_blocks_per_sm(fmt, combine);
+    if (fmt >= 0) {
+        b->fmt = fmt;
+        b->combine = combine;
+    }
+    b->prepared_units = pu;
+    return FTV_OK;
+}
+
+static cudaError_t enqueue(ftv_batch* b, cudaStream_t s) {
+    const Header* hdr = reinterpret_cast<const Header*>(b->d_desc + b->lay.header);
+    const PackTask* pack = reinterpret_cast<const PackTask*>(b->d_desc + b->lay.pack);
+    const TempUnit* temp = reinterpret_cast<const TempUnit*>(b->d_desc + b->lay.temp);
+    RefJob* jobs = reinterpret_cast<RefJob*>(b->d_desc + b->lay.jobs);
+    const WtaUnit* wta = reinterpret_cast<const WtaUnit*>(b->d_desc + b->lay.wta);
+    const int g = b->n_sm * 4;
+    cudaError_t e = cudaMemcpyAsync(b->d_desc, b->h_stage, b->lay.total, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    pack_multi_kernel<<<g, 256, 0, s>>>(hdr, pack, b->d_status);
+    temporal_zero_multi_kernel<<<g, 256, 0, s>>>(hdr, temp);
+    temporal_accumulate_multi_kernel<<<g, 256, 0, s>>>(hdr, temp, b->d_status);
+    temporal_finalize_multi_kernel<<<std::min(b->max_units, 1024), 1024, 0, s>>>(hdr, temp);
+    zero_changed_rows_kernel<<<dim3(64, std::min(b->max_units, 65535)), 256, 0, s>>>(hdr, jobs);
+    e = launch_plan_device(jobs, &hdr->n_units, b->d_plan, s);
+    if (e != cudaSuccess) return e;
+    e = launch_cost(jobs, b->d_plan, b->fmt, b->combine, b->cost_grid, s);
+    if (e != cudaSuccess) return e;
+    wta_multi_kernel<<<g, 256, 0, s>>>(hdr, wta);
+    depth_multi_kernel<<<g, 256, 0, s>>>(hdr, wta, b->d_status);
+    b->launches += 9;
+    return cudaGetLastError();
+}
+
+ftv_status ftv_batch_launch(ftv_batch* b, ftv_stream stream) {
+    if (!b || b->fmt < 0) return FTV_ERR_STATE;
+    int prev_dev = -1;
+    cudaGetDevice(&prev_dev);
+    if (prev_dev != b->device) cudaSetDevice(b->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = enqueue(b, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b->done, s);
+    if (prev_dev >= 0 && prev_dev != b->device) cudaSetDevice(prev_dev);
+    return e == cudaSuccess ? FTV_OK : FTV_ERR_CUDA;
+}
+
+ftv_status ftv_batch_replay(ftv_batch* b, ftv_stream stream) {
+    if (!b || b->fmt < 0) return FTV_ERR_STATE;
+    int prev_dev = -1;
+    cudaGetDevice(&prev_dev);
+    if (prev_dev != b->device) cudaSetDevice(b->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (!b->exec || b->graph_fmt != b->fmt || b->graph_combine != b->combine) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+        cudaStream_t cap;
+        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) {
+            e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                const cudaError_t e1 = enqueue(b, cap);
+                b->launches -= 9;
+                e = cudaStreamEndCapture(cap, &b->graph);
+                if (e1 != cudaSuccess) e = e1;
+            }
+            cudaStreamDestroy(cap);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        if (e == cudaSuccess) {
+            b->graph_fmt = b->fmt;
+            b->graph_combine = b->combine;
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, s);
+    if (e == cudaSuccess) {
+        b->launches += 9;
+        e = cudaEventRecord(b->done, s);
+    }
+    if (prev_dev >= 0 && prev_dev != b->device) cudaSetDevice(prev_dev);
+    return e == cudaSuccess ? FTV_OK : FTV_ERR_CUDA;
+}
+
+ftv_status ftv_batch_query(ftv_batch* b) {
+    if (!b) return FTV_ERR_INVALID_ARG;
+    const cudaError_t e = cudaEventQuery(b->done);
+    if (e == cudaErrorNotReady) return FTV_ERR_BUSY;
+    return e == cudaSuccess ? FTV_OK : FTV_ERR_CUDA;
+}
+
+ftv_status ftv_batch_wait(ftv_batch* b) {
+    if (!b) return FTV_ERR_INVALID_ARG;
+    if (cudaEventSynchronize(b->done) != cudaSuccess) return FTV_ERR_CUDA;
+    uint32_t st = 0;
+    if (cudaMemcpy(&st, b->d_status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return FTV_ERR_CUDA;
+    if (st) {
+        cudaMemset(b->d_status, 0, sizeof(st));
+        return (st & ST_OVERFLOW) ? FTV_ERR_OVERFLOW : FTV_ERR_INVALID_ARG;
+    }
+    return FTV_OK;
+}
+
+int64_t ftv_batch_launch_count(const ftv_batch* b) { return b ? b->launches : 0; }
+
+}  // extern "C"

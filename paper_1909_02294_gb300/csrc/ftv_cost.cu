@@ -160,8 +160,8 @@ __device__ __forceinline__ int upper_index(const int32_t* a, int lo, int hi, int
 }
 
 template <int FMT, int COMB>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob* __restrict__ jobs, int n_jobs,
-                                                        Plan* __restrict__ plan) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob* __restrict__ jobs,
+                                                                    Plan* __restrict__ plan) {
     __shared__ HEntry sH[kHEntries];
     __shared__ const void* sBase[FTV_MAX_NBRS];
     __shared__ int sAcc[kSegAcc * kMaxLB];
@@ -170,6 +170,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int total = *reinterpret_cast<volatile int*>(&plan->total_items);
+    const int n_jobs = *reinterpret_cast<volatile int*>(&plan->n_jobs);
     for (int i = tid; i < kSegAcc * kMaxLB; i += kThreads) sAcc[i] = 0;
 
     for (;;) {
@@ -363,10 +364,9 @@ int cost_blocks_per_sm(int fmt, int combine) {
                                       : blocks_per_sm_for<FMT_U16X4, FTV_COMBINE_SUM>();
 }
 
-cudaError_t launch_cost(const RefJob* jobs, int n_jobs, const Plan* plan, int fmt, int combine, int grid,
-                        cudaStream_t s) {
+cudaError_t launch_cost(const RefJob* jobs, const Plan* plan, int fmt, int combine, int grid, cudaStream_t s) {
     Plan* p = const_cast<Plan*>(plan);
-#define FTV_LAUNCH(F, C) cost_kernel<F, C><<<grid, kThreads, 0, s>>>(jobs, n_jobs, p)
+#define FTV_LAUNCH(F, C) cost_kernel<F, C><<<grid, kThreads, 0, s>>>(jobs, p)
     if (fmt == FMT_U8X4) {
         if (combine == FTV_COMBINE_MIN) FTV_LAUNCH(FMT_U8X4, FTV_COMBINE_MIN);
         else FTV_LAUNCH(FMT_U8X4, FTV_COMBINE_SUM);

@@ -153,56 +153,77 @@ struct PlanArgs {
     RefJob jobs[CAP];
 };
 
-// One block of 1024 threads. For every (job, reference) unit: the listed pixel prefix (woffs), the
-// number of work items (tiles x label blocks) and the unit's first item; then the launch total. The
-// descriptors arrive as kernel parameters and are written, completed, to `out`.
+// Completes the plan fields of one (job, reference) unit: the listed pixel prefix (woffs), the number
+// of work items (tiles x label blocks) and the unit's first item. Called by all threads of one block
+// of 1024 with the same unit; *base is the running item count in shared memory.
+__device__ void plan_unit(const RefJob& J, RefJob* out, int* base) {
+    int n_work = J.S;
+    if (J.list != nullptr) n_work = min(max(*J.n_listed, 0), J.S);
+    int n_rec;
+    if (J.list == nullptr) {
+        n_rec = J.offs[J.S];
+    } else {
+        const int per = (n_work + blockDim.x - 1) / blockDim.x;
+        const int b = threadIdx.x * per, e = min(n_work, b + per);
+        int sum = 0;
+        for (int i = b; i < e; ++i) {
+            const int s = J.list[i];
+            if ((unsigned)s < (unsigned)J.S) sum += J.offs[s + 1] - J.offs[s];
+        }
+        int total;
+        int run = block_exclusive_scan(sum, &total);
+        for (int i = b; i < e; ++i) {
+            J.woffs[i] = run;
+            const int s = J.list[i];
+            if ((unsigned)s < (unsigned)J.S) run += J.offs[s + 1] - J.offs[s];
+        }
+        if (threadIdx.x == 0) J.woffs[n_work] = total;
+        n_rec = total;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int tiles = (n_rec + kTile - 1) / kTile;
+        RefJob o = J;
+        if (o.list == nullptr) o.woffs = const_cast<int32_t*>(o.offs);
+        o.n_work = n_work;
+        o.n_rec = n_rec;
+        o.n_items = tiles * o.nLB;
+        o.item_base = *base;
+        *out = o;
+        *base += o.n_items;
+    }
+    __syncthreads();
+}
+
+// One block of 1024 threads; descriptors arrive as kernel parameters and are written, completed, to `out`.
 template <int CAP>
 __global__ void plan_kernel(const __grid_constant__ PlanArgs<CAP> args, int n_jobs, RefJob* out, Plan* plan) {
     __shared__ int s_base;
     if (threadIdx.x == 0) s_base = 0;
     __syncthreads();
+    for (int j = 0; j < n_jobs; ++j) plan_unit(args.jobs[j], &out[j], &s_base);
+    if (threadIdx.x == 0) {
+        plan->total_items = s_base;
+        plan->counter = 0;
+        plan->n_jobs = n_jobs;
+    }
+}
+
+// One block of 1024 threads; descriptors already in device memory are completed in place.
+__global__ void plan_device_kernel(RefJob* jobs, const int32_t* n_jobs_ptr, Plan* plan) {
+    __shared__ int s_base;
+    if (threadIdx.x == 0) s_base = 0;
+    __syncthreads();
+    const int n_jobs = *n_jobs_ptr;
     for (int j = 0; j < n_jobs; ++j) {
-        const RefJob& J = args.jobs[j];
-        int n_work = J.S;
-        if (J.list != nullptr) n_work = min(max(*J.n_listed, 0), J.S);
-        int n_rec;
-        if (J.list == nullptr) {
-            n_rec = J.offs[J.S];
-        } else {
-            const int per = (n_work + blockDim.x - 1) / blockDim.x;
-            const int b = threadIdx.x * per, e = min(n_work, b + per);
-            int sum = 0;
-            for (int i = b; i < e; ++i) {
-                const int s = J.list[i];
-                if ((unsigned)s < (unsigned)J.S) sum += J.offs[s + 1] - J.offs[s];
-            }
-            int total;
-            int run = block_exclusive_scan(sum, &total);
-            for (int i = b; i < e; ++i) {
-                J.woffs[i] = run;
-                const int s = J.list[i];
-                if ((unsigned)s < (unsigned)J.S) run += J.offs[s + 1] - J.offs[s];
-            }
-            if (threadIdx.x == 0) J.woffs[n_work] = total;
-            n_rec = total;
-        }
+        const RefJob J = jobs[j];
         __syncthreads();
-        if (threadIdx.x == 0) {
-            const int tiles = (n_rec + kTile - 1) / kTile;
-            RefJob o = J;
-            if (o.list == nullptr) o.woffs = const_cast<int32_t*>(o.offs);
-            o.n_work = n_work;
-            o.n_rec = n_rec;
-            o.n_items = tiles * o.nLB;
-            o.item_base = s_base;
-            out[j] = o;
-            s_base += o.n_items;
-        }
-        __syncthreads();
+        plan_unit(J, &jobs[j], &s_base);
     }
     if (threadIdx.x == 0) {
         plan->total_items = s_base;
         plan->counter = 0;
+        plan->n_jobs = n_jobs;
     }
 }
 
@@ -255,6 +276,11 @@ static cudaError_t launch_plan_cap(const RefJob* host_jobs, int n_jobs, RefJob* 
     PlanArgs<CAP> args;
     for (int j = 0; j < n_jobs; ++j) args.jobs[j] = host_jobs[j];
     plan_kernel<CAP><<<1, 1024, 0, s>>>(args, n_jobs, d_jobs, plan);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plan_device(RefJob* d_jobs, const int32_t* n_jobs, Plan* plan, cudaStream_t s) {
+    plan_device_kernel<<<1, 1024, 0, s>>>(d_jobs, n_jobs, plan);
     return cudaGetLastError();
 }
 

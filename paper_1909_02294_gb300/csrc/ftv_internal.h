@@ -67,7 +67,8 @@ struct RefJob {
 struct Plan {
     int32_t total_items;
     int32_t counter;           // next item to take (persistent CTAs)
-    int32_t pad[2];
+    int32_t n_jobs;            // units in the launch
+    int32_t pad;
 };
 
 struct RefState {
@@ -83,6 +84,31 @@ struct RefState {
     uint32_t* d_pix = nullptr;   // [W * H]
     int32_t S_indexed = -1;      // segment count of the cached index (-1: none)
     std::vector<float> h_H;      // host copy of the table
+};
+
+// Resident per-stream state of one reference view (ftv_stream_init).
+struct StreamRef {
+    uint16_t* d_prev_label = nullptr;  // [S] labels of the previous frame (updated in place)
+    uint16_t* d_i_label = nullptr;     // [S] labels of the last I frame
+    uint8_t* d_mask = nullptr;         // [S]
+    int32_t* d_changed = nullptr;      // [S]
+    int32_t* d_n_changed = nullptr;    // [1]
+    int64_t* d_stats = nullptr;        // [S][8]
+    int32_t* d_cost = nullptr;         // [S][L] cost scratch
+    int32_t* d_labels = nullptr;       // [H][W] copy of the reference label map
+    NbrView* d_nbrs_ring[3] = {nullptr, nullptr, nullptr};  // neighbour geometry into ring buffer b
+    int32_t S = 0;
+};
+
+// Resident per-stream state: a ring of three packed frames (current, previous P, I) and per-reference
+// label states, so that consecutive frames of one camera stream can skip unchanged segments.
+struct StreamState {
+    bool ready = false;
+    int32_t t_p = 0, t_i = 0, mode = 0;
+    void* d_ring[3] = {nullptr, nullptr, nullptr};
+    int32_t prev = -1, iframe = -1;
+    int64_t frames = 0;
+    std::vector<StreamRef> refs;
 };
 
 }  // namespace ftv
@@ -111,9 +137,13 @@ struct ftv_ctx {
     bool profiling = false;
     bool timed = false;
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
+    ftv::StreamState stream;
 };
 
 namespace ftv {
+
+// Stream state (ftv_batch.cu)
+void free_stream_state(ftv_ctx* c);
 
 // Host geometry (ftv_geometry.cpp)
 bool label_inv_depths(int L, double z_near, double z_far, std::vector<double>& iz);
@@ -127,13 +157,15 @@ cudaError_t launch_segment_index(const int32_t* labels, int W, int H, int S, int
 // Descriptors travel as kernel parameters (graph-capturable, no host staging buffer to race on).
 constexpr int kMaxUnits = 240;  // (job, reference) units per launch
 cudaError_t launch_plan(const RefJob* host_jobs, int n_jobs, RefJob* d_jobs, Plan* plan, cudaStream_t s);
+// Same plan for descriptors already in device memory (completed in place); the unit count is read from
+// *n_jobs on the device, so one captured launch serves any batch composition.
+cudaError_t launch_plan_device(RefJob* d_jobs, const int32_t* n_jobs, Plan* plan, cudaStream_t s);
 cudaError_t launch_zero_rows(int32_t* cost, int L, int S, const int32_t* list, const int32_t* n_listed,
                              cudaStream_t s);
 
 // Cost kernel (ftv_cost.cu)
 int cost_blocks_per_sm(int fmt, int combine);
-cudaError_t launch_cost(const RefJob* jobs, int n_jobs, const Plan* plan, int fmt, int combine, int grid,
-                        cudaStream_t s);
+cudaError_t launch_cost(const RefJob* jobs, const Plan* plan, int fmt, int combine, int grid, cudaStream_t s);
 
 // Temporal / WTA (ftv_temporal.cu)
 cudaError_t launch_temporal(const void* const* cur, const int64_t* cur_pitch, const void* const* prev,

@@ -67,6 +67,16 @@ def _load() -> ctypes.CDLL:
         "ftv_wta_depth": [vp, i32, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp],
         "ftv_check": [vp, vp],
         "ftv_set_profiling": [vp, i32],
+        "ftv_stream_init": [vp, vp, vp, i32, i32, i32, vp],
+        "ftv_stream_footprint": [vp, vp, vp],
+        "ftv_stream_labels": [vp, i32, vp],
+        "ftv_batch_create": [i32, i32, i32, vp],
+        "ftv_batch_destroy": [vp],
+        "ftv_batch_prepare": [vp, vp, i32],
+        "ftv_batch_launch": [vp, vp],
+        "ftv_batch_replay": [vp, vp],
+        "ftv_batch_query": [vp],
+        "ftv_batch_wait": [vp],
         "ftv_temporal_mask_static": [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp,
                                      vp],
         "ftv_last_kernel_ms": [vp, vp],
@@ -75,6 +85,8 @@ def _load() -> ctypes.CDLL:
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = ctypes.c_int
+    lib.ftv_batch_launch_count.argtypes = [vp]
+    lib.ftv_batch_launch_count.restype = i64
     lib.ftv_launch_count.argtypes = [vp]
     lib.ftv_launch_count.restype = i64
     lib.ftv_status_str.argtypes = [ctypes.c_int]
@@ -87,7 +99,9 @@ lib = _load()
 EXPORTED = ["ftv_depth_init", "ftv_depth_destroy", "ftv_compute_homographies", "ftv_get_homographies", "ftv_get_neighbours",
             "ftv_get_label_depths", "ftv_segment_index", "ftv_cost_volume", "ftv_temporal_mask",
             "ftv_wta_depth", "ftv_check", "ftv_launch_count", "ftv_status_str", "ftv_set_profiling",
-            "ftv_last_kernel_ms", "ftv_temporal_mask_static"]
+            "ftv_last_kernel_ms", "ftv_temporal_mask_static", "ftv_stream_init", "ftv_stream_footprint",
+            "ftv_stream_labels", "ftv_batch_create", "ftv_batch_destroy", "ftv_batch_prepare", "ftv_batch_launch",
+            "ftv_batch_replay", "ftv_batch_query", "ftv_batch_wait", "ftv_batch_launch_count"]
 
 
 def _ok(code: int, where: str) -> None:
@@ -312,3 +326,99 @@ def ftv_temporal_mask_static(width: int, height: int, sample_bytes: int, cur, pr
     _ok(lib.ftv_temporal_mask_static(width, height, sample_bytes, cp, cpi, pp, ppi, ip, ipi, _ptr(labels), n_segments,
                                      t_p, t_i, mode, _ptr(mask), _ptr(changed_list), _ptr(n_changed), _ptr(status),
                                      _stream(stream)), "ftv_temporal_mask_static")
+
+
+FTV_FRAME_I, FTV_FRAME_P = 0, 1
+
+
+class ftv_frame_job(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("d_planes", ctypes.c_void_p), ("pitch_bytes", ctypes.c_void_p),
+                ("frame_type", ctypes.c_int32), ("d_label_out", ctypes.c_void_p), ("d_depth_out", ctypes.c_void_p)]
+
+
+def ftv_stream_init(ctx: Context, labels, n_segments, t_p: int, t_i: int, mode: int, stream=None) -> None:
+    """Make ctx a camera stream with static label maps labels[r] (int32 [H][W] device tensors)."""
+    lab = _arr(ctypes.c_void_p, [_ptr(l) for l in labels])
+    ns = _arr(ctypes.c_int32, n_segments)
+    _ok(lib.ftv_stream_init(ctx.handle, lab, ns, t_p, t_i, mode, _stream(stream)), "ftv_stream_init")
+
+
+def ftv_stream_footprint(ctx: Context, n_segments) -> int:
+    out = ctypes.c_int64()
+    _ok(lib.ftv_stream_footprint(ctx.handle, _arr(ctypes.c_int32, n_segments), ctypes.byref(out)),
+        "ftv_stream_footprint")
+    return int(out.value)
+
+
+def ftv_stream_labels(ctx: Context, ref_index: int) -> int:
+    p = ctypes.c_void_p()
+    _ok(lib.ftv_stream_labels(ctx.handle, ref_index, ctypes.byref(p)), "ftv_stream_labels")
+    return int(p.value)
+
+
+class Batch:
+    """Owns an ftv_batch handle."""
+
+    def __init__(self, max_jobs: int, max_units: int, max_views: int):
+        h = ctypes.c_void_p()
+        _ok(lib.ftv_batch_create(max_jobs, max_units, max_views, ctypes.byref(h)), "ftv_batch_create")
+        self.handle = h.value
+
+    def close(self) -> None:
+        if self.handle:
+            _ok(lib.ftv_batch_destroy(self.handle), "ftv_batch_destroy")
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ftv_batch_create(max_jobs: int, max_units: int, max_views: int) -> Batch:
+    return Batch(max_jobs, max_units, max_views)
+
+
+def ftv_batch_prepare(batch: Batch, jobs) -> int:
+    """jobs: list of dicts {ctx, planes (per view (Y, Cb, Cr) tensors), frame_type, label_out (list or
+    None), depth_out (list or None)}. Returns the status code (FTV_ERR_BUSY while the batch is in use)."""
+    keep = []
+    arr = (ftv_frame_job * max(1, len(jobs)))()
+    for k, j in enumerate(jobs):
+        ptrs, pitches = [], []
+        for trip in j["planes"]:
+            for t in trip:
+                ptrs.append(_ptr(t))
+                pitches.append(int(t.stride(0)) * t.element_size())
+        pa, pi = _arr(ctypes.c_void_p, ptrs), _arr(ctypes.c_int64, pitches)
+        lo = _arr(ctypes.c_void_p, [_ptr(t) for t in j["label_out"]]) if j.get("label_out") is not None else None
+        do = _arr(ctypes.c_void_p, [_ptr(t) for t in j["depth_out"]]) if j.get("depth_out") is not None else None
+        keep += [pa, pi, lo, do]
+        arr[k].ctx = j["ctx"].handle
+        arr[k].d_planes = ctypes.cast(pa, ctypes.c_void_p)
+        arr[k].pitch_bytes = ctypes.cast(pi, ctypes.c_void_p)
+        arr[k].frame_type = j["frame_type"]
+        arr[k].d_label_out = ctypes.cast(lo, ctypes.c_void_p) if lo is not None else None
+        arr[k].d_depth_out = ctypes.cast(do, ctypes.c_void_p) if do is not None else None
+    return int(lib.ftv_batch_prepare(batch.handle, arr, len(jobs)))
+
+
+def ftv_batch_launch(batch: Batch, stream=None) -> None:
+    _ok(lib.ftv_batch_launch(batch.handle, _stream(stream)), "ftv_batch_launch")
+
+
+def ftv_batch_replay(batch: Batch, stream=None) -> None:
+    _ok(lib.ftv_batch_replay(batch.handle, _stream(stream)), "ftv_batch_replay")
+
+
+def ftv_batch_query(batch: Batch) -> int:
+    return int(lib.ftv_batch_query(batch.handle))
+
+
+def ftv_batch_wait(batch: Batch) -> int:
+    return int(lib.ftv_batch_wait(batch.handle))
+
+
+def ftv_batch_launch_count(batch: Batch) -> int:
+    return int(lib.ftv_batch_launch_count(batch.handle))

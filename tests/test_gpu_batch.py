@@ -1,0 +1,177 @@
+"""GPU parity of the batched / served form: camera streams with resident temporal state, many jobs
+per launch, captured-graph replay.
+
+Reference: the oracle run frame by frame as Sec. III-E describes (I frame: every segment estimated;
+P frame: temporal test against the previous P and the I frame, cost only for changed segments,
+winner-take-all for those, adoption for the others). Integer outputs: bit-exact.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synth import configs
+from synth.configs import make_workload
+
+pytestmark = pytest.mark.gpu
+
+ftv = pytest.importorskip("paper_1909_02294_gb300")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from gpu_runs import dev  # noqa: E402
+
+T_P, T_I = 12, 4  # the paper's 8-bit thresholds (3, 1) scaled to 10-bit samples
+
+
+def _streams():
+    a = make_workload("temporal", reduced=True)  # 8 views 244x138, 40 labels, moving planes
+    b = configs._temporal(configs.BASE_SEED + 41, W=320, H=180, f=250.0, L=24, refs=[0, 2, 4], n_frames=4,
+                          name="temporal_b")
+    return [a, b]
+
+
+class Stream:
+    def __init__(self, wl, mode=0):
+        self.wl = wl
+        self.S = [wl.labels(r)[1] for r in wl.ref_views]
+        self.ctx = ftv.ftv_depth_init(wl.cams, wl.ref_views, wl.n_labels, wl.z_near, wl.z_far,
+                                      sample_bytes=wl.sample_bytes, bit_depth=wl.bit_depth,
+                                      oob_penalty=wl.oob_penalty, max_segments=max(self.S))
+        labels = [dev(wl.labels(r)[0]) for r in wl.ref_views]
+        ftv.ftv_stream_init(self.ctx, labels, self.S, T_P, T_I, mode)
+        self.out = [torch.zeros(s, dtype=torch.int16, device="cuda") for s in self.S]
+        self.depth = [torch.zeros((wl.cams[r].height, wl.cams[r].width), dtype=torch.float32, device="cuda")
+                      for r in wl.ref_views]
+
+    def job(self, frame, frame_type, depth=False):
+        planes = [(dev(v.Y), dev(v.U), dev(v.V)) for v in self.wl.views(frame)]
+        return {"ctx": self.ctx, "planes": planes, "frame_type": frame_type, "label_out": self.out,
+                "depth_out": self.depth if depth else None}
+
+    def labels(self):
+        return [o.cpu().numpy().view(np.uint16).copy() for o in self.out]
+
+
+class OracleStream:
+    """The paper's I/P procedure on the CPU oracle."""
+
+    def __init__(self, wl, mode=0):
+        self.wl, self.mode = wl, mode
+        self.prev_frame = self.i_frame = None
+        self.prev = {}
+        self.ilab = {}
+
+    def step(self, frame, frame_type):
+        wl = self.wl
+        out = []
+        for r in wl.ref_views:
+            lab, S = wl.labels(r)
+            H = oracle.homography_table(wl.cams, r, wl.neighbours(r), wl.n_labels, wl.z_near, wl.z_far)
+            if frame_type == ftv.FTV_FRAME_I:
+                mask = np.zeros(S, np.uint8)
+                changed = np.arange(S, dtype=np.int32)
+            else:
+                mask, changed, _ = oracle.temporal_mask(lab, S, wl.view(r, frame), wl.view(r, self.prev_frame),
+                                                        wl.view(r, self.i_frame), wl.sample_bytes, T_P, T_I, self.mode)
+            vol = np.zeros((S, wl.n_labels), np.int32)
+            if len(changed):
+                vol = oracle.cost_volume(wl.cams, wl.views(frame), wl.sample_bytes, r, wl.neighbours(r), H,
+                                         wl.n_labels, lab, S, wl.oob_penalty, seg_list=changed, out=vol)
+            if frame_type == ftv.FTV_FRAME_I:
+                labels = oracle.wta(vol)
+                self.ilab[r] = labels.copy()
+            else:
+                labels = oracle.wta(vol, mask, self.prev[r], self.ilab[r])
+            self.prev[r] = labels.copy()
+            out.append(labels)
+        self.prev_frame = frame
+        if frame_type == ftv.FTV_FRAME_I:
+            self.i_frame = frame
+        return out
+
+
+def _run(batch, jobs, replay=False):
+    assert ftv.ftv_batch_prepare(batch, jobs) == 0
+    (ftv.ftv_batch_replay if replay else ftv.ftv_batch_launch)(batch)
+    assert ftv.ftv_batch_wait(batch) == 0
+
+
+SCHEDULE = [(0, 0), (1, 1), (2, 1), (3, 1)]  # (frame, type): I then P frames
+
+
+def test_batched_streams_match_oracle_frame_by_frame():
+    wls = _streams()
+    streams = [Stream(w) for w in wls]
+    refs = [OracleStream(w) for w in wls]
+    batch = ftv.ftv_batch_create(4, 32, 32)
+    for frame, ftype in SCHEDULE:
+        _run(batch, [s.job(frame, ftype, depth=(k == 0)) for k, s in enumerate(streams)])
+        for s, o in zip(streams, refs):
+            got = s.labels()
+            want = o.step(frame, ftype)
+            for r, (g, w) in enumerate(zip(got, want)):
+                assert np.array_equal(g, w), (s.wl.name, frame, r, int((g != w).sum()))
+        # per-pixel depth of the first stream's references
+        s0 = streams[0]
+        for r_i, r in enumerate(s0.wl.ref_views):
+            lab, S = s0.wl.labels(r)
+            want_d = oracle.depth_map(lab, S, refs[0].prev[r], s0.wl.n_labels, s0.wl.z_near, s0.wl.z_far)
+            assert np.array_equal(s0.depth[r_i].cpu().numpy(), want_d)
+    assert ftv.ftv_batch_launch_count(batch) == 9 * len(SCHEDULE)
+    batch.close()
+    for s in streams:
+        s.ctx.close()
+
+
+def test_results_identical_alone_in_the_mix_and_replayed():
+    wls = _streams()
+    # alone: one stream per batch, direct launches
+    alone = []
+    for w in wls:
+        s = Stream(w)
+        b = ftv.ftv_batch_create(1, 16, 16)
+        res = []
+        for frame, ftype in SCHEDULE:
+            _run(b, [s.job(frame, ftype)])
+            res.append(s.labels())
+        alone.append(res)
+        b.close()
+        s.ctx.close()
+    # in the mix, through the captured graph (the first replay captures, later ones replay)
+    streams = [Stream(w) for w in wls]
+    b = ftv.ftv_batch_create(4, 32, 32)
+    mixed = [[], []]
+    for frame, ftype in SCHEDULE:
+        _run(b, [s.job(frame, ftype) for s in streams], replay=True)
+        for k, s in enumerate(streams):
+            mixed[k].append(s.labels())
+    for k in range(2):
+        for fa, fb in zip(alone[k], mixed[k]):
+            for a, c in zip(fa, fb):
+                assert np.array_equal(a, c)
+    # a batch whose staging block is in use reports busy instead of racing
+    assert ftv.ftv_batch_prepare(b, [streams[0].job(0, 0)]) in (0, ftv.FTV_ERR_BUSY)
+    b.close()
+    for s in streams:
+        s.ctx.close()
+
+
+def test_batch_argument_errors():
+    w = _streams()[0]
+    s = Stream(w)
+    b = ftv.ftv_batch_create(1, 16, 16)
+    # a P frame before any I frame
+    assert ftv.ftv_batch_prepare(b, [s.job(1, ftv.FTV_FRAME_P)]) == ftv.FTV_ERR_STATE
+    # the same stream twice in one batch
+    b2 = ftv.ftv_batch_create(2, 32, 32)
+    assert ftv.ftv_batch_prepare(b2, [s.job(0, 0), s.job(0, 0)]) == ftv.FTV_ERR_INVALID_ARG
+    # over capacity
+    b3 = ftv.ftv_batch_create(1, 2, 16)
+    assert ftv.ftv_batch_prepare(b3, [s.job(0, 0)]) == ftv.FTV_ERR_BUSY
+    assert ftv.ftv_stream_footprint(s.ctx, s.S) > 0
+    for x in (b, b2, b3):
+        x.close()
+    s.ctx.close()
