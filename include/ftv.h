@@ -283,6 +283,11 @@ FTV_API ftv_status ftv_stream_footprint(const ftv_ctx* ctx, const int32_t* n_seg
 /* Device pointer to a stream's current per-segment labels of reference ref_index (uint16 [S]). */
 FTV_API ftv_status ftv_stream_labels(const ftv_ctx* ctx, int32_t ref_index, const uint16_t** d_labels_out);
 
+/* Device pointers to a stream's temporal mask of reference ref_index (uint8 [S]: FTV_MASK_*) and to the
+ * count of segments its last frame re-estimated (int32 [1]); valid after that frame's batch completes. */
+FTV_API ftv_status ftv_stream_mask(const ftv_ctx* ctx, int32_t ref_index, const uint8_t** d_mask,
+                                   const int32_t** d_n_changed);
+
 /* A batch executor with room for max_jobs frames, max_units (job, reference) units (<= 240) and
  * max_views views in total; owns a device descriptor block and a pinned staging copy of it. */
 FTV_API ftv_status ftv_batch_create(int32_t max_jobs, int32_t max_units, int32_t max_views, ftv_batch** out);

@@ -507,6 +507,14 @@ ftv_status ftv_stream_labels(const ftv_ctx* ctx, int32_t ref_index, const uint16
     return FTV_OK;
 }
 
+ftv_status ftv_stream_mask(const ftv_ctx* ctx, int32_t ref_index, const uint8_t** d_mask, const int32_t** d_n_changed) {
+    if (!ctx || !d_mask || !d_n_changed || !ctx->stream.ready || ref_index < 0 || ref_index >= ctx->n_refs)
+        return FTV_ERR_INVALID_ARG;
+    *d_mask = ctx->stream.refs[ref_index].d_mask;
+    *d_n_changed = ctx->stream.refs[ref_index].d_n_changed;
+    return FTV_OK;
+}
+
 ftv_status ftv_batch_create(int32_t max_jobs, int32_t max_units, int32_t max_views, ftv_batch** out) {
     if (!out || max_jobs < 1 || max_units < 1 || max_views < 1 || max_units > kMaxUnits) return FTV_ERR_INVALID_ARG;
     *out = nullptr;

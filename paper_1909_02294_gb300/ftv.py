@@ -70,6 +70,7 @@ def _load() -> ctypes.CDLL:
         "ftv_stream_init": [vp, vp, vp, i32, i32, i32, vp],
         "ftv_stream_footprint": [vp, vp, vp],
         "ftv_stream_labels": [vp, i32, vp],
+        "ftv_stream_mask": [vp, i32, vp, vp],
         "ftv_batch_create": [i32, i32, i32, vp],
         "ftv_batch_destroy": [vp],
         "ftv_batch_prepare": [vp, vp, i32],
@@ -100,7 +101,7 @@ EXPORTED = ["ftv_depth_init", "ftv_depth_destroy", "ftv_compute_homographies", "
             "ftv_get_label_depths", "ftv_segment_index", "ftv_cost_volume", "ftv_temporal_mask",
             "ftv_wta_depth", "ftv_check", "ftv_launch_count", "ftv_status_str", "ftv_set_profiling",
             "ftv_last_kernel_ms", "ftv_temporal_mask_static", "ftv_stream_init", "ftv_stream_footprint",
-            "ftv_stream_labels", "ftv_batch_create", "ftv_batch_destroy", "ftv_batch_prepare", "ftv_batch_launch",
+            "ftv_stream_labels", "ftv_stream_mask", "ftv_batch_create", "ftv_batch_destroy", "ftv_batch_prepare", "ftv_batch_launch",
             "ftv_batch_replay", "ftv_batch_query", "ftv_batch_wait", "ftv_batch_launch_count"]
 
 
@@ -354,6 +355,17 @@ def ftv_stream_labels(ctx: Context, ref_index: int) -> int:
     p = ctypes.c_void_p()
     _ok(lib.ftv_stream_labels(ctx.handle, ref_index, ctypes.byref(p)), "ftv_stream_labels")
     return int(p.value)
+
+
+def ftv_stream_mask(ctx: Context, ref_index: int) -> tuple[int, int]:
+    """(device pointer of the uint8 mask [S], device pointer of the int32 changed count)."""
+    m, n = ctx_void(), ctx_void()
+    _ok(lib.ftv_stream_mask(ctx.handle, ref_index, ctypes.byref(m), ctypes.byref(n)), "ftv_stream_mask")
+    return int(m.value), int(n.value)
+
+
+def ctx_void():
+    return ctypes.c_void_p()
 
 
 class Batch:

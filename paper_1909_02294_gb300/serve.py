@@ -1,0 +1,357 @@
+"""Serving loop: continuous batching of depth jobs from many camera streams.
+
+A thin host driver over the C ABI (all per-pixel work runs in the library's kernels). Each camera
+stream is an ftv_ctx with resident temporal state (ftv_stream_init): its label maps, segment indexes,
+previous-P and I frames and their per-segment labels stay on the device, so P frames only estimate
+segments whose colour changed (Sec. III-E; 9 P frames between I frames as in the paper's experiments).
+
+Served mode: up to `slots` batches are in flight on separate CUDA streams. Whenever a slot is free,
+every request that has arrived, whose stream has no frame in flight (in-stream order is kept) and whose
+input frame fits the HBM admission budget is admitted into one batch: its planes are copied from pinned
+host memory on the slot's stream and the batch's captured graph is replayed (ftv_batch_prepare +
+ftv_batch_replay). Requests that arrive while others are on the GPU join the next free slot.
+
+Plain mode (the comparison): the same requests in arrival order, one job at a time, each launched on
+its own (ftv_batch_launch of a single job, no graph) and completed before the next starts.
+
+Both modes run the same kernels on the same stream states and produce bit-identical labels.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import sys
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import ftv
+
+T_P_10BIT, T_I_10BIT = 12, 4  # the paper's T_P = 3, T_I = 1 for 8-bit samples, scaled to 10 bits
+
+
+@dataclass
+class Request:
+    rid: int
+    sid: int
+    seq: int          # position in its stream
+    arrival: float    # seconds from the start of the run
+    admitted: float = -1.0
+    done: float = -1.0
+
+
+class Stream:
+    def __init__(self, wl, n_frames: int, gop: int, device, keep_labels: bool = False):
+        self.wl = wl
+        self.gop = gop
+        self.S = [wl.labels(r)[1] for r in wl.ref_views]
+        self.ctx = ftv.ftv_depth_init(wl.cams, wl.ref_views, wl.n_labels, wl.z_near, wl.z_far,
+                                      sample_bytes=wl.sample_bytes, bit_depth=wl.bit_depth,
+                                      oob_penalty=wl.oob_penalty, max_segments=max(self.S))
+        labels = [torch.from_numpy(wl.labels(r)[0]).to(device) for r in wl.ref_views]
+        ftv.ftv_stream_init(self.ctx, labels, self.S, T_P_10BIT, T_I_10BIT, ftv.FTV_TM_Y_ONLY)
+        self.frames = []
+        for k in range(n_frames):
+            self.frames.append([[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (v.Y, v.U, v.V)]
+                                for v in wl.views(k)])
+            wl.drop_frame(k)
+        self.frame_bytes = sum(t.numel() * t.element_size() for trip in self.frames[0] for t in trip)
+        self.out = [torch.zeros(s, dtype=torch.int16, device=device) for s in self.S]
+        self.keep = keep_labels
+        self.history = []
+        self.busy = False
+        self.n_refs = len(wl.ref_views)
+        self.n_views = wl.n_views
+        self.shape = (wl.cams[0].width, wl.cams[0].height, wl.n_views, wl.n_labels)
+
+    def frame_type(self, seq: int) -> int:
+        return ftv.FTV_FRAME_I if seq % self.gop == 0 else ftv.FTV_FRAME_P
+
+    def upload(self, seq: int, stream):
+        host = self.frames[seq % len(self.frames)]
+        with torch.cuda.stream(stream):
+            return [[t.to(stream.device, non_blocking=True) for t in trip] for trip in host]
+
+    def job(self, seq: int, planes) -> dict:
+        return {"ctx": self.ctx, "planes": planes, "frame_type": self.frame_type(seq), "label_out": self.out}
+
+    def record(self):
+        if self.keep:
+            self.history.append([o.cpu().numpy().view(np.uint16).copy() for o in self.out])
+
+    def close(self):
+        self.ctx.close()
+
+
+def poisson_trace(n_streams: int, n_jobs: int, rate: float, seed: int) -> list[Request]:
+    """n_jobs requests, Poisson arrivals of total rate `rate` (jobs/s), stream chosen uniformly."""
+    rng = np.random.default_rng(seed)
+    t, reqs, seq = 0.0, [], [0] * n_streams
+    for i in range(n_jobs):
+        t += rng.exponential(1.0 / rate) if rate > 0 else 0.0
+        sid = int(rng.integers(n_streams))
+        reqs.append(Request(i, sid, seq[sid], t))
+        seq[sid] += 1
+    return reqs
+
+
+@dataclass
+class Slot:
+    batch: object
+    stream: object
+    reqs: list = field(default_factory=list)
+    inputs: list = field(default_factory=list)
+    bytes: int = 0
+
+
+def run_served(streams: list[Stream], reqs: list[Request], slots: int = 3, budget_bytes: int = 8 << 30,
+               max_jobs: int = 32, by_class: bool = True) -> dict:
+    """by_class: a batch only takes jobs of one stream shape (the shape of the earliest admissible
+    request), so small jobs are not held until a large job in the same batch completes."""
+    dev = torch.device("cuda")
+    max_units = min(240, sum(s.n_refs for s in streams))
+    max_views = sum(s.n_views for s in streams)
+    pool = [Slot(ftv.ftv_batch_create(max_jobs, max_units, max_views), torch.cuda.Stream(dev)) for _ in range(slots)]
+    pending = list(reqs)  # arrival order
+    inflight_bytes, done, batches, batch_sizes = 0, 0, 0, []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while done < len(reqs):
+        now = time.perf_counter() - t0
+        progressed = False
+        for sl in pool:
+            if sl.reqs and ftv.ftv_batch_query(sl.batch) == 0:
+                st = ftv.ftv_batch_wait(sl.batch)
+                if st != 0:
+                    raise RuntimeError(f"batch failed: {ftv.ftv_status_str(st)}")
+                t_done = time.perf_counter() - t0
+                for r in sl.reqs:
+                    r.done = t_done
+                    streams[r.sid].busy = False
+                    streams[r.sid].record()
+                done += len(sl.reqs)
+                inflight_bytes -= sl.bytes
+                sl.reqs, sl.inputs, sl.bytes = [], [], 0
+                progressed = True
+        free = [sl for sl in pool if not sl.reqs]
+        if free:
+            chosen, units, views, add_bytes, seen, cls = [], 0, 0, 0, set(), None
+            for r in pending:
+                if r.arrival > now:
+                    break
+                s = streams[r.sid]
+                if r.sid in seen:
+                    continue  # only a stream's earliest pending request may go (in-stream order)
+                seen.add(r.sid)
+                if s.busy:
+                    continue
+                if inflight_bytes + add_bytes + s.frame_bytes > budget_bytes and (inflight_bytes or chosen):
+                    continue  # admission by HBM footprint: wait until in-flight inputs free up (a job
+                    # larger than the whole budget still runs, alone, when nothing else is in flight)
+                if len(chosen) >= max_jobs or units + s.n_refs > max_units or views + s.n_views > max_views:
+                    continue
+                if by_class and cls is not None and s.shape != cls:
+                    continue
+                cls = s.shape
+                chosen.append(r)
+                units += s.n_refs
+                views += s.n_views
+                add_bytes += s.frame_bytes
+            if chosen:
+                sl = free[0]
+                jobs = []
+                for r in chosen:
+                    s = streams[r.sid]
+                    planes = s.upload(r.seq, sl.stream)
+                    sl.inputs.append(planes)
+                    jobs.append(s.job(r.seq, planes))
+                    s.busy = True
+                    r.admitted = now
+                    pending.remove(r)
+                rc = ftv.ftv_batch_prepare(sl.batch, jobs)
+                if rc != 0:
+                    raise RuntimeError(f"prepare failed: {ftv.ftv_status_str(rc)}")
+                ftv.ftv_batch_replay(sl.batch, sl.stream)
+                sl.reqs, sl.bytes = chosen, add_bytes
+                inflight_bytes += add_bytes
+                batches += 1
+                batch_sizes.append(len(chosen))
+                progressed = True
+        if not progressed:
+            time.sleep(20e-6)
+    launches = sum(ftv.ftv_batch_launch_count(sl.batch) for sl in pool)
+    for sl in pool:
+        sl.batch.close()
+    out = _stats(streams, reqs)
+    out.update({"mode": "served", "slots": slots, "batches": batches,
+                "mean_batch_jobs": float(np.mean(batch_sizes)) if batch_sizes else 0.0, "gpu_launches": launches})
+    return out
+
+
+def run_plain(streams: list[Stream], reqs: list[Request]) -> dict:
+    dev = torch.device("cuda")
+    st = torch.cuda.Stream(dev)
+    batch = ftv.ftv_batch_create(1, max(s.n_refs for s in streams), max(s.n_views for s in streams))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in reqs:
+        while time.perf_counter() - t0 < r.arrival:
+            time.sleep(20e-6)
+        r.admitted = time.perf_counter() - t0
+        s = streams[r.sid]
+        planes = s.upload(r.seq, st)
+        rc = ftv.ftv_batch_prepare(batch, [s.job(r.seq, planes)])
+        if rc != 0:
+            raise RuntimeError(f"prepare failed: {ftv.ftv_status_str(rc)}")
+        ftv.ftv_batch_launch(batch, st)
+        rc = ftv.ftv_batch_wait(batch)
+        if rc != 0:
+            raise RuntimeError(f"batch failed: {ftv.ftv_status_str(rc)}")
+        r.done = time.perf_counter() - t0
+        s.record()
+    launches = ftv.ftv_batch_launch_count(batch)
+    batch.close()
+    out = _stats(streams, reqs)
+    out.update({"mode": "plain", "gpu_launches": launches})
+    return out
+
+
+class _DeviceArray:
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3}
+
+
+def _device_int32(ptr: int):
+    return torch.as_tensor(_DeviceArray(ptr, (1,), "<i4"), device="cuda")
+
+
+def run_sequence(wl, n_frames: int, gop: int, replay: bool = True) -> dict:
+    """One camera stream over n_frames consecutive frames (I frame every `gop` frames, P frames between):
+    device-resident inputs, each frame timed with CUDA events on the launching stream. Reports depth
+    maps/s over the sequence and the fraction of segments each P frame re-estimated."""
+    dev = torch.device("cuda")
+    s = Stream(wl, 0, gop, dev)
+    frames = []
+    for k in range(n_frames):
+        frames.append([[torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (v.Y, v.U, v.V)]
+                       for v in wl.views(k)])
+        wl.drop_frame(k)
+    batch = ftv.ftv_batch_create(1, s.n_refs, s.n_views)
+    st = torch.cuda.current_stream(dev)
+    counts = [ftv.ftv_stream_mask(s.ctx, i)[1] for i in range(s.n_refs)]
+    ms, changed = [], []
+    torch.cuda.synchronize()
+    for k in range(n_frames):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        rc = ftv.ftv_batch_prepare(batch, [s.job(k, frames[k])])
+        if rc != 0:
+            raise RuntimeError(ftv.ftv_status_str(rc))
+        a.record(st)
+        (ftv.ftv_batch_replay if replay else ftv.ftv_batch_launch)(batch, st)
+        b.record(st)
+        if ftv.ftv_batch_wait(batch) != 0:
+            raise RuntimeError("sequence frame failed")
+        ms.append(a.elapsed_time(b))
+        n = sum(int(_device_int32(p).item()) for p in counts)
+        changed.append(n / sum(s.S))
+    batch.close()
+    s.close()
+    p_idx = [k for k in range(n_frames) if k % gop]
+    total_s = sum(ms) / 1e3
+    return {"frames": n_frames, "gop": gop, "depth_maps": n_frames * s.n_refs,
+            "depth_maps_per_s": n_frames * s.n_refs / total_s, "ms_per_frame": sum(ms) / n_frames,
+            "ms_i_frame": float(np.mean([ms[k] for k in range(n_frames) if k % gop == 0])),
+            "ms_p_frame": float(np.mean([ms[k] for k in p_idx])) if p_idx else None,
+            "changed_fraction_p_frames": float(np.mean([changed[k] for k in p_idx])) if p_idx else None,
+            "evaluations_i_frame": wl.evaluations()}
+
+
+def _stats(streams, reqs) -> dict:
+    lat = np.array([r.done - r.arrival for r in reqs]) * 1e3
+    maps = sum(streams[r.sid].n_refs for r in reqs)
+    span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
+    by_shape = {}
+    for r in reqs:
+        key = f"{streams[r.sid].wl.cams[0].width}x{streams[r.sid].wl.cams[0].height}"
+        by_shape.setdefault(key, []).append((r.done - r.arrival) * 1e3)
+    return {"jobs": len(reqs), "depth_maps": maps, "wall_s": span, "depth_maps_per_s": maps / span,
+            "jobs_per_s": len(reqs) / span, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "p99_ms_by_shape": {k: float(np.percentile(v, 99)) for k, v in sorted(by_shape.items())}}
+
+
+def make_streams(per_shape: int, gop: int, n_frames: int, keep_labels: bool = False, shapes=None):
+    import synth.configs as configs
+    wls = configs.serving_streams(per_shape)
+    if shapes is not None:
+        wls = [w for w in wls if any(w.name.startswith(p) for p in shapes)]
+    dev = torch.device("cuda")
+    return [Stream(w, n_frames if w.cams[0].width < 3840 else max(2, n_frames // 2), gop, dev, keep_labels)
+            for w in wls]
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--jobs", type=int, default=2000)
+    ap.add_argument("--per-shape", type=int, default=4, help="streams per shape (3 shapes)")
+    ap.add_argument("--gop", type=int, default=10, help="frames per I frame (paper: 9 P frames between I frames)")
+    ap.add_argument("--frames", type=int, default=4, help="distinct frames rendered per stream (cycled)")
+    ap.add_argument("--slots", type=int, default=3)
+    ap.add_argument("--budget-gb", type=float, default=8.0, help="HBM admission budget for in-flight inputs")
+    ap.add_argument("--rate-frac", type=float, default=0.7, help="arrival rate as a fraction of measured capacity")
+    ap.add_argument("--capacity-jobs", type=int, default=0, help="jobs of the saturated capacity run (0: --jobs)")
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--shapes", default=None, help="comma-separated stream name prefixes (default: all)")
+    ap.add_argument("--mixed-batches", action="store_true", help="let one batch mix stream shapes")
+    ap.add_argument("--sequence", default=None, help="run one stream of this workload (e.g. temporal) over --frames")
+    args = ap.parse_args(argv)
+    shapes = args.shapes.split(",") if args.shapes else None
+    if args.sequence:
+        import synth
+        res = run_sequence(synth.make_workload(args.sequence), args.frames, args.gop)
+        res["workload"] = args.sequence
+        print(json.dumps(res), flush=True)
+        return res
+
+    def fresh():
+        return make_streams(args.per_shape, args.gop, args.frames, shapes=shapes)
+
+    budget = int(args.budget_gb * (1 << 30))
+    n_cap = args.capacity_jobs or args.jobs
+    results = {}
+    # capacity of each mode: every request present at t = 0
+    for mode in ("served", "plain"):
+        streams = fresh()
+        trace = poisson_trace(len(streams), n_cap, 0.0, args.seed)
+        res = run_served(streams, trace, args.slots, budget, by_class=not args.mixed_batches) \
+            if mode == "served" else run_plain(streams, trace)
+        results[f"capacity_{mode}"] = res
+        for s in streams:
+            s.close()
+    results["served_vs_plain_depth_maps_per_s"] = (results["capacity_served"]["depth_maps_per_s"] /
+                                                   results["capacity_plain"]["depth_maps_per_s"])
+    # latency under Poisson arrivals at rate_frac of each mode's own capacity
+    for mode in ("served", "plain"):
+        rate = args.rate_frac * results[f"capacity_{mode}"]["jobs_per_s"]
+        streams = fresh()
+        trace = poisson_trace(len(streams), args.jobs, rate, args.seed + 7)
+        res = run_served(streams, trace, args.slots, budget, by_class=not args.mixed_batches) \
+            if mode == "served" else run_plain(streams, trace)
+        res["rate_jobs_per_s"] = rate
+        results[f"poisson_{mode}"] = res
+        for s in streams:
+            s.close()
+    results["config"] = {"streams": len(streams), "jobs": args.jobs, "class_batches": not args.mixed_batches,
+                         "gop": args.gop, "slots": args.slots, "budget_gb": args.budget_gb,
+                         "rate_frac": args.rate_frac, "shapes": "960x540/3v/64L, 1920x1080/8v/250L, 3840x2160/15v/400L"}
+    print(json.dumps(results), flush=True)
+    return results
+
+
+if __name__ == "__main__":
+    main()

@@ -203,6 +203,46 @@ def _serving_small(seed: int) -> Workload:
     return Workload("serving_small", cams, [0, 1, 2], 64, 1.0, 20.0, 10, planes, cell=10, seed=seed)
 
 
+def _movers(cam: Camera, f: float, seed: int, coverage: float = 0.05) -> list[Plane]:
+    """Three textured planes parallel to `cam`'s image plane that translate 4 px/frame along its x axis
+    (world shift 4 z / f per frame), each covering about `coverage` of the image."""
+    fov_x, fov_y = cam.width / (2 * f), cam.height / (2 * f)
+    out = []
+    for k, (z, a, b) in enumerate([(2.0, -0.55, -0.1), (2.6, 0.2, 0.35), (3.2, 0.6, -0.4)]):
+        half = 0.5 * math.sqrt(coverage * 4 * fov_x * fov_y) * z
+        p = fronto_plane(cam, z, half, centre_xy=(a * fov_x * z, b * fov_y * z), texel=_texel(z, f),
+                         seed=seed + 100 + k)
+        p.velocity = cam.R.T @ np.array([4.0 * z / f, 0.0, 0.0])
+        out.append(p)
+    return out
+
+
+def serving_streams(per_shape: int = 4) -> list[Workload]:
+    """Camera streams of the serving workload: per_shape streams of each of 960x540 / 3 views / 64 labels,
+    1920x1080 / 8 views / 250 labels and 3840x2160 / 15 views / 400 labels (10-bit 4:4:4 in uint16),
+    each a seeded plane scene with three moving planes and sensor noise (sigma 2 LSB), so that about
+    15 % of the segments change from frame to frame."""
+    streams = []
+    for i in range(per_shape):
+        seed = BASE_SEED + 4 + 1000 * (i + 1)
+        cams = linear_rig(3, 0.10, 750.0, 960, 540)
+        rng = np.random.default_rng(seed)
+        planes = _layered(cams[1], 750.0, 8, 4.0, 12.0, 18.0, seed, rng) + _movers(cams[1], 750.0, seed)
+        streams.append(Workload(f"s540_{i}", cams, [0, 1, 2], 64, 1.0, 20.0, 10, planes, cell=10, seed=seed,
+                                noise_sigma=2.0))
+    for i in range(per_shape):
+        seed = BASE_SEED + 4 + 1000 * (i + 1) + 1
+        streams.append(_temporal(seed, name=f"s1080_{i}"))
+    for i in range(per_shape):
+        seed = BASE_SEED + 4 + 1000 * (i + 1) + 2
+        wl = _uhd15(seed, name=f"s2160_{i}")
+        wl.planes = wl.planes + _movers(wl.cams[7], 3000.0, seed)
+        wl.noise_sigma = 2.0
+        wl.specular_frac = 0.0  # per-frame specular flicker would mark most segments as changed
+        streams.append(wl)
+    return streams
+
+
 def make_workload(name: str, reduced: bool = False, painted: bool = False) -> Workload:
     """Build a named workload. `reduced` gives a small variant of the same structure (rig type,
     bit depth, chroma handling, noise, all references) that the CPU oracle finishes in seconds while
