@@ -59,7 +59,8 @@ class Stream:
             self.frames.append([[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (v.Y, v.U, v.V)]
                                 for v in wl.views(k)])
             wl.drop_frame(k)
-        self.frame_bytes = sum(t.numel() * t.element_size() for trip in self.frames[0] for t in trip)
+        self.frame_bytes = sum(t.numel() * t.element_size() for trip in self.frames[0] for t in trip) \
+            if self.frames else 0
         self.out = [torch.zeros(s, dtype=torch.int16, device=device) for s in self.S]
         self.keep = keep_labels
         self.history = []
