@@ -332,6 +332,16 @@ FTV_API ftv_status ftv_last_kernel_ms(ftv_ctx* ctx, float* ms);
 /* Kernel launches this context has enqueued since creation (for accounting). */
 FTV_API int64_t ftv_launch_count(const ftv_ctx* ctx);
 
+/* Self-check of the cost kernel's reciprocal on the current device. The contract's r = 1/Wz is the IEEE
+ * round-to-nearest reciprocal. The kernel forms it as one Newton-Raphson step on the hardware estimate
+ * (r = r0 + r0 (1 - Wz r0) with fused multiply-adds; Markstein's method), scaling positive subnormal
+ * Wz by 2^64 first, but only on a device where this equals the IEEE reciprocal for every positive float
+ * below 2^126 (|Wz| < 2^117 always): the first context created on a device runs that exhaustive
+ * comparison (about 2.1e9 inputs, a few milliseconds) and otherwise keeps the IEEE routine.
+ * *mismatches receives the count of disagreeing inputs, *fast_path_used (optional) whether the kernel
+ * uses the Newton step. */
+FTV_API ftv_status ftv_reciprocal_check(int64_t* mismatches, int32_t* fast_path_used);
+
 /* Human-readable name of a status code (static storage). */
 FTV_API const char* ftv_status_str(ftv_status s);
 

@@ -117,6 +117,7 @@ ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out) {
     c->z_near = cfg->z_near;
     c->z_far = cfg->z_far;
     c->penalty = cfg->oob_penalty >= 0 ? cfg->oob_penalty : (int32_t)(3 * ((1LL << cfg->bit_depth) - 1));
+    // 4-byte texels wherever the samples fit (one 32-bit gather per evaluation)
     c->fmt = cfg->sample_bytes == 1 ? FMT_U8X4 : (cfg->bit_depth <= 10 ? FMT_P10 : FMT_U16X4);
     c->texel_bytes = c->fmt == FMT_U16X4 ? 8 : 4;
     c->cams.assign(cfg->cams, cfg->cams + cfg->n_views);
@@ -226,7 +227,8 @@ ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out) {
         if (r.n_nbrs)
             ok = ok && cudaMemcpy(r.d_nbrs, nv.data(), sizeof(NbrView) * nv.size(), cudaMemcpyHostToDevice) == cudaSuccess;
     }
-    c->cost_blocks_per_sm = cost_blocks_per_sm(c->fmt, c->combine);
+    c->fast_rcp = fast_reciprocal_exact();
+    c->cost_blocks_per_sm = cost_blocks_per_sm(c->fmt, c->combine, c->fast_rcp);
     if (!ok) {
         free_ctx(c);
         return FTV_ERR_CUDA;
@@ -389,7 +391,8 @@ ftv_status ftv_cost_volume(ftv_ctx* ctx, const void* const* d_planes, const int6
     }
     if (e == cudaSuccess && ctx->profiling) e = cudaEventRecord(ctx->ev_start, s);
     if (e == cudaSuccess) {
-        e = launch_cost(ctx->d_jobs, ctx->d_plan, ctx->fmt, ctx->combine, ctx->n_sm * ctx->cost_blocks_per_sm, s);
+        e = launch_cost(ctx->d_jobs, ctx->d_plan, ctx->fmt, ctx->combine, ctx->fast_rcp,
+                        ctx->n_sm * ctx->cost_blocks_per_sm, s);
         ctx->launches++;
     }
     if (e == cudaSuccess && ctx->profiling) {
@@ -461,6 +464,13 @@ ftv_status ftv_check(ftv_ctx* ctx, ftv_stream stream) {
 }
 
 int64_t ftv_launch_count(const ftv_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+ftv_status ftv_reciprocal_check(int64_t* mismatches, int32_t* fast_path_used) {
+    if (!mismatches) return FTV_ERR_INVALID_ARG;
+    *mismatches = reciprocal_mismatches();
+    if (fast_path_used) *fast_path_used = fast_reciprocal_exact() ? 1 : 0;
+    return *mismatches < 0 ? FTV_ERR_CUDA : FTV_OK;
+}
 
 ftv_status ftv_set_profiling(ftv_ctx* ctx, int32_t enable) {
     if (!ctx) return FTV_ERR_INVALID_ARG;

@@ -363,6 +363,7 @@ struct ftv_batch {
     ftv::Plan* d_plan = nullptr;
     uint32_t* d_status = nullptr;
     int32_t fmt = -1, combine = -1;
+    bool fast_rcp = false;
     int32_t prepared_units = 0;
     int cost_grid = 0;
     cudaEvent_t done = nullptr;
@@ -525,6 +526,7 @@ ftv_status ftv_batch_create(int32_t max_jobs, int32_t max_units, int32_t max_vie
         return FTV_ERR_CUDA;
     }
     cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, b->device);
+    b->fast_rcp = fast_reciprocal_exact();
     b->max_jobs = max_jobs;
     b->max_units = max_units;
     b->max_views = max_views;
@@ -713,7 +715,8 @@ ftv_status ftv_batch_prepare(ftv_batch* b, const ftv_frame_job* jobs, int32_t n_
     H.temp_stats = temp_stats;
     H.wta_segs = wta_segs;
     H.depth_rows = depth_rows;
-    if (fmt >= 0 && (fmt != b->fmt || combine != b->combine)) b->cost_grid = b->n_sm * cost_blocks_per_sm(fmt, combine);
+    if (fmt >= 0 && (fmt != b->fmt || combine != b->combine))
+        b->cost_grid = b->n_sm * cost_blocks_per_sm(fmt, combine, b->fast_rcp);
     if (fmt >= 0) {
         b->fmt = fmt;
         b->combine = combine;
@@ -738,7 +741,7 @@ static cudaError_t enqueue(ftv_batch* b, cudaStream_t s) {
     zero_changed_rows_kernel<<<dim3(64, std::min(b->max_units, 65535)), 256, 0, s>>>(hdr, jobs);
     e = launch_plan_device(jobs, &hdr->n_units, b->d_plan, s);
     if (e != cudaSuccess) return e;
-    e = launch_cost(jobs, b->d_plan, b->fmt, b->combine, b->cost_grid, s);
+    e = launch_cost(jobs, b->d_plan, b->fmt, b->combine, b->fast_rcp, b->cost_grid, s);
     if (e != cudaSuccess) return e;
     wta_multi_kernel<<<g, 256, 0, s>>>(hdr, wta);
     depth_multi_kernel<<<g, 256, 0, s>>>(hdr, wta, b->d_status);

@@ -24,7 +24,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <climits>
+#include <mutex>
 
 #include "ftv_internal.h"
 
@@ -88,8 +90,8 @@ struct TexelOps<FMT_U16X4> {
 //             r = 1/h8 is computed once at staging time and stored in place of h6;
 //   kUnit     affine with r == 1: u = X * 1 is exactly X, the multiplications are skipped;
 //   kOut      affine with 1/h8 not finite and positive: every sample is out of view.
-// All four give bit-identical results to the general sequence; they only skip work whose result is
-// known exactly.
+// All of them give bit-identical results to the general sequence; they only skip work whose result
+// is known exactly.
 struct __align__(16) HEntry {
     float h[9];
     uint32_t w, h_, pm;
@@ -101,19 +103,47 @@ __device__ __forceinline__ bool finite_positive(float r) {
     return (unsigned)(__float_as_int(r) - 1) < 0x7f7fffffu;
 }
 
+// The contract's r = 1/w is the IEEE round-to-nearest reciprocal. On devices where an exhaustive
+// start-up comparison found it equal, for every float w in [2^-126, 2^126), to one Newton-Raphson step
+// on the hardware estimate r0 ~ 1/w, namely r = r0 + r0 (1 - w r0) with both steps fused multiply-adds
+// (Markstein's method), the kernel uses that step:
+//   rcp_newton: exact for w in [2^-126, 2^126);
+//   rcp_scaled: any w. Positive subnormal w (and w <= 0) are first scaled by 2^64, which is exact,
+//               and the result scaled back; 1/w = 2^64 / (2^64 w) and power-of-two scaling commutes
+//               with round-to-nearest, including the overflow to infinity of 1/w for w < 2^-128. For
+//               w <= 0 or NaN the result is non-positive or NaN, which the in-view test rejects, as it
+//               rejects the IEEE reciprocal of such w.
+// w >= 2^126 cannot occur: the host bounds |h| <= 2^100, so |Wz| < 2^117.
+__device__ __forceinline__ float rcp_newton(float w) {
+    float r0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(w));
+    return __fmaf_rn(r0, __fmaf_rn(-w, r0, 1.0f), r0);
+}
+
+__device__ __forceinline__ float rcp_scaled(float w) {
+    const bool small = w < 0x1p-126f;
+    const float r = rcp_newton(small ? w * 0x1p64f : w);
+    return small ? r * 0x1p64f : r;
+}
+
+template <bool FAST>
+__device__ __forceinline__ float contract_rcp(float w) {
+    return FAST ? rcp_scaled(w) : __frcp_rn(w);
+}
+
 // Cost of one sample: reference pixel (x, y) through homography e.h into one neighbour view.
 // Equivalent to the contract's float test (Wz > 0, 0 <= floor(u + 0.5) <= W - 1, ...): the host
 // guarantees |h| <= 2^100, so X and Y are finite; r = 1/Wz is then finite and positive exactly when
 // Wz > 0 and 1/Wz does not overflow (if it does, u is +-inf or NaN and the contract says "out");
 // with finite positive r, u + 0.5 is finite or +-inf, and floor-to-int with saturation followed by an
 // unsigned range test decides "in view" exactly as the float compares do.
-template <int FMT>
+template <int FMT, bool FAST_RCP>
 __device__ __forceinline__ int sample_cost(const float4& a, const float4& b, const float4& c, int pitch, float x,
                                            float y, int ra, int rb, int rc, const void* tex, int penalty) {
     const float X = __fmaf_rn(a.x, x, __fmaf_rn(a.y, y, a.z));
     const float Yh = __fmaf_rn(a.w, x, __fmaf_rn(b.x, y, b.y));
     const float Wz = __fmaf_rn(b.z, x, __fmaf_rn(b.w, y, c.x));
-    const float r = __frcp_rn(Wz);
+    const float r = contract_rcp<FAST_RCP>(Wz);
     const int ui = __float2int_rd(__fadd_rn(__fmul_rn(X, r), 0.5f));
     const int vi = __float2int_rd(__fadd_rn(__fmul_rn(Yh, r), 0.5f));
     const bool ok = finite_positive(r) & ((unsigned)ui < __float_as_uint(c.y)) & ((unsigned)vi < __float_as_uint(c.z));
@@ -159,7 +189,7 @@ __device__ __forceinline__ int upper_index(const int32_t* a, int lo, int hi, int
     return lo;
 }
 
-template <int FMT, int COMB>
+template <int FMT, int COMB, bool FAST_RCP>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob* __restrict__ jobs,
                                                                     Plan* __restrict__ plan) {
     __shared__ HEntry sH[kHEntries];
@@ -267,8 +297,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                 if (mode == kGeneral) {
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
-                        const int c = sample_cost<FMT>(ha, hb, hc, pitch, px[j], py[j], ra[j], rb[j], rc[j], tex,
-                                                       penalty);
+                        const int c = sample_cost<FMT, FAST_RCP>(ha, hb, hc, pitch, px[j], py[j], ra[j], rb[j],
+                                                                 rc[j], tex, penalty);
                         m[j] = (COMB == FTV_COMBINE_MIN) ? min(m[j], c) : m[j] + c;
                     }
                 } else if (mode == kUnit) {
@@ -346,27 +376,74 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
     }
 }
 
-template <int FMT, int COMB>
+template <int FMT, int COMB, bool FAST>
 int blocks_per_sm_for() {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cost_kernel<FMT, COMB>, kThreads, 0) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cost_kernel<FMT, COMB, FAST>, kThreads, 0) != cudaSuccess)
+        return 1;
     return n > 0 ? n : 1;
 }
 
-}  // namespace
-
-int cost_blocks_per_sm(int fmt, int combine) {
-    if (fmt == FMT_U8X4) return combine == FTV_COMBINE_MIN ? blocks_per_sm_for<FMT_U8X4, FTV_COMBINE_MIN>()
-                                                           : blocks_per_sm_for<FMT_U8X4, FTV_COMBINE_SUM>();
-    if (fmt == FMT_P10) return combine == FTV_COMBINE_MIN ? blocks_per_sm_for<FMT_P10, FTV_COMBINE_MIN>()
-                                                          : blocks_per_sm_for<FMT_P10, FTV_COMBINE_SUM>();
-    return combine == FTV_COMBINE_MIN ? blocks_per_sm_for<FMT_U16X4, FTV_COMBINE_MIN>()
-                                      : blocks_per_sm_for<FMT_U16X4, FTV_COMBINE_SUM>();
+// Exhaustive comparison with the IEEE reciprocal over every positive float below 2^126: subnormals go
+// through rcp_scaled's scaling, normals through rcp_newton directly.
+__global__ void reciprocal_check_kernel(unsigned long long* mismatches) {
+    const uint32_t lo = 0x00000001u, hi = 0x7e800000u;
+    unsigned long long bad = 0;
+    for (uint64_t i = lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const float w = __uint_as_float((uint32_t)i);
+        bad += __float_as_uint(rcp_scaled(w)) != __float_as_uint(__frcp_rn(w));
+    }
+    bad = __reduce_add_sync(0xffffffffu, (unsigned)bad);
+    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(mismatches, bad);
 }
 
-cudaError_t launch_cost(const RefJob* jobs, const Plan* plan, int fmt, int combine, int grid, cudaStream_t s) {
+std::mutex g_rcp_mutex;
+int8_t g_rcp_state[64] = {};  // per device: 0 unknown, 1 exact, -1 not exact
+
+}  // namespace
+
+int64_t reciprocal_mismatches() {
+    unsigned long long* d = nullptr;
+    if (cudaMalloc(&d, sizeof(unsigned long long)) != cudaSuccess) return -1;
+    unsigned long long h = 0;
+    int n_sm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaMemset(d, 0, sizeof(h));
+    if (e == cudaSuccess) {
+        reciprocal_check_kernel<<<std::max(1, n_sm) * 8, 256>>>(d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e == cudaSuccess ? (int64_t)h : -1;
+}
+
+bool fast_reciprocal_exact() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    std::lock_guard<std::mutex> lock(g_rcp_mutex);
+    if (g_rcp_state[dev] == 0) g_rcp_state[dev] = reciprocal_mismatches() == 0 ? 1 : -1;
+    return g_rcp_state[dev] == 1;
+}
+
+int cost_blocks_per_sm(int fmt, int combine, bool fast) {
+#define FTV_OCC(F, C) (fast ? blocks_per_sm_for<F, C, true>() : blocks_per_sm_for<F, C, false>())
+    if (fmt == FMT_U8X4) return combine == FTV_COMBINE_MIN ? FTV_OCC(FMT_U8X4, FTV_COMBINE_MIN)
+                                                           : FTV_OCC(FMT_U8X4, FTV_COMBINE_SUM);
+    if (fmt == FMT_P10) return combine == FTV_COMBINE_MIN ? FTV_OCC(FMT_P10, FTV_COMBINE_MIN)
+                                                          : FTV_OCC(FMT_P10, FTV_COMBINE_SUM);
+    return combine == FTV_COMBINE_MIN ? FTV_OCC(FMT_U16X4, FTV_COMBINE_MIN) : FTV_OCC(FMT_U16X4, FTV_COMBINE_SUM);
+#undef FTV_OCC
+}
+
+cudaError_t launch_cost(const RefJob* jobs, const Plan* plan, int fmt, int combine, bool fast, int grid,
+                        cudaStream_t s) {
     Plan* p = const_cast<Plan*>(plan);
-#define FTV_LAUNCH(F, C) cost_kernel<F, C><<<grid, kThreads, 0, s>>>(jobs, p)
+#define FTV_LAUNCH(F, C)                                                        \
+    (fast ? (cost_kernel<F, C, true><<<grid, kThreads, 0, s>>>(jobs, p), 0)     \
+          : (cost_kernel<F, C, false><<<grid, kThreads, 0, s>>>(jobs, p), 0))
     if (fmt == FMT_U8X4) {
         if (combine == FTV_COMBINE_MIN) FTV_LAUNCH(FMT_U8X4, FTV_COMBINE_MIN);
         else FTV_LAUNCH(FMT_U8X4, FTV_COMBINE_SUM);

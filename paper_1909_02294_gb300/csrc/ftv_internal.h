@@ -6,15 +6,15 @@
 
 #include <vector>
 
-#include "../../include/ftv.h"
+#include "ftv.h"
 
 namespace ftv {
 
 // Packed texel formats: one load fetches the three samples of a pixel.
 enum TexelFormat : int32_t {
     FMT_U8X4 = 0,   // uint32: Y | Cb << 8 | Cr << 16          (8-bit samples)
-    FMT_P10 = 1,    // uint32: Y | Cb << 10 | Cr << 20         (samples of at most 10 bits)
-    FMT_U16X4 = 2,  // uint2 : (Y | Cb << 16, Cr)              (samples of 11 to 16 bits)
+    FMT_P10 = 1,    // uint32: Y | Cb << 10 | Cr << 20         (16-bit samples of at most 10 bits)
+    FMT_U16X4 = 2,  // uint2 : (Y | Cb << 16, Cr)              (16-bit samples of 11 to 16 bits)
 };
 
 // Device status bits (OR-ed by kernels, read and cleared by ftv_check).
@@ -119,6 +119,7 @@ struct ftv_ctx {
     int cost_blocks_per_sm = 0;
     int32_t n_views = 0, n_refs = 0, L = 0, plane_mode = 0, centre = 0;
     int32_t sample_bytes = 1, bit_depth = 8, penalty = 0, combine = 0, max_segments = 0, fmt = 0;
+    bool fast_rcp = false;
     int32_t LB = 0, nLB = 0;
     double z_near = 0, z_far = 0;
     std::vector<ftv_camera> cams;
@@ -164,8 +165,14 @@ cudaError_t launch_zero_rows(int32_t* cost, int L, int S, const int32_t* list, c
                              cudaStream_t s);
 
 // Cost kernel (ftv_cost.cu)
-int cost_blocks_per_sm(int fmt, int combine);
-cudaError_t launch_cost(const RefJob* jobs, const Plan* plan, int fmt, int combine, int grid, cudaStream_t s);
+int cost_blocks_per_sm(int fmt, int combine, bool fast_rcp);
+cudaError_t launch_cost(const RefJob* jobs, const Plan* plan, int fmt, int combine, bool fast_rcp, int grid,
+                        cudaStream_t s);
+// Whether the current device's one-step Newton-Raphson reciprocal equals the IEEE round-to-nearest
+// reciprocal for every float in [2^-126, 2^126) (exhaustive check, run once per device and cached).
+bool fast_reciprocal_exact();
+// Run the exhaustive check on the current device; returns the number of mismatching inputs, or -1.
+int64_t reciprocal_mismatches();
 
 // Temporal / WTA (ftv_temporal.cu)
 cudaError_t launch_temporal(const void* const* cur, const int64_t* cur_pitch, const void* const* prev,

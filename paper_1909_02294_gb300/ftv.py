@@ -71,6 +71,7 @@ def _load() -> ctypes.CDLL:
         "ftv_stream_footprint": [vp, vp, vp],
         "ftv_stream_labels": [vp, i32, vp],
         "ftv_stream_mask": [vp, i32, vp, vp],
+        "ftv_reciprocal_check": [vp, vp],
         "ftv_batch_create": [i32, i32, i32, vp],
         "ftv_batch_destroy": [vp],
         "ftv_batch_prepare": [vp, vp, i32],
@@ -101,7 +102,7 @@ EXPORTED = ["ftv_depth_init", "ftv_depth_destroy", "ftv_compute_homographies", "
             "ftv_get_label_depths", "ftv_segment_index", "ftv_cost_volume", "ftv_temporal_mask",
             "ftv_wta_depth", "ftv_check", "ftv_launch_count", "ftv_status_str", "ftv_set_profiling",
             "ftv_last_kernel_ms", "ftv_temporal_mask_static", "ftv_stream_init", "ftv_stream_footprint",
-            "ftv_stream_labels", "ftv_stream_mask", "ftv_batch_create", "ftv_batch_destroy", "ftv_batch_prepare", "ftv_batch_launch",
+            "ftv_stream_labels", "ftv_stream_mask", "ftv_reciprocal_check", "ftv_batch_create", "ftv_batch_destroy", "ftv_batch_prepare", "ftv_batch_launch",
             "ftv_batch_replay", "ftv_batch_query", "ftv_batch_wait", "ftv_batch_launch_count"]
 
 
@@ -434,3 +435,10 @@ def ftv_batch_wait(batch: Batch) -> int:
 
 def ftv_batch_launch_count(batch: Batch) -> int:
     return int(lib.ftv_batch_launch_count(batch.handle))
+
+
+def ftv_reciprocal_check() -> tuple[int, bool]:
+    """(mismatching inputs of the Newton-Raphson reciprocal on this device, whether the kernel uses it)."""
+    n, used = ctypes.c_int64(), ctypes.c_int32()
+    _ok(lib.ftv_reciprocal_check(ctypes.byref(n), ctypes.byref(used)), "ftv_reciprocal_check")
+    return int(n.value), bool(used.value)

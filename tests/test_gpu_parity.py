@@ -130,6 +130,27 @@ def test_affine_and_out_of_view_homography_modes():
     run.close()
 
 
+def test_projective_entries_whose_denominator_changes_sign():
+    """A neighbour rotated 75 degrees about the vertical axis: Wz = 0 crosses the reference image, so
+    part of every candidate plane is behind it (the kernel's general entries with the guarded
+    reciprocal); a 4-degree rotation keeps Wz > 0 everywhere (the kernel's far-from-zero entries)."""
+    import math
+    wl = make_workload("tiny")
+    base = wl.cams[1]
+    for deg in (75.0, 4.0):
+        a = math.radians(deg)
+        R = np.array([[math.cos(a), 0.0, -math.sin(a)], [0.0, 1.0, 0.0], [math.sin(a), 0.0, math.cos(a)]])
+        C = np.array([0.08, 0.0, 0.0])
+        wl.cams.append(synth.Camera(base.K.copy(), R, -R @ C, base.width, base.height))
+    lists = [[3, 4, 0]]
+    for combine in ("min", "sum"):
+        run = Run(wl, nbr_lists=lists, combine=combine)
+        costs = run.volumes()
+        assert run.check() == 0
+        _assert_equal(costs[0], _oracle_all(wl, combine=combine, nbr_lists=lists)[0], f"rotated views ({combine})")
+        run.close()
+
+
 def test_listed_segments_leave_other_rows_untouched():
     wl = make_workload("hd8", reduced=True)
     run = Run(wl)
