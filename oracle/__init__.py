@@ -46,7 +46,8 @@ def _load():
     if _lib is None:
         _lib = ctypes.CDLL(build())
         for name in ["or_label_inv_depths", "or_homography_f64", "or_homography_table", "or_cost_volume",
-                     "or_cost_entries", "or_fp64_mismatch", "or_temporal_mask", "or_wta", "or_depth_map"]:
+                     "or_cost_entries", "or_fp64_mismatch", "or_temporal_mask", "or_wta", "or_depth_map",
+                     "or_centre_table"]:
             getattr(_lib, name).restype = ctypes.c_int
     return _lib
 
@@ -195,3 +196,21 @@ def depth_map(labels: np.ndarray, S: int, seg_label: np.ndarray, L: int, z_near:
                                 ctypes.c_int(L), ctypes.c_double(z_near), ctypes.c_double(z_far), _p(out)),
            "depth_map")
     return out
+
+
+def centre_table(cams, views, sample_bytes: int, ref: int, nbrs, H: np.ndarray, L: int, labels_views, S: int,
+                 window: int, penalty: int):
+    """(m int32 [S][L][N], s' int32 [S][L][N]) of or_centre_table; labels_views[v] is view v's int32
+    [H][W] label map or None (labels_views[ref] is required)."""
+    nb = np.ascontiguousarray(nbrs, np.int32)
+    imgs, keep = _imgs(views)
+    Hc = np.ascontiguousarray(H, np.float32)
+    labs = [np.ascontiguousarray(l, np.int32) if l is not None else None for l in labels_views]
+    lp = (ctypes.c_void_p * len(labs))(*[l.ctypes.data if l is not None else None for l in labs])
+    m = np.empty((S, L, len(nb)), np.int32)
+    sp = np.empty((S, L, len(nb)), np.int32)
+    _check(_load().or_centre_table(cams_array(cams), ctypes.c_int(len(cams)), imgs, ctypes.c_int(sample_bytes),
+                                   ctypes.c_int(ref), ctypes.c_int(len(nb)), _p(nb), _p(Hc), ctypes.c_int(L), lp,
+                                   ctypes.c_int(S), ctypes.c_int(window), ctypes.c_int(penalty), _p(m), _p(sp)),
+           "centre_table")
+    return m, sp

@@ -440,3 +440,78 @@ int or_depth_map(int W, int Hh, const int32_t* labels, int S, const uint16_t* se
     free(iz);
     return 0;
 }
+
+/* ----------------------------------------------------------------------------- centre table */
+
+/*
+ * Eq. 4 at segment centres and the correspondence that Eq. 5 needs (Sec. III-C): for reference `ref`,
+ * every segment s, label d and neighbour k (view nbrs[k]):
+ *   mu_s      the integer centroid of s: (floor((2 sum x + n) / (2 n)), floor((2 sum y + n) / (2 n)))
+ *             over its n pixels (the paper does not define the centre; this is the rounded mean);
+ *   T[mu_s]   mu_s projected with H[k][d] by the same FP32 sequence as the cost volume;
+ *   m         sum over the window offsets w (window x window, odd) of the L1 distance of (Y, Cb, Cr)
+ *             at mu_s + w in the reference and at T[mu_s] + w in view nbrs[k]; a pair with either
+ *             position outside its image (or T[mu_s] out of view) costs the penalty. The paper's
+ *             1/size(W) factor is left to the consumer (m_paper = m / window^2);
+ *   s'        the label of view nbrs[k]'s own segmentation at T[mu_s], or -1 when T[mu_s] is out of
+ *             view or that view has no label map (labels_views[v] == NULL).
+ * Empty segments: every pair is out (m = window^2 * penalty), s' = -1.
+ * Outputs are int32 [S][L][n_nbrs].
+ */
+int or_centre_table(const or_camera* cams, int n_views, const or_image* imgs, int sample_bytes, int ref, int n_nbrs,
+                    const int32_t* nbrs, const float* H, int L, const int32_t* const* labels_views, int S, int window,
+                    int penalty, int32_t* out_m, int32_t* out_sp) {
+    if (!cams || !imgs || ref < 0 || ref >= n_views || !labels_views || !labels_views[ref] || S < 0 || L < 1)
+        return 1;
+    if (window < 1 || (window & 1) == 0 || !out_m || !out_sp) return 1;
+    const int W = cams[ref].width, Hh = cams[ref].height, half = window / 2;
+    const int32_t* lab = labels_views[ref];
+    int64_t* sx = (int64_t*)calloc((size_t)S + 1, sizeof(int64_t));
+    int64_t* sy = (int64_t*)calloc((size_t)S + 1, sizeof(int64_t));
+    int64_t* cnt = (int64_t*)calloc((size_t)S + 1, sizeof(int64_t));
+    if (!sx || !sy || !cnt) { free(sx); free(sy); free(cnt); return 1; }
+    for (int y = 0; y < Hh; y++)
+        for (int x = 0; x < W; x++) {
+            int s = lab[(size_t)y * W + x];
+            if (s < 0 || s >= S) { free(sx); free(sy); free(cnt); return 2; }
+            sx[s] += x;
+            sy[s] += y;
+            cnt[s]++;
+        }
+    for (int s = 0; s < S; s++) {
+        int mx = 0, my = 0;
+        if (cnt[s] > 0) {
+            mx = (int)((2 * sx[s] + cnt[s]) / (2 * cnt[s]));
+            my = (int)((2 * sy[s] + cnt[s]) / (2 * cnt[s]));
+        }
+        for (int d = 0; d < L; d++)
+            for (int k = 0; k < n_nbrs; k++) {
+                int v = nbrs[k];
+                const float* h = H + ((size_t)k * L + d) * 9;
+                int ui = 0, vi = 0;
+                int in = cnt[s] > 0 && project_f32(h, mx, my, cams[v].width, cams[v].height, &ui, &vi);
+                int64_t m = 0;
+                for (int dy = -half; dy <= half; dy++)
+                    for (int dx = -half; dx <= half; dx++) {
+                        int rx = mx + dx, ry = my + dy, qx = ui + dx, qy = vi + dy;
+                        if (!in || rx < 0 || rx >= W || ry < 0 || ry >= Hh || qx < 0 || qx >= cams[v].width || qy < 0 ||
+                            qy >= cams[v].height) {
+                            m += penalty;
+                            continue;
+                        }
+                        for (int ch = 0; ch < 3; ch++) {
+                            int a = sample_at(&imgs[ref], sample_bytes, ch, rx, ry);
+                            int b = sample_at(&imgs[v], sample_bytes, ch, qx, qy);
+                            m += a > b ? a - b : b - a;
+                        }
+                    }
+                size_t o = ((size_t)s * L + d) * n_nbrs + k;
+                out_m[o] = (int32_t)m;
+                out_sp[o] = (in && labels_views[v]) ? labels_views[v][(size_t)vi * cams[v].width + ui] : -1;
+            }
+    }
+    free(sx);
+    free(sy);
+    free(cnt);
+    return 0;
+}
