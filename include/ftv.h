@@ -318,6 +318,25 @@ FTV_API ftv_status ftv_batch_wait(ftv_batch* b);
 /* Kernel launches this batch object has enqueued (for accounting). */
 FTV_API int64_t ftv_batch_launch_count(const ftv_batch* b);
 
+/*
+ * Centre table (Sec. III-C as written): Eq. 4 on a window around each segment's centre and the
+ * neighbour segment that the centre maps to, i.e. what a graph-cut consumer needs to form Eq. 5's
+ * M = min{0, m - K} (K = 30 in the paper) when d_s = d_s'. For every reference r, segment s, label d
+ * and neighbour k (table order of ftv_get_neighbours):
+ *   mu_s  integer centroid (floor((2 sum x + n) / (2 n)), floor((2 sum y + n) / (2 n))) of s;
+ *   m     sum over the window x window offsets w (odd, <= 15; the paper uses 3) of the L1 (Y, Cb, Cr)
+ *         distance between mu_s + w in r and T[mu_s] + w in view k, T[.] being the volume's FP32
+ *         projection; pairs with a position outside its image, or a centre out of view, cost the
+ *         penalty. Eq. 4's 1/size(W) is left to the consumer (m_paper = m / window^2);
+ *   s'    d_labels_views[view k]'s label at T[mu_s], or -1 if out of view or that map is NULL.
+ * d_labels_views: host array of n_views device label maps (int32 [H][W] per view; every reference's is
+ * required, the others are optional). n_segments[r]: segment count of reference r. d_m[r], d_sprime[r]:
+ * int32 [S_r][n_labels][n_nbrs_r]. Also (re)builds the references' cached segment indexes. Asynchronous.
+ */
+FTV_API ftv_status ftv_centre_table(ftv_ctx* ctx, const void* const* d_planes, const int64_t* pitch_bytes,
+                                    const int32_t* const* d_labels_views, const int32_t* n_segments, int32_t window,
+                                    int32_t* const* d_m, int32_t* const* d_sprime, ftv_stream stream);
+
 /* Wait for `stream`, then return and clear the context's device status word (FTV_OK if clean). */
 FTV_API ftv_status ftv_check(ftv_ctx* ctx, ftv_stream stream);
 

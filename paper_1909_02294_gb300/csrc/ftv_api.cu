@@ -49,6 +49,8 @@ void free_ctx(ftv_ctx* c) {
         cudaFree(r.d_cursor);
         cudaFree(r.d_woffs);
         cudaFree(r.d_pix);
+        cudaFree(r.d_centre);
+        cudaFree(r.d_nbr_labels);
     }
     cudaFree(c->d_packed);
     cudaFree(c->d_status);
@@ -205,6 +207,8 @@ ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out) {
         ok = ok && dalloc(&r.d_cursor, (size_t)c->max_segments) == cudaSuccess;
         ok = ok && dalloc(&r.d_woffs, (size_t)c->max_segments + 1) == cudaSuccess;
         ok = ok && dalloc(&r.d_pix, (size_t)r.W * r.H) == cudaSuccess;
+        ok = ok && dalloc(&r.d_centre, (size_t)c->max_segments) == cudaSuccess;
+        ok = ok && dalloc(&r.d_nbr_labels, (size_t)std::max(1, r.n_nbrs)) == cudaSuccess;
     }
     if (!ok) {
         cudaGetLastError();

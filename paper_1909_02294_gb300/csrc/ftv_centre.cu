@@ -1,0 +1,206 @@
+// Centre table: Eq. 4 evaluated the way the paper states it, on a window around each segment's centre,
+// together with the segment s' of the neighbouring view that the centre maps to (the correspondence
+// Eq. 5 needs to form M = min{0, m - K} when d_s = d_s').
+//
+// Paper, Sec. III-C: m_{s,s'}(d_s) = 1/size(W) * sum_{w in W} || YCbCr(mu_s + w) - YCbCr(T[mu_s] + w) ||_1
+// with mu_s the centre of segment s and T[.] the transform into the neighbouring view for depth d_s;
+// the matching is done "only for centers of segments". Here:
+//   mu_s  = integer centroid floor((2 sum x + n) / (2 n)) of the segment's n pixels (the paper does not
+//           define the centre);
+//   T     = the same FP32 homography and rounding as the cost volume;
+//   m     = the raw window sum (the consumer divides by size(W)); a window pair with a position outside
+//           its image, or a centre that projects out of view, costs the out-of-view penalty;
+//   s'    = the neighbour view's label at T[mu_s] (-1 when out of view or no label map is given).
+// Work: one thread per (segment, label, neighbour); this is not the volume's hot loop (one window per
+// segment instead of every pixel), so the contract's sequence is written out literally.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ftv_internal.h"
+
+namespace ftv {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ void texel(const void* base, int fmt, int64_t i, int* v) {
+    if (fmt == FMT_U16X4) {
+        const uint2 t = static_cast<const uint2*>(base)[i];
+        v[0] = t.x & 0xffff;
+        v[1] = t.x >> 16;
+        v[2] = t.y;
+    } else {
+        const uint32_t t = static_cast<const uint32_t*>(base)[i];
+        const int sh = fmt == FMT_P10 ? 10 : 8;
+        const uint32_t m = (1u << sh) - 1u;
+        v[0] = t & m;
+        v[1] = (t >> sh) & m;
+        v[2] = t >> (2 * sh);
+    }
+}
+
+// One warp per segment: rounded mean of its pixel coordinates from the segment index. (-1, -1) marks
+// an empty segment.
+__global__ void centroid_kernel(const int32_t* __restrict__ offs, const uint32_t* __restrict__ pix, int S,
+                                int2* __restrict__ centre) {
+    const int lane = threadIdx.x & 31;
+    for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += (gridDim.x * blockDim.x) >> 5) {
+        const int b = offs[s], e = offs[s + 1];
+        long long sx = 0, sy = 0;
+        for (int i = b + lane; i < e; i += 32) {
+            const uint32_t xy = pix[i];
+            sx += xy & 0xffff;
+            sy += xy >> 16;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(kFull, sx, o);
+            sy += __shfl_xor_sync(kFull, sy, o);
+        }
+        if (lane == 0) {
+            const long long n = e - b;
+            centre[s] = n > 0 ? make_int2((int)((2 * sx + n) / (2 * n)), (int)((2 * sy + n) / (2 * n))) : make_int2(-1, -1);
+        }
+    }
+}
+
+struct CentreArgs {
+    const int2* centre;
+    const float* H;         // [N][L][9]
+    const void* ref_tex;    // packed reference view
+    const NbrView* nbrs;    // [N]
+    const int32_t* const* labels_v;  // [N] neighbour label maps (entries may be null)
+    int32_t* m;             // [S][L][N]
+    int32_t* sp;            // [S][L][N]
+    int32_t S, L, N, W, H_, window, penalty, fmt;
+};
+
+__global__ void centre_table_kernel(CentreArgs a) {
+    const int64_t total = (int64_t)a.S * a.L * a.N;
+    const int half = a.window / 2;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e % a.N);
+        const int64_t t = e / a.N;
+        const int d = (int)(t % a.L);
+        const int s = (int)(t / a.L);
+        const int2 c = a.centre[s];
+        const NbrView nv = a.nbrs[k];
+        const float* h = a.H + ((int64_t)k * a.L + d) * 9;
+        bool in = c.x >= 0;
+        int ui = 0, vi = 0;
+        if (in) {
+            const float x = (float)c.x, y = (float)c.y;
+            const float X = __fmaf_rn(h[0], x, __fmaf_rn(h[1], y, h[2]));
+            const float Yh = __fmaf_rn(h[3], x, __fmaf_rn(h[4], y, h[5]));
+            const float Wz = __fmaf_rn(h[6], x, __fmaf_rn(h[7], y, h[8]));
+            in = Wz > 0.0f;
+            if (in) {
+                const float r = __frcp_rn(Wz);
+                const float fu = floorf(__fadd_rn(__fmul_rn(X, r), 0.5f));
+                const float fv = floorf(__fadd_rn(__fmul_rn(Yh, r), 0.5f));
+                in = fu >= 0.0f && fu <= (float)(nv.w - 1) && fv >= 0.0f && fv <= (float)(nv.h - 1);
+                if (in) {
+                    ui = (int)fu;
+                    vi = (int)fv;
+                }
+            }
+        }
+        long long m = 0;
+        for (int dy = -half; dy <= half; ++dy)
+            for (int dx = -half; dx <= half; ++dx) {
+                const int rx = c.x + dx, ry = c.y + dy, qx = ui + dx, qy = vi + dy;
+                if (!in || rx < 0 || rx >= a.W || ry < 0 || ry >= a.H_ || qx < 0 || qx >= nv.w || qy < 0 || qy >= nv.h) {
+                    m += a.penalty;
+                    continue;
+                }
+                int p[3], q[3];
+                texel(a.ref_tex, a.fmt, (int64_t)ry * a.W + rx, p);
+                texel(nv.texels, a.fmt, (int64_t)qy * nv.pitch + qx, q);
+                m += abs(p[0] - q[0]) + abs(p[1] - q[1]) + abs(p[2] - q[2]);
+            }
+        a.m[e] = (int32_t)m;
+        const int32_t* lv = a.labels_v[k];
+        a.sp[e] = (in && lv) ? lv[(int64_t)vi * nv.w + ui] : -1;
+    }
+}
+
+}  // namespace
+}  // namespace ftv
+
+using namespace ftv;
+
+extern "C" ftv_status ftv_centre_table(ftv_ctx* ctx, const void* const* d_planes, const int64_t* pitch_bytes,
+                                       const int32_t* const* d_labels_views, const int32_t* n_segments,
+                                       int32_t window, int32_t* const* d_m, int32_t* const* d_sprime,
+                                       ftv_stream stream) {
+    if (!ctx || !d_planes || !pitch_bytes || !d_labels_views || !n_segments || !d_m || !d_sprime)
+        return FTV_ERR_INVALID_ARG;
+    if (window < 1 || window > 15 || (window & 1) == 0) return FTV_ERR_INVALID_ARG;
+    if (ctx->n_refs > kMaxUnits) return FTV_ERR_INVALID_ARG;
+    for (int i = 0; i < ctx->n_refs; ++i) {
+        const RefState& r = ctx->refs[i];
+        if (!d_labels_views[r.view] || !d_m[i] || !d_sprime[i]) return FTV_ERR_INVALID_ARG;
+        if (n_segments[i] < 0 || n_segments[i] > ctx->max_segments) return FTV_ERR_INVALID_ARG;
+    }
+    for (int v = 0; v < ctx->n_views; ++v)
+        for (int c = 0; c < 3; ++c)
+            if (!d_planes[3 * v + c] || pitch_bytes[3 * v + c] < (int64_t)ctx->cams[v].width * ctx->sample_bytes)
+                return FTV_ERR_INVALID_ARG;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device) cudaSetDevice(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; v < ctx->n_views && e == cudaSuccess; ++v) {
+        e = launch_pack(d_planes + 3 * v, pitch_bytes + 3 * v, ctx->sample_bytes, ctx->bit_depth, ctx->fmt,
+                        ctx->cams[v].width, ctx->cams[v].height,
+                        static_cast<char*>(ctx->d_packed) + ctx->view_offset_bytes[v], ctx->d_status, s);
+        ctx->launches++;
+    }
+    for (int i = 0; i < ctx->n_refs && e == cudaSuccess; ++i) {
+        RefState& r = ctx->refs[i];
+        const int S = n_segments[i];
+        // same int32 bound as ftv_cost_volume, since the index is cached for later volume calls
+        const int64_t one = std::max<int64_t>(ctx->penalty, 3LL * ((1LL << ctx->bit_depth) - 1));
+        const int64_t mpc = ctx->combine == FTV_COMBINE_MIN ? one : one * std::max(1, r.n_nbrs);
+        e = launch_segment_index(d_labels_views[r.view], r.W, r.H, S, mpc, r.d_offs, r.d_cursor, r.d_pix, ctx->d_status,
+                                 s, &ctx->launches);
+        r.S_indexed = S;
+        if (e != cudaSuccess) break;
+        centroid_kernel<<<std::max(1, std::min(65535, (S + 7) / 8)), 256, 0, s>>>(r.d_offs, r.d_pix, S, r.d_centre);
+        ctx->launches++;
+        std::vector<const int32_t*> lv(r.n_nbrs);
+        for (int k = 0; k < r.n_nbrs; ++k) lv[k] = d_labels_views[r.nbrs[k]];
+        // the table of label-map pointers is copied into the reference's scratch, ordered on the stream
+        e = cudaMemcpyAsync(r.d_nbr_labels, lv.data(), sizeof(const int32_t*) * std::max(1, r.n_nbrs),
+                            cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) break;
+        CentreArgs a{};
+        a.centre = r.d_centre;
+        a.H = r.d_H;
+        a.ref_tex = static_cast<char*>(ctx->d_packed) + ctx->view_offset_bytes[r.view];
+        a.nbrs = r.d_nbrs;
+        a.labels_v = r.d_nbr_labels;
+        a.m = d_m[i];
+        a.sp = d_sprime[i];
+        a.S = S;
+        a.L = ctx->L;
+        a.N = r.n_nbrs;
+        a.W = r.W;
+        a.H_ = r.H;
+        a.window = window;
+        a.penalty = ctx->penalty;
+        a.fmt = ctx->fmt;
+        const int64_t total = (int64_t)S * ctx->L * r.n_nbrs;
+        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)ctx->n_sm * 16));
+        if (total > 0) {
+            centre_table_kernel<<<blocks, 256, 0, s>>>(a);
+            ctx->launches++;
+        }
+        e = cudaGetLastError();
+    }
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+    return e == cudaSuccess ? FTV_OK : FTV_ERR_CUDA;
+}

@@ -83,6 +83,8 @@ struct RefState {
     int32_t* d_woffs = nullptr;  // [max_segments + 1]
     uint32_t* d_pix = nullptr;   // [W * H]
     int32_t S_indexed = -1;      // segment count of the cached index (-1: none)
+    int2* d_centre = nullptr;    // [max_segments] segment centres (centre table)
+    const int32_t** d_nbr_labels = nullptr;  // [N] neighbour label maps (centre table)
     std::vector<float> h_H;      // host copy of the table
 };
 

@@ -72,6 +72,7 @@ def _load() -> ctypes.CDLL:
         "ftv_stream_labels": [vp, i32, vp],
         "ftv_stream_mask": [vp, i32, vp, vp],
         "ftv_reciprocal_check": [vp, vp],
+        "ftv_centre_table": [vp, vp, vp, vp, vp, i32, vp, vp, vp],
         "ftv_batch_create": [i32, i32, i32, vp],
         "ftv_batch_destroy": [vp],
         "ftv_batch_prepare": [vp, vp, i32],
@@ -102,7 +103,7 @@ EXPORTED = ["ftv_depth_init", "ftv_depth_destroy", "ftv_compute_homographies", "
             "ftv_get_label_depths", "ftv_segment_index", "ftv_cost_volume", "ftv_temporal_mask",
             "ftv_wta_depth", "ftv_check", "ftv_launch_count", "ftv_status_str", "ftv_set_profiling",
             "ftv_last_kernel_ms", "ftv_temporal_mask_static", "ftv_stream_init", "ftv_stream_footprint",
-            "ftv_stream_labels", "ftv_stream_mask", "ftv_reciprocal_check", "ftv_batch_create", "ftv_batch_destroy", "ftv_batch_prepare", "ftv_batch_launch",
+            "ftv_stream_labels", "ftv_stream_mask", "ftv_reciprocal_check", "ftv_centre_table", "ftv_batch_create", "ftv_batch_destroy", "ftv_batch_prepare", "ftv_batch_launch",
             "ftv_batch_replay", "ftv_batch_query", "ftv_batch_wait", "ftv_batch_launch_count"]
 
 
@@ -442,3 +443,18 @@ def ftv_reciprocal_check() -> tuple[int, bool]:
     n, used = ctypes.c_int64(), ctypes.c_int32()
     _ok(lib.ftv_reciprocal_check(ctypes.byref(n), ctypes.byref(used)), "ftv_reciprocal_check")
     return int(n.value), bool(used.value)
+
+
+def ftv_centre_table(ctx: Context, planes, labels_views, n_segments, window: int, m_out, sprime_out,
+                     stream=None) -> None:
+    """planes as in ftv_cost_volume; labels_views: per view an int32 [H][W] tensor or None;
+    m_out / sprime_out: per reference int32 [S][L][N] tensors."""
+    ptrs, pitches = [], []
+    for trip in planes:
+        for t in trip:
+            ptrs.append(_ptr(t))
+            pitches.append(int(t.stride(0)) * t.element_size())
+    _ok(lib.ftv_centre_table(ctx.handle, _arr(ctypes.c_void_p, ptrs), _arr(ctypes.c_int64, pitches),
+                             _arr(ctypes.c_void_p, [_ptr(l) for l in labels_views]), _arr(ctypes.c_int32, n_segments),
+                             window, _arr(ctypes.c_void_p, [_ptr(t) for t in m_out]),
+                             _arr(ctypes.c_void_p, [_ptr(t) for t in sprime_out]), _stream(stream)), "ftv_centre_table")

@@ -1,0 +1,42 @@
+"""GPU parity of the centre table (Eq. 4 at segment centres with the Eq. 5 correspondence s')."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synth.configs import make_workload
+
+pytestmark = pytest.mark.gpu
+
+ftv = pytest.importorskip("paper_1909_02294_gb300")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from gpu_runs import Run, dev  # noqa: E402
+
+
+@pytest.mark.parametrize("name,window,drop", [("tiny", 3, None), ("tiny", 5, 0), ("hd8", 3, 2), ("uhd15", 3, 1)])
+def test_centre_table_bit_exact(name, window, drop):
+    wl = make_workload(name, reduced=(name != "tiny"))
+    run = Run(wl)
+    labels_h = [wl.labels(v)[0] for v in range(wl.n_views)]
+    if drop is not None and drop not in wl.ref_views:
+        labels_h[drop] = None  # a neighbour without a segmentation: s' = -1 there
+    labels_d = [dev(l) if l is not None else None for l in labels_h]
+    L = wl.n_labels
+    ms, sps = [], []
+    for i, r in enumerate(wl.ref_views):
+        n = len(wl.neighbours(r))
+        ms.append(torch.empty((run.S[i], L, n), dtype=torch.int32, device="cuda"))
+        sps.append(torch.empty((run.S[i], L, n), dtype=torch.int32, device="cuda"))
+    ftv.ftv_centre_table(run.ctx, run.planes(), labels_d, run.S, window, ms, sps)
+    assert run.check() == 0
+    for i, r in enumerate(wl.ref_views):
+        H = oracle.homography_table(wl.cams, r, wl.neighbours(r), L, wl.z_near, wl.z_far)
+        m, sp = oracle.centre_table(wl.cams, wl.views(), wl.sample_bytes, r, wl.neighbours(r), H, L, labels_h,
+                                    run.S[i], window, wl.oob_penalty)
+        assert np.array_equal(ms[i].cpu().numpy(), m), (name, r)
+        assert np.array_equal(sps[i].cpu().numpy(), sp), (name, r)
+    run.close()
