@@ -47,7 +47,7 @@ def _load():
         _lib = ctypes.CDLL(build())
         for name in ["or_label_inv_depths", "or_homography_f64", "or_homography_table", "or_cost_volume",
                      "or_cost_entries", "or_fp64_mismatch", "or_temporal_mask", "or_wta", "or_depth_map",
-                     "or_centre_table"]:
+                     "or_centre_table", "or_adjacency"]:
             getattr(_lib, name).restype = ctypes.c_int
     return _lib
 
@@ -214,3 +214,22 @@ def centre_table(cams, views, sample_bytes: int, ref: int, nbrs, H: np.ndarray, 
                                    ctypes.c_int(S), ctypes.c_int(window), ctypes.c_int(penalty), _p(m), _p(sp)),
            "centre_table")
     return m, sp
+
+
+def adjacency(labels: np.ndarray, S: int, frame, sample_bytes: int, connectivity: int = 4, beta0: float = 1.0,
+              min_diff: float = 1.0, cap: int | None = None):
+    """(edge_s int32, edge_t int32, beta float32) of or_adjacency, edges in increasing (s, t) order."""
+    lab = np.ascontiguousarray(labels, np.int32)
+    H, W = lab.shape
+    im, keep = _imgs([frame])
+    cap = cap if cap is not None else 4 * H * W + 1
+    es = np.empty(cap, np.int32)
+    et = np.empty(cap, np.int32)
+    bt = np.empty(cap, np.float32)
+    n = ctypes.c_int32(0)
+    _check(_load().or_adjacency(ctypes.c_int(W), ctypes.c_int(H), _p(lab), ctypes.c_int(S), ctypes.byref(im[0]),
+                                ctypes.c_int(sample_bytes), ctypes.c_int(connectivity), ctypes.c_double(beta0),
+                                ctypes.c_double(min_diff), ctypes.c_int(cap), _p(es), _p(et), _p(bt),
+                                ctypes.byref(n)), "adjacency")
+    k = min(n.value, cap)
+    return es[:k].copy(), et[:k].copy(), bt[:k].copy()

@@ -515,3 +515,74 @@ int or_centre_table(const or_camera* cams, int n_views, const or_image* imgs, in
     free(cnt);
     return 0;
 }
+
+/* -------------------------------------------------------------------- adjacency and beta */
+
+static int cmp_u64(const void* a, const void* b) {
+    uint64_t x = *(const uint64_t*)a, y = *(const uint64_t*)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/*
+ * Intra-view discontinuity weights of Eq. 2-3 (Sec. III-D): the segments s < t that are adjacent (some
+ * pixel of s and some pixel of t are neighbours: 4-connected, or 8-connected with connectivity 8),
+ * listed in increasing (s, t) order, and for each edge beta = beta0 / || mean_s - mean_t ||_1, the
+ * L1 distance of the segments' mean (Y, Cb, Cr) vectors in this frame. The paper leaves a zero
+ * distance open: the distance is floored at min_diff (a distance below it counts as min_diff). With
+ * per-channel sums S and counts n the distance is sum_c |S_cs n_t - S_ct n_s| / (n_s n_t), evaluated
+ * as beta = beta0 * (n_s n_t) / num in double (num the exact int64 numerator), and rounded to float.
+ * Returns the number of edges in *n_edges (at most cap are written).
+ */
+int or_adjacency(int W, int Hh, const int32_t* labels, int S, const or_image* frame, int sample_bytes,
+                 int connectivity, double beta0, double min_diff, int cap, int32_t* edge_s, int32_t* edge_t,
+                 float* beta, int32_t* n_edges) {
+    if (!labels || S < 0 || !frame || (connectivity != 4 && connectivity != 8) || !n_edges) return 1;
+    size_t P = (size_t)W * Hh, maxp = P * 4 + 1, np = 0;
+    uint64_t* pairs = (uint64_t*)malloc(sizeof(uint64_t) * maxp);
+    int64_t* sum = (int64_t*)calloc((size_t)S * 4 + 4, sizeof(int64_t));
+    if (!pairs || !sum) { free(pairs); free(sum); return 1; }
+    static const int dxs[4] = {1, 0, 1, -1}, dys[4] = {0, 1, 1, 1};
+    int ndir = connectivity == 8 ? 4 : 2;
+    for (int y = 0; y < Hh; y++)
+        for (int x = 0; x < W; x++) {
+            int s = labels[(size_t)y * W + x];
+            if (s < 0 || s >= S) { free(pairs); free(sum); return 2; }
+            sum[(size_t)s * 4 + 0]++;
+            for (int c = 0; c < 3; c++) sum[(size_t)s * 4 + 1 + c] += sample_at(frame, sample_bytes, c, x, y);
+            for (int k = 0; k < ndir; k++) {
+                int qx = x + dxs[k], qy = y + dys[k];
+                if (qx < 0 || qx >= W || qy < 0 || qy >= Hh) continue;
+                int t = labels[(size_t)qy * W + qx];
+                if (t < 0 || t >= S) { free(pairs); free(sum); return 2; }
+                if (t == s) continue;
+                uint64_t a = (uint64_t)(s < t ? s : t), b = (uint64_t)(s < t ? t : s);
+                pairs[np++] = (a << 32) | b;
+            }
+        }
+    qsort(pairs, np, sizeof(uint64_t), cmp_u64);
+    int32_t e = 0;
+    for (size_t i = 0; i < np; i++) {
+        if (i > 0 && pairs[i] == pairs[i - 1]) continue;
+        int s = (int)(pairs[i] >> 32), t = (int)(pairs[i] & 0xffffffffu);
+        if (e < cap) {
+            const int64_t* a = &sum[(size_t)s * 4];
+            const int64_t* b = &sum[(size_t)t * 4];
+            int64_t num = 0;
+            for (int c = 1; c <= 3; c++) {
+                int64_t d = a[c] * b[0] - b[c] * a[0];
+                num += d < 0 ? -d : d;
+            }
+            double den = (double)(a[0] * b[0]);
+            double dist = (double)num / den;
+            double bt = dist < min_diff ? beta0 / min_diff : (beta0 * den) / (double)num;
+            if (edge_s) edge_s[e] = s;
+            if (edge_t) edge_t[e] = t;
+            if (beta) beta[e] = (float)bt;
+        }
+        e++;
+    }
+    *n_edges = e;
+    free(pairs);
+    free(sum);
+    return 0;
+}
