@@ -337,6 +337,24 @@ FTV_API ftv_status ftv_centre_table(ftv_ctx* ctx, const void* const* d_planes, c
                                     const int32_t* const* d_labels_views, const int32_t* n_segments, int32_t window,
                                     int32_t* const* d_m, int32_t* const* d_sprime, ftv_stream stream);
 
+/*
+ * Segment adjacency and adaptive smoothing weights of Sec. III-D (Eq. 2-3) for reference ref_index:
+ * the adjacent segment pairs s < t of label map d_labels (int32 [H][W], n_segments segments; pixels
+ * 4-connected, or also diagonally with connectivity 8), in increasing (s, t) order, and for each pair
+ * beta = beta0 / || mean YCbCr_s - mean YCbCr_t ||_1 in the colours of d_frame (3 device planes, pitches
+ * in bytes). The paper leaves a zero distance open: distances below min_diff (> 0) count as min_diff.
+ * The distance is the exact rational sum_c |S_cs n_t - S_ct n_s| / (n_s n_t) and beta is formed in
+ * double as beta0 * (n_s n_t) / numerator, then rounded to float (exact for n_s n_t 3 (2^bd - 1) < 2^63).
+ * Writes min(count, capacity) edges to d_edge_s, d_edge_t, d_beta and the full count to *d_n_edges
+ * (device). A segment with more than 32 neighbours t > s sets FTV_ERR_OVERFLOW in the status word
+ * (its list is truncated). Also (re)builds the reference's cached segment index. Asynchronous.
+ */
+FTV_API ftv_status ftv_adjacency(ftv_ctx* ctx, int32_t ref_index, const void* const* d_frame,
+                                 const int64_t* frame_pitch, const int32_t* d_labels, int32_t n_segments,
+                                 int32_t connectivity, double beta0, double min_diff, int32_t capacity,
+                                 int32_t* d_edge_s, int32_t* d_edge_t, float* d_beta, int32_t* d_n_edges,
+                                 ftv_stream stream);
+
 /* Wait for `stream`, then return and clear the context's device status word (FTV_OK if clean). */
 FTV_API ftv_status ftv_check(ftv_ctx* ctx, ftv_stream stream);
 

@@ -58,6 +58,9 @@ void free_ctx(ftv_ctx* c) {
     cudaFree(c->d_plan);
     cudaFree(c->d_tstats);
     cudaFree(c->d_label_z);
+    cudaFree(c->d_adj_deg);
+    cudaFree(c->d_adj_slots);
+    cudaFree(c->d_adj_offs);
     if (c->ev_start) cudaEventDestroy(c->ev_start);
     if (c->ev_stop) cudaEventDestroy(c->ev_stop);
     delete c;
@@ -200,6 +203,9 @@ ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out) {
     ok = ok && dalloc(&c->d_plan, 1) == cudaSuccess;
     ok = ok && dalloc(&c->d_tstats, (size_t)c->max_segments * 8) == cudaSuccess;
     ok = ok && dalloc(&c->d_label_z, (size_t)c->L) == cudaSuccess;
+    ok = ok && dalloc(&c->d_adj_deg, (size_t)c->max_segments) == cudaSuccess;
+    ok = ok && dalloc(&c->d_adj_slots, (size_t)c->max_segments * 32) == cudaSuccess;
+    ok = ok && dalloc(&c->d_adj_offs, (size_t)c->max_segments) == cudaSuccess;
     for (auto& r : c->refs) {
         ok = ok && dalloc(&r.d_H, r.h_H.size()) == cudaSuccess;
         ok = ok && dalloc(&r.d_nbrs, (size_t)r.n_nbrs) == cudaSuccess;

@@ -136,6 +136,9 @@ struct ftv_ctx {
     ftv::Plan* d_plan = nullptr;
     int64_t* d_tstats = nullptr;              // temporal accumulators [max_segments][7]
     float* d_label_z = nullptr;               // [L]
+    int32_t* d_adj_deg = nullptr;             // [max_segments] adjacency: neighbours t > s per segment
+    int32_t* d_adj_slots = nullptr;           // [max_segments][32]
+    int32_t* d_adj_offs = nullptr;            // [max_segments]
     int64_t launches = 0;
     bool profiling = false;
     bool timed = false;

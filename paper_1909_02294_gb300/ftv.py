@@ -73,6 +73,8 @@ def _load() -> ctypes.CDLL:
         "ftv_stream_mask": [vp, i32, vp, vp],
         "ftv_reciprocal_check": [vp, vp],
         "ftv_centre_table": [vp, vp, vp, vp, vp, i32, vp, vp, vp],
+        "ftv_adjacency": [vp, i32, vp, vp, vp, i32, i32, ctypes.c_double, ctypes.c_double, i32, vp, vp, vp, vp,
+                          vp],
         "ftv_batch_create": [i32, i32, i32, vp],
         "ftv_batch_destroy": [vp],
         "ftv_batch_prepare": [vp, vp, i32],
@@ -103,7 +105,7 @@ EXPORTED = ["ftv_depth_init", "ftv_depth_destroy", "ftv_compute_homographies", "
             "ftv_get_label_depths", "ftv_segment_index", "ftv_cost_volume", "ftv_temporal_mask",
             "ftv_wta_depth", "ftv_check", "ftv_launch_count", "ftv_status_str", "ftv_set_profiling",
             "ftv_last_kernel_ms", "ftv_temporal_mask_static", "ftv_stream_init", "ftv_stream_footprint",
-            "ftv_stream_labels", "ftv_stream_mask", "ftv_reciprocal_check", "ftv_centre_table", "ftv_batch_create", "ftv_batch_destroy", "ftv_batch_prepare", "ftv_batch_launch",
+            "ftv_stream_labels", "ftv_stream_mask", "ftv_reciprocal_check", "ftv_centre_table", "ftv_adjacency", "ftv_batch_create", "ftv_batch_destroy", "ftv_batch_prepare", "ftv_batch_launch",
             "ftv_batch_replay", "ftv_batch_query", "ftv_batch_wait", "ftv_batch_launch_count"]
 
 
@@ -458,3 +460,13 @@ def ftv_centre_table(ctx: Context, planes, labels_views, n_segments, window: int
                              _arr(ctypes.c_void_p, [_ptr(l) for l in labels_views]), _arr(ctypes.c_int32, n_segments),
                              window, _arr(ctypes.c_void_p, [_ptr(t) for t in m_out]),
                              _arr(ctypes.c_void_p, [_ptr(t) for t in sprime_out]), _stream(stream)), "ftv_centre_table")
+
+
+def ftv_adjacency(ctx: Context, ref_index: int, frame, labels, n_segments: int, connectivity: int, beta0: float,
+                  min_diff: float, edge_s, edge_t, beta, n_edges, stream=None) -> None:
+    """frame: (Y, Cb, Cr) tensors; edge_s/edge_t int32, beta float32 tensors of equal capacity;
+    n_edges: one-element int32 tensor receiving the edge count."""
+    fp, fpi = _trip(frame)
+    _ok(lib.ftv_adjacency(ctx.handle, ref_index, fp, fpi, _ptr(labels), n_segments, connectivity, beta0, min_diff,
+                          int(edge_s.numel()) if edge_s is not None else 0, _ptr(edge_s), _ptr(edge_t), _ptr(beta),
+                          _ptr(n_edges), _stream(stream)), "ftv_adjacency")
