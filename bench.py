@@ -33,6 +33,23 @@ UNIT = "evals/s"
 WORKLOAD = "hd8"
 
 
+def reduce_max(value: float, device) -> float:
+    """Largest value over the ranks of the default process group (the value itself without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, slowest_seconds: float) -> float:
+    """Whole-job throughput of `world` replicas that each processed units_per_rank units, timed by the
+    slowest rank."""
+    return world * units_per_rank / slowest_seconds
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -292,13 +309,9 @@ def main():
     if world > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1000.0
-    if world > 1:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = reduce_max(sum(step_ms) / 1000.0, dev)
     evals = wl.evaluations()
-    value = world * evals * args.steps / total_s
+    value = whole_job_rate(world, evals * args.steps, total_s)
     st = ftv.ftv_check(ctx)
     if st != 0:
         raise RuntimeError(f"device status {ftv.ftv_status_str(st)}")
@@ -325,12 +338,8 @@ def main():
         b.record(stream)
         e2e_ev.append((a, b))
     torch.cuda.synchronize()
-    e2e_s = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1000.0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * evals * len(e2e_ev) / e2e_s
+    e2e_s = reduce_max(sum(a.elapsed_time(b) for a, b in e2e_ev) / 1000.0, dev)
+    e2e_value = whole_job_rate(world, evals * len(e2e_ev), e2e_s)
 
     if rank == 0:
         peak, peak_kind = _peaks()
@@ -349,7 +358,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+i32", "data": "synthetic",
             "config": {"workload": _workload_desc(wl), "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "depth_maps_per_s": world * R * args.steps / total_s,
+                       "depth_maps_per_s": whole_job_rate(world, R * args.steps, total_s),
                        "cost_kernel_ms": kms, "evaluations_per_step": evals},
             "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Tops/s",
                          "frac": alu_achieved / alu_peak, "traffic": traffic,
