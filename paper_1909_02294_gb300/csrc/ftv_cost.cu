@@ -89,6 +89,9 @@ struct TexelOps<FMT_U16X4> {
 //   kAffine   h6 == h7 == 0: Wz = fma(h6, x, fma(h7, y, h8)) is exactly h8 for every pixel, so
 //             r = 1/h8 is computed once at staging time and stored in place of h6;
 //   kUnit     affine with r == 1: u = X * 1 is exactly X, the multiplications are skipped;
+//   kRect     unit with h0 = 1, h1 = 0, h3 = 0, h4 = 1, |h5| < 0.25 (rectified rigs: the row is kept):
+//             X = fma(1, x, fma(0, y, h2)) is x + h2 rounded once, and Y = y + h5 rounded once lies
+//             within 0.25 + 2^-9 of the integer y < 2^15, so floor(Y + 0.5) is exactly y;
 //   kOut      affine with 1/h8 not finite and positive: every sample is out of view.
 // All of them give bit-identical results to the general sequence; they only skip work whose result
 // is known exactly.
@@ -96,7 +99,7 @@ struct __align__(16) HEntry {
     float h[9];
     uint32_t w, h_, pm;
 };
-enum : uint32_t { kGeneral = 0, kAffine = 1, kUnit = 2, kOut = 3 };
+enum : uint32_t { kGeneral = 0, kAffine = 1, kUnit = 2, kOut = 3, kRect = 4 };
 constexpr uint32_t kPitchMask = (1u << 28) - 1u;
 
 __device__ __forceinline__ bool finite_positive(float r) {
@@ -166,6 +169,17 @@ __device__ __forceinline__ int sample_cost_affine(const float4& a, const float4&
     const bool ok = ((unsigned)ui < __float_as_uint(c.y)) & ((unsigned)vi < __float_as_uint(c.z));
     int cst = penalty;
     if (ok) cst = TexelOps<FMT>::cost(tex, vi * pitch + ui, ra, rb, rc);
+    return cst;
+}
+
+// Rectified entries (kRect): u = x + h2, the sample row is the reference row y.
+template <int FMT>
+__device__ __forceinline__ int sample_cost_rect(float h2, uint32_t wv, uint32_t hv, int pitch, float x, int iy, int ra,
+                                                int rb, int rc, const void* tex, int penalty) {
+    const int ui = __float2int_rd(__fadd_rn(__fadd_rn(x, h2), 0.5f));
+    const bool ok = ((unsigned)ui < wv) & ((unsigned)iy < hv);
+    int cst = penalty;
+    if (ok) cst = TexelOps<FMT>::cost(tex, iy * pitch + ui, ra, rb, rc);
     return cst;
 }
 
@@ -240,6 +254,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
             if (E.h[6] == 0.0f && E.h[7] == 0.0f) {
                 const float r = __frcp_rn(E.h[8]);
                 mode = !finite_positive(r) ? kOut : (r == 1.0f ? kUnit : kAffine);
+                if (mode == kUnit && E.h[0] == 1.0f && E.h[1] == 0.0f && E.h[3] == 0.0f && E.h[4] == 1.0f &&
+                    fabsf(E.h[5]) < 0.25f)
+                    mode = kRect;
                 E.h[6] = r;
             }
             E.w = (uint32_t)nbrs[n].w;
@@ -261,11 +278,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
 
         // this thread's pixels
         float px[kPPT], py[kPPT];
-        int ra[kPPT], rb[kPPT], rc[kPPT], key[kPPT];
+        int ra[kPPT], rb[kPPT], rc[kPPT], key[kPPT], iy[kPPT];
 #pragma unroll
         for (int j = 0; j < kPPT; ++j) {
             const int w = w0 + j * kThreads + tid;
             key[j] = kSentinel;
+            iy[j] = 0;
             px[j] = py[j] = 0.0f;
             ra[j] = rb[j] = rc[j] = 0;
             if (w < w1) {
@@ -278,6 +296,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                 const int x = xy & 0xffff, y = xy >> 16;
                 px[j] = (float)x;
                 py[j] = (float)y;
+                iy[j] = y;
                 TexelOps<FMT>::unpack_ref(ref_tex, (int64_t)y * W + x, ra[j], rb[j], rc[j]);
                 key[j] = k - k0;
             }
@@ -299,6 +318,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                     for (int j = 0; j < kPPT; ++j) {
                         const int c = sample_cost<FMT, FAST_RCP>(ha, hb, hc, pitch, px[j], py[j], ra[j], rb[j],
                                                                  rc[j], tex, penalty);
+                        m[j] = (COMB == FTV_COMBINE_MIN) ? min(m[j], c) : m[j] + c;
+                    }
+                } else if (mode == kRect) {
+#pragma unroll
+                    for (int j = 0; j < kPPT; ++j) {
+                        const int c = sample_cost_rect<FMT>(ha.z, __float_as_uint(hc.y), __float_as_uint(hc.z), pitch,
+                                                            px[j], iy[j], ra[j], rb[j], rc[j], tex, penalty);
                         m[j] = (COMB == FTV_COMBINE_MIN) ? min(m[j], c) : m[j] + c;
                     }
                 } else if (mode == kUnit) {

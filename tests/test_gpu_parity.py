@@ -115,15 +115,25 @@ def test_affine_and_out_of_view_homography_modes():
     for C in ([0.0, 0.0, 0.3], [0.02, 0.0, 1.0]):
         R = np.eye(3)
         wl.cams.append(synth.Camera(base.K.copy(), R, -R @ np.array(C), base.width, base.height))
-    wl.nbr_views = {1: [0, 3, 4]}
-    run = Run(wl, nbr_lists=[[0, 3, 4]])
+    # a parallel camera with another focal length and a vertical offset: affine with unit scale but not
+    # row-preserving (h0 != 1, h5 far from 0), next to the rectified views 0 and 2
+    K2 = base.K.copy()
+    K2[0, 0] *= 1.1
+    K2[1, 1] *= 1.1
+    wl.cams.append(synth.Camera(K2, np.eye(3), -np.array([0.03, 0.02, 0.0]), base.width, base.height))
+    lists = [[0, 3, 4, 5, 2]]
+    wl.nbr_views = {1: lists[0]}
+    run = Run(wl, nbr_lists=lists)
     for combine in ("min", "sum"):
         run.close()
-        run = Run(wl, nbr_lists=[[0, 3, 4]], combine=combine)
+        run = Run(wl, nbr_lists=lists, combine=combine)
         costs = run.volumes()
         assert run.check() == 0
-        ref = _oracle_all(wl, combine=combine, nbr_lists=[[0, 3, 4]])
+        ref = _oracle_all(wl, combine=combine, nbr_lists=lists)
         _assert_equal(costs[0], ref[0], f"affine modes ({combine})")
+    H5 = oracle.homography_table(wl.cams, 1, [5, 0], wl.n_labels, wl.z_near, wl.z_far)
+    assert np.all(H5[0, :, 8] == 1.0) and np.all(H5[0, :, 0] != 1.0)  # unit, not rectified
+    assert np.all(H5[1, :, 0] == 1.0) and np.all(H5[1, :, 4] == 1.0) and np.all(H5[1, :, 3] == 0.0)  # rectified
     H = oracle.homography_table(wl.cams, 1, [3, 4], wl.n_labels, wl.z_near, wl.z_far)
     assert np.all(H[:, :, 6] == 0) and np.all(H[:, :, 7] == 0)
     assert np.any(H[0, :, 8] != 1.0) and np.any(H[1, :, 8] <= 0) and np.any(H[1, :, 8] > 0)
