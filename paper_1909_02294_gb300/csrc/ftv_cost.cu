@@ -203,6 +203,24 @@ __device__ __forceinline__ int upper_index(const int32_t* a, int lo, int hi, int
     return lo;
 }
 
+// Warp-cooperative version (all 32 lanes call it): 32 probes per round narrow the range ~33-fold, so a
+// search over n entries takes about log33(n) dependent loads instead of log2(n).
+__device__ __forceinline__ int warp_upper_index(const int32_t* a, int lo, int hi, int w) {
+    const int lane = threadIdx.x & 31;
+    while (hi - lo > 32) {
+        const int64_t span = hi - lo;
+        const bool le = a[lo + (int)(span * (lane + 1) / 33)] <= w;
+        const int cnt = __popc(__ballot_sync(0xffffffffu, le));  // the true probes are a prefix
+        const int nlo = cnt ? lo + (int)(span * cnt / 33) : lo;
+        const int nhi = cnt < 32 ? lo + (int)(span * (cnt + 1) / 33) : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    const int p = lo + lane;
+    const unsigned m = __ballot_sync(0xffffffffu, p < hi && a[p] <= w);
+    return lo + 31 - __clz(m);
+}
+
 template <int FMT, int COMB, bool FAST_RCP>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob* __restrict__ jobs,
                                                                     Plan* __restrict__ plan) {
@@ -264,9 +282,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
             E.pm = (uint32_t)nbrs[n].pitch | (mode << 28);
         }
         for (int i = tid; i < N; i += kThreads) sBase[i] = nbrs[i].texels;
-        if (tid == 0) {
-            s_k0 = upper_index(woffs, 0, n_work + 1, w0);
-            s_k1 = upper_index(woffs, 0, n_work + 1, w1 - 1);
+        if (tid < 32) {
+            const int k = warp_upper_index(woffs, 0, n_work + 1, w0);
+            if (lane == 0) s_k0 = k;
+        } else if (tid < 64) {
+            const int k = warp_upper_index(woffs, 0, n_work + 1, w1 - 1);
+            if (lane == 0) s_k1 = k;
         }
         __syncthreads();
         const int k0 = s_k0, k1 = s_k1;
