@@ -238,6 +238,7 @@ ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out) {
             ok = ok && cudaMemcpy(r.d_nbrs, nv.data(), sizeof(NbrView) * nv.size(), cudaMemcpyHostToDevice) == cudaSuccess;
     }
     c->fast_rcp = fast_reciprocal_exact();
+    c->penalty_floor = (int64_t)c->penalty >= max_sample_cost(c);
     c->cost_blocks_per_sm = cost_blocks_per_sm(c->fmt, c->combine, c->fast_rcp);
     if (!ok) {
         free_ctx(c);
@@ -401,7 +402,7 @@ ftv_status ftv_cost_volume(ftv_ctx* ctx, const void* const* d_planes, const int6
     }
     if (e == cudaSuccess && ctx->profiling) e = cudaEventRecord(ctx->ev_start, s);
     if (e == cudaSuccess) {
-        e = launch_cost(ctx->d_jobs, ctx->d_plan, ctx->fmt, ctx->combine, ctx->fast_rcp,
+        e = launch_cost(ctx->d_jobs, ctx->d_plan, ctx->fmt, ctx->combine, ctx->fast_rcp, ctx->penalty_floor,
                         ctx->n_sm * ctx->cost_blocks_per_sm, s);
         ctx->launches++;
     }

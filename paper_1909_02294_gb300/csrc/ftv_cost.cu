@@ -134,53 +134,63 @@ __device__ __forceinline__ float contract_rcp(float w) {
     return FAST ? rcp_scaled(w) : __frcp_rn(w);
 }
 
-// Cost of one sample: reference pixel (x, y) through homography e.h into one neighbour view.
-// Equivalent to the contract's float test (Wz > 0, 0 <= floor(u + 0.5) <= W - 1, ...): the host
-// guarantees |h| <= 2^100, so X and Y are finite; r = 1/Wz is then finite and positive exactly when
-// Wz > 0 and 1/Wz does not overflow (if it does, u is +-inf or NaN and the contract says "out");
-// with finite positive r, u + 0.5 is finite or +-inf, and floor-to-int with saturation followed by an
-// unsigned range test decides "in view" exactly as the float compares do.
-template <int FMT, bool FAST_RCP>
-__device__ __forceinline__ int sample_cost(const float4& a, const float4& b, const float4& c, int pitch, float x,
-                                           float y, int ra, int rb, int rc, const void* tex, int penalty) {
+// Position of one sample: reference pixel (x, y) through homography e.h into one neighbour view.
+// Returns whether it is in view and its texel index. Equivalent to the contract's float test (Wz > 0,
+// 0 <= floor(u + 0.5) <= W - 1, ...): the host guarantees |h| <= 2^100, so X and Y are finite;
+// r = 1/Wz is then finite and positive exactly when Wz > 0 and 1/Wz does not overflow (if it does, u
+// is +-inf or NaN and the contract says "out"); with finite positive r, u + 0.5 is finite or +-inf,
+// and floor-to-int with saturation followed by an unsigned range test decides "in view" exactly as
+// the float compares do.
+template <bool FAST_RCP>
+__device__ __forceinline__ bool pos_general(const float4& a, const float4& b, const float4& c, int pitch, float x,
+                                            float y, int& idx) {
     const float X = __fmaf_rn(a.x, x, __fmaf_rn(a.y, y, a.z));
     const float Yh = __fmaf_rn(a.w, x, __fmaf_rn(b.x, y, b.y));
     const float Wz = __fmaf_rn(b.z, x, __fmaf_rn(b.w, y, c.x));
     const float r = contract_rcp<FAST_RCP>(Wz);
     const int ui = __float2int_rd(__fadd_rn(__fmul_rn(X, r), 0.5f));
     const int vi = __float2int_rd(__fadd_rn(__fmul_rn(Yh, r), 0.5f));
-    const bool ok = finite_positive(r) & ((unsigned)ui < __float_as_uint(c.y)) & ((unsigned)vi < __float_as_uint(c.z));
-    int cst = penalty;
-    if (ok) cst = TexelOps<FMT>::cost(tex, vi * pitch + ui, ra, rb, rc);
-    return cst;
+    idx = vi * pitch + ui;
+    return finite_positive(r) & ((unsigned)ui < __float_as_uint(c.y)) & ((unsigned)vi < __float_as_uint(c.z));
 }
 
 // Affine entries: r (finite, positive) was hoisted out of the pixel loop; UNIT means r == 1.
-template <int FMT, bool UNIT>
-__device__ __forceinline__ int sample_cost_affine(const float4& a, const float4& b, const float4& c, float r,
-                                                  int pitch, float x, float y, int ra, int rb, int rc,
-                                                  const void* tex, int penalty) {
+template <bool UNIT>
+__device__ __forceinline__ bool pos_affine(const float4& a, const float4& b, const float4& c, float r, int pitch,
+                                           float x, float y, int& idx) {
     const float X = __fmaf_rn(a.x, x, __fmaf_rn(a.y, y, a.z));
     const float Yh = __fmaf_rn(a.w, x, __fmaf_rn(b.x, y, b.y));
     const float u = UNIT ? X : __fmul_rn(X, r);
     const float v = UNIT ? Yh : __fmul_rn(Yh, r);
     const int ui = __float2int_rd(__fadd_rn(u, 0.5f));
     const int vi = __float2int_rd(__fadd_rn(v, 0.5f));
-    const bool ok = ((unsigned)ui < __float_as_uint(c.y)) & ((unsigned)vi < __float_as_uint(c.z));
-    int cst = penalty;
-    if (ok) cst = TexelOps<FMT>::cost(tex, vi * pitch + ui, ra, rb, rc);
-    return cst;
+    idx = vi * pitch + ui;
+    return ((unsigned)ui < __float_as_uint(c.y)) & ((unsigned)vi < __float_as_uint(c.z));
 }
 
 // Rectified entries (kRect): u = x + h2, the sample row is the reference row y.
-template <int FMT>
-__device__ __forceinline__ int sample_cost_rect(float h2, uint32_t wv, uint32_t hv, int pitch, float x, int iy, int ra,
-                                                int rb, int rc, const void* tex, int penalty) {
+__device__ __forceinline__ bool pos_rect(float h2, uint32_t wv, uint32_t hv, int pitch, float x, int iy, int& idx) {
     const int ui = __float2int_rd(__fadd_rn(__fadd_rn(x, h2), 0.5f));
-    const bool ok = ((unsigned)ui < wv) & ((unsigned)iy < hv);
-    int cst = penalty;
-    if (ok) cst = TexelOps<FMT>::cost(tex, iy * pitch + ui, ra, rb, rc);
-    return cst;
+    idx = iy * pitch + ui;
+    return ((unsigned)ui < wv) & ((unsigned)iy < hv);
+}
+
+// Folds one sample into the pixel's running combination over views (min or sum). With the kernel's PF
+// (min only, the penalty at least the largest possible sample cost) the running minimum starts at the
+// penalty, which an out-of-view sample cannot lower; the projective path then lets only in-view
+// samples update it (PF here), which pays off where many samples fall outside (wide convergent
+// baselines), while the rectified and affine paths keep the select form, measured faster there. Both
+// forms give the minimum over in-view costs and penalties of the contract.
+template <int FMT, int COMB, bool PF>
+__device__ __forceinline__ void accumulate(int& m, bool ok, const void* tex, int idx, int a, int b, int c,
+                                           int penalty) {
+    if (COMB == FTV_COMBINE_MIN && PF) {
+        if (ok) m = min(m, TexelOps<FMT>::cost(tex, idx, a, b, c));
+    } else {
+        int cst = penalty;
+        if (ok) cst = TexelOps<FMT>::cost(tex, idx, a, b, c);
+        m = COMB == FTV_COMBINE_MIN ? min(m, cst) : m + cst;
+    }
 }
 
 __device__ __forceinline__ int find_job(const RefJob* __restrict__ jobs, int n_jobs, int item) {
@@ -221,7 +231,7 @@ __device__ __forceinline__ int warp_upper_index(const int32_t* a, int lo, int hi
     return lo + 31 - __clz(m);
 }
 
-template <int FMT, int COMB, bool FAST_RCP>
+template <int FMT, int COMB, bool FAST_RCP, bool PF>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob* __restrict__ jobs,
                                                                     Plan* __restrict__ plan) {
     __shared__ HEntry sH[kHEntries];
@@ -276,6 +286,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                     fabsf(E.h[5]) < 0.25f)
                     mode = kRect;
                 E.h[6] = r;
+                E.h[8] = E.h[2];  // Wz is not needed any more; a rectified entry then reads one float4
             }
             E.w = (uint32_t)nbrs[n].w;
             E.h_ = (uint32_t)nbrs[n].h;
@@ -326,43 +337,48 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
         for (int l = 0; l < LBa; ++l) {
             int m[kPPT];
 #pragma unroll
-            for (int j = 0; j < kPPT; ++j) m[j] = (COMB == FTV_COMBINE_MIN && N > 0) ? INT_MAX : 0;
+            for (int j = 0; j < kPPT; ++j)
+                m[j] = (COMB == FTV_COMBINE_MIN && N > 0) ? (PF ? penalty : INT_MAX) : 0;
             for (int n = 0; n < N; ++n) {
                 const float4* e4 = reinterpret_cast<const float4*>(&sH[n * LBa + l]);
-                const float4 ha = e4[0], hb = e4[1], hc = e4[2];
+                const float4 hc = e4[2];
                 const void* tex = sBase[n];
                 const uint32_t pm = __float_as_uint(hc.w);
                 const uint32_t mode = pm >> 28;
                 const int pitch = (int)(pm & kPitchMask);
-                if (mode == kGeneral) {
+                if (mode == kRect) {
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
-                        const int c = sample_cost<FMT, FAST_RCP>(ha, hb, hc, pitch, px[j], py[j], ra[j], rb[j],
-                                                                 rc[j], tex, penalty);
-                        m[j] = (COMB == FTV_COMBINE_MIN) ? min(m[j], c) : m[j] + c;
+                        int idx;
+                        const bool ok = pos_rect(hc.x, __float_as_uint(hc.y), __float_as_uint(hc.z), pitch, px[j], iy[j],
+                                                 idx);
+                        accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty);
                     }
-                } else if (mode == kRect) {
+                } else if (mode == kGeneral) {
+                    const float4 ha = e4[0], hb = e4[1];
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
-                        const int c = sample_cost_rect<FMT>(ha.z, __float_as_uint(hc.y), __float_as_uint(hc.z), pitch,
-                                                            px[j], iy[j], ra[j], rb[j], rc[j], tex, penalty);
-                        m[j] = (COMB == FTV_COMBINE_MIN) ? min(m[j], c) : m[j] + c;
+                        int idx;
+                        const bool ok = pos_general<FAST_RCP>(ha, hb, hc, pitch, px[j], py[j], idx);
+                        accumulate<FMT, COMB, PF>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty);
                     }
                 } else if (mode == kUnit) {
+                    const float4 ha = e4[0], hb = e4[1];
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
-                        const int c = sample_cost_affine<FMT, true>(ha, hb, hc, 1.0f, pitch, px[j], py[j], ra[j],
-                                                                    rb[j], rc[j], tex, penalty);
-                        m[j] = (COMB == FTV_COMBINE_MIN) ? min(m[j], c) : m[j] + c;
+                        int idx;
+                        const bool ok = pos_affine<true>(ha, hb, hc, 1.0f, pitch, px[j], py[j], idx);
+                        accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty);
                     }
                 } else if (mode == kAffine) {
+                    const float4 ha = e4[0], hb = e4[1];
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
-                        const int c = sample_cost_affine<FMT, false>(ha, hb, hc, hb.z, pitch, px[j], py[j], ra[j],
-                                                                     rb[j], rc[j], tex, penalty);
-                        m[j] = (COMB == FTV_COMBINE_MIN) ? min(m[j], c) : m[j] + c;
+                        int idx;
+                        const bool ok = pos_affine<false>(ha, hb, hc, hb.z, pitch, px[j], py[j], idx);
+                        accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty);
                     }
-                } else {
+                } else if (!(COMB == FTV_COMBINE_MIN && PF)) {
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) m[j] = (COMB == FTV_COMBINE_MIN) ? min(m[j], penalty) : m[j] + penalty;
                 }
@@ -426,7 +442,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
 template <int FMT, int COMB, bool FAST>
 int blocks_per_sm_for() {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cost_kernel<FMT, COMB, FAST>, kThreads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cost_kernel<FMT, COMB, FAST, COMB == FTV_COMBINE_MIN>,
+                                                      kThreads, 0) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }
@@ -485,12 +502,20 @@ int cost_blocks_per_sm(int fmt, int combine, bool fast) {
 #undef FTV_OCC
 }
 
-cudaError_t launch_cost(const RefJob* jobs, const Plan* plan, int fmt, int combine, bool fast, int grid,
+cudaError_t launch_cost(const RefJob* jobs, const Plan* plan, int fmt, int combine, bool fast, bool pf, int grid,
                         cudaStream_t s) {
     Plan* p = const_cast<Plan*>(plan);
-#define FTV_LAUNCH(F, C)                                                        \
-    (fast ? (cost_kernel<F, C, true><<<grid, kThreads, 0, s>>>(jobs, p), 0)     \
-          : (cost_kernel<F, C, false><<<grid, kThreads, 0, s>>>(jobs, p), 0))
+#define FTV_GO(F, C, R, P) cost_kernel<F, C, R, P><<<grid, kThreads, 0, s>>>(jobs, p)
+#define FTV_LAUNCH(F, C)                                           \
+    do {                                                           \
+        if (C == FTV_COMBINE_MIN && pf) {                          \
+            if (fast) FTV_GO(F, C, true, true);                    \
+            else FTV_GO(F, C, false, true);                        \
+        } else {                                                   \
+            if (fast) FTV_GO(F, C, true, false);                   \
+            else FTV_GO(F, C, false, false);                       \
+        }                                                          \
+    } while (0)
     if (fmt == FMT_U8X4) {
         if (combine == FTV_COMBINE_MIN) FTV_LAUNCH(FMT_U8X4, FTV_COMBINE_MIN);
         else FTV_LAUNCH(FMT_U8X4, FTV_COMBINE_SUM);
@@ -502,6 +527,7 @@ cudaError_t launch_cost(const RefJob* jobs, const Plan* plan, int fmt, int combi
         else FTV_LAUNCH(FMT_U16X4, FTV_COMBINE_SUM);
     }
 #undef FTV_LAUNCH
+#undef FTV_GO
     return cudaGetLastError();
 }
 

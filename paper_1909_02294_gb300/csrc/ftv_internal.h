@@ -122,6 +122,7 @@ struct ftv_ctx {
     int32_t n_views = 0, n_refs = 0, L = 0, plane_mode = 0, centre = 0;
     int32_t sample_bytes = 1, bit_depth = 8, penalty = 0, combine = 0, max_segments = 0, fmt = 0;
     bool fast_rcp = false;
+    bool penalty_floor = false;  // penalty >= 3 (2^bit_depth - 1)
     int32_t LB = 0, nLB = 0;
     double z_near = 0, z_far = 0;
     std::vector<ftv_camera> cams;
@@ -171,7 +172,9 @@ cudaError_t launch_zero_rows(int32_t* cost, int L, int S, const int32_t* list, c
 
 // Cost kernel (ftv_cost.cu)
 int cost_blocks_per_sm(int fmt, int combine, bool fast_rcp);
-cudaError_t launch_cost(const RefJob* jobs, const Plan* plan, int fmt, int combine, bool fast_rcp, int grid,
+// pf: the penalty is at least the largest possible sample cost (lets the min combination skip
+// out-of-view samples; see accumulate() in ftv_cost.cu).
+cudaError_t launch_cost(const RefJob* jobs, const Plan* plan, int fmt, int combine, bool fast_rcp, bool pf, int grid,
                         cudaStream_t s);
 // Whether the current device's one-step Newton-Raphson reciprocal equals the IEEE round-to-nearest
 // reciprocal for every float in [2^-126, 2^126) (exhaustive check, run once per device and cached).

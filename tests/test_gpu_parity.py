@@ -43,9 +43,12 @@ def _assert_equal(got, ref, what):
     assert bad == 0, f"{what}: {bad} of {ref.size} entries differ"
 
 
-@pytest.mark.parametrize("combine", ["min", "sum"])
-def test_tiny_volume_wta_and_depth_bit_exact(combine):
+@pytest.mark.parametrize("combine,penalty", [("min", None), ("sum", None), ("min", 100), ("sum", 100)])
+def test_tiny_volume_wta_and_depth_bit_exact(combine, penalty):
+    """penalty 100 is below the largest sample cost (765): the kernel's min keeps out-of-view samples."""
     wl = make_workload("tiny")
+    if penalty is not None:
+        wl.penalty = penalty
     run = Run(wl, combine=combine)
     costs = run.volumes()
     assert run.check() == 0
