@@ -187,6 +187,15 @@ ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out) {
             }
     }
 
+    // Classify the entries the way the cost kernel's staging does: projective-only when no entry has
+    // h6 = h7 = 0, so that no entry takes an affine or rectified path.
+    {
+        bool any_affine = false;
+        for (const auto& r : c->refs)
+            for (size_t e = 0; e < r.h_H.size(); e += 9) any_affine = any_affine || (r.h_H[e + 6] == 0.0f && r.h_H[e + 7] == 0.0f);
+        c->kind = any_affine ? kKindMixed : kKindProjective;
+    }
+
     // device scratch (all host-side validation is done by now)
     if (cudaGetDevice(&c->device) != cudaSuccess) { free_ctx(c); return FTV_ERR_CUDA; }
     cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
@@ -402,7 +411,7 @@ ftv_status ftv_cost_volume(ftv_ctx* ctx, const void* const* d_planes, const int6
     }
     if (e == cudaSuccess && ctx->profiling) e = cudaEventRecord(ctx->ev_start, s);
     if (e == cudaSuccess) {
-        e = launch_cost(ctx->d_jobs, ctx->d_plan, ctx->fmt, ctx->combine, ctx->fast_rcp, ctx->penalty_floor,
+        e = launch_cost(ctx->d_jobs, ctx->d_plan, ctx->fmt, ctx->combine, ctx->fast_rcp, ctx->penalty_floor, ctx->kind,
                         ctx->n_sm * ctx->cost_blocks_per_sm, s);
         ctx->launches++;
     }

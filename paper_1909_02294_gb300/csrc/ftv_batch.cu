@@ -365,6 +365,7 @@ struct ftv_batch {
     int32_t fmt = -1, combine = -1;
     bool fast_rcp = false;
     bool penalty_floor = false;
+    int kind = 0;
     int32_t prepared_units = 0;
     int cost_grid = 0;
     cudaEvent_t done = nullptr;
@@ -372,6 +373,7 @@ struct ftv_batch {
     cudaGraphExec_t exec = nullptr;
     int graph_fmt = -1, graph_combine = -1;
     bool graph_pf = false;
+    int graph_kind = -1;
     int64_t launches = 0;
 };
 
@@ -575,6 +577,7 @@ ftv_status ftv_batch_prepare(ftv_batch* b, const ftv_frame_job* jobs, int32_t n_
     cudaGetLastError();
     int n_views = 0, n_units = 0, fmt = -1, combine = -1;
     bool pf_all = true;
+    int kind = kKindMixed;
     for (int j = 0; j < n_jobs; ++j) {
         const ftv_frame_job& J = jobs[j];
         if (!J.ctx || !J.ctx->stream.ready || !J.d_planes || !J.pitch_bytes) return FTV_ERR_INVALID_ARG;
@@ -587,6 +590,7 @@ ftv_status ftv_batch_prepare(ftv_batch* b, const ftv_frame_job* jobs, int32_t n_
         fmt = J.ctx->fmt;
         combine = J.ctx->combine;
         pf_all = pf_all && J.ctx->penalty_floor;
+        kind = j == 0 ? J.ctx->kind : (kind == J.ctx->kind ? kind : kKindMixed);
         n_views += J.ctx->n_views;
         n_units += J.ctx->n_refs;
         for (int v = 0; v < J.ctx->n_views; ++v)
@@ -725,6 +729,7 @@ ftv_status ftv_batch_prepare(ftv_batch* b, const ftv_frame_job* jobs, int32_t n_
         b->fmt = fmt;
         b->combine = combine;
         b->penalty_floor = pf_all;
+        b->kind = kind;
     }
     b->prepared_units = pu;
     return FTV_OK;
@@ -746,7 +751,7 @@ static cudaError_t enqueue(ftv_batch* b, cudaStream_t s) {
     zero_changed_rows_kernel<<<dim3(64, std::min(b->max_units, 65535)), 256, 0, s>>>(hdr, jobs);
     e = launch_plan_device(jobs, &hdr->n_units, b->d_plan, s);
     if (e != cudaSuccess) return e;
-    e = launch_cost(jobs, b->d_plan, b->fmt, b->combine, b->fast_rcp, b->penalty_floor, b->cost_grid, s);
+    e = launch_cost(jobs, b->d_plan, b->fmt, b->combine, b->fast_rcp, b->penalty_floor, b->kind, b->cost_grid, s);
     if (e != cudaSuccess) return e;
     wta_multi_kernel<<<g, 256, 0, s>>>(hdr, wta);
     depth_multi_kernel<<<g, 256, 0, s>>>(hdr, wta, b->d_status);
@@ -773,7 +778,8 @@ ftv_status ftv_batch_replay(ftv_batch* b, ftv_stream stream) {
     if (prev_dev != b->device) cudaSetDevice(b->device);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
-    if (!b->exec || b->graph_fmt != b->fmt || b->graph_combine != b->combine || b->graph_pf != b->penalty_floor) {
+    if (!b->exec || b->graph_fmt != b->fmt || b->graph_combine != b->combine || b->graph_pf != b->penalty_floor ||
+        b->graph_kind != b->kind) {
         if (b->exec) cudaGraphExecDestroy(b->exec);
         if (b->graph) cudaGraphDestroy(b->graph);
         b->exec = nullptr;
@@ -795,6 +801,7 @@ ftv_status ftv_batch_replay(ftv_batch* b, ftv_stream stream) {
             b->graph_fmt = b->fmt;
             b->graph_combine = b->combine;
             b->graph_pf = b->penalty_floor;
+            b->graph_kind = b->kind;
         }
     }
     if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, s);

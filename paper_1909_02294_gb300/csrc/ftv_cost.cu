@@ -231,7 +231,7 @@ __device__ __forceinline__ int warp_upper_index(const int32_t* a, int lo, int hi
     return lo + 31 - __clz(m);
 }
 
-template <int FMT, int COMB, bool FAST_RCP, bool PF>
+template <int FMT, int COMB, bool FAST_RCP, bool PF, int KIND>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob* __restrict__ jobs,
                                                                     Plan* __restrict__ plan) {
     __shared__ HEntry sH[kHEntries];
@@ -346,7 +346,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                 const uint32_t pm = __float_as_uint(hc.w);
                 const uint32_t mode = pm >> 28;
                 const int pitch = (int)(pm & kPitchMask);
-                if (mode == kRect) {
+                // a projective-only launch (no entry with h6 = h7 = 0) keeps the general path alone; a
+                // rectified-only instantiation measured slower than this mixed loop, so there is none
+                if (KIND == kKindMixed && mode == kRect) {
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
                         int idx;
@@ -354,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                                                  idx);
                         accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty);
                     }
-                } else if (mode == kGeneral) {
+                } else if (KIND == kKindProjective || (KIND == kKindMixed && mode == kGeneral)) {
                     const float4 ha = e4[0], hb = e4[1];
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
@@ -362,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                         const bool ok = pos_general<FAST_RCP>(ha, hb, hc, pitch, px[j], py[j], idx);
                         accumulate<FMT, COMB, PF>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty);
                     }
-                } else if (mode == kUnit) {
+                } else if (KIND == kKindMixed && mode == kUnit) {
                     const float4 ha = e4[0], hb = e4[1];
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
@@ -370,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                         const bool ok = pos_affine<true>(ha, hb, hc, 1.0f, pitch, px[j], py[j], idx);
                         accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty);
                     }
-                } else if (mode == kAffine) {
+                } else if (KIND == kKindMixed && mode == kAffine) {
                     const float4 ha = e4[0], hb = e4[1];
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
@@ -378,7 +380,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                         const bool ok = pos_affine<false>(ha, hb, hc, hb.z, pitch, px[j], py[j], idx);
                         accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty);
                     }
-                } else if (!(COMB == FTV_COMBINE_MIN && PF)) {
+                } else if (KIND == kKindMixed && !(COMB == FTV_COMBINE_MIN && PF)) {
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) m[j] = (COMB == FTV_COMBINE_MIN) ? min(m[j], penalty) : m[j] + penalty;
                 }
@@ -442,7 +444,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
 template <int FMT, int COMB, bool FAST>
 int blocks_per_sm_for() {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cost_kernel<FMT, COMB, FAST, COMB == FTV_COMBINE_MIN>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cost_kernel<FMT, COMB, FAST, COMB == FTV_COMBINE_MIN, kKindMixed>,
                                                       kThreads, 0) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
@@ -502,32 +504,40 @@ int cost_blocks_per_sm(int fmt, int combine, bool fast) {
 #undef FTV_OCC
 }
 
-cudaError_t launch_cost(const RefJob* jobs, const Plan* plan, int fmt, int combine, bool fast, bool pf, int grid,
-                        cudaStream_t s) {
-    Plan* p = const_cast<Plan*>(plan);
-#define FTV_GO(F, C, R, P) cost_kernel<F, C, R, P><<<grid, kThreads, 0, s>>>(jobs, p)
-#define FTV_LAUNCH(F, C)                                           \
-    do {                                                           \
-        if (C == FTV_COMBINE_MIN && pf) {                          \
-            if (fast) FTV_GO(F, C, true, true);                    \
-            else FTV_GO(F, C, false, true);                        \
-        } else {                                                   \
-            if (fast) FTV_GO(F, C, true, false);                   \
-            else FTV_GO(F, C, false, false);                       \
-        }                                                          \
-    } while (0)
-    if (fmt == FMT_U8X4) {
-        if (combine == FTV_COMBINE_MIN) FTV_LAUNCH(FMT_U8X4, FTV_COMBINE_MIN);
-        else FTV_LAUNCH(FMT_U8X4, FTV_COMBINE_SUM);
-    } else if (fmt == FMT_P10) {
-        if (combine == FTV_COMBINE_MIN) FTV_LAUNCH(FMT_P10, FTV_COMBINE_MIN);
-        else FTV_LAUNCH(FMT_P10, FTV_COMBINE_SUM);
+namespace {
+
+template <int FMT, int COMB, bool FAST, bool PF>
+void launch_kind(const RefJob* jobs, Plan* p, int kind, int grid, cudaStream_t s) {
+    if (kind == kKindProjective) cost_kernel<FMT, COMB, FAST, PF, kKindProjective><<<grid, kThreads, 0, s>>>(jobs, p);
+    else cost_kernel<FMT, COMB, FAST, PF, kKindMixed><<<grid, kThreads, 0, s>>>(jobs, p);
+}
+
+template <int FMT, int COMB>
+void launch_fast_pf(const RefJob* jobs, Plan* p, bool fast, bool pf, int kind, int grid, cudaStream_t s) {
+    const bool use_pf = COMB == FTV_COMBINE_MIN && pf;
+    if (fast) {
+        if (use_pf) launch_kind<FMT, COMB, true, true>(jobs, p, kind, grid, s);
+        else launch_kind<FMT, COMB, true, false>(jobs, p, kind, grid, s);
     } else {
-        if (combine == FTV_COMBINE_MIN) FTV_LAUNCH(FMT_U16X4, FTV_COMBINE_MIN);
-        else FTV_LAUNCH(FMT_U16X4, FTV_COMBINE_SUM);
+        if (use_pf) launch_kind<FMT, COMB, false, true>(jobs, p, kind, grid, s);
+        else launch_kind<FMT, COMB, false, false>(jobs, p, kind, grid, s);
     }
-#undef FTV_LAUNCH
-#undef FTV_GO
+}
+
+template <int FMT>
+void launch_comb(const RefJob* jobs, Plan* p, int combine, bool fast, bool pf, int kind, int grid, cudaStream_t s) {
+    if (combine == FTV_COMBINE_MIN) launch_fast_pf<FMT, FTV_COMBINE_MIN>(jobs, p, fast, pf, kind, grid, s);
+    else launch_fast_pf<FMT, FTV_COMBINE_SUM>(jobs, p, fast, pf, kind, grid, s);
+}
+
+}  // namespace
+
+cudaError_t launch_cost(const RefJob* jobs, const Plan* plan, int fmt, int combine, bool fast, bool pf, int kind,
+                        int grid, cudaStream_t s) {
+    Plan* p = const_cast<Plan*>(plan);
+    if (fmt == FMT_U8X4) launch_comb<FMT_U8X4>(jobs, p, combine, fast, pf, kind, grid, s);
+    else if (fmt == FMT_P10) launch_comb<FMT_P10>(jobs, p, combine, fast, pf, kind, grid, s);
+    else launch_comb<FMT_U16X4>(jobs, p, combine, fast, pf, kind, grid, s);
     return cudaGetLastError();
 }
 

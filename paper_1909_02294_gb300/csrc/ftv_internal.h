@@ -123,6 +123,7 @@ struct ftv_ctx {
     int32_t sample_bytes = 1, bit_depth = 8, penalty = 0, combine = 0, max_segments = 0, fmt = 0;
     bool fast_rcp = false;
     bool penalty_floor = false;  // penalty >= 3 (2^bit_depth - 1)
+    int kind = 0;                // entry classification for the cost kernel (kKind*)
     int32_t LB = 0, nLB = 0;
     double z_near = 0, z_far = 0;
     std::vector<ftv_camera> cams;
@@ -174,8 +175,11 @@ cudaError_t launch_zero_rows(int32_t* cost, int L, int S, const int32_t* list, c
 int cost_blocks_per_sm(int fmt, int combine, bool fast_rcp);
 // pf: the penalty is at least the largest possible sample cost (lets the min combination skip
 // out-of-view samples; see accumulate() in ftv_cost.cu).
-cudaError_t launch_cost(const RefJob* jobs, const Plan* plan, int fmt, int combine, bool fast_rcp, bool pf, int grid,
-                        cudaStream_t s);
+// kind: kKindProjective when no homography entry of the launch is affine (h6 = h7 = 0), else kKindMixed;
+// the projective instantiation of the cost kernel has the general path alone.
+enum : int { kKindMixed = 0, kKindProjective = 1 };
+cudaError_t launch_cost(const RefJob* jobs, const Plan* plan, int fmt, int combine, bool fast_rcp, bool pf, int kind,
+                        int grid, cudaStream_t s);
 // Whether the current device's one-step Newton-Raphson reciprocal equals the IEEE round-to-nearest
 // reciprocal for every float in [2^-126, 2^126) (exhaustive check, run once per device and cached).
 bool fast_reciprocal_exact();
