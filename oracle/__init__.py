@@ -47,7 +47,7 @@ def _load():
         _lib = ctypes.CDLL(build())
         for name in ["or_label_inv_depths", "or_homography_f64", "or_homography_table", "or_cost_volume",
                      "or_cost_entries", "or_fp64_mismatch", "or_temporal_mask", "or_wta", "or_depth_map",
-                     "or_centre_table", "or_adjacency"]:
+                     "or_centre_table", "or_adjacency", "or_snic", "or_connectivity", "or_superpixels"]:
             getattr(_lib, name).restype = ctypes.c_int
     return _lib
 
@@ -233,3 +233,41 @@ def adjacency(labels: np.ndarray, S: int, frame, sample_bytes: int, connectivity
                                 ctypes.byref(n)), "adjacency")
     k = min(n.value, cap)
     return es[:k].copy(), et[:k].copy(), bt[:k].copy()
+
+
+def grid_segments(W: int, H: int, S: int) -> int:
+    """Number of grid cells (= labels) of the S x S seed grid: ceil(W / S) * ceil(H / S)."""
+    return -(-W // S) * -(-H // S)
+
+
+def snic(frame, sample_bytes: int, bit_depth: int, S: int, m: int) -> np.ndarray:
+    """int32 [H][W] labels of or_snic (sequential SNIC, the paper's segmentation)."""
+    H, W = np.asarray(frame.Y).shape
+    im, keep = _imgs([frame])
+    out = np.empty((H, W), np.int32)
+    _check(_load().or_snic(ctypes.c_int(W), ctypes.c_int(H), ctypes.byref(im[0]), ctypes.c_int(sample_bytes),
+                           ctypes.c_int(bit_depth), ctypes.c_int(S), ctypes.c_int(m), _p(out)), "snic")
+    return out
+
+
+def connectivity(labels: np.ndarray, K: int, frame, sample_bytes: int) -> np.ndarray:
+    """or_connectivity applied to a copy of labels (int32 [H][W], values in [0, K)), colours from frame."""
+    lab = np.array(labels, np.int32, order="C", copy=True)
+    H, W = lab.shape
+    im, keep = _imgs([frame])
+    _check(_load().or_connectivity(ctypes.c_int(W), ctypes.c_int(H), _p(lab), ctypes.c_int(K), ctypes.byref(im[0]),
+                                   ctypes.c_int(sample_bytes)), "connectivity")
+    return lab
+
+
+def superpixels(frame, sample_bytes: int, bit_depth: int, S: int, m: int, iterations: int,
+                connect: bool = True) -> np.ndarray:
+    """int32 [H][W] labels of or_superpixels (the data-parallel reformulation the GPU computes)."""
+    H, W = np.asarray(frame.Y).shape
+    im, keep = _imgs([frame])
+    out = np.empty((H, W), np.int32)
+    _check(_load().or_superpixels(ctypes.c_int(W), ctypes.c_int(H), ctypes.byref(im[0]),
+                                  ctypes.c_int(sample_bytes), ctypes.c_int(bit_depth), ctypes.c_int(S),
+                                  ctypes.c_int(m), ctypes.c_int(iterations), ctypes.c_int(1 if connect else 0),
+                                  _p(out)), "superpixels")
+    return out

@@ -1,7 +1,7 @@
 /*
  * Plain CPU oracle for the segment x depth-label matching-cost volume, the per-segment temporal
- * consistency test and the winner-take-all readout of Mieloch, Stankiewicz and Domanski,
- * "Depth Map Estimation for Free-Viewpoint Television" (arXiv:1909.02294).
+ * consistency test, the winner-take-all readout and the superpixel segmentation of Mieloch,
+ * Stankiewicz and Domanski, "Depth Map Estimation for Free-Viewpoint Television" (arXiv:1909.02294).
  *
  * TEST INFRASTRUCTURE ONLY. The library under test never links, loads or calls this file; only the
  * tests, the smoke check and the benchmark's CPU-baseline leg do. It shares no code, header, table
@@ -585,4 +585,335 @@ int or_adjacency(int W, int Hh, const int32_t* labels, int S, const or_image* fr
     free(pairs);
     free(sum);
     return 0;
+}
+
+/* ------------------------------------------------------------------ superpixel segmentation */
+
+/*
+ * Segmentation (Sec. IV-C): the label maps the method consumes come from SNIC superpixels computed in
+ * (Y, Cb, Cr) with compactness factor m = 5 and 8-connected segments. The paper gives no more; the
+ * readings both functions below share are:
+ *  - seeds lie on an S x S grid: cell (i, j) covers x in [iS, min(iS + S, W)) and y in
+ *    [jS, min(jS + S, H)), has label j * ceil(W / S) + i, and its seed is the cell's middle pixel
+ *    (iS + (w - 1) / 2, jS + (h - 1) / 2) with w, h the cell's width and height;
+ *  - the distance of pixel p to a cluster with mean position x_k and mean colour c_k is SNIC's (and
+ *    SLIC's) weighting of colour against space, squared and multiplied by S^2:
+ *        D = S^2 * ||c_p - c_k||^2 + m^2 * ||x_p - x_k||^2,
+ *    with colours on the 8-bit scale: for bit depth bd > 8 the spatial term is multiplied by
+ *    4^(bd - 8) instead of dividing the colours, for bd < 8 the colour term by 4^(8 - bd).
+ */
+static void grid_dims(int W, int Hh, int S, int* gw, int* gh) {
+    *gw = (W + S - 1) / S;
+    *gh = (Hh + S - 1) / S;
+}
+
+static int seed_coord(int n, int S, int i) {
+    int w = n - i * S < S ? n - i * S : S;
+    return i * S + (w - 1) / 2;
+}
+
+static void dist_weights(int S, int m, int bd, uint64_t* wc, uint64_t* ws) {
+    *wc = (uint64_t)S * (uint64_t)S;
+    *ws = (uint64_t)m * (uint64_t)m;
+    if (bd > 8) *ws <<= 2 * (bd - 8);
+    if (bd < 8) *wc <<= 2 * (8 - bd);
+}
+
+/* --- sequential SNIC (the segmentation the paper uses), for quality comparison only --- */
+
+typedef struct {
+    double d;
+    int64_t seq;
+    int32_t x, y, k;
+} snic_elem;
+
+static int elem_less(const snic_elem* a, const snic_elem* b) {
+    return a->d < b->d || (a->d == b->d && a->seq < b->seq);
+}
+
+static void heap_push(snic_elem* h, size_t* n, snic_elem e) {
+    size_t i = (*n)++;
+    h[i] = e;
+    while (i > 0) {
+        size_t p = (i - 1) / 2;
+        if (!elem_less(&h[i], &h[p])) break;
+        snic_elem t = h[i]; h[i] = h[p]; h[p] = t;
+        i = p;
+    }
+}
+
+static snic_elem heap_pop(snic_elem* h, size_t* n) {
+    snic_elem top = h[0];
+    h[0] = h[--(*n)];
+    size_t i = 0;
+    for (;;) {
+        size_t l = 2 * i + 1, r = l + 1, s = i;
+        if (l < *n && elem_less(&h[l], &h[s])) s = l;
+        if (r < *n && elem_less(&h[r], &h[s])) s = r;
+        if (s == i) break;
+        snic_elem t = h[i]; h[i] = h[s]; h[s] = t;
+        i = s;
+    }
+    return top;
+}
+
+/*
+ * SNIC (Achanta and Suesstrunk, CVPR 2017), as Sec. IV-C uses it: every seed enters a priority queue
+ * with distance 0; repeatedly the element of least distance (earliest pushed on ties) is taken, and if
+ * its pixel has no label yet the pixel joins the element's cluster, the cluster's running mean of
+ * position and colour absorbs it, and each unlabelled 8-neighbour is pushed with its distance D (in
+ * double, exact means) to that cluster. Labels are the grid labels; every pixel ends labelled.
+ */
+int or_snic(int W, int Hh, const or_image* img, int sample_bytes, int bit_depth, int S, int m, int32_t* labels) {
+    if (W < 1 || Hh < 1 || !img || !labels || S < 1 || m < 0) return 1;
+    int gw, gh;
+    grid_dims(W, Hh, S, &gw, &gh);
+    int K = gw * gh;
+    uint64_t wc, ws;
+    dist_weights(S, m, bit_depth, &wc, &ws);
+    size_t P = (size_t)W * Hh, cap = 8 * P + (size_t)K + 1, n = 0;
+    snic_elem* heap = (snic_elem*)malloc(sizeof(snic_elem) * cap);
+    double* acc = (double*)calloc((size_t)K * 6, sizeof(double)); /* n, sx, sy, sY, sCb, sCr */
+    if (!heap || !acc) { free(heap); free(acc); return 1; }
+    for (size_t p = 0; p < P; p++) labels[p] = -1;
+    int64_t seq = 0;
+    for (int j = 0; j < gh; j++)
+        for (int i = 0; i < gw; i++) {
+            snic_elem e = {0.0, seq++, seed_coord(W, S, i), seed_coord(Hh, S, j), j * gw + i};
+            heap_push(heap, &n, e);
+        }
+    while (n > 0) {
+        snic_elem e = heap_pop(heap, &n);
+        size_t p = (size_t)e.y * W + e.x;
+        if (labels[p] >= 0) continue;
+        labels[p] = e.k;
+        double* a = &acc[(size_t)e.k * 6];
+        a[0] += 1.0;
+        a[1] += e.x;
+        a[2] += e.y;
+        for (int c = 0; c < 3; c++) a[3 + c] += sample_at(img, sample_bytes, c, e.x, e.y);
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                int qx = e.x + dx, qy = e.y + dy;
+                if ((dx == 0 && dy == 0) || qx < 0 || qx >= W || qy < 0 || qy >= Hh) continue;
+                if (labels[(size_t)qy * W + qx] >= 0) continue;
+                double ex = qx - a[1] / a[0], ey = qy - a[2] / a[0], dc = 0.0;
+                for (int c = 0; c < 3; c++) {
+                    double t = sample_at(img, sample_bytes, c, qx, qy) - a[3 + c] / a[0];
+                    dc += t * t;
+                }
+                snic_elem q = {(double)wc * dc + (double)ws * (ex * ex + ey * ey), seq++, qx, qy, e.k};
+                if (n < cap) heap_push(heap, &n, q);
+            }
+    }
+    free(heap);
+    free(acc);
+    return 0;
+}
+
+/* --- the data-parallel reformulation the GPU computes --- */
+
+/* union-find over component names: the root of a set is its smallest name */
+static int32_t uf_find(int32_t* par, int32_t x) {
+    while (par[x] != x) x = par[x];
+    return x;
+}
+
+/*
+ * Connectivity step: makes every label's pixel set 8-connected (Sec. IV-C asks for 8-connected
+ * segments; SNIC's growth gives them by construction, a data-parallel clustering does not).
+ *  - Components are the maximal 8-connected sets of equally labelled pixels, named by their first
+ *    pixel in raster order.
+ *  - A label's main component is its largest (the earliest named on ties). Main components are
+ *    anchored groups that keep their label; every other component starts as an unanchored group.
+ *  - A group's mean colour is M_c = floor((32 S_c + n) / (2 n)) per channel (n pixels, channel
+ *    sums S_c), in 1/16 units.
+ *  - In a round, every unanchored group g picks, among the groups with a pixel 8-adjacent to a pixel
+ *    of g, the group h of least sum_c |M_c(g) - M_c(h)| (the smallest name on ties). All picked
+ *    pairs are merged at once; a merged group is named by its smallest member name and, if it holds
+ *    an anchored group (at most one: only unanchored groups pick), is anchored with that label.
+ *  - Rounds repeat until every group is anchored (each round at least halves the unanchored groups);
+ *    every pixel then takes its group's label.
+ * Labels must lie in [0, K).
+ */
+int or_connectivity(int W, int Hh, int32_t* labels, int K, const or_image* img, int sample_bytes) {
+    if (W < 1 || Hh < 1 || !labels || K < 1 || !img) return 1;
+    size_t P = (size_t)W * Hh;
+    for (size_t p = 0; p < P; p++)
+        if (labels[p] < 0 || labels[p] >= K) return 2;
+    int32_t* comp = (int32_t*)malloc(sizeof(int32_t) * P);
+    int32_t* stack = (int32_t*)malloc(sizeof(int32_t) * P);
+    int32_t* size = (int32_t*)calloc(P, sizeof(int32_t));
+    int32_t* main_of = (int32_t*)malloc(sizeof(int32_t) * (size_t)K);
+    int32_t* grp = (int32_t*)malloc(sizeof(int32_t) * P);  /* group of each component name */
+    int32_t* par = (int32_t*)malloc(sizeof(int32_t) * P);  /* union-find over group names */
+    int32_t* glab = (int32_t*)malloc(sizeof(int32_t) * P); /* label of an anchored group, -1 if none */
+    int64_t* gsum = (int64_t*)malloc(sizeof(int64_t) * P * 4);
+    int64_t* best = (int64_t*)malloc(sizeof(int64_t) * P * 2); /* (distance, name) picked by a group */
+    if (!comp || !stack || !size || !main_of || !grp || !par || !glab || !gsum || !best) {
+        free(comp); free(stack); free(size); free(main_of); free(grp); free(par); free(glab); free(gsum); free(best);
+        return 1;
+    }
+    for (size_t p = 0; p < P; p++) comp[p] = -1;
+    /* flood fill in raster order: the seed pixel of each fill is its component's first pixel */
+    for (size_t p0 = 0; p0 < P; p0++) {
+        if (comp[p0] >= 0) continue;
+        size_t top = 0;
+        comp[p0] = (int32_t)p0;
+        stack[top++] = (int32_t)p0;
+        while (top > 0) {
+            int32_t p = stack[--top];
+            size[p0]++;
+            int x = p % W, y = p / W;
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    int qx = x + dx, qy = y + dy;
+                    if (qx < 0 || qx >= W || qy < 0 || qy >= Hh) continue;
+                    size_t q = (size_t)qy * W + qx;
+                    if (comp[q] >= 0 || labels[q] != labels[p0]) continue;
+                    comp[q] = (int32_t)p0;
+                    stack[top++] = (int32_t)q;
+                }
+        }
+    }
+    for (int k = 0; k < K; k++) main_of[k] = -1;
+    for (size_t r = 0; r < P; r++) {
+        if (comp[r] != (int32_t)r) continue;
+        int k = labels[r];
+        if (main_of[k] < 0 || size[r] > size[main_of[k]]) main_of[k] = (int32_t)r; /* raster order: earliest on ties */
+    }
+    for (size_t r = 0; r < P; r++) {
+        grp[r] = comp[r] == (int32_t)r ? (int32_t)r : -1;
+        glab[r] = (comp[r] == (int32_t)r && main_of[labels[r]] == (int32_t)r) ? labels[r] : -1;
+    }
+    int rc = 0;
+    for (int round = 0;; round++) {
+        int unanchored = 0;
+        for (size_t r = 0; r < P; r++)
+            if (grp[r] == (int32_t)r && glab[r] < 0) unanchored++;
+        if (unanchored == 0) break;
+        if (round > 64) { rc = 3; break; } /* cannot happen: each round at least halves the count */
+        memset(gsum, 0, sizeof(int64_t) * P * 4);
+        for (size_t p = 0; p < P; p++) {
+            int64_t* g = &gsum[(size_t)grp[comp[p]] * 4];
+            int x = (int)(p % W), y = (int)(p / W);
+            g[0]++;
+            for (int c = 0; c < 3; c++) g[1 + c] += sample_at(img, sample_bytes, c, x, y);
+        }
+        for (size_t r = 0; r < P; r++) best[2 * r] = -1;
+        for (size_t p = 0; p < P; p++) {
+            int32_t a = grp[comp[p]];
+            if (glab[a] >= 0) continue;
+            int x = (int)(p % W), y = (int)(p / W);
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    int qx = x + dx, qy = y + dy;
+                    if (qx < 0 || qx >= W || qy < 0 || qy >= Hh) continue;
+                    int32_t b = grp[comp[(size_t)qy * W + qx]];
+                    if (b == a) continue;
+                    const int64_t* sa = &gsum[(size_t)a * 4];
+                    const int64_t* sb = &gsum[(size_t)b * 4];
+                    int64_t d = 0;
+                    for (int c = 1; c <= 3; c++) {
+                        int64_t ma = (32 * sa[c] + sa[0]) / (2 * sa[0]), mb = (32 * sb[c] + sb[0]) / (2 * sb[0]);
+                        d += ma > mb ? ma - mb : mb - ma;
+                    }
+                    int64_t* bt = &best[2 * (size_t)a];
+                    if (bt[0] < 0 || d < bt[0] || (d == bt[0] && b < bt[1])) { bt[0] = d; bt[1] = b; }
+                }
+        }
+        /* merge every picked pair at once */
+        for (size_t r = 0; r < P; r++) par[r] = (int32_t)r;
+        for (size_t r = 0; r < P; r++) {
+            if (grp[r] != (int32_t)r || glab[r] >= 0 || best[2 * r] < 0) continue;
+            int32_t u = uf_find(par, (int32_t)r), v = uf_find(par, (int32_t)best[2 * r + 1]);
+            if (u < v) par[v] = u;
+            else if (v < u) par[u] = v;
+        }
+        for (size_t r = 0; r < P; r++) {
+            if (grp[r] != (int32_t)r || glab[r] < 0) continue;
+            int32_t t = uf_find(par, (int32_t)r);
+            glab[t] = glab[r]; /* the merged group holds this anchored group only */
+        }
+        for (size_t r = 0; r < P; r++)
+            if (grp[r] >= 0) grp[r] = uf_find(par, grp[r]);
+    }
+    if (rc == 0)
+        for (size_t p = 0; p < P; p++) labels[p] = glab[grp[comp[p]]];
+    free(comp); free(stack); free(size); free(main_of); free(grp); free(par); free(glab); free(gsum); free(best);
+    return rc;
+}
+
+/*
+ * Grid-seeded clustering with SNIC's distance, in passes that parallelise (the GPU's reformulation of
+ * Sec. IV-C's segmentation; SNIC's single priority queue does not).
+ *  - Cluster k starts at its seed pixel: mean position and colour are those of the pixel.
+ *  - Means are kept in fixed point with 4 fractional bits: M = floor((32 * sum + n) / (2 n)), the
+ *    nearest multiple of 1/16 (halves rounded up); D is then evaluated exactly in 64-bit integers on
+ *    16 * (pixel value) - M.
+ *  - Assignment pass: a pixel in grid cell (i, j) joins the cluster of least D among the cells
+ *    (i + a, j + b), a, b in {-1, 0, 1}, that exist; ties go to the smallest label.
+ *  - Update: each cluster's mean becomes that of its assigned pixels; a cluster with no pixel keeps it.
+ *  - `iterations` assignment passes run with an update between consecutive passes; the last pass's
+ *    assignment is the clustering, and `connect` then applies or_connectivity.
+ */
+int or_superpixels(int W, int Hh, const or_image* img, int sample_bytes, int bit_depth, int S, int m,
+                   int iterations, int connect, int32_t* labels) {
+    if (W < 1 || Hh < 1 || !img || !labels || S < 1 || m < 0 || iterations < 1) return 1;
+    int gw, gh;
+    grid_dims(W, Hh, S, &gw, &gh);
+    int K = gw * gh;
+    uint64_t wc, ws;
+    dist_weights(S, m, bit_depth, &wc, &ws);
+    int64_t* mean = (int64_t*)malloc(sizeof(int64_t) * (size_t)K * 5); /* 16x: x, y, Y, Cb, Cr */
+    int64_t* sum = (int64_t*)malloc(sizeof(int64_t) * (size_t)K * 6);  /* n, x, y, Y, Cb, Cr */
+    if (!mean || !sum) { free(mean); free(sum); return 1; }
+    for (int j = 0; j < gh; j++)
+        for (int i = 0; i < gw; i++) {
+            int64_t* M = &mean[((size_t)j * gw + i) * 5];
+            int sx = seed_coord(W, S, i), sy = seed_coord(Hh, S, j);
+            M[0] = 16 * (int64_t)sx;
+            M[1] = 16 * (int64_t)sy;
+            for (int c = 0; c < 3; c++) M[2 + c] = 16 * (int64_t)sample_at(img, sample_bytes, c, sx, sy);
+        }
+    for (int it = 0; it < iterations; it++) {
+        for (int y = 0; y < Hh; y++)
+            for (int x = 0; x < W; x++) {
+                int ci = x / S, cj = y / S, best = -1;
+                uint64_t bestD = 0;
+                int64_t v[5] = {16 * (int64_t)x, 16 * (int64_t)y, 0, 0, 0};
+                for (int c = 0; c < 3; c++) v[2 + c] = 16 * (int64_t)sample_at(img, sample_bytes, c, x, y);
+                for (int b = -1; b <= 1; b++)
+                    for (int a = -1; a <= 1; a++) {
+                        int i = ci + a, j = cj + b;
+                        if (i < 0 || i >= gw || j < 0 || j >= gh) continue;
+                        int k = j * gw + i;
+                        const int64_t* M = &mean[(size_t)k * 5];
+                        uint64_t dsp = 0, dcol = 0;
+                        for (int t = 0; t < 2; t++) dsp += (uint64_t)((v[t] - M[t]) * (v[t] - M[t]));
+                        for (int t = 2; t < 5; t++) dcol += (uint64_t)((v[t] - M[t]) * (v[t] - M[t]));
+                        uint64_t D = wc * dcol + ws * dsp;
+                        if (best < 0 || D < bestD) { best = k; bestD = D; } /* labels visited in increasing order */
+                    }
+                labels[(size_t)y * W + x] = best;
+            }
+        if (it + 1 == iterations) break;
+        memset(sum, 0, sizeof(int64_t) * (size_t)K * 6);
+        for (int y = 0; y < Hh; y++)
+            for (int x = 0; x < W; x++) {
+                int64_t* s = &sum[(size_t)labels[(size_t)y * W + x] * 6];
+                s[0] += 1;
+                s[1] += x;
+                s[2] += y;
+                for (int c = 0; c < 3; c++) s[3 + c] += sample_at(img, sample_bytes, c, x, y);
+            }
+        for (int k = 0; k < K; k++) {
+            const int64_t* s = &sum[(size_t)k * 6];
+            if (s[0] == 0) continue;
+            for (int t = 0; t < 5; t++) mean[(size_t)k * 5 + t] = (32 * s[1 + t] + s[0]) / (2 * s[0]);
+        }
+    }
+    free(mean);
+    free(sum);
+    return connect ? or_connectivity(W, Hh, labels, K, img, sample_bytes) : 0;
 }

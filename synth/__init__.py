@@ -222,4 +222,32 @@ def grid_labels(width: int, height: int, cell: int, jitter: int, seed: int) -> t
     return lab, int(n)
 
 
+def mosaic(width: int, height: int, n_regions: int, *, bit_depth: int = 8, noise_sigma: float = 0.0,
+           seed: int = 0) -> View:
+    """Piecewise-constant (Y, Cb, Cr) image: the Voronoi cells of n_regions uniformly drawn sites, each
+    with a uniform random colour, plus rounded N(0, noise_sigma^2) noise clamped to the sample range.
+    plane_id holds each pixel's cell (the ground-truth regions for segmentation quality)."""
+    rng = np.random.default_rng(seed)
+    vmax = (1 << bit_depth) - 1
+    sx = rng.uniform(0, width, n_regions)
+    sy = rng.uniform(0, height, n_regions)
+    col = rng.integers(0, vmax + 1, (n_regions, 3))
+    ys, xs = np.mgrid[0:height, 0:width]
+    rid = np.zeros((height, width), np.int32)
+    best = np.full((height, width), np.inf)
+    for k in range(n_regions):
+        d = (xs - sx[k]) ** 2 + (ys - sy[k]) ** 2
+        closer = d < best
+        best[closer] = d[closer]
+        rid[closer] = k
+    dtype = np.uint8 if bit_depth <= 8 else np.uint16
+    planes = []
+    for c in range(3):
+        v = col[rid, c].astype(np.float64)
+        if noise_sigma > 0:
+            v = v + np.rint(rng.normal(0.0, noise_sigma, v.shape))
+        planes.append(np.clip(v, 0, vmax).astype(dtype))
+    return View(planes[0], planes[1], planes[2], None, rid)
+
+
 from .configs import Workload, make_workload, CONFIG_NAMES  # noqa: E402,F401
