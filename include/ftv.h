@@ -6,7 +6,8 @@
  *     combined over the neighbouring views of Eq. 1),
  *   - the per-segment temporal consistency test of Sec. III-E,
  *   - a winner-take-all readout of the volume (a stand-in for the paper's graph cut, Sec. IV-B),
- *   - a batched form that runs many such jobs in one persistent launch.
+ *   - a batched form that runs many such jobs in one persistent launch,
+ *   - the superpixel segmentation that produces the label maps (Sec. IV-C).
  *
  * Conventions shared by every entry point
  *   - Pointers named d_* are CUDA device pointers owned by the caller; host_* / plain pointers are
@@ -354,6 +355,82 @@ FTV_API ftv_status ftv_adjacency(ftv_ctx* ctx, int32_t ref_index, const void* co
                                  int32_t connectivity, double beta0, double min_diff, int32_t capacity,
                                  int32_t* d_edge_s, int32_t* d_edge_t, float* d_beta, int32_t* d_n_edges,
                                  ftv_stream stream);
+
+/* ------------------------------------------------------------------------ superpixel segmentation -----
+ *
+ * Sec. IV-C: the label maps come from SNIC superpixels computed in (Y, Cb, Cr) with compactness factor
+ * m (the paper uses m = 5) and 8-connected segments. SNIC's single priority queue is sequential; these
+ * entry points compute its data-parallel reformulation, defined exactly as follows.
+ *   - Seeds lie on an S x S grid (S = grid_step): cell (i, j) covers x in [iS, min(iS + S, W)) and
+ *     y in [jS, min(jS + S, H)), has label j * ceil(W/S) + i and seed (iS + (w-1)/2, jS + (h-1)/2) for a
+ *     cell w wide and h high. An image has ceil(W/S) * ceil(H/S) labels (some may end empty).
+ *   - Distance of a pixel (position x, colour c) to a cluster (mean position X, mean colour C):
+ *     D = S^2 ||c - C||^2 + m^2 ||x - X||^2 with colours on the 8-bit scale (for bit depth bd > 8 the
+ *     spatial term is multiplied by 4^(bd - 8), for bd < 8 the colour term by 4^(8 - bd)). Means are
+ *     held in 1/16 units, M = floor((32 sum + n) / (2 n)), and D is evaluated exactly in integers on
+ *     16 * value - M.
+ *   - `iterations` assignment passes: a pixel of cell (i, j) joins the cluster of least D among the cells
+ *     (i + a, j + b), a, b in {-1, 0, 1} (smallest label on ties); between passes each cluster's mean
+ *     becomes that of its pixels (a cluster without pixels keeps its mean). Clusters start at their
+ *     seed pixel.
+ *   - Connectivity: components are the 8-connected sets of equally labelled pixels, named by their first
+ *     pixel in raster order. A label's largest component (earliest named on ties) keeps the label; every
+ *     other component is merged in rounds: each group not yet holding a kept component joins the
+ *     8-adjacent group whose mean colour (rounded to 1/16, L1 over the three channels) is nearest (the
+ *     smallest name on ties), all joins of a round at once, until every group holds one. Every label is
+ *     then one 8-connected set (or empty).
+ * The result is unique, independent of tiling and scheduling.
+ */
+typedef struct ftv_segmenter ftv_segmenter;
+
+#define FTV_SEG_MAX_IMAGES 4096
+#define FTV_SEG_MAX_STEP 64
+
+/*
+ *   n_images            images segmented by one call (views of a rig, frames), 1..FTV_SEG_MAX_IMAGES
+ *   widths, heights     [n_images] sizes, 1..FTV_MAX_DIM (host memory, copied); all pixels of all images
+ *                       together must stay below 2^31 - 1
+ *   sample_bytes        1 (uint8) or 2 (uint16) samples
+ *   bit_depth           significant bits, <= 8 * sample_bytes; samples must not exceed 2^bit_depth - 1
+ *   grid_step           S, 1..FTV_SEG_MAX_STEP
+ *   compactness         m, 0..255
+ *   iterations          assignment passes, 1..64
+ */
+typedef struct ftv_segmenter_config {
+    int32_t n_images;
+    const int32_t* widths;
+    const int32_t* heights;
+    int32_t sample_bytes;
+    int32_t bit_depth;
+    int32_t grid_step;
+    int32_t compactness;
+    int32_t iterations;
+} ftv_segmenter_config;
+
+/* Create a segmenter for a fixed set of image sizes on the current device; allocates its device scratch
+ * (about 100 bytes per pixel) and a pinned staging block. Synchronous. FTV_ERR_INVALID_ARG,
+ * FTV_ERR_OUT_OF_MEMORY. */
+FTV_API ftv_status ftv_segmenter_init(const ftv_segmenter_config* cfg, ftv_segmenter** out);
+
+/* Host: label count of every image, n_segments[n_images] = ceil(W/S) * ceil(H/S). */
+FTV_API ftv_status ftv_segmenter_segments(const ftv_segmenter* sg, int32_t* n_segments);
+
+/* Segment every image. d_planes[3 * n_images]: device Y, Cb, Cr planes of image i at 3i..3i+2, row pitches
+ * in bytes in pitch_bytes[3 * n_images] (>= width * sample_bytes); d_labels[n_images]: device int32 [H][W]
+ * outputs, dense rows. Asynchronous on `stream`, except that it first waits until the previous call's
+ * descriptor upload has left the staging block. One stream at a time per segmenter. A device-side bound
+ * that trips (it cannot on valid input) is reported by ftv_segmenter_check. */
+FTV_API ftv_status ftv_superpixels(ftv_segmenter* sg, const void* const* d_planes, const int64_t* pitch_bytes,
+                                   int32_t* const* d_labels, ftv_stream stream);
+
+/* Wait for `stream`, then return and clear the segmenter's device status word (FTV_OK if clean,
+ * FTV_ERR_TIMEOUT if a bounded loop gave up). */
+FTV_API ftv_status ftv_segmenter_check(ftv_segmenter* sg, ftv_stream stream);
+
+/* Kernel launches this segmenter has enqueued since creation. */
+FTV_API int64_t ftv_segmenter_launch_count(const ftv_segmenter* sg);
+
+FTV_API ftv_status ftv_segmenter_destroy(ftv_segmenter* sg);
 
 /* Wait for `stream`, then return and clear the context's device status word (FTV_OK if clean). */
 FTV_API ftv_status ftv_check(ftv_ctx* ctx, ftv_stream stream);

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libftv.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["ftv_api.cu", "ftv_cost.cu", "ftv_index.cu", "ftv_temporal.cu", "ftv_batch.cu", "ftv_noalloc.cu",
-           "ftv_centre.cu", "ftv_adjacency.cu", "ftv_geometry.cpp"]
+           "ftv_centre.cu", "ftv_adjacency.cu", "ftv_superpixels.cu", "ftv_geometry.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,671 @@
+// Superpixel segmentation (Sec. IV-C): the label maps the method consumes, as SNIC-like superpixels in
+// (Y, Cb, Cr) with compactness factor m and 8-connected segments.
+//
+// SNIC grows every cluster from its seed through a single priority queue, which is sequential. This is
+// its data-parallel reformulation (the clustering SNIC itself derives from), with SNIC's seeds, distance
+// and connectivity:
+//   - seeds on an S x S grid: cell (i, j) of width w and height h has label j * ceil(W/S) + i and seed
+//     (iS + (w-1)/2, jS + (h-1)/2);
+//   - D = S^2 ||c_p - c_k||^2 + m^2 ||x_p - x_k||^2 on the 8-bit colour scale (the spatial weight times
+//     4^(bd-8) above 8 bits, the colour weight times 4^(8-bd) below), evaluated exactly in 64-bit
+//     integers on 16 * (pixel value) - (cluster mean in 1/16 units);
+//   - assignment passes: a pixel of cell (i, j) joins the least-D cluster among cells (i+a, j+b),
+//     a, b in {-1, 0, 1} (smallest label on ties); between passes every cluster mean becomes
+//     floor((32 sum + n) / (2 n)) of its pixels (an empty cluster keeps its mean);
+//   - connectivity: components are the 8-connected sets of equally labelled pixels (named by their first
+//     pixel); a label's largest component (earliest on ties) is anchored with that label; the other
+//     components merge in rounds, each unanchored group joining the 8-adjacent group of nearest mean
+//     colour (L1 of the rounded 1/16 means; smallest name on ties), all picks of a round at once, until
+//     every group is anchored.
+// The result is unique (integer arithmetic, order-free rules), so it equals the CPU definition exactly.
+//
+// Kernels: seeds; per pass a tiled assignment (32 x 8 pixels per CTA, the CTA's candidate centres staged
+// in shared memory, warp-segmented sums into the clusters) and an update; union-find components over the
+// pixels (atomicMin linking: a root is its component's first pixel); component sums and the main
+// component per label; then per round a pair scan over the pixels of unanchored groups, a link, a
+// flatten that moves group sums and anchors, and a finish that forms the means and counts the
+// unanchored groups (every round kernel returns at once when the count is zero); a final relabel.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "ftv.h"
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kTileW = 32, kTileH = 8;  // assignment tile: one warp per row
+constexpr int kMaxCells = (kTileW + 2) * (kTileH + 2) + 64;  // cells a tile can see (S = 1: 34 x 10)
+constexpr int kThreads = 256;
+constexpr int kLoopCap = 1 << 26;  // bound of every union-find walk (parents strictly decrease anyway)
+constexpr unsigned long long kNone = ~0ull;
+
+enum : uint32_t { SP_LOOP_CAP = 1u, SP_ROUND_CAP = 2u };
+
+struct SegImage {
+    const void* plane[3];
+    int64_t pitch[3];
+    int32_t* out;
+    int32_t W, H, gw, gh;
+    int32_t pix_base, seg_base, K, pad;
+};
+
+struct alignas(32) Centre {
+    int x, y, c0, c1, c2, p0, p1, p2;
+};
+
+struct alignas(32) Sums {
+    uint32_t n, x, y, c0, c1, c2, p0, p1;
+};
+
+struct alignas(32) GSum {
+    unsigned long long n, c0, c1, c2;
+};
+
+struct Scratch {
+    const SegImage* img;
+    Centre* cen;
+    Sums* sums;
+    unsigned long long* mainkey;  // [K]: (size << 32) | ~name of the label's largest component
+    int32_t* lab;                 // [P] global segment id of each pixel
+    int32_t* par;                 // [P] union-find over pixels, then the component name
+    uint4* csum;                  // [P] per component name: n, sum Y, sum Cb, sum Cr
+    int32_t* gpar;                // [P] union-find over component names (groups)
+    int32_t* glab;                // [P] anchored label of a group (-1 unanchored)
+    uint8_t* groot;               // [P] component name is a group root
+    GSum* gsum;                   // [P] group sums (valid at group roots)
+    int4* gmean;                  // [P] group mean colour in 1/16 units
+    unsigned long long* best;     // [P] (distance << 32) | name picked by an unanchored group
+    int32_t* comps;               // [P] list of component names
+    int2* orph;                   // [P] (pixel, image) of pixels outside main components
+    int32_t* cnt;                 // [0] comps, [1] orphan pixels, [2 + r] unanchored groups at round r
+    uint32_t* status;
+    int32_t S, sb, wide, rounds;
+    unsigned long long wc, ws;
+};
+
+__device__ __forceinline__ int sample(const SegImage& im, int c, int x, int y, int sb) {
+    const char* row = static_cast<const char*>(im.plane[c]) + (int64_t)y * im.pitch[c];
+    return sb == 1 ? (int)reinterpret_cast<const uint8_t*>(row)[x] : (int)reinterpret_cast<const uint16_t*>(row)[x];
+}
+
+__device__ __forceinline__ int seed_coord(int n, int S, int i) {
+    const int w = min(S, n - i * S);
+    return i * S + (w - 1) / 2;
+}
+
+// round(16 * s / n), halves up: floor((32 s + n) / (2 n))
+__device__ __forceinline__ int mean16(unsigned long long s, unsigned long long n) {
+    return (int)((32ull * s + n) / (2ull * n));
+}
+
+__device__ int find_root(const int32_t* par, int32_t x, uint32_t* status) {
+    for (int it = 0; it < kLoopCap; ++it) {
+        const int32_t p = par[x];
+        if (p == x) return x;
+        x = p;
+    }
+    atomicOr(status, SP_LOOP_CAP);
+    return x;
+}
+
+// Link the sets of a and b; the smaller root becomes the parent (so a root is its set's smallest name).
+__device__ void unite(int32_t* par, int32_t a, int32_t b, uint32_t* status) {
+    for (int it = 0; it < kLoopCap; ++it) {
+        a = find_root(par, a, status);
+        b = find_root(par, b, status);
+        if (a == b) return;
+        if (a > b) {
+            const int32_t t = a;
+            a = b;
+            b = t;
+        }
+        const int32_t old = atomicMin(&par[b], a);
+        if (old == b) return;  // b was a root and now hangs under a
+        b = old;               // b was linked meanwhile: join a with b's new parent instead
+    }
+    atomicOr(status, SP_LOOP_CAP);
+}
+
+// ---------------------------------------------------------------------------------------- clustering
+
+__global__ void seed_kernel(Scratch s) {
+    const SegImage im = s.img[blockIdx.y];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= im.K) return;
+    const int i = k % im.gw, j = k / im.gw;
+    const int x = seed_coord(im.W, s.S, i), y = seed_coord(im.H, s.S, j);
+    Centre c{};
+    c.x = 16 * x;
+    c.y = 16 * y;
+    c.c0 = 16 * sample(im, 0, x, y, s.sb);
+    c.c1 = 16 * sample(im, 1, x, y, s.sb);
+    c.c2 = 16 * sample(im, 2, x, y, s.sb);
+    s.cen[im.seg_base + k] = c;
+    s.sums[im.seg_base + k] = Sums{};
+    s.mainkey[im.seg_base + k] = 0;
+}
+
+template <bool WIDE>
+__device__ __forceinline__ unsigned long long distance(const Centre& c, int vx, int vy, int v0, int v1, int v2,
+                                                       unsigned long long wc, unsigned long long ws) {
+    const int dx = vx - c.x, dy = vy - c.y;
+    const uint32_t dsp = (uint32_t)(dx * dx) + (uint32_t)(dy * dy);
+    const int d0 = v0 - c.c0, d1 = v1 - c.c1, d2 = v2 - c.c2;
+    unsigned long long dcol;
+    if (WIDE) {
+        dcol = (unsigned long long)((long long)d0 * d0) + (unsigned long long)((long long)d1 * d1) +
+               (unsigned long long)((long long)d2 * d2);
+    } else {
+        // |d| <= 16 (2^11 - 1) for samples within the bit depth: each square and the sum fit 32 bits
+        dcol = (uint32_t)d0 * (uint32_t)d0 + (uint32_t)d1 * (uint32_t)d1 + (uint32_t)d2 * (uint32_t)d2;
+    }
+    return wc * dcol + ws * (unsigned long long)dsp;
+}
+
+// One assignment pass over a 32 x 8 tile. accumulate: add every pixel into its cluster's sums for the
+// next update. last: also start the component search (par = self, component sums cleared).
+template <bool WIDE>
+__global__ void __launch_bounds__(kThreads) assign_kernel(Scratch s, int accumulate, int last) {
+    const SegImage im = s.img[blockIdx.z];
+    const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTileH;
+    if (x0 >= im.W || y0 >= im.H) return;  // uniform over the CTA
+    const int S = s.S;
+    const int cx0 = max(0, x0 / S - 1), cx1 = min(im.gw - 1, min(im.W - 1, x0 + kTileW - 1) / S + 1);
+    const int cy0 = max(0, y0 / S - 1), cy1 = min(im.gh - 1, min(im.H - 1, y0 + kTileH - 1) / S + 1);
+    const int ncx = cx1 - cx0 + 1, ncells = ncx * (cy1 - cy0 + 1);
+    __shared__ Centre sC[kMaxCells];
+    const int tid = threadIdx.y * kTileW + threadIdx.x;
+    for (int e = tid; e < ncells; e += kThreads) {
+        const int j = cy0 + e / ncx, i = cx0 + e % ncx;
+        sC[e] = s.cen[im.seg_base + j * im.gw + i];
+    }
+    __syncthreads();
+
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const bool valid = x < im.W && y < im.H;
+    int best = -1, v0 = 0, v1 = 0, v2 = 0;
+    if (valid) {
+        v0 = sample(im, 0, x, y, s.sb);
+        v1 = sample(im, 1, x, y, s.sb);
+        v2 = sample(im, 2, x, y, s.sb);
+        const int ci = x / S, cj = y / S;
+        const int vx = 16 * x, vy = 16 * y, w0 = 16 * v0, w1 = 16 * v1, w2 = 16 * v2;
+        unsigned long long bestD = 0;
+#pragma unroll
+        for (int b = -1; b <= 1; ++b) {
+            const int j = cj + b;
+            if (j < 0 || j >= im.gh) continue;
+#pragma unroll
+            for (int a = -1; a <= 1; ++a) {
+                const int i = ci + a;
+                if (i < 0 || i >= im.gw) continue;
+                const Centre& c = sC[(j - cy0) * ncx + (i - cx0)];
+                const unsigned long long D = distance<WIDE>(c, vx, vy, w0, w1, w2, s.wc, s.ws);
+                if (best < 0 || D < bestD) {  // labels visited in increasing order: ties keep the smaller
+                    best = j * im.gw + i;
+                    bestD = D;
+                }
+            }
+        }
+        const int64_t gp = (int64_t)im.pix_base + (int64_t)y * im.W + x;
+        s.lab[gp] = im.seg_base + best;
+        if (last) {
+            s.par[gp] = (int32_t)gp;
+            s.csum[gp] = make_uint4(0, 0, 0, 0);
+        }
+    }
+    if (!accumulate) return;
+    // warp-segmented sums: a warp is one row of the tile, so it holds a few distinct clusters
+    const int lane = threadIdx.x;
+    unsigned rem = __ballot_sync(kFull, valid);
+    while (rem) {
+        const int leader = __ffs(rem) - 1;
+        const int kk = __shfl_sync(kFull, best, leader);
+        const bool mine = valid && best == kk;
+        const unsigned grp = __ballot_sync(kFull, mine);
+        const uint32_t sx = __reduce_add_sync(kFull, mine ? (uint32_t)x : 0u);
+        const uint32_t sy = __reduce_add_sync(kFull, mine ? (uint32_t)y : 0u);
+        const uint32_t s0 = __reduce_add_sync(kFull, mine ? (uint32_t)v0 : 0u);
+        const uint32_t s1 = __reduce_add_sync(kFull, mine ? (uint32_t)v1 : 0u);
+        const uint32_t s2 = __reduce_add_sync(kFull, mine ? (uint32_t)v2 : 0u);
+        if (lane == leader) {
+            Sums* t = &s.sums[im.seg_base + kk];
+            atomicAdd(&t->n, (uint32_t)__popc(grp));
+            atomicAdd(&t->x, sx);
+            atomicAdd(&t->y, sy);
+            atomicAdd(&t->c0, s0);
+            atomicAdd(&t->c1, s1);
+            atomicAdd(&t->c2, s2);
+        }
+        rem &= ~grp;
+    }
+}
+
+__global__ void update_kernel(Scratch s) {
+    const SegImage im = s.img[blockIdx.y];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= im.K) return;
+    Sums& t = s.sums[im.seg_base + k];
+    const unsigned long long n = t.n;
+    if (n > 0) {
+        Centre& c = s.cen[im.seg_base + k];
+        c.x = mean16(t.x, n);
+        c.y = mean16(t.y, n);
+        c.c0 = mean16(t.c0, n);
+        c.c1 = mean16(t.c1, n);
+        c.c2 = mean16(t.c2, n);
+    }
+    t = Sums{};
+}
+
+// ------------------------------------------------------------------------------------- connectivity
+
+// 8-connected components of equal labels: each pixel links with its earlier neighbours (left, and the
+// three above) that carry its label.
+__global__ void __launch_bounds__(kThreads) union_kernel(Scratch s) {
+    const SegImage im = s.img[blockIdx.z];
+    const int x = blockIdx.x * kTileW + threadIdx.x, y = blockIdx.y * kTileH + threadIdx.y;
+    if (x >= im.W || y >= im.H) return;
+    const int32_t gp = im.pix_base + y * im.W + x;
+    const int32_t l = s.lab[gp];
+    if (x > 0 && s.lab[gp - 1] == l) unite(s.par, gp, gp - 1, s.status);
+    if (y > 0) {
+        const int32_t up = gp - im.W;
+        if (x > 0 && s.lab[up - 1] == l) unite(s.par, gp, up - 1, s.status);
+        if (s.lab[up] == l) unite(s.par, gp, up, s.status);
+        if (x + 1 < im.W && s.lab[up + 1] == l) unite(s.par, gp, up + 1, s.status);
+    }
+}
+
+// Component name of every pixel, and the component's pixel count and colour sums.
+__global__ void __launch_bounds__(kThreads) flatten_kernel(Scratch s) {
+    const SegImage im = s.img[blockIdx.z];
+    const int x = blockIdx.x * kTileW + threadIdx.x, y = blockIdx.y * kTileH + threadIdx.y;
+    const bool valid = x < im.W && y < im.H;
+    int32_t r = -1;
+    int v0 = 0, v1 = 0, v2 = 0;
+    if (valid) {
+        const int32_t gp = im.pix_base + y * im.W + x;
+        r = find_root(s.par, gp, s.status);
+        s.par[gp] = r;
+        v0 = sample(im, 0, x, y, s.sb);
+        v1 = sample(im, 1, x, y, s.sb);
+        v2 = sample(im, 2, x, y, s.sb);
+    }
+    const int lane = threadIdx.x;
+    unsigned rem = __ballot_sync(kFull, valid);
+    while (rem) {
+        const int leader = __ffs(rem) - 1;
+        const int32_t rr = __shfl_sync(kFull, r, leader);
+        const bool mine = valid && r == rr;
+        const unsigned grp = __ballot_sync(kFull, mine);
+        const uint32_t s0 = __reduce_add_sync(kFull, mine ? (uint32_t)v0 : 0u);
+        const uint32_t s1 = __reduce_add_sync(kFull, mine ? (uint32_t)v1 : 0u);
+        const uint32_t s2 = __reduce_add_sync(kFull, mine ? (uint32_t)v2 : 0u);
+        if (lane == leader) {
+            uint4* t = &s.csum[rr];
+            atomicAdd(&t->x, (uint32_t)__popc(grp));
+            atomicAdd(&t->y, s0);
+            atomicAdd(&t->z, s1);
+            atomicAdd(&t->w, s2);
+        }
+        rem &= ~grp;
+    }
+}
+
+// Every component offers itself as its label's main component: the largest, the earliest named on ties.
+__global__ void __launch_bounds__(kThreads) main_kernel(Scratch s) {
+    const SegImage im = s.img[blockIdx.z];
+    const int x = blockIdx.x * kTileW + threadIdx.x, y = blockIdx.y * kTileH + threadIdx.y;
+    if (x >= im.W || y >= im.H) return;
+    const int32_t gp = im.pix_base + y * im.W + x;
+    if (s.par[gp] != gp) return;
+    const unsigned long long key = ((unsigned long long)s.csum[gp].x << 32) | (unsigned long long)(~(uint32_t)gp);
+    atomicMax(&s.mainkey[s.lab[gp]], key);
+    s.comps[atomicAdd(&s.cnt[0], 1)] = gp;
+}
+
+// Groups start as single components; main components are anchored with their label.
+__global__ void group_init_kernel(Scratch s) {
+    const int n = s.cnt[0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int32_t c = s.comps[i];
+        const int32_t k = s.lab[c];
+        const bool is_main = (uint32_t)(~s.mainkey[k]) == (uint32_t)c;
+        s.gpar[c] = c;
+        s.groot[c] = 1;
+        s.glab[c] = is_main ? k : -1;
+        const uint4 t = s.csum[c];
+        s.gsum[c] = GSum{t.x, t.y, t.z, t.w};
+        s.gmean[c] = make_int4(mean16(t.y, t.x), mean16(t.z, t.x), mean16(t.w, t.x), 0);
+        s.best[c] = kNone;
+        if (!is_main) atomicAdd(&s.cnt[2], 1);
+    }
+}
+
+// Pixels outside their label's main component (the only pixels of unanchored groups).
+__global__ void __launch_bounds__(kThreads) orphan_kernel(Scratch s) {
+    if (s.cnt[2] == 0) return;
+    const SegImage im = s.img[blockIdx.z];
+    const int x = blockIdx.x * kTileW + threadIdx.x, y = blockIdx.y * kTileH + threadIdx.y;
+    if (x >= im.W || y >= im.H) return;
+    const int32_t gp = im.pix_base + y * im.W + x;
+    if (s.glab[s.par[gp]] < 0) s.orph[atomicAdd(&s.cnt[1], 1)] = make_int2(gp, (int)blockIdx.z);
+}
+
+// Round r, pick: every unanchored group takes the 8-adjacent group of nearest mean colour.
+__global__ void pick_kernel(Scratch s, int r) {
+    if (s.cnt[2 + r] == 0) return;
+    const int n = s.cnt[1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int2 o = s.orph[i];
+        const int32_t a = s.gpar[s.par[o.x]];
+        if (s.glab[a] >= 0) continue;
+        const SegImage& im = s.img[o.y];
+        const int local = o.x - im.pix_base;
+        const int x = local % im.W, y = local / im.W;
+        const int4 ma = s.gmean[a];
+        unsigned long long best = kNone;
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int qx = x + dx, qy = y + dy;
+                if ((dx == 0 && dy == 0) || qx < 0 || qx >= im.W || qy < 0 || qy >= im.H) continue;
+                const int32_t b = s.gpar[s.par[o.x + dy * im.W + dx]];
+                if (b == a) continue;
+                const int4 mb = s.gmean[b];
+                const unsigned long long d = (unsigned long long)(abs(ma.x - mb.x) + abs(ma.y - mb.y) + abs(ma.z - mb.z));
+                best = min(best, (d << 32) | (unsigned long long)(uint32_t)b);
+            }
+        if (best != kNone) atomicMin(&s.best[a], best);
+    }
+}
+
+// Round r, link: all picks at once.
+__global__ void link_kernel(Scratch s, int r) {
+    if (s.cnt[2 + r] == 0) return;
+    const int n = s.cnt[0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int32_t c = s.comps[i];
+        const unsigned long long b = s.best[c];
+        if (b != kNone) unite(s.gpar, c, (int32_t)(uint32_t)b, s.status);
+    }
+}
+
+// Round r, flatten: each component learns its group's root; a former root merged under another adds
+// its sums there, and an anchored label moves to the new root (a merged group holds at most one).
+__global__ void merge_kernel(Scratch s, int r) {
+    if (s.cnt[2 + r] == 0) return;
+    const int n = s.cnt[0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int32_t c = s.comps[i];
+        const int32_t t = find_root(s.gpar, c, s.status);
+        if (s.groot[c] && t != c) {
+            const GSum g = s.gsum[c];
+            GSum* d = &s.gsum[t];
+            atomicAdd(&d->n, g.n);
+            atomicAdd(&d->c0, g.c0);
+            atomicAdd(&d->c1, g.c1);
+            atomicAdd(&d->c2, g.c2);
+            if (s.glab[c] >= 0) s.glab[t] = s.glab[c];
+        }
+    }
+}
+
+// Round r, finish: roots, means and the count of unanchored groups for round r + 1.
+__global__ void finish_kernel(Scratch s, int r) {
+    if (s.cnt[2 + r] == 0) return;
+    const int n = s.cnt[0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int32_t c = s.comps[i];
+        const int32_t t = find_root(s.gpar, c, s.status);
+        s.gpar[c] = t;
+        s.best[c] = kNone;
+        s.groot[c] = t == c;
+        if (t == c) {
+            const GSum g = s.gsum[c];
+            s.gmean[c] = make_int4(mean16(g.c0, g.n), mean16(g.c1, g.n), mean16(g.c2, g.n), 0);
+            if (s.glab[c] < 0) atomicAdd(&s.cnt[3 + r], 1);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) relabel_kernel(Scratch s) {
+    const SegImage im = s.img[blockIdx.z];
+    const int x = blockIdx.x * kTileW + threadIdx.x, y = blockIdx.y * kTileH + threadIdx.y;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0 &&
+        s.cnt[2 + s.rounds] != 0)
+        atomicOr(s.status, SP_ROUND_CAP);
+    if (x >= im.W || y >= im.H) return;
+    const int32_t gp = im.pix_base + y * im.W + x;
+    const int32_t g = s.gpar[s.par[gp]];
+    const int32_t k = s.glab[g];
+    im.out[(int64_t)y * im.W + x] = (k >= 0 ? k : s.lab[gp]) - im.seg_base;
+}
+
+}  // namespace
+
+struct ftv_segmenter {
+    int device = 0;
+    int n_images = 0, sb = 1, bd = 8, S = 1, m = 0, T = 1;
+    std::vector<SegImage> h_meta;  // sizes and bases (pointers filled per call)
+    int64_t P = 0;
+    int32_t K = 0;
+    int max_W = 0, max_H = 0, max_K = 0, rounds = 0;
+    unsigned long long wc = 0, ws = 0;
+    SegImage* h_img = nullptr;  // pinned staging of the per-call descriptors
+    SegImage* d_img = nullptr;
+    Scratch sc{};
+    std::vector<void*> blocks;  // every device allocation, freed at destroy
+    cudaEvent_t staged = nullptr;
+    int64_t launches = 0;
+};
+
+namespace {
+
+template <class T>
+bool dalloc(ftv_segmenter* g, T** p, size_t n) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, sizeof(T) * std::max<size_t>(n, 1)) != cudaSuccess) return false;
+    g->blocks.push_back(q);
+    *p = static_cast<T*>(q);
+    return true;
+}
+
+void release(ftv_segmenter* g) {
+    for (void* q : g->blocks) cudaFree(q);
+    g->blocks.clear();
+    if (g->h_img) cudaFreeHost(g->h_img);
+    if (g->staged) cudaEventDestroy(g->staged);
+    delete g;
+}
+
+}  // namespace
+
+extern "C" ftv_status ftv_segmenter_init(const ftv_segmenter_config* cfg, ftv_segmenter** out) {
+    if (!cfg || !out) return FTV_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (cfg->n_images < 1 || cfg->n_images > FTV_SEG_MAX_IMAGES || !cfg->widths || !cfg->heights)
+        return FTV_ERR_INVALID_ARG;
+    if (cfg->sample_bytes != 1 && cfg->sample_bytes != 2) return FTV_ERR_INVALID_ARG;
+    if (cfg->bit_depth < 1 || cfg->bit_depth > 8 * cfg->sample_bytes) return FTV_ERR_INVALID_ARG;
+    if (cfg->grid_step < 1 || cfg->grid_step > FTV_SEG_MAX_STEP) return FTV_ERR_INVALID_ARG;
+    if (cfg->compactness < 0 || cfg->compactness > 255) return FTV_ERR_INVALID_ARG;
+    if (cfg->iterations < 1 || cfg->iterations > 64) return FTV_ERR_INVALID_ARG;
+    auto* g = new ftv_segmenter();
+    g->n_images = cfg->n_images;
+    g->sb = cfg->sample_bytes;
+    g->bd = cfg->bit_depth;
+    g->S = cfg->grid_step;
+    g->m = cfg->compactness;
+    g->T = cfg->iterations;
+    int64_t P = 0, K = 0;
+    for (int i = 0; i < g->n_images; ++i) {
+        const int W = cfg->widths[i], H = cfg->heights[i];
+        if (W < 1 || H < 1 || W > FTV_MAX_DIM || H > FTV_MAX_DIM) {
+            delete g;
+            return FTV_ERR_INVALID_ARG;
+        }
+        SegImage m{};
+        m.W = W;
+        m.H = H;
+        m.gw = (W + g->S - 1) / g->S;
+        m.gh = (H + g->S - 1) / g->S;
+        m.K = m.gw * m.gh;
+        m.pix_base = (int32_t)std::min<int64_t>(P, INT32_MAX);
+        m.seg_base = (int32_t)std::min<int64_t>(K, INT32_MAX);
+        P += (int64_t)W * H;
+        K += m.K;
+        g->max_W = std::max(g->max_W, W);
+        g->max_H = std::max(g->max_H, H);
+        g->max_K = std::max(g->max_K, m.K);
+        g->h_meta.push_back(m);
+    }
+    // global pixel names must fit 31 bits (component names are packed into 32-bit key halves)
+    if (P >= INT32_MAX || K >= INT32_MAX) {
+        delete g;
+        return FTV_ERR_INVALID_ARG;
+    }
+    g->P = P;
+    g->K = (int32_t)K;
+    g->wc = (unsigned long long)g->S * g->S;
+    g->ws = (unsigned long long)g->m * g->m;
+    if (g->bd > 8) g->ws <<= 2 * (g->bd - 8);
+    if (g->bd < 8) g->wc <<= 2 * (8 - g->bd);
+    // unanchored groups at least halve every round
+    int64_t maxP = 0;
+    for (const auto& m : g->h_meta) maxP = std::max<int64_t>(maxP, (int64_t)m.W * m.H);
+    int rounds = 1;
+    while ((1LL << (rounds - 1)) < maxP) ++rounds;
+    g->rounds = rounds + 1;
+    cudaGetDevice(&g->device);
+
+    Scratch& s = g->sc;
+    bool ok = cudaMallocHost(reinterpret_cast<void**>(&g->h_img), sizeof(SegImage) * g->n_images) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&g->staged, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && dalloc(g, &g->d_img, g->n_images);
+    ok = ok && dalloc(g, &s.cen, K) && dalloc(g, &s.sums, K) && dalloc(g, &s.mainkey, K);
+    ok = ok && dalloc(g, &s.lab, P) && dalloc(g, &s.par, P) && dalloc(g, &s.csum, P) && dalloc(g, &s.gpar, P);
+    ok = ok && dalloc(g, &s.glab, P) && dalloc(g, &s.groot, P) && dalloc(g, &s.gsum, P) && dalloc(g, &s.gmean, P);
+    ok = ok && dalloc(g, &s.best, P) && dalloc(g, &s.comps, P) && dalloc(g, &s.orph, P);
+    ok = ok && dalloc(g, &s.cnt, 3 + g->rounds) && dalloc(g, &s.status, 1);
+    ok = ok && cudaMemset(s.status, 0, sizeof(uint32_t)) == cudaSuccess;
+    if (!ok) {
+        release(g);
+        cudaGetLastError();
+        return FTV_ERR_OUT_OF_MEMORY;
+    }
+    s.img = g->d_img;
+    s.S = g->S;
+    s.sb = g->sb;
+    s.wide = g->bd > 11;
+    s.rounds = g->rounds;
+    s.wc = g->wc;
+    s.ws = g->ws;
+    *out = g;
+    return FTV_OK;
+}
+
+extern "C" ftv_status ftv_segmenter_segments(const ftv_segmenter* g, int32_t* n_segments) {
+    if (!g || !n_segments) return FTV_ERR_INVALID_ARG;
+    for (int i = 0; i < g->n_images; ++i) n_segments[i] = g->h_meta[i].K;
+    return FTV_OK;
+}
+
+extern "C" ftv_status ftv_superpixels(ftv_segmenter* g, const void* const* d_planes, const int64_t* pitch_bytes,
+                                      int32_t* const* d_labels, ftv_stream stream) {
+    if (!g || !d_planes || !pitch_bytes || !d_labels) return FTV_ERR_INVALID_ARG;
+    for (int i = 0; i < g->n_images; ++i) {
+        if (!d_labels[i]) return FTV_ERR_INVALID_ARG;
+        for (int c = 0; c < 3; ++c)
+            if (!d_planes[3 * i + c] || pitch_bytes[3 * i + c] < (int64_t)g->h_meta[i].W * g->sb)
+                return FTV_ERR_INVALID_ARG;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != g->device) cudaSetDevice(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    // the staging copy of the previous call must have left before it is rewritten
+    if (cudaEventSynchronize(g->staged) != cudaSuccess) {
+        if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
+        return FTV_ERR_CUDA;
+    }
+    for (int i = 0; i < g->n_images; ++i) {
+        SegImage m = g->h_meta[i];
+        for (int c = 0; c < 3; ++c) {
+            m.plane[c] = d_planes[3 * i + c];
+            m.pitch[c] = pitch_bytes[3 * i + c];
+        }
+        m.out = d_labels[i];
+        g->h_img[i] = m;
+    }
+    Scratch& s = g->sc;
+    cudaError_t e = cudaMemcpyAsync(g->d_img, g->h_img, sizeof(SegImage) * g->n_images, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(g->staged, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.cnt, 0, sizeof(int32_t) * (3 + g->rounds), st);
+    if (e != cudaSuccess) {
+        if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
+        return FTV_ERR_CUDA;
+    }
+    const dim3 kgrid((g->max_K + kThreads - 1) / kThreads, g->n_images);
+    const dim3 tgrid((g->max_W + kTileW - 1) / kTileW, (g->max_H + kTileH - 1) / kTileH, g->n_images);
+    const dim3 tblock(kTileW, kTileH);
+    int sm = 0;
+    cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, g->device);
+    const int lgrid = std::max(1, std::min<int>((int)((g->P + kThreads - 1) / kThreads), sm * 8));
+    int64_t n = 0;
+    seed_kernel<<<kgrid, kThreads, 0, st>>>(s);
+    ++n;
+    for (int it = 0; it < g->T; ++it) {
+        const int acc = it + 1 < g->T, last = it + 1 == g->T;
+        if (s.wide) assign_kernel<true><<<tgrid, tblock, 0, st>>>(s, acc, last);
+        else assign_kernel<false><<<tgrid, tblock, 0, st>>>(s, acc, last);
+        ++n;
+        if (acc) {
+            update_kernel<<<kgrid, kThreads, 0, st>>>(s);
+            ++n;
+        }
+    }
+    union_kernel<<<tgrid, tblock, 0, st>>>(s);
+    flatten_kernel<<<tgrid, tblock, 0, st>>>(s);
+    main_kernel<<<tgrid, tblock, 0, st>>>(s);
+    group_init_kernel<<<lgrid, kThreads, 0, st>>>(s);
+    orphan_kernel<<<tgrid, tblock, 0, st>>>(s);
+    n += 5;
+    for (int r = 0; r < g->rounds; ++r) {
+        pick_kernel<<<lgrid, kThreads, 0, st>>>(s, r);
+        link_kernel<<<lgrid, kThreads, 0, st>>>(s, r);
+        merge_kernel<<<lgrid, kThreads, 0, st>>>(s, r);
+        finish_kernel<<<lgrid, kThreads, 0, st>>>(s, r);
+        n += 4;
+    }
+    relabel_kernel<<<tgrid, tblock, 0, st>>>(s);
+    ++n;
+    g->launches += n;
+    e = cudaGetLastError();
+    if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
+    return e == cudaSuccess ? FTV_OK : FTV_ERR_CUDA;
+}
+
+extern "C" ftv_status ftv_segmenter_check(ftv_segmenter* g, ftv_stream stream) {
+    if (!g) return FTV_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return FTV_ERR_CUDA;
+    uint32_t st = 0;
+    if (cudaMemcpy(&st, g->sc.status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return FTV_ERR_CUDA;
+    if (st && cudaMemset(g->sc.status, 0, sizeof(st)) != cudaSuccess) return FTV_ERR_CUDA;
+    return st ? FTV_ERR_TIMEOUT : FTV_OK;
+}
+
+extern "C" int64_t ftv_segmenter_launch_count(const ftv_segmenter* g) { return g ? g->launches : 0; }
+
+extern "C" ftv_status ftv_segmenter_destroy(ftv_segmenter* g) {
+    if (!g) return FTV_ERR_INVALID_ARG;
+    cudaEventSynchronize(g->staged);
+    release(g);
+    return FTV_OK;
+}

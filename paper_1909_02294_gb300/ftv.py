@@ -49,6 +49,13 @@ class ftv_config(ctypes.Structure):
                 ("max_segments", ctypes.c_int32)]
 
 
+class ftv_segmenter_config(ctypes.Structure):
+    _fields_ = [("n_images", ctypes.c_int32), ("widths", ctypes.POINTER(ctypes.c_int32)),
+                ("heights", ctypes.POINTER(ctypes.c_int32)), ("sample_bytes", ctypes.c_int32),
+                ("bit_depth", ctypes.c_int32), ("grid_step", ctypes.c_int32), ("compactness", ctypes.c_int32),
+                ("iterations", ctypes.c_int32)]
+
+
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is not built; run __graft_entry__.build() (nvcc, sm_103a)")
@@ -85,6 +92,11 @@ def _load() -> ctypes.CDLL:
         "ftv_temporal_mask_static": [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp,
                                      vp],
         "ftv_last_kernel_ms": [vp, vp],
+        "ftv_segmenter_init": [ctypes.POINTER(ftv_segmenter_config), vp],
+        "ftv_segmenter_segments": [vp, vp],
+        "ftv_superpixels": [vp, vp, vp, vp, vp],
+        "ftv_segmenter_check": [vp, vp],
+        "ftv_segmenter_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -94,6 +106,8 @@ def _load() -> ctypes.CDLL:
     lib.ftv_batch_launch_count.restype = i64
     lib.ftv_launch_count.argtypes = [vp]
     lib.ftv_launch_count.restype = i64
+    lib.ftv_segmenter_launch_count.argtypes = [vp]
+    lib.ftv_segmenter_launch_count.restype = i64
     lib.ftv_status_str.argtypes = [ctypes.c_int]
     lib.ftv_status_str.restype = ctypes.c_char_p
     return lib
@@ -106,7 +120,9 @@ EXPORTED = ["ftv_depth_init", "ftv_depth_destroy", "ftv_compute_homographies", "
             "ftv_wta_depth", "ftv_check", "ftv_launch_count", "ftv_status_str", "ftv_set_profiling",
             "ftv_last_kernel_ms", "ftv_temporal_mask_static", "ftv_stream_init", "ftv_stream_footprint",
             "ftv_stream_labels", "ftv_stream_mask", "ftv_reciprocal_check", "ftv_centre_table", "ftv_adjacency", "ftv_batch_create", "ftv_batch_destroy", "ftv_batch_prepare", "ftv_batch_launch",
-            "ftv_batch_replay", "ftv_batch_query", "ftv_batch_wait", "ftv_batch_launch_count"]
+            "ftv_batch_replay", "ftv_batch_query", "ftv_batch_wait", "ftv_batch_launch_count",
+            "ftv_segmenter_init", "ftv_segmenter_segments", "ftv_superpixels", "ftv_segmenter_check",
+            "ftv_segmenter_launch_count", "ftv_segmenter_destroy"]
 
 
 def _ok(code: int, where: str) -> None:
@@ -470,3 +486,69 @@ def ftv_adjacency(ctx: Context, ref_index: int, frame, labels, n_segments: int, 
     _ok(lib.ftv_adjacency(ctx.handle, ref_index, fp, fpi, _ptr(labels), n_segments, connectivity, beta0, min_diff,
                           int(edge_s.numel()) if edge_s is not None else 0, _ptr(edge_s), _ptr(edge_t), _ptr(beta),
                           _ptr(n_edges), _stream(stream)), "ftv_adjacency")
+
+
+FTV_SEG_MAX_IMAGES, FTV_SEG_MAX_STEP = 4096, 64
+
+
+class Segmenter:
+    """Owns an ftv_segmenter handle (superpixel segmentation of a fixed set of image sizes)."""
+
+    def __init__(self, sizes, sample_bytes: int, bit_depth: int, grid_step: int, compactness: int = 5,
+                 iterations: int = 10):
+        """sizes: list of (width, height)."""
+        self.sizes = [(int(w), int(h)) for w, h in sizes]
+        ws = _arr(ctypes.c_int32, [w for w, _ in self.sizes])
+        hs = _arr(ctypes.c_int32, [h for _, h in self.sizes])
+        cfg = ftv_segmenter_config(len(self.sizes), ws, hs, sample_bytes, bit_depth, grid_step, compactness,
+                                   iterations)
+        h = ctypes.c_void_p()
+        _ok(lib.ftv_segmenter_init(ctypes.byref(cfg), ctypes.byref(h)), "ftv_segmenter_init")
+        self.handle = h.value
+
+    def close(self) -> None:
+        if self.handle:
+            _ok(lib.ftv_segmenter_destroy(self.handle), "ftv_segmenter_destroy")
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ftv_segmenter_init(sizes, sample_bytes: int, bit_depth: int, grid_step: int, compactness: int = 5,
+                       iterations: int = 10) -> Segmenter:
+    return Segmenter(sizes, sample_bytes, bit_depth, grid_step, compactness, iterations)
+
+
+def ftv_segmenter_segments(sg: Segmenter) -> list[int]:
+    out = np.empty(len(sg.sizes), np.int32)
+    _ok(lib.ftv_segmenter_segments(sg.handle, out.ctypes.data), "ftv_segmenter_segments")
+    return [int(v) for v in out]
+
+
+def ftv_superpixels(sg: Segmenter, planes, labels, stream=None) -> None:
+    """planes: per image a (Y, Cb, Cr) triple of 2-D CUDA tensors (uint8 or uint16, any row pitch);
+    labels: per image a dense int32 [H][W] CUDA tensor."""
+    ptrs, pitches = [], []
+    for trip in planes:
+        for t in trip:
+            ptrs.append(_ptr(t))
+            pitches.append(int(t.stride(0)) * t.element_size())
+    _ok(lib.ftv_superpixels(sg.handle, _arr(ctypes.c_void_p, ptrs), _arr(ctypes.c_int64, pitches),
+                            _arr(ctypes.c_void_p, [_ptr(l) for l in labels]), _stream(stream)), "ftv_superpixels")
+
+
+def ftv_segmenter_check(sg: Segmenter, stream=None) -> int:
+    """Wait for the stream and return the segmenter's device status code (0 = clean)."""
+    return int(lib.ftv_segmenter_check(sg.handle, _stream(stream)))
+
+
+def ftv_segmenter_launch_count(sg: Segmenter) -> int:
+    return int(lib.ftv_segmenter_launch_count(sg.handle))
+
+
+def ftv_segmenter_destroy(sg: Segmenter) -> None:
+    sg.close()

@@ -87,3 +87,24 @@ def test_init_rejects_bad_arguments_before_any_device_call(ftv):
         ftv.ftv_depth_init([bad_cam] + wl.cams[1:], [1], 64, 0.5, 10.0, **good)
     assert e.value.code == 1
     assert ftv.ftv_status_str(4).startswith("segment cost")
+
+
+@pytest.mark.parametrize("sizes,sb,bd,S,m,T", [
+    ([], 1, 8, 8, 5, 10),              # no image
+    ([(0, 5)], 1, 8, 8, 5, 10),        # empty width
+    ([(40000, 5)], 1, 8, 8, 5, 10),    # wider than FTV_MAX_DIM
+    ([(64, 48)], 3, 8, 8, 5, 10),      # sample size
+    ([(64, 48)], 1, 9, 8, 5, 10),      # 9 bits in one byte
+    ([(64, 48)], 2, 0, 8, 5, 10),      # no bits
+    ([(64, 48)], 1, 8, 0, 5, 10),      # grid step 0
+    ([(64, 48)], 1, 8, 65, 5, 10),     # grid step above FTV_SEG_MAX_STEP
+    ([(64, 48)], 1, 8, 8, -1, 10),     # negative compactness
+    ([(64, 48)], 1, 8, 8, 256, 10),    # compactness above 255
+    ([(64, 48)], 1, 8, 8, 5, 0),       # no pass
+    ([(64, 48)], 1, 8, 8, 5, 65),      # too many passes
+    ([(32767, 32767), (32767, 32767), (32767, 32767)], 2, 10, 8, 5, 10),  # 2^31 pixels or more
+])
+def test_segmenter_rejects_bad_configurations_on_the_host(ftv, sizes, sb, bd, S, m, T):
+    with pytest.raises(ftv.FtvError) as e:
+        ftv.Segmenter(sizes, sb, bd, S, m, T)
+    assert e.value.code == ftv.FTV_ERR_INVALID_ARG
