@@ -8,6 +8,7 @@ with the inputs copied from pinned host memory and the depth labels read back in
 region. The L2 is flushed (256 MB write) before every timed step.
 
 --impl reference times the CPU oracle as it stands on a bounded sample of the same workload.
+--part segmentation times the superpixel segmentation (Sec. IV-C) of every view of the workload instead.
 Multi-GPU (torchrun): every rank runs an independent replica (the work shards by frames/jobs; there is
 no exchange step), rank 0 prints the whole-job throughput from the slowest rank's time.
 """
@@ -121,11 +122,12 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _traffic_for_current_kernel(workload_key: str):
-    """DRAM bytes per cost-kernel launch from the committed ncu summary, if it was taken on the current
-    kernel source (hash match); otherwise None."""
-    path = os.path.join(ROOT, "profiles", "cost_kernel_traffic.txt")
-    src = os.path.join(ROOT, "paper_1909_02294_gb300", "csrc", "ftv_cost.cu")
+def _traffic_for_current_kernel(workload_key: str, table: str = "cost_kernel_traffic.txt",
+                                source: str = "ftv_cost.cu"):
+    """DRAM bytes per launch of a kernel from the committed ncu summary table, if it was taken on the
+    current source of that kernel (hash match); otherwise None."""
+    path = os.path.join(ROOT, "profiles", table)
+    src = os.path.join(ROOT, "paper_1909_02294_gb300", "csrc", source)
     if not os.path.exists(path):
         return None
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -193,6 +195,158 @@ def cpu_baseline(wl, budget_s: float = 12.0, min_rows: int = 4):
     return ev / dt, f"oracle, 1 thread: cost rows of segments 0..{k - 1} of reference {r} ({ev:.3e} evaluations)", k
 
 
+# Superpixel segmentation (Sec. IV-C). Operations the distance contract performs per (pixel, candidate
+# cluster) pair of an assignment pass: 2 coordinate and 3 colour differences, 5 squares, 3 adds, the two
+# weight products and their sum, 1 compare and 1 select.
+SEG_OPS_PER_CANDIDATE = 18
+SEG_COMPACTNESS, SEG_PASSES = 5, 10
+
+
+def seg_candidates(W: int, H: int, S: int) -> int:
+    """Exact (pixel, candidate cell) pairs of one assignment pass: the 3 x 3 neighbouring cells that exist."""
+    def axis(n):
+        cells = -(-n // S)
+        ci = np.arange(n) // S
+        return int(np.sum(np.minimum(ci + 1, cells - 1) - np.maximum(ci - 1, 0) + 1))
+    return axis(W) * axis(H)
+
+
+def seg_cpu_baseline(view, sb, bd, S, budget_s: float = 10.0):
+    """The oracle's segmentation as it stands (one thread) on the first rows of one view, the row count
+    chosen so the run takes about budget_s seconds. Returns (pixels/s, sample description)."""
+    import oracle
+    import synth
+
+    def crop(rows):
+        return synth.View(*(np.ascontiguousarray(np.asarray(a)[:rows]) for a in (view.Y, view.U, view.V)))
+
+    W = np.asarray(view.Y).shape[1]
+    rows = 2 * S
+    t = time.perf_counter()
+    oracle.superpixels(crop(rows), sb, bd, S, SEG_COMPACTNESS, SEG_PASSES)
+    dt = time.perf_counter() - t
+    rows = int(min(np.asarray(view.Y).shape[0], max(rows, rows * budget_s / max(dt, 1e-3))))
+    t = time.perf_counter()
+    oracle.superpixels(crop(rows), sb, bd, S, SEG_COMPACTNESS, SEG_PASSES)
+    dt = time.perf_counter() - t
+    return W * rows / dt, f"oracle, 1 thread: rows 0..{rows - 1} of view 0 ({W * rows} pixels, {SEG_PASSES} passes)"
+
+
+def run_segmentation(args, rank, world, local):
+    """One step = segmenting every view of the workload in one call (ftv_superpixels)."""
+    import torch
+    import torch.distributed as dist
+    import paper_1909_02294_gb300 as ftv
+    import synth
+
+    wl = synth.make_workload(args.workload)
+    dev = torch.device("cuda", local)
+    S, sb, bd = wl.cell, wl.sample_bytes, wl.bit_depth
+    views = wl.views()
+    sizes = [(np.asarray(v.Y).shape[1], np.asarray(v.Y).shape[0]) for v in views]
+    sg = ftv.Segmenter(sizes, sb, bd, S, SEG_COMPACTNESS, SEG_PASSES)
+    segs = ftv.ftv_segmenter_segments(sg)
+    host_planes = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (v.Y, v.U, v.V)] for v in views]
+    planes = [[t.to(dev) for t in trip] for trip in host_planes]
+    labels = [torch.empty((h, w), dtype=torch.int32, device=dev) for w, h in sizes]
+    host_labels = [torch.empty((h, w), dtype=torch.int32).pin_memory() for w, h in sizes]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        ftv.ftv_superpixels(sg, planes, labels)
+
+    for _ in range(args.warmup):
+        step()
+    if ftv.ftv_segmenter_check(sg) != 0:
+        raise RuntimeError("segmenter device status")
+    ftv.ftv_segmenter_set_profiling(sg, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    assign_ms = []
+    launches0 = ftv.ftv_segmenter_launch_count(sg)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            assign_ms.append(ftv.ftv_segmenter_kernel_ms(sg)[0])
+        torch.cuda.synchronize()
+    launches = ftv.ftv_segmenter_launch_count(sg) - launches0
+    if world > 1:
+        dist.barrier()
+    total_s = reduce_max(sum(a.elapsed_time(b) for a, b in ev) / 1000.0, dev)
+    pixels = sum(w * h for w, h in sizes)
+    value = whole_job_rate(world, pixels * args.steps, total_s)
+    if ftv.ftv_segmenter_check(sg) != 0:
+        raise RuntimeError("segmenter device status")
+
+    ftv.ftv_segmenter_set_profiling(sg, False)
+    h2d = sum(t.numel() * t.element_size() for trip in host_planes for t in trip)
+    d2h = sum(t.numel() * t.element_size() for t in host_labels)
+    e2e_ev = []
+    torch.cuda.synchronize()
+    for k in range(max(3, args.steps // 2)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for trip_h, trip_d in zip(host_planes, planes):
+            for th, td in zip(trip_h, trip_d):
+                td.copy_(th, non_blocking=True)
+        step()
+        for th, td in zip(host_labels, labels):
+            th.copy_(td, non_blocking=True)
+        b.record(stream)
+        e2e_ev.append((a, b))
+    torch.cuda.synchronize()
+    e2e_s = reduce_max(sum(a.elapsed_time(b) for a, b in e2e_ev) / 1000.0, dev)
+
+    if rank == 0:
+        peak, peak_kind = _peaks()
+        clk = clocks.summary()
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        sm_mhz = clk["sm_mhz"] if clk else 2070.0
+        alu_peak = n_sm * 128 * sm_mhz * 1e6 / 1e12
+        ams = statistics.mean(assign_ms)
+        ops = sum(seg_candidates(w, h, S) for w, h in sizes) * SEG_OPS_PER_CANDIDATE
+        pass_bytes = pixels * (3 * sb + 4)
+        c = wl.cams[0]
+        line = {
+            "metric": "segmented pixels/s", "value": value, "unit": "px/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "i32+i64", "data": "synthetic",
+            "config": {"workload": f"superpixels of {wl.name}: {len(views)} views {c.width}x{c.height} {bd}-bit, "
+                                   f"S = {S} ({segs[0]} segments/view), m = {SEG_COMPACTNESS}, {SEG_PASSES} passes",
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "segmentations_per_s": whole_job_rate(world, len(views) * args.steps, total_s),
+                       "assign_pass_ms": ams},
+            "roofline": {"bound": "alu", "achieved": ops / (ams / 1000.0) / 1e12, "peak": alu_peak, "unit": "Tops/s",
+                         "frac": ops / (ams / 1000.0) / 1e12 / alu_peak,
+                         "traffic": _traffic_for_current_kernel(args.workload, "assign_kernel_traffic.txt",
+                                                                "ftv_superpixels.cu"),
+                         "peak_kind": f"{n_sm} SMs x 128 lanes x {sm_mhz:.0f} MHz (median sampled SM clock)",
+                         "algorithmic_ops_per_launch": ops, "ops_per_candidate": SEG_OPS_PER_CANDIDATE,
+                         "kernel": "assign_kernel (one assignment pass over every view)"},
+            "hbm_roofline": {"bound": "hbm", "achieved": pass_bytes / (ams / 1000.0) / 1e9, "peak": peak,
+                             "unit": "GB/s", "frac": pass_bytes / (ams / 1000.0) / 1e9 / peak,
+                             "peak_kind": peak_kind, "algorithmic_bytes_per_launch": pass_bytes,
+                             "definition": "three samples read and one int32 label written per pixel"},
+            "e2e": {"value": whole_job_rate(world, pixels * len(e2e_ev), e2e_s), "unit": "px/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            rate, desc = seg_cpu_baseline(views[0], sb, bd, S)
+            line["cpu_baseline"] = {"value": rate, "unit": "px/s", "cores": 1, "kind": "oracle", "sample": desc}
+        print(json.dumps(line), flush=True)
+    sg.close()
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -242,6 +396,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="synthetic workload (default: the 1920x1080 8-view configuration; others for profiling)")
+    ap.add_argument("--part", default="depth", choices=["depth", "segmentation"],
+                    help="depth: the cost-volume hot path (default); segmentation: superpixels of every view")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -257,6 +413,12 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    if args.part == "segmentation":
+        run_segmentation(args, rank, world, local)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     import paper_1909_02294_gb300 as ftv
     import synth

@@ -430,6 +430,15 @@ FTV_API ftv_status ftv_segmenter_check(ftv_segmenter* sg, ftv_stream stream);
 /* Kernel launches this segmenter has enqueued since creation. */
 FTV_API int64_t ftv_segmenter_launch_count(const ftv_segmenter* sg);
 
+/* Timing: with enable != 0 every ftv_superpixels call records CUDA events on its stream around the whole
+ * call and around each assignment-pass launch (the events belong to the segmenter). */
+FTV_API ftv_status ftv_segmenter_set_profiling(ftv_segmenter* sg, int32_t enable);
+
+/* Of the most recent timed call: *assign_ms = mean duration of one assignment-pass launch, *total_ms =
+ * device time of the whole call (either pointer may be NULL). Waits for the call's end event.
+ * FTV_ERR_STATE if no call was timed. */
+FTV_API ftv_status ftv_segmenter_kernel_ms(ftv_segmenter* sg, float* assign_ms, float* total_ms);
+
 FTV_API ftv_status ftv_segmenter_destroy(ftv_segmenter* sg);
 
 /* Wait for `stream`, then return and clear the context's device status word (FTV_OK if clean). */

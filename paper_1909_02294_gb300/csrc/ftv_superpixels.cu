@@ -19,17 +19,22 @@
 //     every group is anchored.
 // The result is unique (integer arithmetic, order-free rules), so it equals the CPU definition exactly.
 //
-// Kernels: seeds; per pass a tiled assignment (32 x 8 pixels per CTA, the CTA's candidate centres staged
-// in shared memory, warp-segmented sums into the clusters) and an update; union-find components over the
-// pixels (atomicMin linking: a root is its component's first pixel); component sums and the main
-// component per label; then per round a pair scan over the pixels of unanchored groups, a link, a
-// flatten that moves group sums and anchors, and a finish that forms the means and counts the
-// unanchored groups (every round kernel returns at once when the count is zero); a final relabel.
+// Kernels: seeds; per pass a tiled assignment (128 x 8 pixels per CTA, 4 adjacent pixels per thread; the
+// CTA's candidate centres staged in shared memory; D in 32-bit integers when the weights reduced by their
+// gcd provably keep it below 2^32, else in 64-bit; runs of equal labels summed in registers, then into
+// per-tile shared accumulators, then one global add per cluster and field) and an update; union-find
+// components over the pixels (atomicMin linking, so a root is its component's first pixel): every pixel
+// points at its row run's start (one warp ballot), and only runs are linked; component sums and the main
+// component per label; then per round a pick (round 0 over every pixel, later rounds over the pixels of
+// unanchored groups that still touched another group, a list that shrinks every round), a link, a merge
+// that moves group sums and anchors, and a finish that forms the means and counts the unanchored groups
+// (every round kernel returns at once when the count is zero); a final relabel.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <algorithm>
 #include <cstring>
+#include <numeric>
 #include <vector>
 
 #include "ftv.h"
@@ -37,13 +42,15 @@
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kTileW = 32, kTileH = 8;  // assignment tile: one warp per row
-constexpr int kMaxCells = (kTileW + 2) * (kTileH + 2) + 64;  // cells a tile can see (S = 1: 34 x 10)
 constexpr int kThreads = 256;
-constexpr int kLoopCap = 1 << 26;  // bound of every union-find walk (parents strictly decrease anyway)
+constexpr int kTileW = 32, kTileH = 8;           // component tiles: one pixel per thread, one warp per row
+constexpr int kPX = 4;                           // assignment: adjacent pixels per thread
+constexpr int kATileW = 32 * kPX, kATileH = 8;   // assignment tile
+constexpr int kLoopCap = 1 << 26;                // bound of every union-find walk (parents strictly decrease)
 constexpr unsigned long long kNone = ~0ull;
 
 enum : uint32_t { SP_LOOP_CAP = 1u, SP_ROUND_CAP = 2u };
+enum : int { DIST_NARROW = 0, DIST_WIDE = 1, DIST_WIDE_COLOUR = 2 };
 
 struct SegImage {
     const void* plane[3];
@@ -65,6 +72,8 @@ struct alignas(32) GSum {
     unsigned long long n, c0, c1, c2;
 };
 
+// counters: [0] components, [1 + r] unanchored groups at the start of round r (r = 0..rounds),
+// [2 + rounds + r] length of round r's pick list
 struct Scratch {
     const SegImage* img;
     Centre* cen;
@@ -80,11 +89,12 @@ struct Scratch {
     int4* gmean;                  // [P] group mean colour in 1/16 units
     unsigned long long* best;     // [P] (distance << 32) | name picked by an unanchored group
     int32_t* comps;               // [P] list of component names
-    int2* orph;                   // [P] (pixel, image) of pixels outside main components
-    int32_t* cnt;                 // [0] comps, [1] orphan pixels, [2 + r] unanchored groups at round r
+    int2* orph[2];                // [P] pick lists of (pixel, image), alternating between rounds
+    int32_t* cnt;
     uint32_t* status;
-    int32_t S, sb, wide, rounds;
-    unsigned long long wc, ws;
+    int32_t S, sb, rounds, max_cells;
+    unsigned long long wc, ws;    // distance weights
+    uint32_t wcn, wsn;            // the weights divided by their gcd (32-bit distance)
 };
 
 __device__ __forceinline__ int sample(const SegImage& im, int c, int x, int y, int sb) {
@@ -97,14 +107,20 @@ __device__ __forceinline__ int seed_coord(int n, int S, int i) {
     return i * S + (w - 1) / 2;
 }
 
-// round(16 * s / n), halves up: floor((32 s + n) / (2 n))
+// round(16 * s / n), halves up: floor((32 s + n) / (2 n)); 32-bit division when it fits
 __device__ __forceinline__ int mean16(unsigned long long s, unsigned long long n) {
-    return (int)((32ull * s + n) / (2ull * n));
+    const unsigned long long num = 32ull * s + n, den = 2ull * n;
+    if ((num >> 32) == 0 && (den >> 32) == 0) return (int)((uint32_t)num / (uint32_t)den);
+    return (int)(num / den);
 }
 
+// Walk to the root. Reads may be stale while other threads link (a stale parent is still an ancestor),
+// so a walk always ends at a node that is or was a root; unite() then corrects itself through the atomic.
+// CG: read parents from L2 (ld.global.cg), for walks that run while other SMs link.
+template <bool CG = false>
 __device__ int find_root(const int32_t* par, int32_t x, uint32_t* status) {
     for (int it = 0; it < kLoopCap; ++it) {
-        const int32_t p = par[x];
+        const int32_t p = CG ? __ldcg(&par[x]) : par[x];
         if (p == x) return x;
         x = p;
     }
@@ -115,8 +131,8 @@ __device__ int find_root(const int32_t* par, int32_t x, uint32_t* status) {
 // Link the sets of a and b; the smaller root becomes the parent (so a root is its set's smallest name).
 __device__ void unite(int32_t* par, int32_t a, int32_t b, uint32_t* status) {
     for (int it = 0; it < kLoopCap; ++it) {
-        a = find_root(par, a, status);
-        b = find_root(par, b, status);
+        a = find_root<true>(par, a, status);
+        b = find_root<true>(par, b, status);
         if (a == b) return;
         if (a > b) {
             const int32_t t = a;
@@ -128,6 +144,29 @@ __device__ void unite(int32_t* par, int32_t a, int32_t b, uint32_t* status) {
         b = old;               // b was linked meanwhile: join a with b's new parent instead
     }
     atomicOr(status, SP_LOOP_CAP);
+}
+
+// Append the threads with keep set to list[*counter...], one atomic per CTA. Every thread of the CTA
+// (kThreads, any shape) must call it.
+template <class T>
+__device__ __forceinline__ void block_append(bool keep, const T& v, T* list, int32_t* counter) {
+    __shared__ int s_off[kThreads / 32 + 1];
+    const int t = threadIdx.y * blockDim.x + threadIdx.x, lane = t & 31, warp = t >> 5;
+    const unsigned m = __ballot_sync(kFull, keep);
+    if (lane == 0) s_off[warp] = __popc(m);
+    __syncthreads();
+    if (t == 0) {
+        int tot = 0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            const int c = s_off[w];
+            s_off[w] = tot;
+            tot += c;
+        }
+        s_off[kThreads / 32] = tot ? atomicAdd(counter, tot) : 0;
+    }
+    __syncthreads();
+    if (keep) list[s_off[kThreads / 32] + s_off[warp] + __popc(m & ((1u << lane) - 1u))] = v;
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------------------- clustering
@@ -149,99 +188,142 @@ __global__ void seed_kernel(Scratch s) {
     s.mainkey[im.seg_base + k] = 0;
 }
 
-template <bool WIDE>
-__device__ __forceinline__ unsigned long long distance(const Centre& c, int vx, int vy, int v0, int v1, int v2,
-                                                       unsigned long long wc, unsigned long long ws) {
-    const int dx = vx - c.x, dy = vy - c.y;
-    const uint32_t dsp = (uint32_t)(dx * dx) + (uint32_t)(dy * dy);
-    const int d0 = v0 - c.c0, d1 = v1 - c.c1, d2 = v2 - c.c2;
-    unsigned long long dcol;
-    if (WIDE) {
-        dcol = (unsigned long long)((long long)d0 * d0) + (unsigned long long)((long long)d1 * d1) +
-               (unsigned long long)((long long)d2 * d2);
+// D of one candidate. NARROW: the gcd-reduced weights in 32 bits (the host has shown that D stays below
+// 2^32); WIDE: 32-bit squares, 64-bit weighted sum; WIDE_COLOUR: 64-bit colour squares (bit depth > 11).
+template <int DM>
+struct Dist {
+    using T = unsigned long long;
+};
+template <>
+struct Dist<DIST_NARROW> {
+    using T = uint32_t;
+};
+
+template <int DM>
+__device__ __forceinline__ typename Dist<DM>::T distance(const int4 a, const int c2, int vx, int vy, int w0, int w1,
+                                                         int w2, const Scratch& s) {
+    const int dx = vx - a.x, dy = vy - a.y;
+    const uint32_t dsp = (uint32_t)dx * (uint32_t)dx + (uint32_t)dy * (uint32_t)dy;
+    const int d0 = w0 - a.z, d1 = w1 - a.w, d2 = w2 - c2;
+    if (DM == DIST_NARROW) {
+        const uint32_t dcol = (uint32_t)d0 * (uint32_t)d0 + (uint32_t)d1 * (uint32_t)d1 + (uint32_t)d2 * (uint32_t)d2;
+        return (typename Dist<DM>::T)(s.wcn * dcol + s.wsn * dsp);
+    } else if (DM == DIST_WIDE) {
+        const uint32_t dcol = (uint32_t)d0 * (uint32_t)d0 + (uint32_t)d1 * (uint32_t)d1 + (uint32_t)d2 * (uint32_t)d2;
+        return (typename Dist<DM>::T)(s.wc * dcol + s.ws * dsp);
     } else {
-        // |d| <= 16 (2^11 - 1) for samples within the bit depth: each square and the sum fit 32 bits
-        dcol = (uint32_t)d0 * (uint32_t)d0 + (uint32_t)d1 * (uint32_t)d1 + (uint32_t)d2 * (uint32_t)d2;
+        const unsigned long long dcol = (unsigned long long)((long long)d0 * d0) +
+                                        (unsigned long long)((long long)d1 * d1) +
+                                        (unsigned long long)((long long)d2 * d2);
+        return (typename Dist<DM>::T)(s.wc * dcol + s.ws * dsp);
     }
-    return wc * dcol + ws * (unsigned long long)dsp;
 }
 
-// One assignment pass over a 32 x 8 tile. accumulate: add every pixel into its cluster's sums for the
-// next update. last: also start the component search (par = self, component sums cleared).
-template <bool WIDE>
+// One assignment pass over a 128 x 8 tile (4 adjacent pixels per thread). accumulate: add every pixel to
+// its cluster's sums for the next update. last: also start the component search (par = self).
+template <int DM>
 __global__ void __launch_bounds__(kThreads) assign_kernel(Scratch s, int accumulate, int last) {
+    extern __shared__ __align__(16) unsigned char smem[];
     const SegImage im = s.img[blockIdx.z];
-    const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTileH;
+    const int x0 = blockIdx.x * kATileW, y0 = blockIdx.y * kATileH;
     if (x0 >= im.W || y0 >= im.H) return;  // uniform over the CTA
-    const int S = s.S;
-    const int cx0 = max(0, x0 / S - 1), cx1 = min(im.gw - 1, min(im.W - 1, x0 + kTileW - 1) / S + 1);
-    const int cy0 = max(0, y0 / S - 1), cy1 = min(im.gh - 1, min(im.H - 1, y0 + kTileH - 1) / S + 1);
+    const int S = s.S, MC = s.max_cells;
+    const int cx0 = max(0, x0 / S - 1), cx1 = min(im.gw - 1, min(im.W - 1, x0 + kATileW - 1) / S + 1);
+    const int cy0 = max(0, y0 / S - 1), cy1 = min(im.gh - 1, min(im.H - 1, y0 + kATileH - 1) / S + 1);
     const int ncx = cx1 - cx0 + 1, ncells = ncx * (cy1 - cy0 + 1);
-    __shared__ Centre sC[kMaxCells];
-    const int tid = threadIdx.y * kTileW + threadIdx.x;
+    int4* sA = reinterpret_cast<int4*>(smem);          // x, y, Y, Cb of each visible cell's centre
+    int* sB = reinterpret_cast<int*>(sA + MC);         // Cr
+    uint32_t* acc = reinterpret_cast<uint32_t*>(sB + MC);  // [6][MC]: n, x, y, Y, Cb, Cr
+    const int tid = threadIdx.y * 32 + threadIdx.x;
     for (int e = tid; e < ncells; e += kThreads) {
         const int j = cy0 + e / ncx, i = cx0 + e % ncx;
-        sC[e] = s.cen[im.seg_base + j * im.gw + i];
+        const Centre c = s.cen[im.seg_base + j * im.gw + i];
+        sA[e] = make_int4(c.x, c.y, c.c0, c.c1);
+        sB[e] = c.c2;
+        if (accumulate)
+            for (int f = 0; f < 6; ++f) acc[f * MC + e] = 0;
     }
     __syncthreads();
 
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    const bool valid = x < im.W && y < im.H;
-    int best = -1, v0 = 0, v1 = 0, v2 = 0;
-    if (valid) {
-        v0 = sample(im, 0, x, y, s.sb);
-        v1 = sample(im, 1, x, y, s.sb);
-        v2 = sample(im, 2, x, y, s.sb);
-        const int ci = x / S, cj = y / S;
-        const int vx = 16 * x, vy = 16 * y, w0 = 16 * v0, w1 = 16 * v1, w2 = 16 * v2;
-        unsigned long long bestD = 0;
-#pragma unroll
-        for (int b = -1; b <= 1; ++b) {
-            const int j = cj + b;
-            if (j < 0 || j >= im.gh) continue;
-#pragma unroll
-            for (int a = -1; a <= 1; ++a) {
-                const int i = ci + a;
-                if (i < 0 || i >= im.gw) continue;
-                const Centre& c = sC[(j - cy0) * ncx + (i - cx0)];
-                const unsigned long long D = distance<WIDE>(c, vx, vy, w0, w1, w2, s.wc, s.ws);
-                if (best < 0 || D < bestD) {  // labels visited in increasing order: ties keep the smaller
-                    best = j * im.gw + i;
-                    bestD = D;
+    const int y = y0 + threadIdx.y;
+    int rk = -1;
+    uint32_t rn = 0, rx = 0, ry = 0, r0 = 0, r1 = 0, r2 = 0;
+    if (y < im.H) {
+        const int cj = y / S;
+        const int jlo = max(cj - 1, 0), jhi = min(cj + 1, im.gh - 1);
+        const int vy = 16 * y;
+        const int64_t row = (int64_t)im.pix_base + (int64_t)y * im.W;
+#pragma unroll 1
+        for (int q = 0; q < kPX; ++q) {
+            const int x = x0 + kPX * threadIdx.x + q;
+            if (x >= im.W) break;
+            const int v0 = sample(im, 0, x, y, s.sb), v1 = sample(im, 1, x, y, s.sb), v2 = sample(im, 2, x, y, s.sb);
+            const int ci = x / S;
+            const int ilo = max(ci - 1, 0), ihi = min(ci + 1, im.gw - 1);
+            const int vx = 16 * x, w0 = 16 * v0, w1 = 16 * v1, w2 = 16 * v2;
+            int be = -1;
+            typename Dist<DM>::T bd = 0;
+            for (int j = jlo; j <= jhi; ++j) {
+                const int rowe = (j - cy0) * ncx - cx0;
+                for (int i = ilo; i <= ihi; ++i) {  // labels in increasing order: ties keep the smaller
+                    const int e = rowe + i;
+                    const typename Dist<DM>::T D = distance<DM>(sA[e], sB[e], vx, vy, w0, w1, w2, s);
+                    if (be < 0 || D < bd) {
+                        be = e;
+                        bd = D;
+                    }
                 }
             }
-        }
-        const int64_t gp = (int64_t)im.pix_base + (int64_t)y * im.W + x;
-        s.lab[gp] = im.seg_base + best;
-        if (last) {
-            s.par[gp] = (int32_t)gp;
-            s.csum[gp] = make_uint4(0, 0, 0, 0);
+            const int bj = cy0 + be / ncx, bi = cx0 + be % ncx;
+            const int64_t gp = row + x;
+            s.lab[gp] = im.seg_base + bj * im.gw + bi;
+            if (last) {
+                s.par[gp] = (int32_t)gp;
+                s.csum[gp] = make_uint4(0, 0, 0, 0);
+            }
+            if (accumulate) {
+                if (be != rk) {
+                    if (rk >= 0) {
+                        atomicAdd(&acc[0 * MC + rk], rn);
+                        atomicAdd(&acc[1 * MC + rk], rx);
+                        atomicAdd(&acc[2 * MC + rk], ry);
+                        atomicAdd(&acc[3 * MC + rk], r0);
+                        atomicAdd(&acc[4 * MC + rk], r1);
+                        atomicAdd(&acc[5 * MC + rk], r2);
+                    }
+                    rk = be;
+                    rn = rx = ry = r0 = r1 = r2 = 0;
+                }
+                rn += 1;
+                rx += x;
+                ry += y;
+                r0 += v0;
+                r1 += v1;
+                r2 += v2;
+            }
         }
     }
     if (!accumulate) return;
-    // warp-segmented sums: a warp is one row of the tile, so it holds a few distinct clusters
-    const int lane = threadIdx.x;
-    unsigned rem = __ballot_sync(kFull, valid);
-    while (rem) {
-        const int leader = __ffs(rem) - 1;
-        const int kk = __shfl_sync(kFull, best, leader);
-        const bool mine = valid && best == kk;
-        const unsigned grp = __ballot_sync(kFull, mine);
-        const uint32_t sx = __reduce_add_sync(kFull, mine ? (uint32_t)x : 0u);
-        const uint32_t sy = __reduce_add_sync(kFull, mine ? (uint32_t)y : 0u);
-        const uint32_t s0 = __reduce_add_sync(kFull, mine ? (uint32_t)v0 : 0u);
-        const uint32_t s1 = __reduce_add_sync(kFull, mine ? (uint32_t)v1 : 0u);
-        const uint32_t s2 = __reduce_add_sync(kFull, mine ? (uint32_t)v2 : 0u);
-        if (lane == leader) {
-            Sums* t = &s.sums[im.seg_base + kk];
-            atomicAdd(&t->n, (uint32_t)__popc(grp));
-            atomicAdd(&t->x, sx);
-            atomicAdd(&t->y, sy);
-            atomicAdd(&t->c0, s0);
-            atomicAdd(&t->c1, s1);
-            atomicAdd(&t->c2, s2);
-        }
-        rem &= ~grp;
+    if (rk >= 0) {
+        atomicAdd(&acc[0 * MC + rk], rn);
+        atomicAdd(&acc[1 * MC + rk], rx);
+        atomicAdd(&acc[2 * MC + rk], ry);
+        atomicAdd(&acc[3 * MC + rk], r0);
+        atomicAdd(&acc[4 * MC + rk], r1);
+        atomicAdd(&acc[5 * MC + rk], r2);
+    }
+    __syncthreads();
+    for (int e = tid; e < ncells; e += kThreads) {
+        const uint32_t n = acc[e];
+        if (n == 0) continue;
+        const int j = cy0 + e / ncx, i = cx0 + e % ncx;
+        Sums* t = &s.sums[im.seg_base + j * im.gw + i];
+        atomicAdd(&t->n, n);
+        atomicAdd(&t->x, acc[1 * MC + e]);
+        atomicAdd(&t->y, acc[2 * MC + e]);
+        atomicAdd(&t->c0, acc[3 * MC + e]);
+        atomicAdd(&t->c1, acc[4 * MC + e]);
+        atomicAdd(&t->c2, acc[5 * MC + e]);
     }
 }
 
@@ -264,21 +346,43 @@ __global__ void update_kernel(Scratch s) {
 
 // ------------------------------------------------------------------------------------- connectivity
 
-// 8-connected components of equal labels: each pixel links with its earlier neighbours (left, and the
-// three above) that carry its label.
-__global__ void __launch_bounds__(kThreads) union_kernel(Scratch s) {
+// 8-connected components of equal labels, built from row runs. A warp holds 32 pixels of a row: a ballot
+// finds each pixel's run start inside the warp's segment, and every pixel points there.
+__global__ void __launch_bounds__(kThreads) runs_kernel(Scratch s) {
     const SegImage im = s.img[blockIdx.z];
     const int x = blockIdx.x * kTileW + threadIdx.x, y = blockIdx.y * kTileH + threadIdx.y;
-    if (x >= im.W || y >= im.H) return;
-    const int32_t gp = im.pix_base + y * im.W + x;
-    const int32_t l = s.lab[gp];
-    if (x > 0 && s.lab[gp - 1] == l) unite(s.par, gp, gp - 1, s.status);
-    if (y > 0) {
-        const int32_t up = gp - im.W;
-        if (x > 0 && s.lab[up - 1] == l) unite(s.par, gp, up - 1, s.status);
-        if (s.lab[up] == l) unite(s.par, gp, up, s.status);
-        if (x + 1 < im.W && s.lab[up + 1] == l) unite(s.par, gp, up + 1, s.status);
-    }
+    const bool valid = x < im.W && y < im.H;
+    const int32_t gp = valid ? im.pix_base + y * im.W + x : -1;
+    const int l = valid ? s.lab[gp] : -1;
+    const int lane = threadIdx.x;
+    const int left = __shfl_up_sync(kFull, l, 1);
+    const unsigned cont = __ballot_sync(kFull, valid && lane > 0 && left == l);  // continues the run on its left
+    const unsigned upto = lane == 31 ? kFull : ((2u << lane) - 1u);
+    const int start = 31 - __clz(~cont & upto);
+    if (valid) s.par[gp] = gp - (lane - start);
+}
+
+// Links between runs: a run continuing across a warp segment; a run and the run above it where they
+// overlap (issued once, from the later of the two run starts) or touch diagonally (from the run's first
+// and last pixel). Runs here are the segment-local ones, so a few links are issued twice.
+__global__ void __launch_bounds__(kThreads) links_kernel(Scratch s) {
+    const SegImage im = s.img[blockIdx.z];
+    const int x = blockIdx.x * kTileW + threadIdx.x, y = blockIdx.y * kTileH + threadIdx.y;
+    const bool valid = x < im.W && y < im.H;
+    const int32_t gp = valid ? im.pix_base + y * im.W + x : -1;
+    const int l = valid ? s.lab[gp] : -1;
+    const int lane = threadIdx.x;
+    const int left = __shfl_up_sync(kFull, l, 1), right = __shfl_down_sync(kFull, l, 1);
+    if (!valid) return;
+    // run starts and ends from the labels (parents change under the links being made)
+    const bool is_start = lane == 0 || left != l;
+    const bool is_end = lane == 31 || x + 1 >= im.W || right != l;
+    if (lane == 0 && x > 0 && s.lab[gp - 1] == l) unite(s.par, gp, gp - 1, s.status);
+    if (y == 0) return;
+    const int32_t up = gp - im.W;
+    if (s.lab[up] == l && (is_start || s.lab[up - 1] != l)) unite(s.par, gp, up, s.status);
+    if (is_start && x > 0 && s.lab[up - 1] == l) unite(s.par, gp, up - 1, s.status);
+    if (is_end && x + 1 < im.W && s.lab[up + 1] == l) unite(s.par, gp, up + 1, s.status);
 }
 
 // Component name of every pixel, and the component's pixel count and colour sums.
@@ -321,12 +425,14 @@ __global__ void __launch_bounds__(kThreads) flatten_kernel(Scratch s) {
 __global__ void __launch_bounds__(kThreads) main_kernel(Scratch s) {
     const SegImage im = s.img[blockIdx.z];
     const int x = blockIdx.x * kTileW + threadIdx.x, y = blockIdx.y * kTileH + threadIdx.y;
-    if (x >= im.W || y >= im.H) return;
-    const int32_t gp = im.pix_base + y * im.W + x;
-    if (s.par[gp] != gp) return;
-    const unsigned long long key = ((unsigned long long)s.csum[gp].x << 32) | (unsigned long long)(~(uint32_t)gp);
-    atomicMax(&s.mainkey[s.lab[gp]], key);
-    s.comps[atomicAdd(&s.cnt[0], 1)] = gp;
+    const bool valid = x < im.W && y < im.H;
+    const int32_t gp = valid ? im.pix_base + y * im.W + x : -1;
+    const bool root = valid && s.par[gp] == gp;
+    if (root) {
+        const unsigned long long key = ((unsigned long long)s.csum[gp].x << 32) | (unsigned long long)(~(uint32_t)gp);
+        atomicMax(&s.mainkey[s.lab[gp]], key);
+    }
+    block_append(root, gp, s.comps, &s.cnt[0]);
 }
 
 // Groups start as single components; main components are anchored with their label.
@@ -343,52 +449,74 @@ __global__ void group_init_kernel(Scratch s) {
         s.gsum[c] = GSum{t.x, t.y, t.z, t.w};
         s.gmean[c] = make_int4(mean16(t.y, t.x), mean16(t.z, t.x), mean16(t.w, t.x), 0);
         s.best[c] = kNone;
-        if (!is_main) atomicAdd(&s.cnt[2], 1);
+        if (!is_main) atomicAdd(&s.cnt[1], 1);
     }
 }
 
-// Pixels outside their label's main component (the only pixels of unanchored groups).
-__global__ void __launch_bounds__(kThreads) orphan_kernel(Scratch s) {
-    if (s.cnt[2] == 0) return;
-    const SegImage im = s.img[blockIdx.z];
-    const int x = blockIdx.x * kTileW + threadIdx.x, y = blockIdx.y * kTileH + threadIdx.y;
-    if (x >= im.W || y >= im.H) return;
-    const int32_t gp = im.pix_base + y * im.W + x;
-    if (s.glab[s.par[gp]] < 0) s.orph[atomicAdd(&s.cnt[1], 1)] = make_int2(gp, (int)blockIdx.z);
+// The pick of one pixel p of group a (unanchored): the neighbouring group of least (distance, name).
+__device__ __forceinline__ bool pick_pixel(const Scratch& s, const SegImage& im, int32_t p, int32_t a) {
+    const int local = p - im.pix_base;
+    const int x = local % im.W, y = local / im.W;
+    const int4 ma = s.gmean[a];
+    unsigned long long best = kNone;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int qx = x + dx, qy = y + dy;
+            if ((dx == 0 && dy == 0) || qx < 0 || qx >= im.W || qy < 0 || qy >= im.H) continue;
+            const int32_t b = s.gpar[s.par[p + dy * im.W + dx]];
+            if (b == a) continue;
+            const int4 mb = s.gmean[b];
+            const unsigned long long d = (unsigned long long)(abs(ma.x - mb.x) + abs(ma.y - mb.y) + abs(ma.z - mb.z));
+            best = min(best, (d << 32) | (unsigned long long)(uint32_t)b);
+        }
+    if (best == kNone) return false;
+    atomicMin(&s.best[a], best);
+    return true;
 }
 
-// Round r, pick: every unanchored group takes the 8-adjacent group of nearest mean colour.
-__global__ void pick_kernel(Scratch s, int r) {
-    if (s.cnt[2 + r] == 0) return;
-    const int n = s.cnt[1];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int2 o = s.orph[i];
-        const int32_t a = s.gpar[s.par[o.x]];
-        if (s.glab[a] >= 0) continue;
-        const SegImage& im = s.img[o.y];
-        const int local = o.x - im.pix_base;
-        const int x = local % im.W, y = local / im.W;
-        const int4 ma = s.gmean[a];
-        unsigned long long best = kNone;
-#pragma unroll
-        for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int qx = x + dx, qy = y + dy;
-                if ((dx == 0 && dy == 0) || qx < 0 || qx >= im.W || qy < 0 || qy >= im.H) continue;
-                const int32_t b = s.gpar[s.par[o.x + dy * im.W + dx]];
-                if (b == a) continue;
-                const int4 mb = s.gmean[b];
-                const unsigned long long d = (unsigned long long)(abs(ma.x - mb.x) + abs(ma.y - mb.y) + abs(ma.z - mb.z));
-                best = min(best, (d << 32) | (unsigned long long)(uint32_t)b);
-            }
-        if (best != kNone) atomicMin(&s.best[a], best);
+// Round r's pick: every unanchored group takes the 8-adjacent group of nearest mean colour. A pixel whose
+// group is anchored, or whose neighbours all lie in its own group, can never matter again (anchors are
+// kept and groups only merge): only the others enter round r + 1's list. Round 0 visits every pixel.
+__global__ void __launch_bounds__(kThreads) pick0_kernel(Scratch s) {
+    if (s.cnt[1] == 0) return;
+    const SegImage im = s.img[blockIdx.z];
+    const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTileH;
+    if (x0 >= im.W || y0 >= im.H) return;  // uniform over the CTA
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    bool keep = false;
+    int32_t gp = -1;
+    if (x < im.W && y < im.H) {
+        gp = im.pix_base + y * im.W + x;
+        const int32_t a = s.gpar[s.par[gp]];
+        keep = s.glab[a] < 0 && pick_pixel(s, im, gp, a);
+    }
+    block_append(keep, make_int2(gp, (int)blockIdx.z), s.orph[1], &s.cnt[2 + s.rounds + 1]);
+}
+
+__global__ void __launch_bounds__(kThreads) pick_kernel(Scratch s, int r) {
+    if (s.cnt[1 + r] == 0) return;
+    const int n = s.cnt[2 + s.rounds + r];
+    const int2* in = s.orph[r & 1];
+    int2* next = s.orph[(r + 1) & 1];
+    int32_t* next_n = &s.cnt[2 + s.rounds + r + 1];
+    for (int base = blockIdx.x * kThreads; base < n; base += gridDim.x * kThreads) {
+        const int i = base + threadIdx.x;
+        bool keep = false;
+        int2 o = make_int2(0, 0);
+        if (i < n) {
+            o = in[i];
+            const int32_t a = s.gpar[s.par[o.x]];
+            keep = s.glab[a] < 0 && pick_pixel(s, s.img[o.y], o.x, a);
+        }
+        block_append(keep, o, next, next_n);
     }
 }
 
 // Round r, link: all picks at once.
 __global__ void link_kernel(Scratch s, int r) {
-    if (s.cnt[2 + r] == 0) return;
+    if (s.cnt[1 + r] == 0) return;
     const int n = s.cnt[0];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int32_t c = s.comps[i];
@@ -397,29 +525,29 @@ __global__ void link_kernel(Scratch s, int r) {
     }
 }
 
-// Round r, flatten: each component learns its group's root; a former root merged under another adds
-// its sums there, and an anchored label moves to the new root (a merged group holds at most one).
+// Round r, merge: a former group root merged under another adds its sums there, and an anchored label
+// moves to the new root (a merged group holds at most one).
 __global__ void merge_kernel(Scratch s, int r) {
-    if (s.cnt[2 + r] == 0) return;
+    if (s.cnt[1 + r] == 0) return;
     const int n = s.cnt[0];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int32_t c = s.comps[i];
+        if (!s.groot[c]) continue;
         const int32_t t = find_root(s.gpar, c, s.status);
-        if (s.groot[c] && t != c) {
-            const GSum g = s.gsum[c];
-            GSum* d = &s.gsum[t];
-            atomicAdd(&d->n, g.n);
-            atomicAdd(&d->c0, g.c0);
-            atomicAdd(&d->c1, g.c1);
-            atomicAdd(&d->c2, g.c2);
-            if (s.glab[c] >= 0) s.glab[t] = s.glab[c];
-        }
+        if (t == c) continue;  // (merge and finish run after every link of the round has landed)
+        const GSum g = s.gsum[c];
+        GSum* d = &s.gsum[t];
+        atomicAdd(&d->n, g.n);
+        atomicAdd(&d->c0, g.c0);
+        atomicAdd(&d->c1, g.c1);
+        atomicAdd(&d->c2, g.c2);
+        if (s.glab[c] >= 0) s.glab[t] = s.glab[c];
     }
 }
 
 // Round r, finish: roots, means and the count of unanchored groups for round r + 1.
 __global__ void finish_kernel(Scratch s, int r) {
-    if (s.cnt[2 + r] == 0) return;
+    if (s.cnt[1 + r] == 0) return;
     const int n = s.cnt[0];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int32_t c = s.comps[i];
@@ -430,7 +558,7 @@ __global__ void finish_kernel(Scratch s, int r) {
         if (t == c) {
             const GSum g = s.gsum[c];
             s.gmean[c] = make_int4(mean16(g.c0, g.n), mean16(g.c1, g.n), mean16(g.c2, g.n), 0);
-            if (s.glab[c] < 0) atomicAdd(&s.cnt[3 + r], 1);
+            if (s.glab[c] < 0) atomicAdd(&s.cnt[2 + r], 1);
         }
     }
 }
@@ -439,7 +567,7 @@ __global__ void __launch_bounds__(kThreads) relabel_kernel(Scratch s) {
     const SegImage im = s.img[blockIdx.z];
     const int x = blockIdx.x * kTileW + threadIdx.x, y = blockIdx.y * kTileH + threadIdx.y;
     if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0 &&
-        s.cnt[2 + s.rounds] != 0)
+        s.cnt[1 + s.rounds] != 0)
         atomicOr(s.status, SP_ROUND_CAP);
     if (x >= im.W || y >= im.H) return;
     const int32_t gp = im.pix_base + y * im.W + x;
@@ -456,7 +584,8 @@ struct ftv_segmenter {
     std::vector<SegImage> h_meta;  // sizes and bases (pointers filled per call)
     int64_t P = 0;
     int32_t K = 0;
-    int max_W = 0, max_H = 0, max_K = 0, rounds = 0;
+    int max_W = 0, max_H = 0, max_K = 0, rounds = 0, dist_mode = 0;
+    size_t assign_smem = 0;
     unsigned long long wc = 0, ws = 0;
     SegImage* h_img = nullptr;  // pinned staging of the per-call descriptors
     SegImage* d_img = nullptr;
@@ -464,6 +593,9 @@ struct ftv_segmenter {
     std::vector<void*> blocks;  // every device allocation, freed at destroy
     cudaEvent_t staged = nullptr;
     int64_t launches = 0;
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;  // profiling: call begin, call end, then a pair per assignment pass
+    bool timed = false;
 };
 
 namespace {
@@ -482,6 +614,7 @@ void release(ftv_segmenter* g) {
     g->blocks.clear();
     if (g->h_img) cudaFreeHost(g->h_img);
     if (g->staged) cudaEventDestroy(g->staged);
+    for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
     delete g;
 }
 
@@ -552,8 +685,9 @@ extern "C" ftv_status ftv_segmenter_init(const ftv_segmenter_config* cfg, ftv_se
     ok = ok && dalloc(g, &s.cen, K) && dalloc(g, &s.sums, K) && dalloc(g, &s.mainkey, K);
     ok = ok && dalloc(g, &s.lab, P) && dalloc(g, &s.par, P) && dalloc(g, &s.csum, P) && dalloc(g, &s.gpar, P);
     ok = ok && dalloc(g, &s.glab, P) && dalloc(g, &s.groot, P) && dalloc(g, &s.gsum, P) && dalloc(g, &s.gmean, P);
-    ok = ok && dalloc(g, &s.best, P) && dalloc(g, &s.comps, P) && dalloc(g, &s.orph, P);
-    ok = ok && dalloc(g, &s.cnt, 3 + g->rounds) && dalloc(g, &s.status, 1);
+    ok = ok && dalloc(g, &s.best, P) && dalloc(g, &s.comps, P) && dalloc(g, &s.orph[0], P) &&
+         dalloc(g, &s.orph[1], P);
+    ok = ok && dalloc(g, &s.cnt, 2 * g->rounds + 3) && dalloc(g, &s.status, 1);
     ok = ok && cudaMemset(s.status, 0, sizeof(uint32_t)) == cudaSuccess;
     if (!ok) {
         release(g);
@@ -563,10 +697,41 @@ extern "C" ftv_status ftv_segmenter_init(const ftv_segmenter_config* cfg, ftv_se
     s.img = g->d_img;
     s.S = g->S;
     s.sb = g->sb;
-    s.wide = g->bd > 11;
     s.rounds = g->rounds;
     s.wc = g->wc;
     s.ws = g->ws;
+    // Distance arithmetic. |x - X| < 3S in pixels for every candidate (a candidate's pixels, hence its
+    // mean, lie within one cell of the candidate's cell), so in 1/16 units dsp < 2 (48 S)^2, and
+    // dcol <= 3 (16 (2^bd - 1))^2 for samples within the bit depth.
+    {
+        const unsigned long long gcd = std::gcd(g->wc, g->ws);
+        const unsigned long long wcn = g->wc / gcd, wsn = g->ws / gcd;
+        const unsigned long long vmax = 16ull * ((1ull << g->bd) - 1), dmax = 48ull * g->S;
+        const unsigned long long bound = wcn * 3ull * vmax * vmax + wsn * 2ull * dmax * dmax;
+        g->dist_mode = bound < (1ull << 32) ? DIST_NARROW : (g->bd <= 11 ? DIST_WIDE : DIST_WIDE_COLOUR);
+        s.wcn = (uint32_t)(g->dist_mode == DIST_NARROW ? wcn : 0);
+        s.wsn = (uint32_t)(g->dist_mode == DIST_NARROW ? wsn : 0);
+    }
+    // shared memory of an assignment tile: the cells it can see, 44 bytes each
+    {
+        const int ncx = (kATileW - 1 + g->S - 1) / g->S + 3, ncy = (kATileH - 1 + g->S - 1) / g->S + 3;
+        s.max_cells = ncx * ncy;
+        g->assign_smem = (size_t)s.max_cells * (sizeof(int4) + sizeof(int) + 6 * sizeof(uint32_t));
+        cudaError_t e = cudaSuccess;
+        if (g->dist_mode == DIST_NARROW)
+            e = cudaFuncSetAttribute(assign_kernel<DIST_NARROW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)g->assign_smem);
+        else if (g->dist_mode == DIST_WIDE)
+            e = cudaFuncSetAttribute(assign_kernel<DIST_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)g->assign_smem);
+        else
+            e = cudaFuncSetAttribute(assign_kernel<DIST_WIDE_COLOUR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)g->assign_smem);
+        if (e != cudaSuccess) {
+            release(g);
+            return FTV_ERR_CUDA;
+        }
+    }
     *out = g;
     return FTV_OK;
 }
@@ -607,38 +772,46 @@ extern "C" ftv_status ftv_superpixels(ftv_segmenter* g, const void* const* d_pla
     Scratch& s = g->sc;
     cudaError_t e = cudaMemcpyAsync(g->d_img, g->h_img, sizeof(SegImage) * g->n_images, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaEventRecord(g->staged, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s.cnt, 0, sizeof(int32_t) * (3 + g->rounds), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.cnt, 0, sizeof(int32_t) * (2 * g->rounds + 3), st);
     if (e != cudaSuccess) {
         if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
         return FTV_ERR_CUDA;
     }
     const dim3 kgrid((g->max_K + kThreads - 1) / kThreads, g->n_images);
     const dim3 tgrid((g->max_W + kTileW - 1) / kTileW, (g->max_H + kTileH - 1) / kTileH, g->n_images);
+    const dim3 agrid((g->max_W + kATileW - 1) / kATileW, (g->max_H + kATileH - 1) / kATileH, g->n_images);
     const dim3 tblock(kTileW, kTileH);
     int sm = 0;
     cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, g->device);
     const int lgrid = std::max(1, std::min<int>((int)((g->P + kThreads - 1) / kThreads), sm * 8));
     int64_t n = 0;
+    const bool prof = g->profiling;
+    if (prof) cudaEventRecord(g->ev[0], st);
     seed_kernel<<<kgrid, kThreads, 0, st>>>(s);
     ++n;
     for (int it = 0; it < g->T; ++it) {
         const int acc = it + 1 < g->T, last = it + 1 == g->T;
-        if (s.wide) assign_kernel<true><<<tgrid, tblock, 0, st>>>(s, acc, last);
-        else assign_kernel<false><<<tgrid, tblock, 0, st>>>(s, acc, last);
+        if (prof) cudaEventRecord(g->ev[2 + 2 * it], st);
+        const size_t sm_bytes = g->assign_smem;
+        if (g->dist_mode == DIST_NARROW) assign_kernel<DIST_NARROW><<<agrid, tblock, sm_bytes, st>>>(s, acc, last);
+        else if (g->dist_mode == DIST_WIDE) assign_kernel<DIST_WIDE><<<agrid, tblock, sm_bytes, st>>>(s, acc, last);
+        else assign_kernel<DIST_WIDE_COLOUR><<<agrid, tblock, sm_bytes, st>>>(s, acc, last);
+        if (prof) cudaEventRecord(g->ev[3 + 2 * it], st);
         ++n;
         if (acc) {
             update_kernel<<<kgrid, kThreads, 0, st>>>(s);
             ++n;
         }
     }
-    union_kernel<<<tgrid, tblock, 0, st>>>(s);
+    runs_kernel<<<tgrid, tblock, 0, st>>>(s);
+    links_kernel<<<tgrid, tblock, 0, st>>>(s);
     flatten_kernel<<<tgrid, tblock, 0, st>>>(s);
     main_kernel<<<tgrid, tblock, 0, st>>>(s);
     group_init_kernel<<<lgrid, kThreads, 0, st>>>(s);
-    orphan_kernel<<<tgrid, tblock, 0, st>>>(s);
     n += 5;
     for (int r = 0; r < g->rounds; ++r) {
-        pick_kernel<<<lgrid, kThreads, 0, st>>>(s, r);
+        if (r == 0) pick0_kernel<<<tgrid, tblock, 0, st>>>(s);
+        else pick_kernel<<<lgrid, kThreads, 0, st>>>(s, r);
         link_kernel<<<lgrid, kThreads, 0, st>>>(s, r);
         merge_kernel<<<lgrid, kThreads, 0, st>>>(s, r);
         finish_kernel<<<lgrid, kThreads, 0, st>>>(s, r);
@@ -646,6 +819,8 @@ extern "C" ftv_status ftv_superpixels(ftv_segmenter* g, const void* const* d_pla
     }
     relabel_kernel<<<tgrid, tblock, 0, st>>>(s);
     ++n;
+    if (prof) cudaEventRecord(g->ev[1], st);
+    g->timed = g->timed || prof;
     g->launches += n;
     e = cudaGetLastError();
     if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
@@ -662,6 +837,34 @@ extern "C" ftv_status ftv_segmenter_check(ftv_segmenter* g, ftv_stream stream) {
 }
 
 extern "C" int64_t ftv_segmenter_launch_count(const ftv_segmenter* g) { return g ? g->launches : 0; }
+
+extern "C" ftv_status ftv_segmenter_set_profiling(ftv_segmenter* g, int32_t enable) {
+    if (!g) return FTV_ERR_INVALID_ARG;
+    if (enable && g->ev.empty()) {
+        g->ev.resize(2 + 2 * g->T, nullptr);
+        for (auto& e : g->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return FTV_ERR_CUDA;
+    }
+    g->profiling = enable != 0;
+    return FTV_OK;
+}
+
+extern "C" ftv_status ftv_segmenter_kernel_ms(ftv_segmenter* g, float* assign_ms, float* total_ms) {
+    if (!g || (!assign_ms && !total_ms)) return FTV_ERR_INVALID_ARG;
+    if (!g->timed) return FTV_ERR_STATE;
+    if (cudaEventSynchronize(g->ev[1]) != cudaSuccess) return FTV_ERR_CUDA;
+    float ms = 0.f, sum = 0.f;
+    for (int it = 0; it < g->T; ++it) {
+        if (cudaEventElapsedTime(&ms, g->ev[2 + 2 * it], g->ev[3 + 2 * it]) != cudaSuccess) return FTV_ERR_CUDA;
+        sum += ms;
+    }
+    if (assign_ms) *assign_ms = sum / g->T;
+    if (total_ms) {
+        if (cudaEventElapsedTime(&ms, g->ev[0], g->ev[1]) != cudaSuccess) return FTV_ERR_CUDA;
+        *total_ms = ms;
+    }
+    return FTV_OK;
+}
 
 extern "C" ftv_status ftv_segmenter_destroy(ftv_segmenter* g) {
     if (!g) return FTV_ERR_INVALID_ARG;

@@ -97,6 +97,8 @@ def _load() -> ctypes.CDLL:
         "ftv_superpixels": [vp, vp, vp, vp, vp],
         "ftv_segmenter_check": [vp, vp],
         "ftv_segmenter_destroy": [vp],
+        "ftv_segmenter_set_profiling": [vp, i32],
+        "ftv_segmenter_kernel_ms": [vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -122,7 +124,8 @@ EXPORTED = ["ftv_depth_init", "ftv_depth_destroy", "ftv_compute_homographies", "
             "ftv_stream_labels", "ftv_stream_mask", "ftv_reciprocal_check", "ftv_centre_table", "ftv_adjacency", "ftv_batch_create", "ftv_batch_destroy", "ftv_batch_prepare", "ftv_batch_launch",
             "ftv_batch_replay", "ftv_batch_query", "ftv_batch_wait", "ftv_batch_launch_count",
             "ftv_segmenter_init", "ftv_segmenter_segments", "ftv_superpixels", "ftv_segmenter_check",
-            "ftv_segmenter_launch_count", "ftv_segmenter_destroy"]
+            "ftv_segmenter_launch_count", "ftv_segmenter_destroy", "ftv_segmenter_set_profiling",
+            "ftv_segmenter_kernel_ms"]
 
 
 def _ok(code: int, where: str) -> None:
@@ -552,3 +555,14 @@ def ftv_segmenter_launch_count(sg: Segmenter) -> int:
 
 def ftv_segmenter_destroy(sg: Segmenter) -> None:
     sg.close()
+
+
+def ftv_segmenter_set_profiling(sg: Segmenter, enable: bool) -> None:
+    _ok(lib.ftv_segmenter_set_profiling(sg.handle, 1 if enable else 0), "ftv_segmenter_set_profiling")
+
+
+def ftv_segmenter_kernel_ms(sg: Segmenter) -> tuple[float, float]:
+    """(mean assignment-pass launch ms, whole-call device ms) of the most recent timed call."""
+    a, t = ctypes.c_float(), ctypes.c_float()
+    _ok(lib.ftv_segmenter_kernel_ms(sg.handle, ctypes.byref(a), ctypes.byref(t)), "ftv_segmenter_kernel_ms")
+    return float(a.value), float(t.value)

@@ -186,3 +186,20 @@ def test_launch_count_accounting():
         assert ftv.ftv_segmenter_check(sg) == 0
     finally:
         sg.close()
+
+
+def test_profiling_events_time_the_assignment_passes():
+    f = synth.mosaic(640, 360, 20, noise_sigma=8, seed=11)
+    sg = ftv.Segmenter([(640, 360)], 1, 8, 8, 5, 4)
+    try:
+        with pytest.raises(ftv.FtvError):
+            ftv.ftv_segmenter_kernel_ms(sg)  # nothing timed yet
+        ftv.ftv_segmenter_set_profiling(sg, True)
+        lab = torch.empty((360, 640), dtype=torch.int32, device="cuda")
+        ftv.ftv_superpixels(sg, [(dev(f.Y), dev(f.U), dev(f.V))], [lab])
+        a, t = ftv.ftv_segmenter_kernel_ms(sg)
+        assert 0 < 4 * a < t
+        assert ftv.ftv_segmenter_check(sg) == 0
+        assert np.array_equal(lab.cpu().numpy(), oracle.superpixels(f, 1, 8, 8, 5, 4))
+    finally:
+        sg.close()
