@@ -15,8 +15,8 @@
 //   - connectivity: components are the 8-connected sets of equally labelled pixels (named by their first
 //     pixel); a label's largest component (earliest on ties) is anchored with that label; the other
 //     components merge in rounds, each unanchored group joining the 8-adjacent group of nearest mean
-//     colour (L1 of the rounded 1/16 means; smallest name on ties), all picks of a round at once, until
-//     every group is anchored.
+//     colour (L1 of the rounded 1/16 means; on ties the group of smallest name, a group's name being its
+//     smallest component name), all picks of a round at once, until every group is anchored.
 // The result is unique (integer arithmetic, order-free rules), so it equals the CPU definition exactly.
 //
 // Kernels: seeds; per pass a tiled assignment (128 x 8 pixels per CTA, 4 adjacent pixels per thread; the
@@ -72,8 +72,9 @@ struct alignas(32) GSum {
     unsigned long long n, c0, c1, c2;
 };
 
-// counters: [0] components, [1 + r] unanchored groups at the start of round r (r = 0..rounds),
-// [2 + rounds + r] length of round r's pick list
+// counters: [0] components, [1 + r] unanchored groups at the start of round r (r = 0..rounds), which
+// is also the length of the round's list uroots, [2 + rounds + r] length of round r's pick list,
+// [3 + 2 rounds] main components
 struct Scratch {
     const SegImage* img;
     Centre* cen;
@@ -84,11 +85,14 @@ struct Scratch {
     uint4* csum;                  // [P] per component name: n, sum Y, sum Cb, sum Cr
     int32_t* gpar;                // [P] union-find over component names (groups)
     int32_t* glab;                // [P] anchored label of a group (-1 unanchored)
-    uint8_t* groot;               // [P] component name is a group root
     GSum* gsum;                   // [P] group sums (valid at group roots)
     int4* gmean;                  // [P] group mean colour in 1/16 units
     unsigned long long* best;     // [P] (distance << 32) | name picked by an unanchored group
     int32_t* comps;               // [P] list of component names
+    int32_t* uroots[2];           // [P] unanchored group roots at the start of a round, alternating
+    int32_t* mains;               // [P] the main components (anchored group roots; they stay roots)
+    int32_t* gname;               // [P] name of a group (its smallest component name), at its root
+    uint8_t* dirty;               // [P] an anchored root gained members this round
     int2* orph[2];                // [P] pick lists of (pixel, image), alternating between rounds
     int32_t* cnt;
     uint32_t* status;
@@ -385,39 +389,41 @@ __global__ void __launch_bounds__(kThreads) links_kernel(Scratch s) {
     if (is_end && x + 1 < im.W && s.lab[up + 1] == l) unite(s.par, gp, up + 1, s.status);
 }
 
-// Component name of every pixel, and the component's pixel count and colour sums.
+// Component name of every pixel, and the component's pixel count and colour sums: one walk per row run
+// (its first lane), broadcast to the run; each run's sums reduced over its lanes.
 __global__ void __launch_bounds__(kThreads) flatten_kernel(Scratch s) {
     const SegImage im = s.img[blockIdx.z];
     const int x = blockIdx.x * kTileW + threadIdx.x, y = blockIdx.y * kTileH + threadIdx.y;
     const bool valid = x < im.W && y < im.H;
+    const int32_t gp = valid ? im.pix_base + y * im.W + x : -1;
+    const int l = valid ? s.lab[gp] : -1;
+    const int lane = threadIdx.x;
+    const int left = __shfl_up_sync(kFull, l, 1);
+    const unsigned cont = __ballot_sync(kFull, valid && lane > 0 && left == l);
+    const int start = 31 - __clz(~cont & (lane == 31 ? kFull : ((2u << lane) - 1u)));
+    const unsigned above = ~cont & (start == 31 ? 0u : ~((2u << start) - 1u));  // run breaks after start
+    const int end = above ? __ffs(above) - 2 : 31;
+    const unsigned run = (end == 31 ? kFull : ((2u << end) - 1u)) & ~((1u << start) - 1u);
     int32_t r = -1;
+    if (valid && lane == start) r = find_root(s.par, gp, s.status);
+    r = __shfl_sync(kFull, r, start);
     int v0 = 0, v1 = 0, v2 = 0;
     if (valid) {
-        const int32_t gp = im.pix_base + y * im.W + x;
-        r = find_root(s.par, gp, s.status);
         s.par[gp] = r;
         v0 = sample(im, 0, x, y, s.sb);
         v1 = sample(im, 1, x, y, s.sb);
         v2 = sample(im, 2, x, y, s.sb);
     }
-    const int lane = threadIdx.x;
-    unsigned rem = __ballot_sync(kFull, valid);
-    while (rem) {
-        const int leader = __ffs(rem) - 1;
-        const int32_t rr = __shfl_sync(kFull, r, leader);
-        const bool mine = valid && r == rr;
-        const unsigned grp = __ballot_sync(kFull, mine);
-        const uint32_t s0 = __reduce_add_sync(kFull, mine ? (uint32_t)v0 : 0u);
-        const uint32_t s1 = __reduce_add_sync(kFull, mine ? (uint32_t)v1 : 0u);
-        const uint32_t s2 = __reduce_add_sync(kFull, mine ? (uint32_t)v2 : 0u);
-        if (lane == leader) {
-            uint4* t = &s.csum[rr];
-            atomicAdd(&t->x, (uint32_t)__popc(grp));
-            atomicAdd(&t->y, s0);
-            atomicAdd(&t->z, s1);
-            atomicAdd(&t->w, s2);
-        }
-        rem &= ~grp;
+    // lanes of one run share the mask; disjoint runs reduce side by side
+    const uint32_t s0 = __reduce_add_sync(run, (uint32_t)v0);
+    const uint32_t s1 = __reduce_add_sync(run, (uint32_t)v1);
+    const uint32_t s2 = __reduce_add_sync(run, (uint32_t)v2);
+    if (valid && lane == start) {
+        uint4* t = &s.csum[r];
+        atomicAdd(&t->x, (uint32_t)__popc(run));
+        atomicAdd(&t->y, s0);
+        atomicAdd(&t->z, s1);
+        atomicAdd(&t->w, s2);
     }
 }
 
@@ -435,21 +441,29 @@ __global__ void __launch_bounds__(kThreads) main_kernel(Scratch s) {
     block_append(root, gp, s.comps, &s.cnt[0]);
 }
 
-// Groups start as single components; main components are anchored with their label.
-__global__ void group_init_kernel(Scratch s) {
+// Groups start as single components; main components are anchored with their label. The unanchored
+// ones form round 0's list.
+__global__ void __launch_bounds__(kThreads) group_init_kernel(Scratch s) {
     const int n = s.cnt[0];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int32_t c = s.comps[i];
-        const int32_t k = s.lab[c];
-        const bool is_main = (uint32_t)(~s.mainkey[k]) == (uint32_t)c;
-        s.gpar[c] = c;
-        s.groot[c] = 1;
-        s.glab[c] = is_main ? k : -1;
-        const uint4 t = s.csum[c];
-        s.gsum[c] = GSum{t.x, t.y, t.z, t.w};
-        s.gmean[c] = make_int4(mean16(t.y, t.x), mean16(t.z, t.x), mean16(t.w, t.x), 0);
-        s.best[c] = kNone;
-        if (!is_main) atomicAdd(&s.cnt[1], 1);
+    for (int base = blockIdx.x * kThreads; base < n; base += gridDim.x * kThreads) {
+        const int i = base + threadIdx.x;
+        bool is_main = false;
+        int32_t c = 0;
+        if (i < n) {
+            c = s.comps[i];
+            const int32_t k = s.lab[c];
+            is_main = (uint32_t)(~s.mainkey[k]) == (uint32_t)c;
+            s.gpar[c] = c;
+            s.gname[c] = c;
+            s.glab[c] = is_main ? k : -1;
+            const uint4 t = s.csum[c];
+            s.gsum[c] = GSum{t.x, t.y, t.z, t.w};
+            s.gmean[c] = make_int4(mean16(t.y, t.x), mean16(t.z, t.x), mean16(t.w, t.x), 0);
+            s.best[c] = kNone;
+            s.dirty[c] = 0;
+        }
+        block_append(i < n && !is_main, c, s.uroots[0], &s.cnt[1]);
+        block_append(is_main, c, s.mains, &s.cnt[3 + 2 * s.rounds]);
     }
 }
 
@@ -465,11 +479,11 @@ __device__ __forceinline__ bool pick_pixel(const Scratch& s, const SegImage& im,
         for (int dx = -1; dx <= 1; ++dx) {
             const int qx = x + dx, qy = y + dy;
             if ((dx == 0 && dy == 0) || qx < 0 || qx >= im.W || qy < 0 || qy >= im.H) continue;
-            const int32_t b = s.gpar[s.par[p + dy * im.W + dx]];
+            const int32_t b = find_root(s.gpar, s.par[p + dy * im.W + dx], s.status);
             if (b == a) continue;
             const int4 mb = s.gmean[b];
             const unsigned long long d = (unsigned long long)(abs(ma.x - mb.x) + abs(ma.y - mb.y) + abs(ma.z - mb.z));
-            best = min(best, (d << 32) | (unsigned long long)(uint32_t)b);
+            best = min(best, (d << 32) | (unsigned long long)(uint32_t)s.gname[b]);
         }
     if (best == kNone) return false;
     atomicMin(&s.best[a], best);
@@ -489,7 +503,7 @@ __global__ void __launch_bounds__(kThreads) pick0_kernel(Scratch s) {
     int32_t gp = -1;
     if (x < im.W && y < im.H) {
         gp = im.pix_base + y * im.W + x;
-        const int32_t a = s.gpar[s.par[gp]];
+        const int32_t a = find_root(s.gpar, s.par[gp], s.status);
         keep = s.glab[a] < 0 && pick_pixel(s, im, gp, a);
     }
     block_append(keep, make_int2(gp, (int)blockIdx.z), s.orph[1], &s.cnt[2 + s.rounds + 1]);
@@ -507,59 +521,104 @@ __global__ void __launch_bounds__(kThreads) pick_kernel(Scratch s, int r) {
         int2 o = make_int2(0, 0);
         if (i < n) {
             o = in[i];
-            const int32_t a = s.gpar[s.par[o.x]];
+            const int32_t a = find_root(s.gpar, s.par[o.x], s.status);
             keep = s.glab[a] < 0 && pick_pixel(s, s.img[o.y], o.x, a);
         }
         block_append(keep, o, next, next_n);
     }
 }
 
-// Round r, link: all picks at once.
+// Group links order roots anchored first, then by smaller name, and hang the later root under the earlier
+// one (compare-and-swap on a root): an anchored root therefore never gets a parent, and the order is total,
+// so no cycle can form. Anchored status does not change while links are made.
+__device__ void unite_groups(Scratch& s, int32_t a, int32_t b) {
+    for (int it = 0; it < kLoopCap; ++it) {
+        a = find_root<true>(s.gpar, a, s.status);
+        b = find_root<true>(s.gpar, b, s.status);
+        if (a == b) return;
+        const bool aa = s.glab[a] >= 0, ab = s.glab[b] >= 0;
+        if (ab > aa || (ab == aa && b < a)) {
+            const int32_t t = a;
+            a = b;
+            b = t;
+        }
+        if (atomicCAS(&s.gpar[b], b, a) == b) return;
+    }
+    atomicOr(s.status, SP_LOOP_CAP);
+}
+
+// Round r, link: all picks at once (the round's unanchored roots with the groups they picked, found from
+// the picked group's name, which is one of its components).
 __global__ void link_kernel(Scratch s, int r) {
-    if (s.cnt[1 + r] == 0) return;
-    const int n = s.cnt[0];
+    const int n = s.cnt[1 + r];
+    const int32_t* u = s.uroots[r & 1];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int32_t c = s.comps[i];
+        const int32_t c = u[i];
         const unsigned long long b = s.best[c];
-        if (b != kNone) unite(s.gpar, c, (int32_t)(uint32_t)b, s.status);
+        if (b != kNone) unite_groups(s, c, (int32_t)(uint32_t)b);
     }
 }
 
-// Round r, merge: a former group root merged under another adds its sums there, and an anchored label
-// moves to the new root (a merged group holds at most one).
+// Round r, merge: every unanchored root that now hangs under another root moves its sums and its name
+// there (only the round's unanchored roots can have gained a parent).
 __global__ void merge_kernel(Scratch s, int r) {
-    if (s.cnt[1 + r] == 0) return;
-    const int n = s.cnt[0];
+    const int n = s.cnt[1 + r];
+    const int32_t* u = s.uroots[r & 1];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int32_t c = s.comps[i];
-        if (!s.groot[c]) continue;
+        const int32_t c = u[i];
         const int32_t t = find_root(s.gpar, c, s.status);
-        if (t == c) continue;  // (merge and finish run after every link of the round has landed)
+        if (t == c) continue;
         const GSum g = s.gsum[c];
         GSum* d = &s.gsum[t];
         atomicAdd(&d->n, g.n);
         atomicAdd(&d->c0, g.c0);
         atomicAdd(&d->c1, g.c1);
         atomicAdd(&d->c2, g.c2);
-        if (s.glab[c] >= 0) s.glab[t] = s.glab[c];
+        atomicMin(&s.gname[t], s.gname[c]);
+        if (s.glab[t] >= 0) s.dirty[t] = 1;
     }
 }
 
-// Round r, finish: roots, means and the count of unanchored groups for round r + 1.
-__global__ void finish_kernel(Scratch s, int r) {
+// Round r, finish: the round's roots point at their new roots; those still unanchored (then still roots)
+// get their mean and form round r + 1's list; anchored roots that gained members get their mean.
+__global__ void __launch_bounds__(kThreads) finish_kernel(Scratch s, int r) {
     if (s.cnt[1 + r] == 0) return;
+    const int n = s.cnt[1 + r];
+    const int32_t* u = s.uroots[r & 1];
+    int32_t* next = s.uroots[(r + 1) & 1];
+    for (int base = blockIdx.x * kThreads; base < n; base += gridDim.x * kThreads) {
+        const int i = base + threadIdx.x;
+        bool keep = false;
+        int32_t c = 0;
+        if (i < n) {
+            c = u[i];
+            s.best[c] = kNone;
+            const int32_t t = find_root(s.gpar, c, s.status);
+            s.gpar[c] = t;
+            if (t == c) {
+                const GSum g = s.gsum[c];
+                s.gmean[c] = make_int4(mean16(g.c0, g.n), mean16(g.c1, g.n), mean16(g.c2, g.n), 0);
+                keep = true;
+            }
+        }
+        block_append(keep, c, next, &s.cnt[2 + r]);
+    }
+    const int nm = s.cnt[3 + 2 * s.rounds];
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < nm; i += gridDim.x * kThreads) {
+        const int32_t t = s.mains[i];
+        if (!s.dirty[t]) continue;
+        s.dirty[t] = 0;
+        const GSum g = s.gsum[t];
+        s.gmean[t] = make_int4(mean16(g.c0, g.n), mean16(g.c1, g.n), mean16(g.c2, g.n), 0);
+    }
+}
+
+// Every component points straight at its group's root.
+__global__ void final_flatten_kernel(Scratch s) {
     const int n = s.cnt[0];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int32_t c = s.comps[i];
-        const int32_t t = find_root(s.gpar, c, s.status);
-        s.gpar[c] = t;
-        s.best[c] = kNone;
-        s.groot[c] = t == c;
-        if (t == c) {
-            const GSum g = s.gsum[c];
-            s.gmean[c] = make_int4(mean16(g.c0, g.n), mean16(g.c1, g.n), mean16(g.c2, g.n), 0);
-            if (s.glab[c] < 0) atomicAdd(&s.cnt[2 + r], 1);
-        }
+        s.gpar[c] = find_root(s.gpar, c, s.status);
     }
 }
 
@@ -684,10 +743,12 @@ extern "C" ftv_status ftv_segmenter_init(const ftv_segmenter_config* cfg, ftv_se
     ok = ok && dalloc(g, &g->d_img, g->n_images);
     ok = ok && dalloc(g, &s.cen, K) && dalloc(g, &s.sums, K) && dalloc(g, &s.mainkey, K);
     ok = ok && dalloc(g, &s.lab, P) && dalloc(g, &s.par, P) && dalloc(g, &s.csum, P) && dalloc(g, &s.gpar, P);
-    ok = ok && dalloc(g, &s.glab, P) && dalloc(g, &s.groot, P) && dalloc(g, &s.gsum, P) && dalloc(g, &s.gmean, P);
+    ok = ok && dalloc(g, &s.glab, P) && dalloc(g, &s.gsum, P) && dalloc(g, &s.gmean, P);
     ok = ok && dalloc(g, &s.best, P) && dalloc(g, &s.comps, P) && dalloc(g, &s.orph[0], P) &&
          dalloc(g, &s.orph[1], P);
-    ok = ok && dalloc(g, &s.cnt, 2 * g->rounds + 3) && dalloc(g, &s.status, 1);
+    ok = ok && dalloc(g, &s.uroots[0], P) && dalloc(g, &s.uroots[1], P) && dalloc(g, &s.mains, P) &&
+         dalloc(g, &s.gname, P) && dalloc(g, &s.dirty, P);
+    ok = ok && dalloc(g, &s.cnt, 2 * g->rounds + 4) && dalloc(g, &s.status, 1);
     ok = ok && cudaMemset(s.status, 0, sizeof(uint32_t)) == cudaSuccess;
     if (!ok) {
         release(g);
@@ -772,7 +833,7 @@ extern "C" ftv_status ftv_superpixels(ftv_segmenter* g, const void* const* d_pla
     Scratch& s = g->sc;
     cudaError_t e = cudaMemcpyAsync(g->d_img, g->h_img, sizeof(SegImage) * g->n_images, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaEventRecord(g->staged, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s.cnt, 0, sizeof(int32_t) * (2 * g->rounds + 3), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.cnt, 0, sizeof(int32_t) * (2 * g->rounds + 4), st);
     if (e != cudaSuccess) {
         if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
         return FTV_ERR_CUDA;
@@ -817,8 +878,9 @@ extern "C" ftv_status ftv_superpixels(ftv_segmenter* g, const void* const* d_pla
         finish_kernel<<<lgrid, kThreads, 0, st>>>(s, r);
         n += 4;
     }
+    final_flatten_kernel<<<lgrid, kThreads, 0, st>>>(s);
     relabel_kernel<<<tgrid, tblock, 0, st>>>(s);
-    ++n;
+    n += 2;
     if (prof) cudaEventRecord(g->ev[1], st);
     g->timed = g->timed || prof;
     g->launches += n;
