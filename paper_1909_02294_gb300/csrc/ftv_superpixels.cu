@@ -50,7 +50,7 @@ constexpr int kLoopCap = 1 << 26;                // bound of every union-find wa
 constexpr unsigned long long kNone = ~0ull;
 
 enum : uint32_t { SP_LOOP_CAP = 1u, SP_ROUND_CAP = 2u };
-enum : int { DIST_NARROW = 0, DIST_WIDE = 1, DIST_WIDE_COLOUR = 2 };
+enum : int { DIST_DOT32 = 0, DIST_NARROW = 1, DIST_WIDE = 2, DIST_WIDE_COLOUR = 3 };
 
 struct SegImage {
     const void* plane[3];
@@ -192,8 +192,13 @@ __global__ void seed_kernel(Scratch s) {
     s.mainkey[im.seg_base + k] = 0;
 }
 
-// D of one candidate. NARROW: the gcd-reduced weights in 32 bits (the host has shown that D stays below
-// 2^32); WIDE: 32-bit squares, 64-bit weighted sum; WIDE_COLOUR: 64-bit colour squares (bit depth > 11).
+// D of one candidate, from the staged cell (a, b). Direct forms (a = x, y, Y, Cb of the mean; b.x = Cr):
+// NARROW uses the gcd-reduced weights in 32 bits (the host has shown that D stays below 2^32); WIDE
+// 32-bit squares and a 64-bit weighted sum; WIDE_COLOUR 64-bit colour squares (bit depth > 11).
+// DOT32 drops the pixel's own squares, common to all candidates: with tile-relative positions,
+// D - wc' |v|^2 - ws' |p|^2 = K - 2 (wc' <v, c> + ws' <p, x>) where K = wc' |c|^2 + ws' |x|^2, so
+// a = (K, -2 ws' x, -2 ws' y, -2 wc' Y), b = (-2 wc' Cb, -2 wc' Cr): five multiply-adds in 32 bits
+// (the host has shown that every partial sum stays below 2^31 in magnitude).
 template <int DM>
 struct Dist {
     using T = unsigned long long;
@@ -202,13 +207,26 @@ template <>
 struct Dist<DIST_NARROW> {
     using T = uint32_t;
 };
+template <>
+struct Dist<DIST_DOT32> {
+    using T = int;
+};
 
 template <int DM>
-__device__ __forceinline__ typename Dist<DM>::T distance(const int4 a, const int c2, int vx, int vy, int w0, int w1,
+__device__ __forceinline__ typename Dist<DM>::T distance(const int4 a, const int4 b, int vx, int vy, int w0, int w1,
                                                          int w2, const Scratch& s) {
+    if (DM == DIST_DOT32) {
+        int d = a.x;
+        d += vx * a.y;
+        d += vy * a.z;
+        d += w0 * a.w;
+        d += w1 * b.x;
+        d += w2 * b.y;
+        return d;
+    }
     const int dx = vx - a.x, dy = vy - a.y;
     const uint32_t dsp = (uint32_t)dx * (uint32_t)dx + (uint32_t)dy * (uint32_t)dy;
-    const int d0 = w0 - a.z, d1 = w1 - a.w, d2 = w2 - c2;
+    const int d0 = w0 - a.z, d1 = w1 - a.w, d2 = w2 - b.x;
     if (DM == DIST_NARROW) {
         const uint32_t dcol = (uint32_t)d0 * (uint32_t)d0 + (uint32_t)d1 * (uint32_t)d1 + (uint32_t)d2 * (uint32_t)d2;
         return (typename Dist<DM>::T)(s.wcn * dcol + s.wsn * dsp);
@@ -225,6 +243,9 @@ __device__ __forceinline__ typename Dist<DM>::T distance(const int4 a, const int
 
 // One assignment pass over a 128 x 8 tile (4 adjacent pixels per thread). accumulate: add every pixel to
 // its cluster's sums for the next update. last: also start the component search (par = self).
+// The 3 x 3 candidates are visited unrolled in increasing label order; a candidate outside the grid is
+// replaced by the nearest existing cell, a repeat of a label already visited with the same D, which the
+// strict comparison ignores.
 template <int DM>
 __global__ void __launch_bounds__(kThreads) assign_kernel(Scratch s, int accumulate, int last) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -235,15 +256,25 @@ __global__ void __launch_bounds__(kThreads) assign_kernel(Scratch s, int accumul
     const int cx0 = max(0, x0 / S - 1), cx1 = min(im.gw - 1, min(im.W - 1, x0 + kATileW - 1) / S + 1);
     const int cy0 = max(0, y0 / S - 1), cy1 = min(im.gh - 1, min(im.H - 1, y0 + kATileH - 1) / S + 1);
     const int ncx = cx1 - cx0 + 1, ncells = ncx * (cy1 - cy0 + 1);
-    int4* sA = reinterpret_cast<int4*>(smem);          // x, y, Y, Cb of each visible cell's centre
-    int* sB = reinterpret_cast<int*>(sA + MC);         // Cr
+    int4* sA = reinterpret_cast<int4*>(smem);
+    int4* sB = sA + MC;
     uint32_t* acc = reinterpret_cast<uint32_t*>(sB + MC);  // [6][MC]: n, x, y, Y, Cb, Cr
     const int tid = threadIdx.y * 32 + threadIdx.x;
     for (int e = tid; e < ncells; e += kThreads) {
         const int j = cy0 + e / ncx, i = cx0 + e % ncx;
         const Centre c = s.cen[im.seg_base + j * im.gw + i];
-        sA[e] = make_int4(c.x, c.y, c.c0, c.c1);
-        sB[e] = c.c2;
+        if (DM == DIST_DOT32) {
+            const int xr = c.x - 16 * x0, yr = c.y - 16 * y0;
+            const long long K = (long long)s.wcn * ((long long)c.c0 * c.c0 + (long long)c.c1 * c.c1 +
+                                                    (long long)c.c2 * c.c2) +
+                                (long long)s.wsn * ((long long)xr * xr + (long long)yr * yr);
+            const int wc2 = 2 * (int)s.wcn, ws2 = 2 * (int)s.wsn;
+            sA[e] = make_int4((int)K, -ws2 * xr, -ws2 * yr, -wc2 * c.c0);
+            sB[e] = make_int4(-wc2 * c.c1, -wc2 * c.c2, 0, 0);
+        } else {
+            sA[e] = make_int4(c.x, c.y, c.c0, c.c1);
+            sB[e] = make_int4(c.c2, 0, 0, 0);
+        }
         if (accumulate)
             for (int f = 0; f < 6; ++f) acc[f * MC + e] = 0;
     }
@@ -254,8 +285,9 @@ __global__ void __launch_bounds__(kThreads) assign_kernel(Scratch s, int accumul
     uint32_t rn = 0, rx = 0, ry = 0, r0 = 0, r1 = 0, r2 = 0;
     if (y < im.H) {
         const int cj = y / S;
-        const int jlo = max(cj - 1, 0), jhi = min(cj + 1, im.gh - 1);
-        const int vy = 16 * y;
+        const int ro[3] = {(max(cj - 1, 0) - cy0) * ncx - cx0, (cj - cy0) * ncx - cx0,
+                           (min(cj + 1, im.gh - 1) - cy0) * ncx - cx0};
+        const int vy = DM == DIST_DOT32 ? 16 * (y - y0) : 16 * y;
         const int64_t row = (int64_t)im.pix_base + (int64_t)y * im.W;
 #pragma unroll 1
         for (int q = 0; q < kPX; ++q) {
@@ -263,19 +295,18 @@ __global__ void __launch_bounds__(kThreads) assign_kernel(Scratch s, int accumul
             if (x >= im.W) break;
             const int v0 = sample(im, 0, x, y, s.sb), v1 = sample(im, 1, x, y, s.sb), v2 = sample(im, 2, x, y, s.sb);
             const int ci = x / S;
-            const int ilo = max(ci - 1, 0), ihi = min(ci + 1, im.gw - 1);
-            const int vx = 16 * x, w0 = 16 * v0, w1 = 16 * v1, w2 = 16 * v2;
-            int be = -1;
-            typename Dist<DM>::T bd = 0;
-            for (int j = jlo; j <= jhi; ++j) {
-                const int rowe = (j - cy0) * ncx - cx0;
-                for (int i = ilo; i <= ihi; ++i) {  // labels in increasing order: ties keep the smaller
-                    const int e = rowe + i;
-                    const typename Dist<DM>::T D = distance<DM>(sA[e], sB[e], vx, vy, w0, w1, w2, s);
-                    if (be < 0 || D < bd) {
-                        be = e;
-                        bd = D;
-                    }
+            const int co[3] = {max(ci - 1, 0), ci, min(ci + 1, im.gw - 1)};
+            const int vx = DM == DIST_DOT32 ? 16 * (x - x0) : 16 * x;
+            const int w0 = 16 * v0, w1 = 16 * v1, w2 = 16 * v2;
+            int be = ro[0] + co[0];
+            typename Dist<DM>::T bd = distance<DM>(sA[be], sB[be], vx, vy, w0, w1, w2, s);
+#pragma unroll
+            for (int c = 1; c < 9; ++c) {
+                const int e = ro[c / 3] + co[c % 3];
+                const typename Dist<DM>::T D = distance<DM>(sA[e], sB[e], vx, vy, w0, w1, w2, s);
+                if (D < bd) {
+                    be = e;
+                    bd = D;
                 }
             }
             const int bj = cy0 + be / ncx, bi = cx0 + be % ncx;
@@ -763,31 +794,46 @@ extern "C" ftv_status ftv_segmenter_init(const ftv_segmenter_config* cfg, ftv_se
     s.ws = g->ws;
     // Distance arithmetic. |x - X| < 3S in pixels for every candidate (a candidate's pixels, hence its
     // mean, lie within one cell of the candidate's cell), so in 1/16 units dsp < 2 (48 S)^2, and
-    // dcol <= 3 (16 (2^bd - 1))^2 for samples within the bit depth.
+    // dcol <= 3 (16 (2^bd - 1))^2 for samples within the bit depth. In the DOT32 form positions are
+    // relative to the tile, |position| <= 16 (127 + 3S) = R, and every partial sum is bounded by
+    // wc' 3 vmax^2 + ws' 6 R^2.
     {
         const unsigned long long gcd = std::gcd(g->wc, g->ws);
         const unsigned long long wcn = g->wc / gcd, wsn = g->ws / gcd;
         const unsigned long long vmax = 16ull * ((1ull << g->bd) - 1), dmax = 48ull * g->S;
-        const unsigned long long bound = wcn * 3ull * vmax * vmax + wsn * 2ull * dmax * dmax;
-        g->dist_mode = bound < (1ull << 32) ? DIST_NARROW : (g->bd <= 11 ? DIST_WIDE : DIST_WIDE_COLOUR);
-        s.wcn = (uint32_t)(g->dist_mode == DIST_NARROW ? wcn : 0);
-        s.wsn = (uint32_t)(g->dist_mode == DIST_NARROW ? wsn : 0);
+        const unsigned long long R = 16ull * (kATileW - 1 + 3ull * g->S);
+        const unsigned long long direct = wcn * 3ull * vmax * vmax + wsn * 2ull * dmax * dmax;
+        const unsigned long long dot = wcn * 3ull * vmax * vmax + wsn * 6ull * R * R;
+        g->dist_mode = dot < (1ull << 31) ? DIST_DOT32
+                       : direct < (1ull << 32) ? DIST_NARROW
+                       : (g->bd <= 11 ? DIST_WIDE : DIST_WIDE_COLOUR);
+        s.wcn = (uint32_t)(g->dist_mode <= DIST_NARROW ? wcn : 0);
+        s.wsn = (uint32_t)(g->dist_mode <= DIST_NARROW ? wsn : 0);
     }
     // shared memory of an assignment tile: the cells it can see, 44 bytes each
     {
         const int ncx = (kATileW - 1 + g->S - 1) / g->S + 3, ncy = (kATileH - 1 + g->S - 1) / g->S + 3;
         s.max_cells = ncx * ncy;
-        g->assign_smem = (size_t)s.max_cells * (sizeof(int4) + sizeof(int) + 6 * sizeof(uint32_t));
+        g->assign_smem = (size_t)s.max_cells * (2 * sizeof(int4) + 6 * sizeof(uint32_t));
         cudaError_t e = cudaSuccess;
-        if (g->dist_mode == DIST_NARROW)
-            e = cudaFuncSetAttribute(assign_kernel<DIST_NARROW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)g->assign_smem);
-        else if (g->dist_mode == DIST_WIDE)
-            e = cudaFuncSetAttribute(assign_kernel<DIST_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)g->assign_smem);
-        else
-            e = cudaFuncSetAttribute(assign_kernel<DIST_WIDE_COLOUR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)g->assign_smem);
+        const int smem_bytes = (int)g->assign_smem;
+        switch (g->dist_mode) {
+            case DIST_DOT32:
+                e = cudaFuncSetAttribute(assign_kernel<DIST_DOT32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_bytes);
+                break;
+            case DIST_NARROW:
+                e = cudaFuncSetAttribute(assign_kernel<DIST_NARROW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_bytes);
+                break;
+            case DIST_WIDE:
+                e = cudaFuncSetAttribute(assign_kernel<DIST_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_bytes);
+                break;
+            default:
+                e = cudaFuncSetAttribute(assign_kernel<DIST_WIDE_COLOUR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_bytes);
+        }
         if (e != cudaSuccess) {
             release(g);
             return FTV_ERR_CUDA;
@@ -854,9 +900,12 @@ extern "C" ftv_status ftv_superpixels(ftv_segmenter* g, const void* const* d_pla
         const int acc = it + 1 < g->T, last = it + 1 == g->T;
         if (prof) cudaEventRecord(g->ev[2 + 2 * it], st);
         const size_t sm_bytes = g->assign_smem;
-        if (g->dist_mode == DIST_NARROW) assign_kernel<DIST_NARROW><<<agrid, tblock, sm_bytes, st>>>(s, acc, last);
-        else if (g->dist_mode == DIST_WIDE) assign_kernel<DIST_WIDE><<<agrid, tblock, sm_bytes, st>>>(s, acc, last);
-        else assign_kernel<DIST_WIDE_COLOUR><<<agrid, tblock, sm_bytes, st>>>(s, acc, last);
+        switch (g->dist_mode) {
+            case DIST_DOT32: assign_kernel<DIST_DOT32><<<agrid, tblock, sm_bytes, st>>>(s, acc, last); break;
+            case DIST_NARROW: assign_kernel<DIST_NARROW><<<agrid, tblock, sm_bytes, st>>>(s, acc, last); break;
+            case DIST_WIDE: assign_kernel<DIST_WIDE><<<agrid, tblock, sm_bytes, st>>>(s, acc, last); break;
+            default: assign_kernel<DIST_WIDE_COLOUR><<<agrid, tblock, sm_bytes, st>>>(s, acc, last);
+        }
         if (prof) cudaEventRecord(g->ev[3 + 2 * it], st);
         ++n;
         if (acc) {
