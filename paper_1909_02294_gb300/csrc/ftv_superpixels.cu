@@ -498,23 +498,37 @@ __global__ void __launch_bounds__(kThreads) group_init_kernel(Scratch s) {
     }
 }
 
-// The pick of one pixel p of group a (unanchored): the neighbouring group of least (distance, name).
-__device__ __forceinline__ bool pick_pixel(const Scratch& s, const SegImage& im, int32_t p, int32_t a) {
+// The pick of one pixel p (component pc) of group a (unanchored): the neighbouring group of least
+// (distance, name). The lookups run in stages over all eight neighbours at once (components, one step
+// up the group forest, the rest of the walk where one is left, then means and names), so that each
+// stage's independent loads are in flight together; neighbours in p's own component are skipped.
+__device__ __forceinline__ bool pick_pixel(const Scratch& s, const SegImage& im, int32_t p, int32_t pc, int32_t a) {
     const int local = p - im.pix_base;
     const int x = local % im.W, y = local / im.W;
+    int32_t g[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int dx = k < 3 ? k - 1 : (k == 3 ? -1 : (k == 4 ? 1 : k - 6));
+        const int dy = k < 3 ? -1 : (k < 5 ? 0 : 1);
+        const int qx = x + dx, qy = y + dy;
+        g[k] = (qx >= 0 && qx < im.W && qy >= 0 && qy < im.H) ? s.par[p + dy * im.W + dx] : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) g[k] = (g[k] < 0 || g[k] == pc) ? -1 : s.gpar[g[k]];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        if (g[k] >= 0) {
+            const int32_t up = s.gpar[g[k]];
+            if (up != g[k]) g[k] = find_root(s.gpar, up, s.status);
+        }
     const int4 ma = s.gmean[a];
     unsigned long long best = kNone;
 #pragma unroll
-    for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-            const int qx = x + dx, qy = y + dy;
-            if ((dx == 0 && dy == 0) || qx < 0 || qx >= im.W || qy < 0 || qy >= im.H) continue;
-            const int32_t b = find_root(s.gpar, s.par[p + dy * im.W + dx], s.status);
-            if (b == a) continue;
-            const int4 mb = s.gmean[b];
+    for (int k = 0; k < 8; ++k)
+        if (g[k] >= 0 && g[k] != a) {
+            const int4 mb = s.gmean[g[k]];
             const unsigned long long d = (unsigned long long)(abs(ma.x - mb.x) + abs(ma.y - mb.y) + abs(ma.z - mb.z));
-            best = min(best, (d << 32) | (unsigned long long)(uint32_t)s.gname[b]);
+            best = min(best, (d << 32) | (unsigned long long)(uint32_t)s.gname[g[k]]);
         }
     if (best == kNone) return false;
     atomicMin(&s.best[a], best);
@@ -534,8 +548,9 @@ __global__ void __launch_bounds__(kThreads) pick0_kernel(Scratch s) {
     int32_t gp = -1;
     if (x < im.W && y < im.H) {
         gp = im.pix_base + y * im.W + x;
-        const int32_t a = find_root(s.gpar, s.par[gp], s.status);
-        keep = s.glab[a] < 0 && pick_pixel(s, im, gp, a);
+        const int32_t pc = s.par[gp];
+        const int32_t a = find_root(s.gpar, pc, s.status);
+        keep = s.glab[a] < 0 && pick_pixel(s, im, gp, pc, a);
     }
     block_append(keep, make_int2(gp, (int)blockIdx.z), s.orph[1], &s.cnt[2 + s.rounds + 1]);
 }
@@ -552,8 +567,9 @@ __global__ void __launch_bounds__(kThreads) pick_kernel(Scratch s, int r) {
         int2 o = make_int2(0, 0);
         if (i < n) {
             o = in[i];
-            const int32_t a = find_root(s.gpar, s.par[o.x], s.status);
-            keep = s.glab[a] < 0 && pick_pixel(s, s.img[o.y], o.x, a);
+            const int32_t pc = s.par[o.x];
+            const int32_t a = find_root(s.gpar, pc, s.status);
+            keep = s.glab[a] < 0 && pick_pixel(s, s.img[o.y], o.x, pc, a);
         }
         block_append(keep, o, next, next_n);
     }
