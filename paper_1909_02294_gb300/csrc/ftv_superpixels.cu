@@ -285,20 +285,25 @@ __global__ void __launch_bounds__(kThreads) assign_kernel(Scratch s, int accumul
     uint32_t rn = 0, rx = 0, ry = 0, r0 = 0, r1 = 0, r2 = 0;
     if (y < im.H) {
         const int cj = y / S;
-        const int ro[3] = {(max(cj - 1, 0) - cy0) * ncx - cx0, (cj - cy0) * ncx - cx0,
-                           (min(cj + 1, im.gh - 1) - cy0) * ncx - cx0};
+        const int jv[3] = {max(cj - 1, 0), cj, min(cj + 1, im.gh - 1)};
+        const int ro[3] = {(jv[0] - cy0) * ncx - cx0, (jv[1] - cy0) * ncx - cx0, (jv[2] - cy0) * ncx - cx0};
         const int vy = DM == DIST_DOT32 ? 16 * (y - y0) : 16 * y;
         const int64_t row = (int64_t)im.pix_base + (int64_t)y * im.W;
+        const int xs = x0 + kPX * threadIdx.x;
+        int ci = xs / S, rem = xs - ci * S;  // cell column of the current pixel, and x within the cell
 #pragma unroll 1
-        for (int q = 0; q < kPX; ++q) {
-            const int x = x0 + kPX * threadIdx.x + q;
+        for (int q = 0; q < kPX; ++q, ++rem) {
+            const int x = xs + q;
             if (x >= im.W) break;
+            if (rem == S) {
+                ++ci;
+                rem = 0;
+            }
             const int v0 = sample(im, 0, x, y, s.sb), v1 = sample(im, 1, x, y, s.sb), v2 = sample(im, 2, x, y, s.sb);
-            const int ci = x / S;
             const int co[3] = {max(ci - 1, 0), ci, min(ci + 1, im.gw - 1)};
             const int vx = DM == DIST_DOT32 ? 16 * (x - x0) : 16 * x;
             const int w0 = 16 * v0, w1 = 16 * v1, w2 = 16 * v2;
-            int be = ro[0] + co[0];
+            int be = ro[0] + co[0], bc = 0;
             typename Dist<DM>::T bd = distance<DM>(sA[be], sB[be], vx, vy, w0, w1, w2, s);
 #pragma unroll
             for (int c = 1; c < 9; ++c) {
@@ -306,10 +311,13 @@ __global__ void __launch_bounds__(kThreads) assign_kernel(Scratch s, int accumul
                 const typename Dist<DM>::T D = distance<DM>(sA[e], sB[e], vx, vy, w0, w1, w2, s);
                 if (D < bd) {
                     be = e;
+                    bc = c;
                     bd = D;
                 }
             }
-            const int bj = cy0 + be / ncx, bi = cx0 + be % ncx;
+            const int bj = bc < 3 ? jv[0] : (bc < 6 ? jv[1] : jv[2]);
+            const int bm = bc - 3 * (bc < 3 ? 0 : (bc < 6 ? 1 : 2));
+            const int bi = bm == 0 ? co[0] : (bm == 1 ? co[1] : co[2]);
             const int64_t gp = row + x;
             s.lab[gp] = im.seg_base + bj * im.gw + bi;
             if (last) {
