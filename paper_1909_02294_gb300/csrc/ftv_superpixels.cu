@@ -82,7 +82,8 @@ struct Scratch {
     unsigned long long* mainkey;  // [K]: (size << 32) | ~name of the label's largest component
     int32_t* lab;                 // [P] global segment id of each pixel
     int32_t* par;                 // [P] union-find over pixels, then the component name
-    uint4* csum;                  // [P] per component name: n, sum Y, sum Cb, sum Cr
+    ulonglong2* csum;             // [P] per component name: (n << 40) + sum Y, (sum Cb << 32) + sum Cr
+                                  // (a component lies in one cluster: n < 2^24, each sum < 2^32)
     int32_t* gpar;                // [P] union-find over component names (groups)
     int32_t* glab;                // [P] anchored label of a group (-1 unanchored)
     GSum* gsum;                   // [P] group sums (valid at group roots)
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(kThreads) assign_kernel(Scratch s, int accumul
             s.lab[gp] = im.seg_base + bj * im.gw + bi;
             if (last) {
                 s.par[gp] = (int32_t)gp;
-                s.csum[gp] = make_uint4(0, 0, 0, 0);
+                s.csum[gp] = make_ulonglong2(0, 0);
             }
             if (accumulate) {
                 if (be != rk) {
@@ -458,11 +459,9 @@ __global__ void __launch_bounds__(kThreads) flatten_kernel(Scratch s) {
     const uint32_t s1 = __reduce_add_sync(run, (uint32_t)v1);
     const uint32_t s2 = __reduce_add_sync(run, (uint32_t)v2);
     if (valid && lane == start) {
-        uint4* t = &s.csum[r];
-        atomicAdd(&t->x, (uint32_t)__popc(run));
-        atomicAdd(&t->y, s0);
-        atomicAdd(&t->z, s1);
-        atomicAdd(&t->w, s2);
+        ulonglong2* t = &s.csum[r];
+        atomicAdd(&t->x, ((unsigned long long)__popc(run) << 40) + s0);
+        atomicAdd(&t->y, ((unsigned long long)s1 << 32) + s2);
     }
 }
 
@@ -474,7 +473,7 @@ __global__ void __launch_bounds__(kThreads) main_kernel(Scratch s) {
     const int32_t gp = valid ? im.pix_base + y * im.W + x : -1;
     const bool root = valid && s.par[gp] == gp;
     if (root) {
-        const unsigned long long key = ((unsigned long long)s.csum[gp].x << 32) | (unsigned long long)(~(uint32_t)gp);
+        const unsigned long long key = ((s.csum[gp].x >> 40) << 32) | (unsigned long long)(~(uint32_t)gp);
         atomicMax(&s.mainkey[s.lab[gp]], key);
     }
     block_append(root, gp, s.comps, &s.cnt[0]);
@@ -495,9 +494,11 @@ __global__ void __launch_bounds__(kThreads) group_init_kernel(Scratch s) {
             s.gpar[c] = c;
             s.gname[c] = c;
             s.glab[c] = is_main ? k : -1;
-            const uint4 t = s.csum[c];
-            s.gsum[c] = GSum{t.x, t.y, t.z, t.w};
-            s.gmean[c] = make_int4(mean16(t.y, t.x), mean16(t.z, t.x), mean16(t.w, t.x), 0);
+            const ulonglong2 t = s.csum[c];
+            const unsigned long long n = t.x >> 40, sy = t.x & ((1ull << 40) - 1), scb = t.y >> 32,
+                                     scr = t.y & 0xffffffffull;
+            s.gsum[c] = GSum{n, sy, scb, scr};
+            s.gmean[c] = make_int4(mean16(sy, n), mean16(scb, n), mean16(scr, n), 0);
             s.best[c] = kNone;
             s.dirty[c] = 0;
         }

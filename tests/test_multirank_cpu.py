@@ -40,3 +40,18 @@ def test_single_process_without_group():
     import bench
     assert bench.reduce_max(1.5, "cpu") == 1.5
     assert bench.whole_job_rate(1, 10.0, 2.0) == 5.0
+
+
+@pytest.mark.parametrize("W,H,S", [(1920, 1080, 10), (37, 23, 5), (1, 1, 1), (7, 9, 64), (13, 4, 3)])
+def test_segmentation_roofline_counts_every_existing_candidate(W, H, S):
+    """The segmentation roofline divides by the exact number of (pixel, candidate cell) pairs of one
+    assignment pass: the cells (i + a, j + b), a, b in {-1, 0, 1}, that exist. Brute force on a grid."""
+    import numpy as np
+
+    import bench
+    gw, gh = -(-W // S), -(-H // S)
+    ci = np.arange(W) // S
+    cj = np.arange(H) // S
+    nx = sum(1 for a in (-1, 0, 1) for i in ci if 0 <= i + a < gw)
+    ny = sum(1 for b in (-1, 0, 1) for j in cj if 0 <= j + b < gh)
+    assert bench.seg_candidates(W, H, S) == nx * ny
