@@ -93,7 +93,7 @@ struct Scratch {
     int32_t* uroots[2];           // [P] unanchored group roots at the start of a round, alternating
     int32_t* mains;               // [P] the main components (anchored group roots; they stay roots)
     int32_t* gname;               // [P] name of a group (its smallest component name), at its root
-    uint8_t* dirty;               // [P] an anchored root gained members this round
+    uint8_t* dirty;               // [P] an anchored root gained members in the current merge round
     int2* orph[2];                // [P] pick lists of (pixel, image), alternating between rounds
     int32_t* cnt;
     uint32_t* status;
