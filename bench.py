@@ -138,12 +138,14 @@ def _traffic_for_current_kernel(workload_key: str, table: str = "cost_kernel_tra
     return None
 
 
-def algorithmic_bytes(wl) -> tuple[int, int]:
-    """Per cost-volume launch: (evaluation bytes, compulsory bytes). One evaluation reads one 3-sample
-    texel of the neighbour view (3 x sample_bytes); compulsory streams are every packed view read once,
-    each reference pixel's index record and reference texel, and the int32 volume written once."""
+def algorithmic_bytes(wl, culled: int = 0) -> tuple[int, int]:
+    """Per cost-volume launch: (evaluation bytes, compulsory bytes). One sampled evaluation reads one
+    3-sample texel of the neighbour view (3 x sample_bytes); evaluations the kernel decided without
+    sampling (a whole tile out of a neighbour's view, ftv_culled_evaluations) read nothing. Compulsory
+    streams are every packed view read once, each reference pixel's index record and reference texel,
+    and the int32 volume written once."""
     sb = wl.sample_bytes
-    evals = wl.evaluations()
+    evals = wl.evaluations() - culled
     comp = 0
     for v in range(wl.n_views):
         c = wl.cams[v]
@@ -164,9 +166,10 @@ OPS_PER_EVAL = 29
 OPS_PER_PIXEL_LABEL = 1
 
 
-def algorithmic_ops(wl) -> int:
+def algorithmic_ops(wl, culled: int = 0) -> int:
+    """Per cost-volume launch; a culled evaluation (decided without sampling) is not charged."""
     px_labels = sum(wl.cams[r].width * wl.cams[r].height * wl.n_labels for r in wl.ref_views)
-    return wl.evaluations() * OPS_PER_EVAL + px_labels * OPS_PER_PIXEL_LABEL
+    return (wl.evaluations() - culled) * OPS_PER_EVAL + px_labels * OPS_PER_PIXEL_LABEL
 
 
 def cpu_baseline(wl, budget_s: float = 12.0, min_rows: int = 4):
@@ -468,6 +471,7 @@ def main():
             kernel_ms.append(ftv.ftv_last_kernel_ms(ctx))
         torch.cuda.synchronize()
     launches = ftv.ftv_launch_count(ctx) - launches0
+    culled = ftv.ftv_culled_evaluations(ctx)  # the same for every step (the last launch's count)
     if world > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -505,7 +509,7 @@ def main():
 
     if rank == 0:
         peak, peak_kind = _peaks()
-        ev_bytes, comp_bytes = algorithmic_bytes(wl)
+        ev_bytes, comp_bytes = algorithmic_bytes(wl, culled)
         kms = statistics.mean(kernel_ms)
         achieved = (ev_bytes + comp_bytes) / (kms / 1000.0) / 1e9
         traffic = _traffic_for_current_kernel(args.workload)
@@ -513,7 +517,7 @@ def main():
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         sm_mhz = clk["sm_mhz"] if clk else 2070.0
         alu_peak = n_sm * 128 * sm_mhz * 1e6 / 1e12  # lane operations per second, Tops/s
-        alu_achieved = algorithmic_ops(wl) / (kms / 1000.0) / 1e12
+        alu_achieved = algorithmic_ops(wl, culled) / (kms / 1000.0) / 1e12
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
@@ -521,17 +525,19 @@ def main():
             "config": {"workload": _workload_desc(wl), "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "depth_maps_per_s": whole_job_rate(world, R * args.steps, total_s),
-                       "cost_kernel_ms": kms, "evaluations_per_step": evals},
+                       "cost_kernel_ms": kms, "evaluations_per_step": evals,
+                       "culled_evaluations_per_step": culled, "culled_fraction": culled / evals},
             "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Tops/s",
                          "frac": alu_achieved / alu_peak, "traffic": traffic,
                          "peak_kind": f"{n_sm} SMs x 128 lanes x {sm_mhz:.0f} MHz (median sampled SM clock)",
-                         "algorithmic_ops_per_launch": algorithmic_ops(wl), "ops_per_evaluation": OPS_PER_EVAL,
+                         "algorithmic_ops_per_launch": algorithmic_ops(wl, culled), "ops_per_evaluation": OPS_PER_EVAL,
                          "kernel": "cost_kernel<FMT_P10, MIN>"},
             "hbm_roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "peak_kind": peak_kind,
                              "algorithmic_bytes_per_launch": ev_bytes + comp_bytes,
-                             "definition": "one 3-sample texel (3 x sample bytes) per evaluation + compulsory "
-                                           "streams, over the cost kernel's event-timed duration"},
+                             "definition": "one 3-sample texel (3 x sample bytes) per sampled evaluation (culled "
+                                           "ones read nothing) + compulsory streams, over the cost kernel's "
+                                           "event-timed duration"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clk,

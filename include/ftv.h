@@ -444,6 +444,16 @@ FTV_API ftv_status ftv_segmenter_destroy(ftv_segmenter* sg);
 /* Wait for `stream`, then return and clear the context's device status word (FTV_OK if clean). */
 FTV_API ftv_status ftv_check(ftv_ctx* ctx, ftv_stream stream);
 
+/* Wait for `stream`, then report in *culled how many pixel x label x neighbour evaluations of the context's
+ * most recent ftv_cost_volume call were decided without sampling. The cost kernel bounds each tile of
+ * pixels by its box and tests every (neighbour, label) homography against the neighbour view at the
+ * box's corners, with a margin that covers the FP32 contract's rounding at every pixel of the box; when
+ * no pixel can land inside the view, every one of those samples costs the out-of-view penalty, which is
+ * what the kernel then applies (under the minimum with a penalty of at least 3 (2^bit_depth - 1), the
+ * default, that changes nothing). Results are identical with and without this; the count is for
+ * accounting (a roofline that charges only the samples taken). */
+FTV_API ftv_status ftv_culled_evaluations(ftv_ctx* ctx, ftv_stream stream, int64_t* culled);
+
 /* Timing of the dominant kernel: with enable != 0, every ftv_cost_volume call records a pair of CUDA
  * events on its stream immediately around its cost-kernel launch (the events belong to the context). */
 FTV_API ftv_status ftv_set_profiling(ftv_ctx* ctx, int32_t enable);

@@ -470,6 +470,15 @@ ftv_status ftv_wta_depth(ftv_ctx* ctx, int32_t ref_index, const int32_t* d_cost,
     return e == cudaSuccess ? FTV_OK : FTV_ERR_CUDA;
 }
 
+ftv_status ftv_culled_evaluations(ftv_ctx* ctx, ftv_stream stream, int64_t* culled) {
+    if (!ctx || !culled) return FTV_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return FTV_ERR_CUDA;
+    unsigned long long v = 0;
+    if (cudaMemcpy(&v, &ctx->d_plan->culled, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return FTV_ERR_CUDA;
+    *culled = (int64_t)v;
+    return FTV_OK;
+}
+
 ftv_status ftv_check(ftv_ctx* ctx, ftv_stream stream) {
     if (!ctx) return FTV_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);

@@ -92,7 +92,8 @@ struct TexelOps<FMT_U16X4> {
 //   kRect     unit with h0 = 1, h1 = 0, h3 = 0, h4 = 1, |h5| < 0.25 (rectified rigs: the row is kept):
 //             X = fma(1, x, fma(0, y, h2)) is x + h2 rounded once, and Y = y + h5 rounded once lies
 //             within 0.25 + 2^-9 of the integer y < 2^15, so floor(Y + 0.5) is exactly y;
-//   kOut      affine with 1/h8 not finite and positive: every sample is out of view.
+//   kOut      affine with 1/h8 not finite and positive, or no pixel of the item's tile can reach the view
+//             (box_out_of_view): every sample is out of view.
 // All of them give bit-identical results to the general sequence; they only skip work whose result
 // is known exactly.
 struct __align__(16) HEntry {
@@ -193,6 +194,43 @@ __device__ __forceinline__ void accumulate(int& m, bool ok, const void* tex, int
     }
 }
 
+// True when no pixel of the box [x0, x1] x [y0, y1] can sample the wv x hv view under the FP32 contract.
+// At every corner the homography must put the point left of u = -1 (X + Wz < 0), right of u = wv
+// (X - wv Wz > 0), above v = -1 or below v = hv (the same with Y), or behind the camera (Wz < 0), each
+// with a margin of 2^-20 times the magnitude of its terms. The contract's FP32 evaluation at any pixel
+// of the box is within 2^-23 of those magnitudes of the exact value, and each condition together with
+// that error bound is convex in the pixel position, so holding at the four corners it holds at every
+// pixel of the box: there a point left of u = -1 has u + 0.5 < 0 after rounding (a column below 0), one
+// right of u = wv rounds to a column of at least wv (likewise for rows), and one behind the camera has
+// Wz <= 0, which the contract counts as out of view. |h| <= 2^100 keeps every term finite; an overflow
+// or a NaN fails the comparisons and keeps the box.
+__device__ __forceinline__ bool box_out_of_view(const float* __restrict__ hg, float x0, float x1, float y0, float y1,
+                                                float wv, float hv) {
+    float h[9];
+#pragma unroll
+    for (int f = 0; f < 9; ++f) h[f] = __ldg(&hg[f]);
+    const float m = 0x1p-20f;
+    bool left = true, right = true, top = true, bottom = true, behind = true;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float x = (k & 1) ? x1 : x0, y = (k & 2) ? y1 : y0;  // x, y >= 0
+        const float X = __fmaf_rn(h[0], x, __fmaf_rn(h[1], y, h[2]));
+        const float Y = __fmaf_rn(h[3], x, __fmaf_rn(h[4], y, h[5]));
+        const float Z = __fmaf_rn(h[6], x, __fmaf_rn(h[7], y, h[8]));
+        const float sx = __fmaf_rn(fabsf(h[0]), x, __fmaf_rn(fabsf(h[1]), y, fabsf(h[2])));
+        const float sy = __fmaf_rn(fabsf(h[3]), x, __fmaf_rn(fabsf(h[4]), y, fabsf(h[5])));
+        const float sz = __fmaf_rn(fabsf(h[6]), x, __fmaf_rn(fabsf(h[7]), y, fabsf(h[8])));
+        const float tl = __fadd_rn(X, Z), tr = __fmaf_rn(-wv, Z, X);
+        const float tt = __fadd_rn(Y, Z), tb = __fmaf_rn(-hv, Z, Y);
+        left = left && tl < -m * (sx + sz + fabsf(tl));
+        right = right && tr > m * (sx + wv * sz + fabsf(tr));
+        top = top && tt < -m * (sy + sz + fabsf(tt));
+        bottom = bottom && tb > m * (sy + hv * sz + fabsf(tb));
+        behind = behind && Z < -m * (sz + fabsf(Z));
+    }
+    return left || right || top || bottom || behind;
+}
+
 __device__ __forceinline__ int find_job(const RefJob* __restrict__ jobs, int n_jobs, int item) {
     int lo = 0, hi = n_jobs - 1;
     while (lo < hi) {
@@ -238,7 +276,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
     __shared__ const void* sBase[FTV_MAX_NBRS];
     __shared__ int sAcc[kSegAcc * kMaxLB];
     __shared__ int sWoffs[kLocCache + 1];
-    __shared__ int s_item, s_k0, s_k1;
+    __shared__ int s_item, s_k0, s_k1, s_culled;
+    __shared__ int s_box[4];  // the tile's pixel box: x min, x max, y min, y max
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int total = *reinterpret_cast<volatile int*>(&plan->total_items);
@@ -293,6 +332,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
             E.pm = (uint32_t)nbrs[n].pitch | (mode << 28);
         }
         for (int i = tid; i < N; i += kThreads) sBase[i] = nbrs[i].texels;
+        if (tid == 0) {
+            s_box[0] = s_box[2] = INT_MAX;
+            s_box[1] = s_box[3] = INT_MIN;
+            s_culled = 0;
+        }
         if (tid < 32) {
             const int k = warp_upper_index(woffs, 0, n_work + 1, w0);
             if (lane == 0) s_k0 = k;
@@ -334,6 +378,48 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
             }
         }
 
+        // An entry whose neighbour view no pixel of the tile can reach (box_out_of_view) takes the penalty
+        // for every pixel, without sampling: it becomes an all-out entry. Only the projective-only
+        // instantiation does this: on a rectified rig an out-of-view sample is already cheap, and there
+        // the test cost more than it saved (1920x1080 linear 8-view rig: 7.8 % of the evaluations culled,
+        // 31.3 against 30.9 ms).
+        if (KIND == kKindProjective) {  // compile-time: every thread takes the same way through the barriers
+            int bx0 = INT_MAX, bx1 = INT_MIN, by0 = INT_MAX, by1 = INT_MIN;
+#pragma unroll
+            for (int j = 0; j < kPPT; ++j)
+                if (key[j] != kSentinel) {
+                    bx0 = min(bx0, (int)px[j]);
+                    bx1 = max(bx1, (int)px[j]);
+                    by0 = min(by0, iy[j]);
+                    by1 = max(by1, iy[j]);
+                }
+            bx0 = __reduce_min_sync(kFull, bx0);
+            bx1 = __reduce_max_sync(kFull, bx1);
+            by0 = __reduce_min_sync(kFull, by0);
+            by1 = __reduce_max_sync(kFull, by1);
+            if (lane == 0) {
+                atomicMin(&s_box[0], bx0);
+                atomicMax(&s_box[1], bx1);
+                atomicMin(&s_box[2], by0);
+                atomicMax(&s_box[3], by1);
+            }
+            __syncthreads();
+            if (s_box[0] <= s_box[1]) {
+                const float fx0 = (float)s_box[0], fx1 = (float)s_box[1], fy0 = (float)s_box[2], fy1 = (float)s_box[3];
+                for (int e = tid; e < nh; e += kThreads) {
+                    const int n = e / LBa, l = e - n * LBa;
+                    HEntry& E = sH[e];
+                    if ((E.pm >> 28) != kOut &&
+                        box_out_of_view(&Hg[((int64_t)n * L + d0 + l) * 9], fx0, fx1, fy0, fy1, (float)E.w, (float)E.h_)) {
+                        E.pm = (E.pm & kPitchMask) | ((uint32_t)kOut << 28);
+                        atomicAdd(&s_culled, 1);
+                    }
+                }
+            }
+            __syncthreads();
+            if (tid == 0 && s_culled > 0) atomicAdd(&plan->culled, (unsigned long long)s_culled * (unsigned)(w1 - w0));
+        }
+
         for (int l = 0; l < LBa; ++l) {
             int m[kPPT];
 #pragma unroll
@@ -355,6 +441,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                         const bool ok = pos_rect(hc.x, __float_as_uint(hc.y), __float_as_uint(hc.z), pitch, px[j], iy[j],
                                                  idx);
                         accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty);
+                    }
+                } else if (KIND == kKindProjective && mode == kOut) {
+                    if (!(COMB == FTV_COMBINE_MIN && PF)) {
+#pragma unroll
+                        for (int j = 0; j < kPPT; ++j) m[j] = (COMB == FTV_COMBINE_MIN) ? min(m[j], penalty) : m[j] + penalty;
                     }
                 } else if (KIND == kKindProjective || (KIND == kKindMixed && mode == kGeneral)) {
                     const float4 ha = e4[0], hb = e4[1];

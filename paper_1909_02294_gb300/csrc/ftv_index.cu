@@ -206,6 +206,7 @@ __global__ void plan_kernel(const __grid_constant__ PlanArgs<CAP> args, int n_jo
         plan->total_items = s_base;
         plan->counter = 0;
         plan->n_jobs = n_jobs;
+        plan->culled = 0;
     }
 }
 
@@ -224,6 +225,7 @@ __global__ void plan_device_kernel(RefJob* jobs, const int32_t* n_jobs_ptr, Plan
         plan->total_items = s_base;
         plan->counter = 0;
         plan->n_jobs = n_jobs;
+        plan->culled = 0;
     }
 }
 

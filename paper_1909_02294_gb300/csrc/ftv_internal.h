@@ -69,6 +69,7 @@ struct Plan {
     int32_t counter;           // next item to take (persistent CTAs)
     int32_t n_jobs;            // units in the launch
     int32_t pad;
+    unsigned long long culled; // evaluations decided without sampling: the tile is out of that view
 };
 
 struct RefState {

@@ -73,6 +73,7 @@ def _load() -> ctypes.CDLL:
         "ftv_temporal_mask": [vp, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp],
         "ftv_wta_depth": [vp, i32, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp],
         "ftv_check": [vp, vp],
+        "ftv_culled_evaluations": [vp, vp, vp],
         "ftv_set_profiling": [vp, i32],
         "ftv_stream_init": [vp, vp, vp, i32, i32, i32, vp],
         "ftv_stream_footprint": [vp, vp, vp],
@@ -119,7 +120,7 @@ lib = _load()
 
 EXPORTED = ["ftv_depth_init", "ftv_depth_destroy", "ftv_compute_homographies", "ftv_get_homographies", "ftv_get_neighbours",
             "ftv_get_label_depths", "ftv_segment_index", "ftv_cost_volume", "ftv_temporal_mask",
-            "ftv_wta_depth", "ftv_check", "ftv_launch_count", "ftv_status_str", "ftv_set_profiling",
+            "ftv_wta_depth", "ftv_check", "ftv_culled_evaluations", "ftv_launch_count", "ftv_status_str", "ftv_set_profiling",
             "ftv_last_kernel_ms", "ftv_temporal_mask_static", "ftv_stream_init", "ftv_stream_footprint",
             "ftv_stream_labels", "ftv_stream_mask", "ftv_reciprocal_check", "ftv_centre_table", "ftv_adjacency", "ftv_batch_create", "ftv_batch_destroy", "ftv_batch_prepare", "ftv_batch_launch",
             "ftv_batch_replay", "ftv_batch_query", "ftv_batch_wait", "ftv_batch_launch_count",
@@ -316,6 +317,14 @@ def ftv_wta_depth(ctx: Context, ref_index: int, cost, n_segments: int, label_out
 def ftv_check(ctx: Context, stream=None) -> int:
     """Wait for the stream and return the context's device status code (0 = clean)."""
     return int(lib.ftv_check(ctx.handle, _stream(stream)))
+
+
+def ftv_culled_evaluations(ctx: Context, stream=None) -> int:
+    """Evaluations of the most recent ftv_cost_volume call decided without sampling (whole tile out of
+    a neighbour's view); waits for the stream."""
+    n = ctypes.c_int64()
+    _ok(lib.ftv_culled_evaluations(ctx.handle, _stream(stream), ctypes.byref(n)), "ftv_culled_evaluations")
+    return int(n.value)
 
 
 def ftv_launch_count(ctx: Context) -> int:

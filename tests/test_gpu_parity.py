@@ -25,7 +25,7 @@ if not torch.cuda.is_available():
 from gpu_runs import Run, dev  # noqa: E402
 
 
-def _oracle_all(wl, combine=None, plane_mode=0, centre=0, nbr_lists=None, frame=0):
+def _oracle_all(wl, combine=None, plane_mode=0, centre=0, nbr_lists=None, frame=0, penalty=None):
     out = []
     for i, r in enumerate(wl.ref_views):
         lab, S = wl.labels(r)
@@ -33,7 +33,7 @@ def _oracle_all(wl, combine=None, plane_mode=0, centre=0, nbr_lists=None, frame=
         H = oracle.homography_table(wl.cams, r, nb, wl.n_labels, wl.z_near, wl.z_far, plane_mode=plane_mode,
                                     centre=centre)
         out.append(oracle.cost_volume(wl.cams, wl.views(frame), wl.sample_bytes, r, nb, H, wl.n_labels, lab, S,
-                                      wl.oob_penalty, combine or wl.combine))
+                                      wl.oob_penalty if penalty is None else penalty, combine or wl.combine))
     return out
 
 
@@ -74,6 +74,12 @@ def test_reduced_workloads_bit_exact(name):
     assert run.check() == 0
     for c, ref, r in zip(costs, _oracle_all(wl), wl.ref_views):
         _assert_equal(c, ref, f"{wl.name} ref {r}")
+    # the convergent rig's projective entries cull whole tiles; the rectified rig's never do
+    culled = ftv.ftv_culled_evaluations(run.ctx)
+    if name == "uhd15":
+        assert 0 < culled < wl.evaluations()
+    if name == "hd8":
+        assert culled == 0
     run.close()
 
 
@@ -161,6 +167,31 @@ def test_projective_entries_whose_denominator_changes_sign():
         costs = run.volumes()
         assert run.check() == 0
         _assert_equal(costs[0], _oracle_all(wl, combine=combine, nbr_lists=lists)[0], f"rotated views ({combine})")
+        run.close()
+
+
+def test_tile_cull_is_exact_in_every_combination():
+    """Two neighbours rotated 75 and 4 degrees about the vertical axis (projective entries only, so the
+    kernel's tile cull runs): tiles that no pixel of which can reach a view are decided without sampling,
+    and the volume still equals the oracle's with the minimum over views under the penalty floor, with a
+    penalty below the largest sample cost (culled samples then take the penalty explicitly), and with
+    the sum."""
+    import math
+    wl = make_workload("tiny")
+    base = wl.cams[1]
+    for deg in (75.0, 4.0):
+        a = math.radians(deg)
+        R = np.array([[math.cos(a), 0.0, -math.sin(a)], [0.0, 1.0, 0.0], [math.sin(a), 0.0, math.cos(a)]])
+        C = np.array([0.08, 0.0, 0.0])
+        wl.cams.append(synth.Camera(base.K.copy(), R, -R @ C, base.width, base.height))
+    lists = [[3, 4]]
+    for combine, penalty in (("min", None), ("min", 100), ("sum", None)):
+        run = Run(wl, nbr_lists=lists, combine=combine, penalty=penalty)
+        costs = run.volumes()
+        assert run.check() == 0
+        assert ftv.ftv_culled_evaluations(run.ctx) > 0
+        want = _oracle_all(wl, combine=combine, nbr_lists=lists, penalty=penalty)[0]
+        _assert_equal(costs[0], want, f"culled tiles ({combine}, penalty {penalty})")
         run.close()
 
 
