@@ -310,6 +310,17 @@ FTV_API ftv_status ftv_batch_launch(ftv_batch* b, ftv_stream stream);
  * within capacity replays the same graph. */
 FTV_API ftv_status ftv_batch_replay(ftv_batch* b, ftv_stream stream);
 
+#define FTV_MAX_BATCH_CHUNKS 16
+
+/* Split the batch's cost work over `chunks` (1..FTV_MAX_BATCH_CHUNKS, default 1) consecutive persistent
+ * launches, each over an equal share of the (tile, label-block) items. The paper has no counterpart: this
+ * is a scheduling aid for serving. One persistent launch holds every SM until the whole batch is done;
+ * between chunks the GPU can start other streams' kernels, higher-priority streams first, so a large
+ * batch launched on a low-priority stream delays a small one on a high-priority stream by at most about
+ * one chunk. Results are identical for every chunk count. Applies from the next ftv_batch_launch, or the
+ * next ftv_batch_replay, which captures a new graph. */
+FTV_API ftv_status ftv_batch_set_chunks(ftv_batch* b, int32_t chunks);
+
 /* Non-blocking completion test of the last launch: FTV_OK when done, FTV_ERR_BUSY while running. */
 FTV_API ftv_status ftv_batch_query(ftv_batch* b);
 

@@ -412,7 +412,7 @@ ftv_status ftv_cost_volume(ftv_ctx* ctx, const void* const* d_planes, const int6
     if (e == cudaSuccess && ctx->profiling) e = cudaEventRecord(ctx->ev_start, s);
     if (e == cudaSuccess) {
         e = launch_cost(ctx->d_jobs, ctx->d_plan, ctx->fmt, ctx->combine, ctx->fast_rcp, ctx->penalty_floor, ctx->kind,
-                        ctx->n_sm * ctx->cost_blocks_per_sm, s);
+                        0, 1, ctx->n_sm * ctx->cost_blocks_per_sm, s);
         ctx->launches++;
     }
     if (e == cudaSuccess && ctx->profiling) {

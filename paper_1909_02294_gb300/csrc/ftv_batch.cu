@@ -366,6 +366,8 @@ struct ftv_batch {
     bool fast_rcp = false;
     bool penalty_floor = false;
     int kind = 0;
+    int chunks = 1;           // cost-kernel launches per batch launch
+    int graph_chunks = 0;
     int32_t prepared_units = 0;
     int cost_grid = 0;
     cudaEvent_t done = nullptr;
@@ -751,11 +753,16 @@ static cudaError_t enqueue(ftv_batch* b, cudaStream_t s) {
     zero_changed_rows_kernel<<<dim3(64, std::min(b->max_units, 65535)), 256, 0, s>>>(hdr, jobs);
     e = launch_plan_device(jobs, &hdr->n_units, b->d_plan, s);
     if (e != cudaSuccess) return e;
-    e = launch_cost(jobs, b->d_plan, b->fmt, b->combine, b->fast_rcp, b->penalty_floor, b->kind, b->cost_grid, s);
+    // The cost items run in `chunks` persistent launches over consecutive item ranges: between two of
+    // them the GPU can start other streams' work (of a higher priority first) instead of waiting for the
+    // whole batch.
+    for (int k = 0; k < b->chunks && e == cudaSuccess; ++k)
+        e = launch_cost(jobs, b->d_plan, b->fmt, b->combine, b->fast_rcp, b->penalty_floor, b->kind, k, b->chunks,
+                        b->cost_grid, s);
     if (e != cudaSuccess) return e;
     wta_multi_kernel<<<g, 256, 0, s>>>(hdr, wta);
     depth_multi_kernel<<<g, 256, 0, s>>>(hdr, wta, b->d_status);
-    b->launches += 9;
+    b->launches += 8 + b->chunks;
     return cudaGetLastError();
 }
 
@@ -779,7 +786,7 @@ ftv_status ftv_batch_replay(ftv_batch* b, ftv_stream stream) {
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
     if (!b->exec || b->graph_fmt != b->fmt || b->graph_combine != b->combine || b->graph_pf != b->penalty_floor ||
-        b->graph_kind != b->kind) {
+        b->graph_kind != b->kind || b->graph_chunks != b->chunks) {
         if (b->exec) cudaGraphExecDestroy(b->exec);
         if (b->graph) cudaGraphDestroy(b->graph);
         b->exec = nullptr;
@@ -790,7 +797,7 @@ ftv_status ftv_batch_replay(ftv_batch* b, ftv_stream stream) {
             e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
                 const cudaError_t e1 = enqueue(b, cap);
-                b->launches -= 9;
+                b->launches -= 8 + b->chunks;
                 e = cudaStreamEndCapture(cap, &b->graph);
                 if (e1 != cudaSuccess) e = e1;
             }
@@ -802,15 +809,24 @@ ftv_status ftv_batch_replay(ftv_batch* b, ftv_stream stream) {
             b->graph_combine = b->combine;
             b->graph_pf = b->penalty_floor;
             b->graph_kind = b->kind;
+            b->graph_chunks = b->chunks;
         }
     }
     if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, s);
     if (e == cudaSuccess) {
-        b->launches += 9;
+        b->launches += 8 + b->chunks;
         e = cudaEventRecord(b->done, s);
     }
     if (prev_dev >= 0 && prev_dev != b->device) cudaSetDevice(prev_dev);
     return e == cudaSuccess ? FTV_OK : FTV_ERR_CUDA;
+}
+
+static_assert(FTV_MAX_BATCH_CHUNKS == kMaxChunks, "chunk limit of the ABI and of the plan");
+
+ftv_status ftv_batch_set_chunks(ftv_batch* b, int32_t chunks) {
+    if (!b || chunks < 1 || chunks > FTV_MAX_BATCH_CHUNKS) return FTV_ERR_INVALID_ARG;
+    b->chunks = chunks;  // the next replay captures a new graph
+    return FTV_OK;
 }
 
 ftv_status ftv_batch_query(ftv_batch* b) {

@@ -271,7 +271,7 @@ __device__ __forceinline__ int warp_upper_index(const int32_t* a, int lo, int hi
 
 template <int FMT, int COMB, bool FAST_RCP, bool PF, int KIND>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob* __restrict__ jobs,
-                                                                    Plan* __restrict__ plan) {
+                                                                    Plan* __restrict__ plan, int chunk, int chunks) {
     __shared__ HEntry sH[kHEntries];
     __shared__ const void* sBase[FTV_MAX_NBRS];
     __shared__ int sAcc[kSegAcc * kMaxLB];
@@ -280,13 +280,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
     __shared__ int s_box[4];  // the tile's pixel box: x min, x max, y min, y max
 
     const int tid = threadIdx.x, lane = tid & 31;
-    const int total = *reinterpret_cast<volatile int*>(&plan->total_items);
+    const int all_items = *reinterpret_cast<volatile int*>(&plan->total_items);
+    const int begin = (int)((long long)all_items * chunk / chunks);
+    const int total = (int)((long long)all_items * (chunk + 1) / chunks);  // this launch's items: [begin, total)
     const int n_jobs = *reinterpret_cast<volatile int*>(&plan->n_jobs);
     for (int i = tid; i < kSegAcc * kMaxLB; i += kThreads) sAcc[i] = 0;
 
     for (;;) {
         __syncthreads();
-        if (tid == 0) s_item = atomicAdd(&plan->counter, 1);
+        if (tid == 0) s_item = begin + atomicAdd(&plan->counter[chunk], 1);
         __syncthreads();
         const int item = s_item;
         if (item >= total) break;
@@ -598,37 +600,41 @@ int cost_blocks_per_sm(int fmt, int combine, bool fast) {
 namespace {
 
 template <int FMT, int COMB, bool FAST, bool PF>
-void launch_kind(const RefJob* jobs, Plan* p, int kind, int grid, cudaStream_t s) {
-    if (kind == kKindProjective) cost_kernel<FMT, COMB, FAST, PF, kKindProjective><<<grid, kThreads, 0, s>>>(jobs, p);
-    else cost_kernel<FMT, COMB, FAST, PF, kKindMixed><<<grid, kThreads, 0, s>>>(jobs, p);
+void launch_kind(const RefJob* jobs, Plan* p, int kind, int ck, int nck, int grid, cudaStream_t s) {
+    if (kind == kKindProjective)
+        cost_kernel<FMT, COMB, FAST, PF, kKindProjective><<<grid, kThreads, 0, s>>>(jobs, p, ck, nck);
+    else cost_kernel<FMT, COMB, FAST, PF, kKindMixed><<<grid, kThreads, 0, s>>>(jobs, p, ck, nck);
 }
 
 template <int FMT, int COMB>
-void launch_fast_pf(const RefJob* jobs, Plan* p, bool fast, bool pf, int kind, int grid, cudaStream_t s) {
+void launch_fast_pf(const RefJob* jobs, Plan* p, bool fast, bool pf, int kind, int ck, int nck, int grid,
+                    cudaStream_t s) {
     const bool use_pf = COMB == FTV_COMBINE_MIN && pf;
     if (fast) {
-        if (use_pf) launch_kind<FMT, COMB, true, true>(jobs, p, kind, grid, s);
-        else launch_kind<FMT, COMB, true, false>(jobs, p, kind, grid, s);
+        if (use_pf) launch_kind<FMT, COMB, true, true>(jobs, p, kind, ck, nck, grid, s);
+        else launch_kind<FMT, COMB, true, false>(jobs, p, kind, ck, nck, grid, s);
     } else {
-        if (use_pf) launch_kind<FMT, COMB, false, true>(jobs, p, kind, grid, s);
-        else launch_kind<FMT, COMB, false, false>(jobs, p, kind, grid, s);
+        if (use_pf) launch_kind<FMT, COMB, false, true>(jobs, p, kind, ck, nck, grid, s);
+        else launch_kind<FMT, COMB, false, false>(jobs, p, kind, ck, nck, grid, s);
     }
 }
 
 template <int FMT>
-void launch_comb(const RefJob* jobs, Plan* p, int combine, bool fast, bool pf, int kind, int grid, cudaStream_t s) {
-    if (combine == FTV_COMBINE_MIN) launch_fast_pf<FMT, FTV_COMBINE_MIN>(jobs, p, fast, pf, kind, grid, s);
-    else launch_fast_pf<FMT, FTV_COMBINE_SUM>(jobs, p, fast, pf, kind, grid, s);
+void launch_comb(const RefJob* jobs, Plan* p, int combine, bool fast, bool pf, int kind, int ck, int nck, int grid,
+                 cudaStream_t s) {
+    if (combine == FTV_COMBINE_MIN) launch_fast_pf<FMT, FTV_COMBINE_MIN>(jobs, p, fast, pf, kind, ck, nck, grid, s);
+    else launch_fast_pf<FMT, FTV_COMBINE_SUM>(jobs, p, fast, pf, kind, ck, nck, grid, s);
 }
 
 }  // namespace
 
 cudaError_t launch_cost(const RefJob* jobs, const Plan* plan, int fmt, int combine, bool fast, bool pf, int kind,
-                        int grid, cudaStream_t s) {
+                        int chunk, int chunks, int grid, cudaStream_t s) {
+    if (chunks < 1 || chunks > kMaxChunks || chunk < 0 || chunk >= chunks) return cudaErrorInvalidValue;
     Plan* p = const_cast<Plan*>(plan);
-    if (fmt == FMT_U8X4) launch_comb<FMT_U8X4>(jobs, p, combine, fast, pf, kind, grid, s);
-    else if (fmt == FMT_P10) launch_comb<FMT_P10>(jobs, p, combine, fast, pf, kind, grid, s);
-    else launch_comb<FMT_U16X4>(jobs, p, combine, fast, pf, kind, grid, s);
+    if (fmt == FMT_U8X4) launch_comb<FMT_U8X4>(jobs, p, combine, fast, pf, kind, chunk, chunks, grid, s);
+    else if (fmt == FMT_P10) launch_comb<FMT_P10>(jobs, p, combine, fast, pf, kind, chunk, chunks, grid, s);
+    else launch_comb<FMT_U16X4>(jobs, p, combine, fast, pf, kind, chunk, chunks, grid, s);
     return cudaGetLastError();
 }
 

@@ -204,7 +204,7 @@ __global__ void plan_kernel(const __grid_constant__ PlanArgs<CAP> args, int n_jo
     for (int j = 0; j < n_jobs; ++j) plan_unit(args.jobs[j], &out[j], &s_base);
     if (threadIdx.x == 0) {
         plan->total_items = s_base;
-        plan->counter = 0;
+        for (int k = 0; k < kMaxChunks; ++k) plan->counter[k] = 0;
         plan->n_jobs = n_jobs;
         plan->culled = 0;
     }
@@ -223,7 +223,7 @@ __global__ void plan_device_kernel(RefJob* jobs, const int32_t* n_jobs_ptr, Plan
     }
     if (threadIdx.x == 0) {
         plan->total_items = s_base;
-        plan->counter = 0;
+        for (int k = 0; k < kMaxChunks; ++k) plan->counter[k] = 0;
         plan->n_jobs = n_jobs;
         plan->culled = 0;
     }

@@ -64,12 +64,12 @@ struct RefJob {
     int32_t item_base;         // first item of this unit in the launch
 };
 
+constexpr int kMaxChunks = 16;  // a launch's items may be split over this many cost-kernel launches
 struct Plan {
     int32_t total_items;
-    int32_t counter;           // next item to take (persistent CTAs)
     int32_t n_jobs;            // units in the launch
-    int32_t pad;
     unsigned long long culled; // evaluations decided without sampling: the tile is out of that view
+    int32_t counter[kMaxChunks];  // next item of each chunk, relative to the chunk's first (persistent CTAs)
 };
 
 struct RefState {
@@ -179,8 +179,10 @@ int cost_blocks_per_sm(int fmt, int combine, bool fast_rcp);
 // kind: kKindProjective when no homography entry of the launch is affine (h6 = h7 = 0), else kKindMixed;
 // the projective instantiation of the cost kernel has the general path alone.
 enum : int { kKindMixed = 0, kKindProjective = 1 };
+// chunk, chunks: this launch takes items [total * chunk / chunks, total * (chunk + 1) / chunks) of the plan
+// (chunks <= kMaxChunks; a whole launch is chunk 0 of 1).
 cudaError_t launch_cost(const RefJob* jobs, const Plan* plan, int fmt, int combine, bool fast_rcp, bool pf, int kind,
-                        int grid, cudaStream_t s);
+                        int chunk, int chunks, int grid, cudaStream_t s);
 // Whether the current device's one-step Newton-Raphson reciprocal equals the IEEE round-to-nearest
 // reciprocal for every float in [2^-126, 2^126) (exhaustive check, run once per device and cached).
 bool fast_reciprocal_exact();

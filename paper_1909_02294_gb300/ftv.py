@@ -88,6 +88,7 @@ def _load() -> ctypes.CDLL:
         "ftv_batch_prepare": [vp, vp, i32],
         "ftv_batch_launch": [vp, vp],
         "ftv_batch_replay": [vp, vp],
+        "ftv_batch_set_chunks": [vp, i32],
         "ftv_batch_query": [vp],
         "ftv_batch_wait": [vp],
         "ftv_temporal_mask_static": [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp,
@@ -123,7 +124,7 @@ EXPORTED = ["ftv_depth_init", "ftv_depth_destroy", "ftv_compute_homographies", "
             "ftv_wta_depth", "ftv_check", "ftv_culled_evaluations", "ftv_launch_count", "ftv_status_str", "ftv_set_profiling",
             "ftv_last_kernel_ms", "ftv_temporal_mask_static", "ftv_stream_init", "ftv_stream_footprint",
             "ftv_stream_labels", "ftv_stream_mask", "ftv_reciprocal_check", "ftv_centre_table", "ftv_adjacency", "ftv_batch_create", "ftv_batch_destroy", "ftv_batch_prepare", "ftv_batch_launch",
-            "ftv_batch_replay", "ftv_batch_query", "ftv_batch_wait", "ftv_batch_launch_count",
+            "ftv_batch_replay", "ftv_batch_query", "ftv_batch_wait", "ftv_batch_launch_count", "ftv_batch_set_chunks",
             "ftv_segmenter_init", "ftv_segmenter_segments", "ftv_superpixels", "ftv_segmenter_check",
             "ftv_segmenter_launch_count", "ftv_segmenter_destroy", "ftv_segmenter_set_profiling",
             "ftv_segmenter_kernel_ms"]
@@ -454,6 +455,13 @@ def ftv_batch_launch(batch: Batch, stream=None) -> None:
 
 def ftv_batch_replay(batch: Batch, stream=None) -> None:
     _ok(lib.ftv_batch_replay(batch.handle, _stream(stream)), "ftv_batch_replay")
+
+
+FTV_MAX_BATCH_CHUNKS = 16
+
+
+def ftv_batch_set_chunks(batch: Batch, chunks: int) -> None:
+    _ok(lib.ftv_batch_set_chunks(batch.handle, chunks), "ftv_batch_set_chunks")
 
 
 def ftv_batch_query(batch: Batch) -> int:

@@ -103,8 +103,10 @@ def poisson_trace(n_streams: int, n_jobs: int, rate: float, seed: int) -> list[R
 
 @dataclass
 class Slot:
-    batch: object
-    stream: object
+    batches: dict   # one ftv_batch per stream shape (each keeps its own captured graph)
+    hi: object      # high-priority stream (batches of light shapes)
+    lo: object      # low-priority stream (batches of heavy shapes)
+    cur: object = None
     reqs: list = field(default_factory=list)
     inputs: list = field(default_factory=list)
     bytes: int = 0
@@ -112,19 +114,26 @@ class Slot:
 
 
 HEAVY_EVALS = 1e11  # a stream whose full frame is this many evaluations saturates the GPU by itself
+HEAVY_CHUNKS = 16   # cost-kernel launches per heavy batch: light work can start between two of them
 
 
 def run_served(streams: list[Stream], reqs: list[Request], slots: int = 3, budget_bytes: int = 8 << 30,
-               max_jobs: int = 32, by_class: bool = True, heavy_exclusive: bool = True) -> dict:
+               max_jobs: int = 32, by_class: bool = True, heavy_exclusive: bool = True,
+               heavy_chunks: int = HEAVY_CHUNKS) -> dict:
     """by_class: a batch only takes jobs of one stream shape (the shape of the earliest admissible
     request), so small jobs are not held until a large job in the same batch completes.
     heavy_exclusive: at most one batch of heavy streams (a full frame >= HEAVY_EVALS evaluations) is in
     flight; such a batch fills the GPU alone, and two of them running concurrently only contend for SMs
-    and L2 (measured: 3 slots 131 vs 1 slot 147 depth maps/s on the full mix)."""
+    and L2 (measured: 3 slots 131 vs 1 slot 147 depth maps/s on the full mix).
+    heavy_chunks: a heavy batch runs its cost work in this many launches on a low-priority stream, light
+    batches in one launch on a high-priority stream, so a light batch waits for at most about one chunk of
+    a heavy one instead of all of it (ftv_batch_set_chunks)."""
     dev = torch.device("cuda")
     max_units = min(240, sum(s.n_refs for s in streams))
     max_views = sum(s.n_views for s in streams)
-    pool = [Slot(ftv.ftv_batch_create(max_jobs, max_units, max_views), torch.cuda.Stream(dev)) for _ in range(slots)]
+    low, high = torch.cuda.Stream.priority_range()  # e.g. (0, -5): a smaller number is a higher priority
+    pool = [Slot({}, torch.cuda.Stream(dev, priority=high), torch.cuda.Stream(dev, priority=low))
+            for _ in range(slots)]
     pending = list(reqs)  # arrival order
     inflight_bytes, done, batches, batch_sizes = 0, 0, 0, []
     torch.cuda.synchronize()
@@ -133,8 +142,8 @@ def run_served(streams: list[Stream], reqs: list[Request], slots: int = 3, budge
         now = time.perf_counter() - t0
         progressed = False
         for sl in pool:
-            if sl.reqs and ftv.ftv_batch_query(sl.batch) == 0:
-                st = ftv.ftv_batch_wait(sl.batch)
+            if sl.reqs and ftv.ftv_batch_query(sl.cur) == 0:
+                st = ftv.ftv_batch_wait(sl.cur)
                 if st != 0:
                     raise RuntimeError(f"batch failed: {ftv.ftv_status_str(st)}")
                 t_done = time.perf_counter() - t0
@@ -175,30 +184,39 @@ def run_served(streams: list[Stream], reqs: list[Request], slots: int = 3, budge
                 add_bytes += s.frame_bytes
             if chosen:
                 sl = free[0]
+                heavy = any(streams[r.sid].heavy for r in chosen)
+                key = cls if by_class else None
+                if key not in sl.batches:
+                    b = ftv.ftv_batch_create(max_jobs, max_units, max_views)
+                    ftv.ftv_batch_set_chunks(b, heavy_chunks if heavy and by_class else 1)
+                    sl.batches[key] = b
+                sl.cur = sl.batches[key]
+                stream = sl.lo if heavy else sl.hi
                 jobs = []
                 for r in chosen:
                     s = streams[r.sid]
-                    planes = s.upload(r.seq, sl.stream)
+                    planes = s.upload(r.seq, stream)
                     sl.inputs.append(planes)
                     jobs.append(s.job(r.seq, planes))
                     s.busy = True
                     r.admitted = now
                     pending.remove(r)
-                rc = ftv.ftv_batch_prepare(sl.batch, jobs)
+                rc = ftv.ftv_batch_prepare(sl.cur, jobs)
                 if rc != 0:
                     raise RuntimeError(f"prepare failed: {ftv.ftv_status_str(rc)}")
-                ftv.ftv_batch_replay(sl.batch, sl.stream)
+                ftv.ftv_batch_replay(sl.cur, stream)
                 sl.reqs, sl.bytes = chosen, add_bytes
-                sl.heavy = any(streams[r.sid].heavy for r in chosen)
+                sl.heavy = heavy
                 inflight_bytes += add_bytes
                 batches += 1
                 batch_sizes.append(len(chosen))
                 progressed = True
         if not progressed:
             time.sleep(20e-6)
-    launches = sum(ftv.ftv_batch_launch_count(sl.batch) for sl in pool)
+    launches = sum(ftv.ftv_batch_launch_count(b) for sl in pool for b in sl.batches.values())
     for sl in pool:
-        sl.batch.close()
+        for b in sl.batches.values():
+            b.close()
     out = _stats(streams, reqs)
     out.update({"mode": "served", "slots": slots, "batches": batches,
                 "mean_batch_jobs": float(np.mean(batch_sizes)) if batch_sizes else 0.0, "gpu_launches": launches})
@@ -328,6 +346,8 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--shapes", default=None, help="comma-separated stream name prefixes (default: all)")
     ap.add_argument("--mixed-batches", action="store_true", help="let one batch mix stream shapes")
+    ap.add_argument("--heavy-chunks", type=int, default=HEAVY_CHUNKS,
+                    help="cost-kernel launches per heavy batch (1: one persistent launch)")
     ap.add_argument("--sequence", default=None, help="run one stream of this workload (e.g. temporal) over --frames")
     args = ap.parse_args(argv)
     shapes = args.shapes.split(",") if args.shapes else None
@@ -348,7 +368,8 @@ def main(argv=None):
     for mode in ("served", "plain"):
         streams = fresh()
         trace = poisson_trace(len(streams), n_cap, 0.0, args.seed)
-        res = run_served(streams, trace, args.slots, budget, by_class=not args.mixed_batches) \
+        res = run_served(streams, trace, args.slots, budget, by_class=not args.mixed_batches,
+                         heavy_chunks=args.heavy_chunks) \
             if mode == "served" else run_plain(streams, trace)
         results[f"capacity_{mode}"] = res
         for s in streams:
@@ -360,7 +381,8 @@ def main(argv=None):
         rate = args.rate_frac * results[f"capacity_{mode}"]["jobs_per_s"]
         streams = fresh()
         trace = poisson_trace(len(streams), args.jobs, rate, args.seed + 7)
-        res = run_served(streams, trace, args.slots, budget, by_class=not args.mixed_batches) \
+        res = run_served(streams, trace, args.slots, budget, by_class=not args.mixed_batches,
+                         heavy_chunks=args.heavy_chunks) \
             if mode == "served" else run_plain(streams, trace)
         res["rate_jobs_per_s"] = rate
         results[f"poisson_{mode}"] = res

@@ -175,3 +175,31 @@ def test_batch_argument_errors():
     for x in (b, b2, b3):
         x.close()
     s.ctx.close()
+
+
+def test_chunked_cost_launches_give_identical_results():
+    """The batch's cost work split over several persistent launches (a scheduling aid for serving) gives
+    the same labels as one launch, launched directly or through the captured graph."""
+    wls = _streams()
+    results = {}
+    for chunks, replay in ((1, False), (5, True), (16, False)):
+        streams = [Stream(w) for w in wls]
+        b = ftv.ftv_batch_create(4, 32, 32)
+        ftv.ftv_batch_set_chunks(b, chunks)
+        res = []
+        for frame, ftype in SCHEDULE:
+            _run(b, [s.job(frame, ftype) for s in streams], replay=replay)
+            res.append([s.labels() for s in streams])
+        assert ftv.ftv_batch_launch_count(b) == (8 + chunks) * len(SCHEDULE)
+        results[chunks] = res
+        for bad in (0, ftv.FTV_MAX_BATCH_CHUNKS + 1):
+            with pytest.raises(ftv.FtvError):
+                ftv.ftv_batch_set_chunks(b, bad)
+        b.close()
+        for s in streams:
+            s.ctx.close()
+    for chunks in (5, 16):
+        for fa, fb in zip(results[1], results[chunks]):
+            for sa, sb in zip(fa, fb):
+                for a, c in zip(sa, sb):
+                    assert np.array_equal(a, c), chunks
