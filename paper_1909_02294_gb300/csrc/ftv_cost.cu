@@ -204,11 +204,8 @@ __device__ __forceinline__ void accumulate(int& m, bool ok, const void* tex, int
 // right of u = wv rounds to a column of at least wv (likewise for rows), and one behind the camera has
 // Wz <= 0, which the contract counts as out of view. |h| <= 2^100 keeps every term finite; an overflow
 // or a NaN fails the comparisons and keeps the box.
-__device__ __forceinline__ bool box_out_of_view(const float* __restrict__ hg, float x0, float x1, float y0, float y1,
-                                                float wv, float hv) {
-    float h[9];
-#pragma unroll
-    for (int f = 0; f < 9; ++f) h[f] = __ldg(&hg[f]);
+__device__ __forceinline__ bool box_out_of_view(const float* h, float x0, float x1, float y0, float y1, float wv,
+                                                float hv) {
     const float m = 0x1p-20f;
     bool left = true, right = true, top = true, bottom = true, behind = true;
 #pragma unroll
@@ -229,6 +226,12 @@ __device__ __forceinline__ bool box_out_of_view(const float* __restrict__ hg, fl
         behind = behind && Z < -m * (sz + fabsf(Z));
     }
     return left || right || top || bottom || behind;
+}
+
+// First item of chunk k when n items are split into K nearly equal consecutive chunks (32-bit, no overflow).
+__device__ __forceinline__ int chunk_begin(int n, int k, int K) {
+    const int q = n / K, r = n - q * K;
+    return k * q + min(k, r);
 }
 
 __device__ __forceinline__ int find_job(const RefJob* __restrict__ jobs, int n_jobs, int item) {
@@ -280,15 +283,17 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
     __shared__ int s_box[4];  // the tile's pixel box: x min, x max, y min, y max
 
     const int tid = threadIdx.x, lane = tid & 31;
-    const int all_items = *reinterpret_cast<volatile int*>(&plan->total_items);
-    const int begin = (int)((long long)all_items * chunk / chunks);
-    const int total = (int)((long long)all_items * (chunk + 1) / chunks);  // this launch's items: [begin, total)
+    // this launch's items: [chunk_begin(chunk), chunk_begin(chunk + 1)); only thread 0 needs the first (it
+    // recomputes it from the plan when it fetches an item, which keeps it out of every thread's registers)
+    const int total = chunk_begin(*reinterpret_cast<volatile int*>(&plan->total_items), chunk + 1, chunks);
     const int n_jobs = *reinterpret_cast<volatile int*>(&plan->n_jobs);
     for (int i = tid; i < kSegAcc * kMaxLB; i += kThreads) sAcc[i] = 0;
 
     for (;;) {
         __syncthreads();
-        if (tid == 0) s_item = begin + atomicAdd(&plan->counter[chunk], 1);
+        if (tid == 0)
+            s_item = chunk_begin(*reinterpret_cast<volatile int*>(&plan->total_items), chunk, chunks) +
+                     atomicAdd(&plan->counter[chunk], 1);
         __syncthreads();
         const int item = s_item;
         if (item >= total) break;
@@ -380,12 +385,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
             }
         }
 
-        // An entry whose neighbour view no pixel of the tile can reach (box_out_of_view) takes the penalty
-        // for every pixel, without sampling: it becomes an all-out entry. Only the projective-only
-        // instantiation does this: on a rectified rig an out-of-view sample is already cheap, and there
-        // the test cost more than it saved (1920x1080 linear 8-view rig: 7.8 % of the evaluations culled,
-        // 31.3 against 30.9 ms).
-        if (KIND == kKindProjective) {  // compile-time: every thread takes the same way through the barriers
+        // An entry whose neighbour view no pixel of the tile can reach (box_out_of_view, on the staged
+        // coefficients) takes the penalty for every pixel, without sampling: it becomes an all-out entry.
+        // Only the projective-only instantiation does this: on a rectified rig an out-of-view sample is
+        // already cheap, and there the test cost more than it saved (1920x1080 linear 8-view rig: 7.8 % of
+        // the evaluations culled, 31.1 against 30.9 ms).
+        if constexpr (KIND == kKindProjective) {  // every thread takes the same way through the barriers
             int bx0 = INT_MAX, bx1 = INT_MIN, by0 = INT_MAX, by1 = INT_MIN;
 #pragma unroll
             for (int j = 0; j < kPPT; ++j)
@@ -409,10 +414,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
             if (s_box[0] <= s_box[1]) {
                 const float fx0 = (float)s_box[0], fx1 = (float)s_box[1], fy0 = (float)s_box[2], fy1 = (float)s_box[3];
                 for (int e = tid; e < nh; e += kThreads) {
-                    const int n = e / LBa, l = e - n * LBa;
                     HEntry& E = sH[e];
-                    if ((E.pm >> 28) != kOut &&
-                        box_out_of_view(&Hg[((int64_t)n * L + d0 + l) * 9], fx0, fx1, fy0, fy1, (float)E.w, (float)E.h_)) {
+                    if ((E.pm >> 28) == kGeneral &&
+                        box_out_of_view(E.h, fx0, fx1, fy0, fy1, (float)E.w, (float)E.h_)) {
                         E.pm = (E.pm & kPitchMask) | ((uint32_t)kOut << 28);
                         atomicAdd(&s_culled, 1);
                     }
