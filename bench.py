@@ -8,7 +8,9 @@ with the inputs copied from pinned host memory and the depth labels read back in
 region. The L2 is flushed (256 MB write) before every timed step.
 
 --impl reference times the CPU oracle as it stands on a bounded sample of the same workload.
---part segmentation times the superpixel segmentation (Sec. IV-C) of every view of the workload instead.
+--part segmentation times the superpixel segmentation (Sec. IV-C) of every view of the workload instead;
+--part centre the centre table (Eq. 4 at segment centres, Eq. 5's correspondence) and --part adjacency the
+segment adjacency and beta (Eq. 2-3) of every reference.
 Multi-GPU (torchrun): every rank runs an independent replica (the work shards by frames/jobs; there is
 no exchange step), rank 0 prints the whole-job throughput from the slowest rank's time.
 """
@@ -381,6 +383,178 @@ def cpu_baseline_all_cores(wl, k_single: int, budget_s: float = 10.0):
                                  f"({ev:.3e} evaluations)")
 
 
+# Centre table (Eq. 4 literal at segment centres with the Eq. 5 correspondence): operations per (segment,
+# label, neighbour) entry: the projection of the centre (6 FMA, 1 reciprocal, 2 multiplies, 2 adds, 2 floors,
+# 5 compares) and per window pixel pair 2 gathers, 3 differences, 3 absolute values, 2 adds, 1 accumulate.
+CENTRE_WINDOW = 3
+
+
+def centre_ops_per_entry(window: int) -> int:
+    return 18 + 11 * window * window
+
+
+def _part_line(args, world, metric, unit, value, total_s, extra_config, roofline, e2e, launches, clocks, wl):
+    c = wl.cams[0]
+    return {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+i32", "data": "synthetic",
+            "config": {"workload": f"{wl.name}: {wl.n_views} views {c.width}x{c.height} {wl.bit_depth}-bit, "
+                                   f"{wl.labels(wl.ref_views[0])[1]} segments/view",
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU", **extra_config},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+
+
+def run_part(args, rank, world, local):
+    """--part centre: one step = the centre table of every reference (ftv_centre_table, one call).
+    --part adjacency: one step = adjacency and beta of every reference (ftv_adjacency per reference).
+    The roofline is taken over the whole call (pack, segment index and the part's kernels)."""
+    import torch
+    import torch.distributed as dist
+    import paper_1909_02294_gb300 as ftv
+    import synth
+    import oracle
+
+    wl = synth.make_workload(args.workload)
+    dev = torch.device("cuda", local)
+    R, L = len(wl.ref_views), wl.n_labels
+    S = [wl.labels(r)[1] for r in wl.ref_views]
+    ctx = ftv.ftv_depth_init(wl.cams, wl.ref_views, L, wl.z_near, wl.z_far, sample_bytes=wl.sample_bytes,
+                             bit_depth=wl.bit_depth, oob_penalty=wl.oob_penalty, max_segments=max(S))
+    views = wl.views()
+    host_planes = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (v.Y, v.U, v.V)] for v in views]
+    planes = [[t.to(dev) for t in trip] for trip in host_planes]
+    host_labels = [torch.from_numpy(wl.labels(v)[0]).pin_memory() for v in range(wl.n_views)]
+    labels = [t.to(dev) for t in host_labels]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    nbrs = [wl.neighbours(r) for r in wl.ref_views]
+    if args.part == "centre":
+        m_out = [torch.empty((S[i], L, len(nbrs[i])), dtype=torch.int32, device=dev) for i in range(R)]
+        sp_out = [torch.empty_like(t) for t in m_out]
+        host_out = [torch.empty(t.shape, dtype=torch.int32).pin_memory() for t in m_out]
+        units = sum(S[i] * L * len(nbrs[i]) for i in range(R))
+
+        def step():
+            ftv.ftv_centre_table(ctx, planes, labels, S, CENTRE_WINDOW, m_out, sp_out)
+    else:
+        cap = [8 * S[i] + 64 for i in range(R)]
+        es = [torch.empty(c, dtype=torch.int32, device=dev) for c in cap]
+        et = [torch.empty(c, dtype=torch.int32, device=dev) for c in cap]
+        beta = [torch.empty(c, dtype=torch.float32, device=dev) for c in cap]
+        ne = [torch.zeros(1, dtype=torch.int32, device=dev) for _ in range(R)]
+        host_out = [torch.empty(c, dtype=torch.float32).pin_memory() for c in cap]
+        units = sum(wl.cams[r].width * wl.cams[r].height for r in wl.ref_views)
+
+        def step():
+            for i, r in enumerate(wl.ref_views):
+                ftv.ftv_adjacency(ctx, i, planes[r], labels[r], S[i], 4, 1.0, 1.0, es[i], et[i], beta[i], ne[i])
+
+    for _ in range(args.warmup):
+        step()
+    if ftv.ftv_check(ctx) != 0:
+        raise RuntimeError("device status")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = ftv.ftv_launch_count(ctx)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    launches = ftv.ftv_launch_count(ctx) - launches0
+    if world > 1:
+        dist.barrier()
+    step_s = [a.elapsed_time(b) / 1000.0 for a, b in ev]
+    total_s = reduce_max(sum(step_s), dev)
+    value = whole_job_rate(world, units * args.steps, total_s)
+    if ftv.ftv_check(ctx) != 0:
+        raise RuntimeError("device status")
+    # end to end: planes and label maps up, the part's result down, every step
+    h2d = sum(t.numel() * t.element_size() for trip in host_planes for t in trip)
+    h2d += sum(t.numel() * t.element_size() for t in host_labels)
+    outs = m_out if args.part == "centre" else beta
+    d2h = sum(t.numel() * t.element_size() for t in host_out)
+    e2e_ev = []
+    torch.cuda.synchronize()
+    for k in range(max(3, args.steps // 2)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for trip_h, trip_d in zip(host_planes, planes):
+            for th, td in zip(trip_h, trip_d):
+                td.copy_(th, non_blocking=True)
+        for th, td in zip(host_labels, labels):
+            td.copy_(th, non_blocking=True)
+        step()
+        for th, td in zip(host_out, outs):
+            th.copy_(td, non_blocking=True)
+        b.record(stream)
+        e2e_ev.append((a, b))
+    torch.cuda.synchronize()
+    e2e_s = reduce_max(sum(a.elapsed_time(b) for a, b in e2e_ev) / 1000.0, dev)
+
+    if rank == 0:
+        clk = clocks.summary()
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        sm_mhz = clk["sm_mhz"] if clk else 2070.0
+        mean_s = statistics.mean(step_s)
+        if args.part == "centre":
+            ops = units * centre_ops_per_entry(CENTRE_WINDOW)
+            peak = n_sm * 128 * sm_mhz * 1e6 / 1e12
+            roof = {"bound": "alu", "achieved": ops / mean_s / 1e12, "peak": peak, "unit": "Tops/s",
+                    "frac": ops / mean_s / 1e12 / peak, "traffic": None,
+                    "peak_kind": f"{n_sm} SMs x 128 lanes x {sm_mhz:.0f} MHz (median sampled SM clock)",
+                    "algorithmic_ops_per_step": ops, "ops_per_entry": centre_ops_per_entry(CENTRE_WINDOW),
+                    "kernel": "the whole ftv_centre_table call (pack, segment index, centroids, table)"}
+            metric, unit = "centre-table entries/s", "entries/s"
+            extra = {"window": CENTRE_WINDOW, "entries_per_step": units, "labels": L,
+                     "neighbours": len(nbrs[0])}
+        else:
+            peak, peak_kind = _peaks()
+            n_edges = sum(int(t.item()) for t in ne)
+            byts = units * (4 + 3 * wl.sample_bytes) + n_edges * 12
+            roof = {"bound": "hbm", "achieved": byts / mean_s / 1e9, "peak": peak, "unit": "GB/s",
+                    "frac": byts / mean_s / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
+                    "algorithmic_bytes_per_step": byts,
+                    "definition": "per pixel its label and three samples read once, per edge 12 bytes written",
+                    "kernel": "the whole ftv_adjacency calls (segment index, neighbours, offsets, edges)"}
+            metric, unit = "adjacency pixels/s", "px/s"
+            extra = {"connectivity": 4, "edges_per_step": n_edges}
+        line = _part_line(args, world, metric, unit, value, total_s, extra, roof,
+                          {"value": whole_job_rate(world, units * len(e2e_ev), e2e_s), "unit": unit,
+                           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}, launches, clk, wl)
+        if world == 1 and not args.no_cpu_baseline:
+            r0 = wl.ref_views[0]
+            lab0, S0 = wl.labels(r0)
+            if args.part == "centre":
+                Lsub = 4
+                H = oracle.homography_table(wl.cams, r0, nbrs[0], L, wl.z_near, wl.z_far)[:, :Lsub]
+                labs_v = [wl.labels(v)[0] for v in range(wl.n_views)]
+                t = time.perf_counter()
+                oracle.centre_table(wl.cams, views, wl.sample_bytes, r0, nbrs[0], np.ascontiguousarray(H), Lsub,
+                                    labs_v, S0, CENTRE_WINDOW, wl.oob_penalty)
+                dt = time.perf_counter() - t
+                n = S0 * Lsub * len(nbrs[0])
+                line["cpu_baseline"] = {"value": n / dt, "unit": unit, "cores": 1, "kind": "oracle",
+                                        "sample": f"oracle, 1 thread: the table of reference {r0} for labels "
+                                                  f"0..{Lsub - 1} ({n} entries)"}
+            else:
+                t = time.perf_counter()
+                oracle.adjacency(lab0, S0, views[r0], wl.sample_bytes, 4, 1.0, 1.0)
+                dt = time.perf_counter() - t
+                n = lab0.size
+                line["cpu_baseline"] = {"value": n / dt, "unit": unit, "cores": 1, "kind": "oracle",
+                                        "sample": f"oracle, 1 thread: adjacency and beta of reference {r0} "
+                                                  f"({n} pixels)"}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -430,8 +604,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="synthetic workload (default: the 1920x1080 8-view configuration; others for profiling)")
-    ap.add_argument("--part", default="depth", choices=["depth", "segmentation"],
-                    help="depth: the cost-volume hot path (default); segmentation: superpixels of every view")
+    ap.add_argument("--part", default="depth", choices=["depth", "segmentation", "centre", "adjacency"],
+                    help="depth: the cost-volume hot path (default); segmentation: superpixels of every view; "
+                         "centre: the centre table of every reference; adjacency: adjacency and beta")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -448,8 +623,8 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    if args.part == "segmentation":
-        run_segmentation(args, rank, world, local)
+    if args.part != "depth":
+        (run_segmentation if args.part == "segmentation" else run_part)(args, rank, world, local)
         if world > 1:
             dist.destroy_process_group()
         return

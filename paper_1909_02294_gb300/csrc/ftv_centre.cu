@@ -75,54 +75,100 @@ struct CentreArgs {
     int32_t* m;             // [S][L][N]
     int32_t* sp;            // [S][L][N]
     int32_t S, L, N, W, H_, window, penalty, fmt;
+    uint32_t l_magic;       // ceil(2^32 / L) for L > 1: j / L = umulhi(j, l_magic) for j < 2^20
 };
 
-__global__ void centre_table_kernel(CentreArgs a) {
-    const int64_t total = (int64_t)a.S * a.L * a.N;
-    const int half = a.window / 2;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(e % a.N);
-        const int64_t t = e / a.N;
-        const int d = (int)(t % a.L);
-        const int s = (int)(t / a.L);
+constexpr int kCentreThreads = 256;
+constexpr int kMaxWindow = 15;
+
+// One CTA per segment (grid-stride): the segment's reference window is unpacked once into shared memory
+// (-1 marks a pixel outside the reference image), then the CTA's threads take the segment's (label,
+// neighbour) entries, label fastest: a warp then works on consecutive labels of one neighbour, whose
+// windows lie a few pixels apart in that view and share its cache lines.
+// WIN: the window side at compile time (3, the paper's, unrolls completely), or 0 for a.window at run time.
+template <int WIN>
+__global__ void __launch_bounds__(kCentreThreads) centre_table_kernel(CentreArgs a) {
+    __shared__ int sref[kMaxWindow * kMaxWindow][3];
+    __shared__ NbrView snb[FTV_MAX_NBRS];
+    __shared__ const int32_t* slab[FTV_MAX_NBRS];
+    const int tid = threadIdx.x;
+    for (int k = tid; k < a.N; k += kCentreThreads) {
+        snb[k] = a.nbrs[k];
+        slab[k] = a.labels_v[k];
+    }
+    const int win = WIN > 0 ? WIN : a.window;
+    const int half = win / 2, ww = win * win, nent = a.L * a.N;
+    for (int s = blockIdx.x; s < a.S; s += gridDim.x) {
         const int2 c = a.centre[s];
-        const NbrView nv = a.nbrs[k];
-        const float* h = a.H + ((int64_t)k * a.L + d) * 9;
-        bool in = c.x >= 0;
-        int ui = 0, vi = 0;
-        if (in) {
-            const float x = (float)c.x, y = (float)c.y;
-            const float X = __fmaf_rn(h[0], x, __fmaf_rn(h[1], y, h[2]));
-            const float Yh = __fmaf_rn(h[3], x, __fmaf_rn(h[4], y, h[5]));
-            const float Wz = __fmaf_rn(h[6], x, __fmaf_rn(h[7], y, h[8]));
-            in = Wz > 0.0f;
-            if (in) {
-                const float r = __frcp_rn(Wz);
-                const float fu = floorf(__fadd_rn(__fmul_rn(X, r), 0.5f));
-                const float fv = floorf(__fadd_rn(__fmul_rn(Yh, r), 0.5f));
-                in = fu >= 0.0f && fu <= (float)(nv.w - 1) && fv >= 0.0f && fv <= (float)(nv.h - 1);
-                if (in) {
-                    ui = (int)fu;
-                    vi = (int)fv;
-                }
+        __syncthreads();  // the previous segment's window is no longer read
+        for (int i = tid; i < ww; i += kCentreThreads) {
+            const int iy = i / win;  // per segment only
+            const int rx = c.x - half + (i - iy * win), ry = c.y - half + iy;
+            if (c.x >= 0 && rx >= 0 && rx < a.W && ry >= 0 && ry < a.H_) {
+                int v[3];
+                texel(a.ref_tex, a.fmt, (int64_t)ry * a.W + rx, v);
+                sref[i][0] = v[0];
+                sref[i][1] = v[1];
+                sref[i][2] = v[2];
+            } else {
+                sref[i][0] = -1;
             }
         }
-        long long m = 0;
-        for (int dy = -half; dy <= half; ++dy)
-            for (int dx = -half; dx <= half; ++dx) {
-                const int rx = c.x + dx, ry = c.y + dy, qx = ui + dx, qy = vi + dy;
-                if (!in || rx < 0 || rx >= a.W || ry < 0 || ry >= a.H_ || qx < 0 || qx >= nv.w || qy < 0 || qy >= nv.h) {
-                    m += a.penalty;
-                    continue;
+        __syncthreads();
+        int32_t* mrow = a.m + (int64_t)s * nent;
+        int32_t* srow = a.sp + (int64_t)s * nent;
+        for (int j = tid; j < nent; j += kCentreThreads) {
+            const int k = a.L == 1 ? j : (int)__umulhi((uint32_t)j, a.l_magic), d = j - k * a.L;
+            const int64_t out = (int64_t)d * a.N + k;
+            const NbrView& nv = snb[k];
+            const float* h = a.H + ((int64_t)k * a.L + d) * 9;
+            bool in = c.x >= 0;
+            int ui = 0, vi = 0;
+            if (in) {
+                const float x = (float)c.x, y = (float)c.y;
+                const float X = __fmaf_rn(__ldg(&h[0]), x, __fmaf_rn(__ldg(&h[1]), y, __ldg(&h[2])));
+                const float Yh = __fmaf_rn(__ldg(&h[3]), x, __fmaf_rn(__ldg(&h[4]), y, __ldg(&h[5])));
+                const float Wz = __fmaf_rn(__ldg(&h[6]), x, __fmaf_rn(__ldg(&h[7]), y, __ldg(&h[8])));
+                in = Wz > 0.0f;
+                if (in) {
+                    const float r = __frcp_rn(Wz);
+                    const float fu = floorf(__fadd_rn(__fmul_rn(X, r), 0.5f));
+                    const float fv = floorf(__fadd_rn(__fmul_rn(Yh, r), 0.5f));
+                    in = fu >= 0.0f && fu <= (float)(nv.w - 1) && fv >= 0.0f && fv <= (float)(nv.h - 1);
+                    if (in) {
+                        ui = (int)fu;
+                        vi = (int)fv;
+                    }
                 }
-                int p[3], q[3];
-                texel(a.ref_tex, a.fmt, (int64_t)ry * a.W + rx, p);
-                texel(nv.texels, a.fmt, (int64_t)qy * nv.pitch + qx, q);
-                m += abs(p[0] - q[0]) + abs(p[1] - q[1]) + abs(p[2] - q[2]);
             }
-        a.m[e] = (int32_t)m;
-        const int32_t* lv = a.labels_v[k];
-        a.sp[e] = (in && lv) ? lv[(int64_t)vi * nv.w + ui] : -1;
+            int m = 0;
+            if (!in) {
+                m = ww * a.penalty;
+            } else {
+                const bool inside = ui >= half && ui + half < nv.w && vi >= half && vi + half < nv.h;
+#pragma unroll
+                for (int wy = 0; wy < (WIN > 0 ? WIN : kMaxWindow); ++wy) {
+                    if (WIN == 0 && wy >= win) break;
+                    const int qy = vi - half + wy;
+                    const int64_t qrow = (int64_t)qy * nv.pitch;
+#pragma unroll
+                    for (int wx = 0; wx < (WIN > 0 ? WIN : kMaxWindow); ++wx) {
+                        if (WIN == 0 && wx >= win) break;
+                        const int i = wy * win + wx, qx = ui - half + wx;
+                        if (sref[i][0] < 0 || (!inside && (qx < 0 || qx >= nv.w || qy < 0 || qy >= nv.h))) {
+                            m += a.penalty;
+                            continue;
+                        }
+                        int q[3];
+                        texel(nv.texels, a.fmt, qrow + qx, q);
+                        m += abs(sref[i][0] - q[0]) + abs(sref[i][1] - q[1]) + abs(sref[i][2] - q[2]);
+                    }
+                }
+            }
+            mrow[out] = m;
+            const int32_t* lv = slab[k];
+            srow[out] = (in && lv) ? lv[(int64_t)vi * nv.w + ui] : -1;
+        }
     }
 }
 
@@ -193,10 +239,12 @@ extern "C" ftv_status ftv_centre_table(ftv_ctx* ctx, const void* const* d_planes
         a.window = window;
         a.penalty = ctx->penalty;
         a.fmt = ctx->fmt;
+        a.l_magic = ctx->L > 1 ? (uint32_t)((0x100000000ull + (uint64_t)ctx->L - 1) / (uint64_t)ctx->L) : 0u;
         const int64_t total = (int64_t)S * ctx->L * r.n_nbrs;
-        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)ctx->n_sm * 16));
+        const int blocks = std::max(1, std::min(S, ctx->n_sm * 8));
         if (total > 0) {
-            centre_table_kernel<<<blocks, 256, 0, s>>>(a);
+            if (window == 3) centre_table_kernel<3><<<blocks, kCentreThreads, 0, s>>>(a);
+            else centre_table_kernel<0><<<blocks, kCentreThreads, 0, s>>>(a);
             ctx->launches++;
         }
         e = cudaGetLastError();

@@ -40,3 +40,30 @@ def test_centre_table_bit_exact(name, window, drop):
         assert np.array_equal(ms[i].cpu().numpy(), m), (name, r)
         assert np.array_equal(sps[i].cpu().numpy(), sp), (name, r)
     run.close()
+
+
+@pytest.mark.parametrize("window", [1, 15])
+def test_centre_table_single_neighbour_empty_segments_and_window_limits(window):
+    """One neighbour (the kernel's label/neighbour split has a special case there), the smallest and the
+    largest window, a one-pixel segment in the corner (its window leaves the image) and an empty segment."""
+    wl = make_workload("tiny")
+    r = wl.ref_views[0]
+    lab, S0 = wl.labels(r)
+    lab = lab.copy()
+    lab[0, 0] = S0
+    S = S0 + 2
+    run = Run(wl, nbr_lists=[[0]], max_segments=S)
+    labels_h = [wl.labels(v)[0] for v in range(wl.n_views)]
+    labels_h[r] = lab
+    L = wl.n_labels
+    m = torch.empty((S, L, 1), dtype=torch.int32, device="cuda")
+    sp = torch.empty((S, L, 1), dtype=torch.int32, device="cuda")
+    ftv.ftv_centre_table(run.ctx, run.planes(), [dev(l) for l in labels_h], [S], window, [m], [sp])
+    assert run.check() == 0
+    H = oracle.homography_table(wl.cams, r, [0], L, wl.z_near, wl.z_far)
+    mo, spo = oracle.centre_table(wl.cams, wl.views(), wl.sample_bytes, r, [0], H, L, labels_h, S, window,
+                                  wl.oob_penalty)
+    assert np.array_equal(m.cpu().numpy(), mo)
+    assert np.array_equal(sp.cpu().numpy(), spo)
+    assert np.all(mo[S0 + 1] == window * window * wl.oob_penalty)
+    run.close()

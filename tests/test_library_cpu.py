@@ -108,3 +108,19 @@ def test_segmenter_rejects_bad_configurations_on_the_host(ftv, sizes, sb, bd, S,
     with pytest.raises(ftv.FtvError) as e:
         ftv.Segmenter(sizes, sb, bd, S, m, T)
     assert e.value.code == ftv.FTV_ERR_INVALID_ARG
+
+
+def test_label_split_by_reciprocal_multiply_is_exact_at_every_label_count():
+    """The centre table splits an entry index j < L * N into (neighbour, label) with
+    umulhi(j, ceil(2^32 / L)) instead of j / L. Its error term grows with j and first shows just below a
+    multiple of L, so checking j = kL - 1 and kL for every k up to N and every L up to the limits covers
+    every j the kernel can see."""
+    hdr = open(os.path.join(ROOT, "include", "ftv.h")).read()
+    nbrs = int(re.search(r"#define FTV_MAX_NBRS (\d+)", hdr).group(1))
+    max_labels = int(re.search(r"#define FTV_MAX_LABELS (\d+)", hdr).group(1))
+    for L in range(2, max_labels + 1):
+        magic = ((1 << 32) + L - 1) // L
+        k = np.arange(1, nbrs + 1, dtype=np.uint64)
+        j = np.concatenate([k * L - 1, (k - 1) * L]).astype(np.uint64)
+        got = (j * np.uint64(magic)) >> np.uint64(32)
+        assert np.array_equal(got, j // np.uint64(L)), L
