@@ -45,7 +45,8 @@ def _load():
     global _lib
     if _lib is None:
         _lib = ctypes.CDLL(build())
-        for name in ["or_label_inv_depths", "or_homography_f64", "or_homography_table", "or_cost_volume",
+        for name in ["or_label_inv_depths", "or_homography_f64", "or_homography_table", "or_homography_table_f64",
+                     "or_cost_volume",
                      "or_cost_entries", "or_fp64_mismatch", "or_temporal_mask", "or_wta", "or_depth_map",
                      "or_centre_table", "or_adjacency", "or_snic", "or_connectivity", "or_superpixels"]:
             getattr(_lib, name).restype = ctypes.c_int
@@ -109,19 +110,43 @@ def homography_table(cams, ref: int, nbrs, L: int, z_near: float, z_far: float, 
     return out
 
 
+def homography_table_f64(cams, ref: int, nbrs, L: int, z_near: float, z_far: float, plane_mode: int = 0,
+                         centre: int = 0) -> np.ndarray:
+    """The same table kept in FP64 (before the rounding to FP32): the FP64 projection's homographies."""
+    nb = np.ascontiguousarray(nbrs, np.int32)
+    out = np.empty((len(nb), L, 9), np.float64)
+    _check(_load().or_homography_table_f64(cams_array(cams), ctypes.c_int(len(cams)), ctypes.c_int(ref),
+                                           ctypes.c_int(len(nb)), _p(nb), ctypes.c_int(L), ctypes.c_double(z_near),
+                                           ctypes.c_double(z_far), ctypes.c_int(plane_mode), ctypes.c_int(centre),
+                                           _p(out)), "homography_table_f64")
+    return out
+
+
+def _tables(H):
+    """(FP32 table, FP64 table) arguments for a table H: a float32 table selects the FP32 contract, a
+    float64 table (homography_table_f64) the FP64 projection. Any other type is refused, not cast."""
+    H = np.asarray(H)
+    if H.dtype == np.float32:
+        return np.ascontiguousarray(H), None
+    if H.dtype == np.float64:
+        return None, np.ascontiguousarray(H)
+    raise TypeError(f"homography table must be float32 or float64, not {H.dtype}")
+
+
 def cost_volume(cams, views, sample_bytes: int, ref: int, nbrs, H: np.ndarray, L: int, labels: np.ndarray,
                 S: int, penalty: int, combine: str = "min", seg_list=None, out: np.ndarray | None = None):
-    """int32 [S][L] cost volume of reference `ref`; rows of unlisted segments keep `out`'s values."""
+    """int32 [S][L] cost volume of reference `ref`; rows of unlisted segments keep `out`'s values. H is
+    the FP32 table (FP32 contract) or the FP64 table (FP64 projection)."""
     nb = np.ascontiguousarray(nbrs, np.int32)
     imgs, keep = _imgs(views)
     lab = np.ascontiguousarray(labels, np.int32)
-    Hc = np.ascontiguousarray(H, np.float32)
+    Hc, H64 = _tables(H)
     if out is None:
         out = np.zeros((S, L), np.int32)
     sl = np.ascontiguousarray(seg_list, np.int32) if seg_list is not None else None
     _check(_load().or_cost_volume(cams_array(cams), ctypes.c_int(len(cams)), imgs, ctypes.c_int(sample_bytes),
-                                  ctypes.c_int(ref), ctypes.c_int(len(nb)), _p(nb), _p(Hc), ctypes.c_int(L),
-                                  _p(lab), ctypes.c_int(S), ctypes.c_int(penalty), ctypes.c_int(COMBINE[combine]),
+                                  ctypes.c_int(ref), ctypes.c_int(len(nb)), _p(nb), _p(Hc), _p(H64),
+                                  ctypes.c_int(L), _p(lab), ctypes.c_int(S), ctypes.c_int(penalty), ctypes.c_int(COMBINE[combine]),
                                   _p(sl), ctypes.c_int(len(sl) if sl is not None else 0), _p(out)), "cost_volume")
     return out
 
@@ -131,13 +156,14 @@ def cost_entries(cams, views, sample_bytes: int, ref: int, nbrs, H: np.ndarray, 
     nb = np.ascontiguousarray(nbrs, np.int32)
     imgs, keep = _imgs(views)
     lm = np.ascontiguousarray(labels, np.int32)
-    Hc = np.ascontiguousarray(H, np.float32)
+    Hc, H64 = _tables(H)
     sg = np.ascontiguousarray(seg, np.int32)
     lb = np.ascontiguousarray(lab, np.int32)
     out = np.empty(len(sg), np.int32)
     _check(_load().or_cost_entries(cams_array(cams), ctypes.c_int(len(cams)), imgs, ctypes.c_int(sample_bytes),
-                                   ctypes.c_int(ref), ctypes.c_int(len(nb)), _p(nb), _p(Hc), ctypes.c_int(L),
-                                   _p(lm), ctypes.c_int(S), ctypes.c_int(penalty), ctypes.c_int(COMBINE[combine]),
+                                   ctypes.c_int(ref), ctypes.c_int(len(nb)), _p(nb), _p(Hc), _p(H64),
+                                   ctypes.c_int(L), _p(lm), ctypes.c_int(S), ctypes.c_int(penalty),
+                                   ctypes.c_int(COMBINE[combine]),
                                    ctypes.c_int(len(sg)), _p(sg), _p(lb), _p(out)), "cost_entries")
     return out
 
@@ -201,16 +227,17 @@ def depth_map(labels: np.ndarray, S: int, seg_label: np.ndarray, L: int, z_near:
 def centre_table(cams, views, sample_bytes: int, ref: int, nbrs, H: np.ndarray, L: int, labels_views, S: int,
                  window: int, penalty: int):
     """(m int32 [S][L][N], s' int32 [S][L][N]) of or_centre_table; labels_views[v] is view v's int32
-    [H][W] label map or None (labels_views[ref] is required)."""
+    [H][W] label map or None (labels_views[ref] is required). H: FP32 or FP64 table, as in cost_volume."""
     nb = np.ascontiguousarray(nbrs, np.int32)
     imgs, keep = _imgs(views)
-    Hc = np.ascontiguousarray(H, np.float32)
+    Hc, H64 = _tables(H)
     labs = [np.ascontiguousarray(l, np.int32) if l is not None else None for l in labels_views]
     lp = (ctypes.c_void_p * len(labs))(*[l.ctypes.data if l is not None else None for l in labs])
     m = np.empty((S, L, len(nb)), np.int32)
     sp = np.empty((S, L, len(nb)), np.int32)
     _check(_load().or_centre_table(cams_array(cams), ctypes.c_int(len(cams)), imgs, ctypes.c_int(sample_bytes),
-                                   ctypes.c_int(ref), ctypes.c_int(len(nb)), _p(nb), _p(Hc), ctypes.c_int(L), lp,
+                                   ctypes.c_int(ref), ctypes.c_int(len(nb)), _p(nb), _p(Hc), _p(H64),
+                                   ctypes.c_int(L), lp,
                                    ctypes.c_int(S), ctypes.c_int(window), ctypes.c_int(penalty), _p(m), _p(sp)),
            "centre_table")
     return m, sp

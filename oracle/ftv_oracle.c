@@ -129,10 +129,11 @@ int or_homography_f64(const or_camera* cr, const or_camera* cv, const or_camera*
     return 0;
 }
 
-/* FP32 table [n_nbrs][L][9] for one reference view. plane_mode 0 = reference planes, 1 = centre. */
-int or_homography_table(const or_camera* cams, int n_views, int ref, int n_nbrs, const int32_t* nbrs, int L,
-                        double z_near, double z_far, int plane_mode, int centre, float* out) {
-    if (!cams || ref < 0 || ref >= n_views || n_nbrs < 0 || L < 1 || !out) return 1;
+/* Table [n_nbrs][L][9] for one reference view, rounded to FP32 (out) or kept in FP64 (out64; exactly one
+ * of the two is given). plane_mode 0 = reference planes, 1 = centre. */
+static int homography_table(const or_camera* cams, int n_views, int ref, int n_nbrs, const int32_t* nbrs, int L,
+                            double z_near, double z_far, int plane_mode, int centre, float* out, double* out64) {
+    if (!cams || ref < 0 || ref >= n_views || n_nbrs < 0 || L < 1 || !out == !out64) return 1;
     if (plane_mode == 1 && (centre < 0 || centre >= n_views)) return 1;
     double* iz = (double*)malloc(sizeof(double) * (size_t)L);
     if (!iz) return 1;
@@ -144,11 +145,26 @@ int or_homography_table(const or_camera* cams, int n_views, int ref, int n_nbrs,
             double H[9];
             int rc = or_homography_f64(&cams[ref], &cams[v], plane_mode == 1 ? &cams[centre] : NULL, iz[d], H);
             if (rc) { free(iz); return rc; }
-            for (int e = 0; e < 9; e++) out[((size_t)k * L + d) * 9 + e] = (float)H[e];
+            for (int e = 0; e < 9; e++) {
+                if (out) out[((size_t)k * L + d) * 9 + e] = (float)H[e];
+                else out64[((size_t)k * L + d) * 9 + e] = H[e];
+            }
         }
     }
     free(iz);
     return 0;
+}
+
+int or_homography_table(const or_camera* cams, int n_views, int ref, int n_nbrs, const int32_t* nbrs, int L,
+                        double z_near, double z_far, int plane_mode, int centre, float* out) {
+    if (!out) return 1;
+    return homography_table(cams, n_views, ref, n_nbrs, nbrs, L, z_near, z_far, plane_mode, centre, out, NULL);
+}
+
+int or_homography_table_f64(const or_camera* cams, int n_views, int ref, int n_nbrs, const int32_t* nbrs, int L,
+                            double z_near, double z_far, int plane_mode, int centre, double* out) {
+    if (!out) return 1;
+    return homography_table(cams, n_views, ref, n_nbrs, nbrs, L, z_near, z_far, plane_mode, centre, NULL, out);
 }
 
 /* ------------------------------------------------------------------------------------ samples */
@@ -178,8 +194,9 @@ static int project_f32(const float* h, int x, int y, int Wv, int Hv, int* ui, in
     return 1;
 }
 
-/* Same decision in FP64 with the unrounded homography: used only to measure how often the FP32
- * contract picks a different sample than exact-ish arithmetic would. */
+/* The FP64 projection: the same decision in IEEE double arithmetic with the unrounded homography, each
+ * operation rounded on its own, the sums taken left to right. It is the sample position of the FP64
+ * precision mode, and the yardstick the FP32 contract's mismatch fraction is measured against. */
 static int project_f64(const double* h, int x, int y, int Wv, int Hv, long* ui, long* vi) {
     double X = h[0] * x + h[1] * y + h[2];
     double Yh = h[3] * x + h[4] * y + h[5];
@@ -194,10 +211,17 @@ static int project_f64(const double* h, int x, int y, int Wv, int Hv, long* ui, 
 
 /* Eq. 4 with a one-pixel window: L1 distance of (Y, Cb, Cr) at reference pixel (x, y) and at the
  * corresponding sample of view v, or the out-of-view penalty. */
-static int view_cost(const or_image* ref_im, const or_image* v_im, int sample_bytes, const float* h, int x, int y,
-                     int Wv, int Hv, int penalty) {
+static int view_cost(const or_image* ref_im, const or_image* v_im, int sample_bytes, const float* h,
+                     const double* h64, int x, int y, int Wv, int Hv, int penalty) {
     int ui, vi;
-    if (!project_f32(h, x, y, Wv, Hv, &ui, &vi)) return penalty;
+    if (h64) {
+        long lu, lv;
+        if (!project_f64(h64, x, y, Wv, Hv, &lu, &lv)) return penalty;
+        ui = (int)lu;
+        vi = (int)lv;
+    } else if (!project_f32(h, x, y, Wv, Hv, &ui, &vi)) {
+        return penalty;
+    }
     int c = 0;
     for (int ch = 0; ch < 3; ch++) {
         int a = sample_at(ref_im, sample_bytes, ch, x, y);
@@ -207,14 +231,17 @@ static int view_cost(const or_image* ref_im, const or_image* v_im, int sample_by
     return c;
 }
 
-/* Per-pixel combination over the neighbouring views: minimum (combine 0) or sum (combine 1). */
+/* Per-pixel combination over the neighbouring views: minimum (combine 0) or sum (combine 1). Sample
+ * positions come from the FP32 table H, or from the FP64 table H64 when that is given. */
 static int pixel_cost(const or_camera* cams, const or_image* imgs, int sample_bytes, int ref, int n_nbrs,
-                      const int32_t* nbrs, const float* H, int L, int d, int x, int y, int penalty, int combine) {
+                      const int32_t* nbrs, const float* H, const double* H64, int L, int d, int x, int y, int penalty,
+                      int combine) {
     int acc = combine == 0 ? INT32_MAX : 0;
     for (int k = 0; k < n_nbrs; k++) {
         int v = nbrs[k];
-        const float* h = H + ((size_t)k * L + d) * 9;
-        int c = view_cost(&imgs[ref], &imgs[v], sample_bytes, h, x, y, cams[v].width, cams[v].height, penalty);
+        const size_t o = ((size_t)k * L + d) * 9;
+        int c = view_cost(&imgs[ref], &imgs[v], sample_bytes, H64 ? NULL : H + o, H64 ? H64 + o : NULL, x, y,
+                          cams[v].width, cams[v].height, penalty);
         if (combine == 0) acc = c < acc ? c : acc;
         else acc += c;
     }
@@ -249,13 +276,15 @@ static int segment_lists(const int32_t* labels, int W, int H, int S, int32_t** o
 /*
  * Cost volume of one reference view: cost[s][d] for every listed segment s (all segments when
  * seg_list is NULL) and every label d; rows of unlisted segments are not written. H is the
- * reference's FP32 table [n_nbrs][L][9] (or_homography_table). Sums are exact int64 and the call
- * fails with 3 if one does not fit in int32.
+ * reference's FP32 table [n_nbrs][L][9] (or_homography_table), or, with H = NULL, H64 its FP64 table
+ * (or_homography_table_f64) for the FP64 projection. Sums are exact int64 and the call fails with 3 if
+ * one does not fit in int32.
  */
 int or_cost_volume(const or_camera* cams, int n_views, const or_image* imgs, int sample_bytes, int ref, int n_nbrs,
-                   const int32_t* nbrs, const float* H, int L, const int32_t* labels, int S, int penalty,
-                   int combine, const int32_t* seg_list, int n_list, int32_t* cost) {
+                   const int32_t* nbrs, const float* H, const double* H64, int L, const int32_t* labels, int S,
+                   int penalty, int combine, const int32_t* seg_list, int n_list, int32_t* cost) {
     if (!cams || !imgs || ref < 0 || ref >= n_views || L < 1 || S < 0 || !labels || !cost) return 1;
+    if (!H == !H64) return 1;
     if (sample_bytes != 1 && sample_bytes != 2) return 1;
     int W = cams[ref].width, Hh = cams[ref].height;
     int32_t *offs, *pix;
@@ -269,7 +298,7 @@ int or_cost_volume(const or_camera* cams, int n_views, const or_image* imgs, int
             int64_t sum = 0;
             for (int32_t q = offs[s]; q < offs[s + 1]; q++) {
                 int x = pix[q] % W, y = pix[q] / W;
-                sum += pixel_cost(cams, imgs, sample_bytes, ref, n_nbrs, nbrs, H, L, d, x, y, penalty, combine);
+                sum += pixel_cost(cams, imgs, sample_bytes, ref, n_nbrs, nbrs, H, H64, L, d, x, y, penalty, combine);
             }
             if (sum > INT32_MAX) rc = 3;
             cost[(size_t)s * L + d] = (int32_t)sum;
@@ -282,9 +311,10 @@ int or_cost_volume(const or_camera* cams, int n_views, const or_image* imgs, int
 
 /* Selected entries cost[seg[i]][lab[i]] of the same volume, each computed on its own. */
 int or_cost_entries(const or_camera* cams, int n_views, const or_image* imgs, int sample_bytes, int ref, int n_nbrs,
-                    const int32_t* nbrs, const float* H, int L, const int32_t* labels, int S, int penalty,
-                    int combine, int n_entries, const int32_t* seg, const int32_t* lab, int32_t* out) {
+                    const int32_t* nbrs, const float* H, const double* H64, int L, const int32_t* labels, int S,
+                    int penalty, int combine, int n_entries, const int32_t* seg, const int32_t* lab, int32_t* out) {
     if (!cams || !imgs || ref < 0 || ref >= n_views || !labels || !out) return 1;
+    if (!H == !H64) return 1;
     int W = cams[ref].width, Hh = cams[ref].height;
     int32_t *offs, *pix;
     int rc = segment_lists(labels, W, Hh, S, &offs, &pix);
@@ -295,7 +325,7 @@ int or_cost_entries(const or_camera* cams, int n_views, const or_image* imgs, in
         int64_t sum = 0;
         for (int32_t q = offs[s]; q < offs[s + 1]; q++) {
             int x = pix[q] % W, y = pix[q] / W;
-            sum += pixel_cost(cams, imgs, sample_bytes, ref, n_nbrs, nbrs, H, L, d, x, y, penalty, combine);
+            sum += pixel_cost(cams, imgs, sample_bytes, ref, n_nbrs, nbrs, H, H64, L, d, x, y, penalty, combine);
         }
         if (sum > INT32_MAX) rc = 3;
         out[i] = (int32_t)sum;
@@ -448,7 +478,8 @@ int or_depth_map(int W, int Hh, const int32_t* labels, int S, const uint16_t* se
  * every segment s, label d and neighbour k (view nbrs[k]):
  *   mu_s      the integer centroid of s: (floor((2 sum x + n) / (2 n)), floor((2 sum y + n) / (2 n)))
  *             over its n pixels (the paper does not define the centre; this is the rounded mean);
- *   T[mu_s]   mu_s projected with H[k][d] by the same FP32 sequence as the cost volume;
+ *   T[mu_s]   mu_s projected with H[k][d] by the same FP32 sequence as the cost volume (or, with
+ *             H = NULL, with the FP64 table H64 by the FP64 projection);
  *   m         sum over the window offsets w (window x window, odd) of the L1 distance of (Y, Cb, Cr)
  *             at mu_s + w in the reference and at T[mu_s] + w in view nbrs[k]; a pair with either
  *             position outside its image (or T[mu_s] out of view) costs the penalty. The paper's
@@ -459,10 +490,11 @@ int or_depth_map(int W, int Hh, const int32_t* labels, int S, const uint16_t* se
  * Outputs are int32 [S][L][n_nbrs].
  */
 int or_centre_table(const or_camera* cams, int n_views, const or_image* imgs, int sample_bytes, int ref, int n_nbrs,
-                    const int32_t* nbrs, const float* H, int L, const int32_t* const* labels_views, int S, int window,
-                    int penalty, int32_t* out_m, int32_t* out_sp) {
+                    const int32_t* nbrs, const float* H, const double* H64, int L, const int32_t* const* labels_views,
+                    int S, int window, int penalty, int32_t* out_m, int32_t* out_sp) {
     if (!cams || !imgs || ref < 0 || ref >= n_views || !labels_views || !labels_views[ref] || S < 0 || L < 1)
         return 1;
+    if (!H == !H64) return 1;
     if (window < 1 || (window & 1) == 0 || !out_m || !out_sp) return 1;
     const int W = cams[ref].width, Hh = cams[ref].height, half = window / 2;
     const int32_t* lab = labels_views[ref];
@@ -487,9 +519,16 @@ int or_centre_table(const or_camera* cams, int n_views, const or_image* imgs, in
         for (int d = 0; d < L; d++)
             for (int k = 0; k < n_nbrs; k++) {
                 int v = nbrs[k];
-                const float* h = H + ((size_t)k * L + d) * 9;
-                int ui = 0, vi = 0;
-                int in = cnt[s] > 0 && project_f32(h, mx, my, cams[v].width, cams[v].height, &ui, &vi);
+                const size_t ho = ((size_t)k * L + d) * 9;
+                int ui = 0, vi = 0, in = 0;
+                if (cnt[s] > 0 && H64) {
+                    long lu = 0, lv = 0;
+                    in = project_f64(H64 + ho, mx, my, cams[v].width, cams[v].height, &lu, &lv);
+                    ui = (int)lu;
+                    vi = (int)lv;
+                } else if (cnt[s] > 0) {
+                    in = project_f32(H + ho, mx, my, cams[v].width, cams[v].height, &ui, &vi);
+                }
                 int64_t m = 0;
                 for (int dy = -half; dy <= half; dy++)
                     for (int dx = -half; dx <= half; dx++) {
