@@ -174,14 +174,21 @@ def algorithmic_ops(wl, culled: int = 0) -> int:
     return (wl.evaluations() - culled) * OPS_PER_EVAL + px_labels * OPS_PER_PIXEL_LABEL
 
 
-def cpu_baseline(wl, budget_s: float = 12.0, min_rows: int = 4):
+def _oracle_table(wl, r, nb, fp64: bool):
+    import oracle
+    table = oracle.homography_table_f64 if fp64 else oracle.homography_table
+    return table(wl.cams, r, nb, wl.n_labels, wl.z_near, wl.z_far)
+
+
+def cpu_baseline(wl, budget_s: float = 12.0, min_rows: int = 4, fp64: bool = False):
     """Time the oracle as it stands on the first k segments of reference 0 (whole label rows), k chosen
-    so the run takes about budget_s seconds. Returns (evals/s, sample description)."""
+    so the run takes about budget_s seconds (FP64 projection mode with fp64). Returns (evals/s, sample
+    description)."""
     import oracle
     r = wl.ref_views[0]
     lab, S = wl.labels(r)
     nb = wl.neighbours(r)
-    H = oracle.homography_table(wl.cams, r, nb, wl.n_labels, wl.z_near, wl.z_far)
+    H = _oracle_table(wl, r, nb, fp64)
     views = wl.views()
     sizes = np.bincount(lab.ravel(), minlength=S)
     out = np.zeros((S, wl.n_labels), np.int32)
@@ -352,7 +359,7 @@ def run_segmentation(args, rank, world, local):
     sg.close()
 
 
-def cpu_baseline_all_cores(wl, k_single: int, budget_s: float = 10.0):
+def cpu_baseline_all_cores(wl, k_single: int, budget_s: float = 10.0, fp64: bool = False):
     """The same oracle, unchanged, on every host core: threads compute disjoint segment rows of reference 0
     (the oracle keeps no global state and ctypes releases the GIL during the call). Each thread takes at
     most the row count one thread did in the single-thread baseline. Returns (evals/s, threads, sample)."""
@@ -361,10 +368,10 @@ def cpu_baseline_all_cores(wl, k_single: int, budget_s: float = 10.0):
     r = wl.ref_views[0]
     lab, S = wl.labels(r)
     nb = wl.neighbours(r)
-    H = oracle.homography_table(wl.cams, r, nb, wl.n_labels, wl.z_near, wl.z_far)
     views = wl.views()
     sizes = np.bincount(lab.ravel(), minlength=S)
     out = np.zeros((S, wl.n_labels), np.int32)
+    H = _oracle_table(wl, r, nb, fp64)
     threads = max(1, os.cpu_count() or 1)
     per = max(1, min(k_single, S // threads))
     parts = [np.arange(t * per, (t + 1) * per, dtype=np.int32) for t in range(threads) if (t + 1) * per <= S]
@@ -604,6 +611,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="synthetic workload (default: the 1920x1080 8-view configuration; others for profiling)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="sample positions of the depth part: the FP32 contract (default) or the FP64 projection")
     ap.add_argument("--part", default="depth", choices=["depth", "segmentation", "centre", "adjacency"],
                     help="depth: the cost-volume hot path (default); segmentation: superpixels of every view; "
                          "centre: the centre table of every reference; adjacency: adjacency and beta")
@@ -636,8 +645,10 @@ def main():
     dev = torch.device("cuda", local)
     R, L = len(wl.ref_views), wl.n_labels
     S = [wl.labels(r)[1] for r in wl.ref_views]
+    fp64 = args.precision == "fp64"
     ctx = ftv.ftv_depth_init(wl.cams, wl.ref_views, L, wl.z_near, wl.z_far, sample_bytes=wl.sample_bytes,
-                             bit_depth=wl.bit_depth, oob_penalty=wl.oob_penalty, max_segments=max(S))
+                             bit_depth=wl.bit_depth, oob_penalty=wl.oob_penalty, max_segments=max(S),
+                             precision=ftv.FTV_PRECISION_FP64 if fp64 else ftv.FTV_PRECISION_FP32)
     host_views = wl.views()
     host_planes = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (v.Y, v.U, v.V)]
                    for v in host_views]
@@ -678,6 +689,7 @@ def main():
         torch.cuda.synchronize()
     launches = ftv.ftv_launch_count(ctx) - launches0
     culled = ftv.ftv_culled_evaluations(ctx)  # the same for every step (the last launch's count)
+    recomputed = ftv.ftv_fp64_recomputed(ctx)
     if world > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -718,7 +730,7 @@ def main():
         ev_bytes, comp_bytes = algorithmic_bytes(wl, culled)
         kms = statistics.mean(kernel_ms)
         achieved = (ev_bytes + comp_bytes) / (kms / 1000.0) / 1e9
-        traffic = _traffic_for_current_kernel(args.workload)
+        traffic = _traffic_for_current_kernel(args.workload + ("_fp64" if fp64 else ""))
         clk = clocks.summary()
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         sm_mhz = clk["sm_mhz"] if clk else 2070.0
@@ -732,12 +744,15 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "depth_maps_per_s": whole_job_rate(world, R * args.steps, total_s),
                        "cost_kernel_ms": kms, "evaluations_per_step": evals,
-                       "culled_evaluations_per_step": culled, "culled_fraction": culled / evals},
+                       "culled_evaluations_per_step": culled, "culled_fraction": culled / evals,
+                       "precision": "FP64 projection" if fp64 else "FP32 contract",
+                       **({"fp64_recomputed_per_step": recomputed, "fp64_recomputed_fraction": recomputed / evals}
+                          if fp64 else {})},
             "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Tops/s",
                          "frac": alu_achieved / alu_peak, "traffic": traffic,
                          "peak_kind": f"{n_sm} SMs x 128 lanes x {sm_mhz:.0f} MHz (median sampled SM clock)",
                          "algorithmic_ops_per_launch": algorithmic_ops(wl, culled), "ops_per_evaluation": OPS_PER_EVAL,
-                         "kernel": "cost_kernel<FMT_P10, MIN>"},
+                         "kernel": "cost_kernel<FMT_P10, MIN" + (", FP64 projection>" if fp64 else ">")},
             "hbm_roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "peak_kind": peak_kind,
                              "algorithmic_bytes_per_launch": ev_bytes + comp_bytes,
@@ -749,9 +764,9 @@ def main():
             "clocks": clk,
         }
         if world == 1 and not args.no_cpu_baseline:
-            rate, desc, k = cpu_baseline(wl)
+            rate, desc, k = cpu_baseline(wl, fp64=fp64)
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
-            rate_mt, threads, desc_mt = cpu_baseline_all_cores(wl, k)
+            rate_mt, threads, desc_mt = cpu_baseline_all_cores(wl, k, fp64=fp64)
             line["cpu_baseline_all_cores"] = {"value": rate_mt, "unit": UNIT, "cores": threads, "kind": "oracle",
                                               "sample": desc_mt}
         print(json.dumps(line), flush=True)

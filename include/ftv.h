@@ -68,6 +68,7 @@ enum { FTV_PLANES_REF = 0, FTV_PLANES_CENTRE = 1 };
 enum { FTV_COMBINE_MIN = 0, FTV_COMBINE_SUM = 1 };
 enum { FTV_TM_Y_ONLY = 0, FTV_TM_ALL_YUV = 1 };
 enum { FTV_MASK_CHANGED = 0, FTV_MASK_REUSE_P = 1, FTV_MASK_REUSE_I = 2 };
+enum { FTV_PRECISION_FP32 = 0, FTV_PRECISION_FP64 = 1 };
 
 #define FTV_MAX_VIEWS 64
 #define FTV_MAX_NBRS 32
@@ -90,6 +91,11 @@ enum { FTV_MASK_CHANGED = 0, FTV_MASK_REUSE_P = 1, FTV_MASK_REUSE_I = 2 };
  *   oob_penalty          cost of a sample that falls outside a view; < 0 selects 3 * (2^bit_depth - 1)
  *   combine              per-pixel combination over neighbours: FTV_COMBINE_MIN or FTV_COMBINE_SUM
  *   max_segments         capacity: largest segment count any reference label map will use
+ *   precision            how sample positions are computed (Eq. 4's T[.]; the paper fixes no precision):
+ *                        FTV_PRECISION_FP32 (0, the default when the field is zero): the FP32 contract
+ *                        of ftv_cost_volume; FTV_PRECISION_FP64: the FP64 projection (same entry),
+ *                        which agrees with double-precision geometry wherever the FP32 contract rounds a
+ *                        sample near a pixel boundary the other way.
  */
 typedef struct ftv_config {
     int32_t n_views;
@@ -108,6 +114,7 @@ typedef struct ftv_config {
     int32_t oob_penalty;
     int32_t combine;
     int32_t max_segments;
+    int32_t precision;
 } ftv_config;
 
 /*
@@ -138,6 +145,10 @@ FTV_API ftv_status ftv_depth_destroy(ftv_ctx* ctx);
 /* Copy the FP32 homography table of reference ref_index (0 <= ref_index < n_refs) into host_out,
  * laid out [n_nbrs][n_labels][9] row-major, neighbours in list order. */
 FTV_API ftv_status ftv_get_homographies(const ftv_ctx* ctx, int32_t ref_index, float* host_out);
+
+/* The same table before its rounding to FP32: FP64 entries [n_nbrs][n_labels][9] into host_out. It is the
+ * homography of the FTV_PRECISION_FP64 projection (available in either precision). */
+FTV_API ftv_status ftv_get_homographies_f64(const ftv_ctx* ctx, int32_t ref_index, double* host_out);
 
 /* Number of neighbours of reference ref_index, and the views they are, in table order
  * (host_views may be NULL; else it receives n entries). */
@@ -178,6 +189,13 @@ FTV_API ftv_status ftv_segment_index(ftv_ctx* ctx, int32_t ref_index, const int3
  *   (ui, vi) = (floor(u + 0.5), floor(v + 0.5)) must satisfy 0 <= ui <= W_v - 1, 0 <= vi <= H_v - 1;
  *   c_v = |Y_r - Y_v| + |Cb_r - Cb_v| + |Cr_r - Cr_v| at (x, y) and (ui, vi) (integer samples), else the
  *   out-of-view penalty. Eq. 4's 1/size(W) factor is dropped (the sum is an argmin-preserving scale).
+ * FTV_PRECISION_FP64 contexts replace the position by the FP64 projection: with h the unrounded FP64
+ * homography (ftv_get_homographies_f64) and IEEE double arithmetic, each operation rounded on its own,
+ *   X = (h0 * x + h1 * y) + h2; Y = (h3 * x + h4 * y) + h5; Wz = (h6 * x + h7 * y) + h8;
+ *   out of view unless Wz > 0; (ui, vi) = (floor(X / Wz + 0.5), floor(Y / Wz + 0.5)), same range test.
+ * (The kernel evaluates it in FP32 in a local frame around each tile of pixels, with a rigorous error
+ * bound, and redoes in FP64 exactly the evaluations that lie within that bound of a rounding boundary:
+ * ftv_fp64_recomputed.)
  * Asynchronous on `stream`.
  */
 FTV_API ftv_status ftv_cost_volume(ftv_ctx* ctx, const void* const* d_planes, const int64_t* pitch_bytes,
@@ -337,8 +355,9 @@ FTV_API int64_t ftv_batch_launch_count(const ftv_batch* b);
  * and neighbour k (table order of ftv_get_neighbours):
  *   mu_s  integer centroid (floor((2 sum x + n) / (2 n)), floor((2 sum y + n) / (2 n))) of s;
  *   m     sum over the window x window offsets w (odd, <= 15; the paper uses 3) of the L1 (Y, Cb, Cr)
- *         distance between mu_s + w in r and T[mu_s] + w in view k, T[.] being the volume's FP32
- *         projection; pairs with a position outside its image, or a centre out of view, cost the
+ *         distance between mu_s + w in r and T[mu_s] + w in view k, T[.] being the volume's projection
+ *         (FP32 contract, or the FP64 projection in FTV_PRECISION_FP64 contexts); pairs with a position
+ *         outside its image, or a centre out of view, cost the
  *         penalty. Eq. 4's 1/size(W) is left to the consumer (m_paper = m / window^2);
  *   s'    d_labels_views[view k]'s label at T[mu_s], or -1 if out of view or that map is NULL.
  * d_labels_views: host array of n_views device label maps (int32 [H][W] per view; every reference's is
@@ -464,6 +483,13 @@ FTV_API ftv_status ftv_check(ftv_ctx* ctx, ftv_stream stream);
  * default, that changes nothing). Results are identical with and without this; the count is for
  * accounting (a roofline that charges only the samples taken). */
 FTV_API ftv_status ftv_culled_evaluations(ftv_ctx* ctx, ftv_stream stream, int64_t* culled);
+
+/* Wait for `stream`, then report in *recomputed how many evaluations of the context's most recent
+ * ftv_cost_volume call (FTV_PRECISION_FP64 contexts) were computed in double precision: those whose
+ * FP32 local-frame position lay within its error bound of a rounding boundary, plus every evaluation of
+ * a (tile, neighbour, label) whose bound could not be established (Wz near zero inside the tile). 0 for
+ * FP32 contexts. Results do not depend on it; the count is for accounting. */
+FTV_API ftv_status ftv_fp64_recomputed(ftv_ctx* ctx, ftv_stream stream, int64_t* recomputed);
 
 /* Timing of the dominant kernel: with enable != 0, every ftv_cost_volume call records a pair of CUDA
  * events on its stream immediately around its cost-kernel launch (the events belong to the context). */

@@ -38,7 +38,8 @@ def _flags() -> list[str]:
 def _compile(src: str) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     path = os.path.join(CSRC, src)
-    deps = [path, os.path.join(CSRC, "ftv_internal.h"), os.path.join(ROOT, "include", "ftv.h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
+    deps = [path, *headers, os.path.join(ROOT, "include", "ftv.h")]
     if os.path.exists(obj) and all(os.path.getmtime(obj) >= os.path.getmtime(d) for d in deps):
         return obj
     cmd = [nvcc(), *_flags(), "-c", path, "-o", obj]

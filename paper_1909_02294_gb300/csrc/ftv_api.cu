@@ -44,6 +44,7 @@ void free_ctx(ftv_ctx* c) {
     free_stream_state(c);
     for (auto& r : c->refs) {
         cudaFree(r.d_H);
+        cudaFree(r.d_H64);
         cudaFree(r.d_nbrs);
         cudaFree(r.d_offs);
         cudaFree(r.d_cursor);
@@ -105,6 +106,7 @@ ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out) {
     if (cfg->bit_depth < 1 || cfg->bit_depth > 8 * cfg->sample_bytes) return FTV_ERR_INVALID_ARG;
     if (cfg->combine != FTV_COMBINE_MIN && cfg->combine != FTV_COMBINE_SUM) return FTV_ERR_INVALID_ARG;
     if (cfg->max_segments < 1) return FTV_ERR_INVALID_ARG;
+    if (cfg->precision != FTV_PRECISION_FP32 && cfg->precision != FTV_PRECISION_FP64) return FTV_ERR_INVALID_ARG;
     for (int v = 0; v < cfg->n_views; ++v)
         if (!valid_camera(cfg->cams[v])) return FTV_ERR_INVALID_ARG;
 
@@ -119,6 +121,7 @@ ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out) {
     c->bit_depth = cfg->bit_depth;
     c->combine = cfg->combine;
     c->max_segments = cfg->max_segments;
+    c->precision = cfg->precision;
     c->z_near = cfg->z_near;
     c->z_far = cfg->z_far;
     c->penalty = cfg->oob_penalty >= 0 ? cfg->oob_penalty : (int32_t)(3 * ((1LL << cfg->bit_depth) - 1));
@@ -164,10 +167,11 @@ ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out) {
     c->nLB = (c->L + lb_max - 1) / lb_max;
     c->LB = (c->L + c->nLB - 1) / c->nLB;
 
-    // homographies (FP64 -> FP32)
+    // homographies (FP64 -> FP32; the FP64 table is kept for the FP64 projection)
     const ftv_camera* cc = c->plane_mode == FTV_PLANES_CENTRE ? &c->cams[c->centre] : nullptr;
     for (auto& r : c->refs) {
         r.h_H.resize((size_t)r.n_nbrs * c->L * 9);
+        r.h_H64.resize(r.h_H.size());
         for (int k = 0; k < r.n_nbrs; ++k)
             for (int d = 0; d < c->L; ++d) {
                 double H[9];
@@ -178,11 +182,12 @@ ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out) {
                 for (int e = 0; e < 9; ++e) {
                     const float f = (float)H[e];
                     // the device's exact in-view test relies on |h| <= 2^100 (finite projections)
-                    if (!(std::fabs(f) <= 0x1p100f)) {
+                    if (!(std::fabs(f) <= 0x1p100f) || !(std::fabs(H[e]) <= 0x1p100)) {
                         free_ctx(c);
                         return FTV_ERR_INVALID_ARG;
                     }
                     r.h_H[((size_t)k * c->L + d) * 9 + e] = f;
+                    r.h_H64[((size_t)k * c->L + d) * 9 + e] = H[e];
                 }
             }
     }
@@ -194,6 +199,7 @@ ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out) {
         for (const auto& r : c->refs)
             for (size_t e = 0; e < r.h_H.size(); e += 9) any_affine = any_affine || (r.h_H[e + 6] == 0.0f && r.h_H[e + 7] == 0.0f);
         c->kind = any_affine ? kKindMixed : kKindProjective;
+        if (c->precision == FTV_PRECISION_FP64) c->kind = kKindPrecise;
     }
 
     // device scratch (all host-side validation is done by now)
@@ -217,6 +223,7 @@ ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out) {
     ok = ok && dalloc(&c->d_adj_offs, (size_t)c->max_segments) == cudaSuccess;
     for (auto& r : c->refs) {
         ok = ok && dalloc(&r.d_H, r.h_H.size()) == cudaSuccess;
+        if (c->precision == FTV_PRECISION_FP64) ok = ok && dalloc(&r.d_H64, r.h_H64.size()) == cudaSuccess;
         ok = ok && dalloc(&r.d_nbrs, (size_t)r.n_nbrs) == cudaSuccess;
         ok = ok && dalloc(&r.d_offs, (size_t)c->max_segments + 1) == cudaSuccess;
         ok = ok && dalloc(&r.d_cursor, (size_t)c->max_segments) == cudaSuccess;
@@ -243,6 +250,9 @@ ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out) {
             nv[k].pad = 0;
         }
         ok = ok && cudaMemcpy(r.d_H, r.h_H.data(), sizeof(float) * r.h_H.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+        if (r.d_H64)
+            ok = ok && cudaMemcpy(r.d_H64, r.h_H64.data(), sizeof(double) * r.h_H64.size(), cudaMemcpyHostToDevice) ==
+                           cudaSuccess;
         if (r.n_nbrs)
             ok = ok && cudaMemcpy(r.d_nbrs, nv.data(), sizeof(NbrView) * nv.size(), cudaMemcpyHostToDevice) == cudaSuccess;
     }
@@ -298,6 +308,13 @@ ftv_status ftv_get_homographies(const ftv_ctx* ctx, int32_t ref_index, float* ho
     if (!ctx || !host_out || ref_index < 0 || ref_index >= ctx->n_refs) return FTV_ERR_INVALID_ARG;
     const auto& r = ctx->refs[ref_index];
     std::memcpy(host_out, r.h_H.data(), sizeof(float) * r.h_H.size());
+    return FTV_OK;
+}
+
+ftv_status ftv_get_homographies_f64(const ftv_ctx* ctx, int32_t ref_index, double* host_out) {
+    if (!ctx || !host_out || ref_index < 0 || ref_index >= ctx->n_refs) return FTV_ERR_INVALID_ARG;
+    const auto& r = ctx->refs[ref_index];
+    std::memcpy(host_out, r.h_H64.data(), sizeof(double) * r.h_H64.size());
     return FTV_OK;
 }
 
@@ -394,6 +411,7 @@ ftv_status ftv_cost_volume(ftv_ctx* ctx, const void* const* d_planes, const int6
         J.n_listed = nl;
         J.woffs = r.d_woffs;
         J.H = r.d_H;
+        J.H64 = r.d_H64;
         J.nbrs = r.d_nbrs;
         J.cost = d_cost[i];
         J.W = r.W;
@@ -468,6 +486,15 @@ ftv_status ftv_wta_depth(ftv_ctx* ctx, int32_t ref_index, const int32_t* d_cost,
         ctx->launches++;
     }
     return e == cudaSuccess ? FTV_OK : FTV_ERR_CUDA;
+}
+
+ftv_status ftv_fp64_recomputed(ftv_ctx* ctx, ftv_stream stream, int64_t* recomputed) {
+    if (!ctx || !recomputed) return FTV_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return FTV_ERR_CUDA;
+    unsigned long long v = 0;
+    if (cudaMemcpy(&v, &ctx->d_plan->recomputed, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return FTV_ERR_CUDA;
+    *recomputed = (int64_t)v;
+    return FTV_OK;
 }
 
 ftv_status ftv_culled_evaluations(ftv_ctx* ctx, ftv_stream stream, int64_t* culled) {

@@ -589,6 +589,8 @@ ftv_status ftv_batch_prepare(ftv_batch* b, const ftv_frame_job* jobs, int32_t n_
         for (int k = 0; k < j; ++k)
             if (jobs[k].ctx == J.ctx) return FTV_ERR_INVALID_ARG;  // one frame per stream per batch
         if (fmt >= 0 && (J.ctx->fmt != fmt || J.ctx->combine != combine)) return FTV_ERR_INVALID_ARG;
+        // one cost-kernel instantiation per launch: FP32- and FP64-precision streams do not share a batch
+        if (j > 0 && J.ctx->precision != jobs[0].ctx->precision) return FTV_ERR_INVALID_ARG;
         fmt = J.ctx->fmt;
         combine = J.ctx->combine;
         pf_all = pf_all && J.ctx->penalty_floor;
@@ -672,6 +674,7 @@ ftv_status ftv_batch_prepare(ftv_batch* b, const ftv_frame_job* jobs, int32_t n_
             q.n_listed = S.d_n_changed;
             q.woffs = r.d_woffs;
             q.H = r.d_H;
+            q.H64 = r.d_H64;
             q.nbrs = S.d_nbrs_ring[cur];
             q.cost = S.d_cost;
             q.W = r.W;

@@ -7,7 +7,8 @@
 // the matching is done "only for centers of segments". Here:
 //   mu_s  = integer centroid floor((2 sum x + n) / (2 n)) of the segment's n pixels (the paper does not
 //           define the centre);
-//   T     = the same FP32 homography and rounding as the cost volume;
+//   T     = the same projection as the cost volume: the FP32 homography and rounding, or the FP64
+//           projection for FP64-precision contexts;
 //   m     = the raw window sum (the consumer divides by size(W)); a window pair with a position outside
 //           its image, or a centre that projects out of view, costs the out-of-view penalty;
 //   s'    = the neighbour view's label at T[mu_s] (-1 when out of view or no label map is given).
@@ -20,6 +21,7 @@
 #include <vector>
 
 #include "ftv_internal.h"
+#include "ftv_project.cuh"
 
 namespace ftv {
 namespace {
@@ -69,6 +71,7 @@ __global__ void centroid_kernel(const int32_t* __restrict__ offs, const uint32_t
 struct CentreArgs {
     const int2* centre;
     const float* H;         // [N][L][9]
+    const double* H64;      // [N][L][9] unrounded table, FP64-precision contexts (else nullptr)
     const void* ref_tex;    // packed reference view
     const NbrView* nbrs;    // [N]
     const int32_t* const* labels_v;  // [N] neighbour label maps (entries may be null)
@@ -124,7 +127,9 @@ __global__ void __launch_bounds__(kCentreThreads) centre_table_kernel(CentreArgs
             const float* h = a.H + ((int64_t)k * a.L + d) * 9;
             bool in = c.x >= 0;
             int ui = 0, vi = 0;
-            if (in) {
+            if (in && a.H64) {
+                in = project_fp64(a.H64 + ((int64_t)k * a.L + d) * 9, c.x, c.y, nv.w, nv.h, &ui, &vi);
+            } else if (in) {
                 const float x = (float)c.x, y = (float)c.y;
                 const float X = __fmaf_rn(__ldg(&h[0]), x, __fmaf_rn(__ldg(&h[1]), y, __ldg(&h[2])));
                 const float Yh = __fmaf_rn(__ldg(&h[3]), x, __fmaf_rn(__ldg(&h[4]), y, __ldg(&h[5])));
@@ -226,6 +231,7 @@ extern "C" ftv_status ftv_centre_table(ftv_ctx* ctx, const void* const* d_planes
         CentreArgs a{};
         a.centre = r.d_centre;
         a.H = r.d_H;
+        a.H64 = r.d_H64;
         a.ref_tex = static_cast<char*>(ctx->d_packed) + ctx->view_offset_bytes[r.view];
         a.nbrs = r.d_nbrs;
         a.labels_v = r.d_nbr_labels;

@@ -29,6 +29,7 @@
 #include <mutex>
 
 #include "ftv_internal.h"
+#include "ftv_project.cuh"
 
 namespace ftv {
 namespace {
@@ -100,7 +101,14 @@ struct __align__(16) HEntry {
     float h[9];
     uint32_t w, h_, pm;
 };
-enum : uint32_t { kGeneral = 0, kAffine = 1, kUnit = 2, kOut = 3, kRect = 4 };
+enum : uint32_t { kGeneral = 0, kAffine = 1, kUnit = 2, kOut = 3, kRect = 4, kSlow = 5 };
+
+// FP64-projection entries (kKindPrecise) stage local-frame coefficients in HEntry::h (stage_precise) and
+// this alongside: the integer column u0 and row v0 the frame is shifted by, and the tie-test thresholds.
+struct __align__(16) PEntry {
+    int32_t u0, v0;
+    float thr_u, thr_v;
+};
 constexpr uint32_t kPitchMask = (1u << 28) - 1u;
 
 __device__ __forceinline__ bool finite_positive(float r) {
@@ -228,6 +236,81 @@ __device__ __forceinline__ bool box_out_of_view(const float* h, float x0, float 
     return left || right || top || bottom || behind;
 }
 
+// Stages one (neighbour, label) entry of an FP64-precision unit for a tile whose pixels lie in the box
+// x0 + [-rx, rx] x y0 + [-ry, ry]. In the local frame x' = x - x0, y' = y - y0 the projection is
+//   u = U0 + X'/W, v = V0 + Y'/W,  X' = X - U0 W = a0 x' + a1 y' + a2,  Y' = Y - V0 W = b0 x' + b1 y' + b2,
+//   W = c0 x' + c1 y' + c2,
+// with (U0, V0) the integer position nearest the box centre's projection. The coefficients are formed in
+// FP64 (that is where the cancellation of X - U0 W happens) and rounded to FP32 into h[]; u' = X'/W then
+// stays within a few pixels, so the FP32 evaluation is accurate to about 2^-24 of the tile's extent
+// instead of 2^-24 of the image coordinates. The bound delta covers, at every pixel of the box:
+//   the FP32 rounding of the coefficients and of the two fused multiply-adds (3 * 2^-24 of the magnitude
+//   M = |a0| rx + |a1| ry + |a2|), the FP64 rounding of the coefficients (2^-50 of the global magnitudes),
+//   the quotient of those errors ((e_X + |u'| e_W) / W), the rounded reciprocal, product and + 0.5
+//   (2^-23 |u'| + 2^-24 (|u'| + 1)), and the FP64 projection's own error against exact arithmetic
+//   (3 * 2^-53 (A_X + |u| A_W) / W + 2 * 2^-53 (|u| + 1)),
+// doubled. Where t = u' + 0.5 computed in FP32 lies farther than delta from every integer, floor(t) + U0
+// is the FP64 projection's column (both floors see the same side of the same integer); otherwise the
+// evaluation is redone in FP64. Returns kGeneral (that test applies), kOut (the FP64 projection puts no
+// pixel of the box in view: behind the camera, or wholly beyond one image edge by more than the bound) or
+// kSlow (no bound: W may come near zero in the box, or delta is large; every evaluation in FP64).
+__device__ uint32_t stage_precise(const double* __restrict__ hg, int x0, int y0, int rx, int ry, int wv, int hv,
+                                  float* h, PEntry& P) {
+    double H[9];
+#pragma unroll
+    for (int f = 0; f < 9; ++f) H[f] = __ldg(&hg[f]);
+    const double u = 0x1p-53;
+    const double dx0 = (double)x0, dy0 = (double)y0, drx = (double)rx, dry = (double)ry;
+    const double ax = fabs(dx0) + drx, ay = fabs(dy0) + dry;
+    const double AX = fabs(H[0]) * ax + fabs(H[1]) * ay + fabs(H[2]);
+    const double AY = fabs(H[3]) * ax + fabs(H[4]) * ay + fabs(H[5]);
+    const double AW = fabs(H[6]) * ax + fabs(H[7]) * ay + fabs(H[8]);
+    const double X0 = fma(H[0], dx0, fma(H[1], dy0, H[2]));
+    const double Y0 = fma(H[3], dx0, fma(H[4], dy0, H[5]));
+    const double W0 = fma(H[6], dx0, fma(H[7], dy0, H[8]));
+    const double gW = fabs(H[6]) * drx + fabs(H[7]) * dry + 0x1p-48 * AW;
+    if (W0 + gW < 0.0) return kOut;  // W < 0 at every pixel of the box
+    const double Wlo = W0 - gW;      // the exact W is at least this at every pixel of the box
+    if (!(Wlo > 0x1p-60)) return kSlow;
+    const double U0 = rint(fmin(fmax((double)__fdiv_rn((float)X0, (float)W0), -0x1p24), 0x1p24));
+    const double V0 = rint(fmin(fmax((double)__fdiv_rn((float)Y0, (float)W0), -0x1p24), 0x1p24));
+    h[0] = __double2float_rn(fma(-U0, H[6], H[0]));
+    h[1] = __double2float_rn(fma(-U0, H[7], H[1]));
+    h[2] = __double2float_rn(fma(-U0, W0, X0));
+    h[3] = __double2float_rn(fma(-V0, H[6], H[3]));
+    h[4] = __double2float_rn(fma(-V0, H[7], H[4]));
+    h[5] = __double2float_rn(fma(-V0, W0, Y0));
+    h[6] = __double2float_rn(H[6]);
+    h[7] = __double2float_rn(H[7]);
+    h[8] = __double2float_rn(W0);
+    const double Ma = fabs((double)h[0]) * drx + fabs((double)h[1]) * dry + fabs((double)h[2]);
+    const double Mb = fabs((double)h[3]) * drx + fabs((double)h[4]) * dry + fabs((double)h[5]);
+    const double Mc = fabs((double)h[6]) * drx + fabs((double)h[7]) * dry + fabs((double)h[8]);
+    const double eX = 0x1.82p-23 * Ma + 0x1p-50 * (Ma + AX + fabs(U0) * AW) + 0x1p-130;
+    const double eY = 0x1.82p-23 * Mb + 0x1p-50 * (Mb + AY + fabs(V0) * AW) + 0x1p-130;
+    const double eW = 0x1.82p-23 * Mc + 0x1p-50 * (Mc + AW) + 0x1p-130;
+    if (!(Wlo > 2.0 * eW)) return kSlow;
+    const double Wl = Wlo - eW;  // lower bound of the FP32 W and of the FP64 projection's W
+    const double Ub = (Ma * (1.0 + 0x1p-20) + 2.0 * eX) / Wl;
+    const double Vb = (Mb * (1.0 + 0x1p-20) + 2.0 * eY) / Wl;
+    const double qu = (eX + Ub * eW) / Wl, qv = (eY + Vb * eW) / Wl;
+    const double du = 2.0 * (qu + 0x1.01p-23 * Ub + 0x1.01p-24 * (Ub + 1.0) +
+                             3.0 * u * (AX + (fabs(U0) + Ub) * AW) / Wl + 2.01 * u * (fabs(U0) + Ub + 1.0)) + 0x1p-30;
+    const double dv = 2.0 * (qv + 0x1.01p-23 * Vb + 0x1.01p-24 * (Vb + 1.0) +
+                             3.0 * u * (AY + (fabs(V0) + Vb) * AW) / Wl + 2.01 * u * (fabs(V0) + Vb + 1.0)) + 0x1p-30;
+    // every pixel of the box has its column (row) beyond one edge by more than the bound
+    if (U0 + Ub + 0.5 + du < 0.0 || U0 - Ub + 0.5 - du >= (double)wv || V0 + Vb + 0.5 + dv < 0.0 ||
+        V0 - Vb + 0.5 - dv >= (double)hv)
+        return kOut;
+    if (!(du < 0.25 && dv < 0.25 && Ub < 0x1p21 && Vb < 0x1p21)) return kSlow;
+    P.u0 = (int)U0;
+    P.v0 = (int)V0;
+    // near a tie when |frac(t) - 0.5| >= thr; 2^-22 more covers the FP32 rounding of that test itself
+    P.thr_u = __double2float_rd(0.5 - du - 0x1p-22);
+    P.thr_v = __double2float_rd(0.5 - dv - 0x1p-22);
+    return kGeneral;
+}
+
 // First item of chunk k when n items are split into K nearly equal consecutive chunks (32-bit, no overflow).
 __device__ __forceinline__ int chunk_begin(int n, int k, int K) {
     const int q = n / K, r = n - q * K;
@@ -281,6 +364,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
     __shared__ int sWoffs[kLocCache + 1];
     __shared__ int s_item, s_k0, s_k1, s_culled;
     __shared__ int s_box[4];  // the tile's pixel box: x min, x max, y min, y max
+    __shared__ PEntry sP[KIND == kKindPrecise ? kHEntries : 1];
+    unsigned n_recomputed = 0;  // FP64-precision evaluations computed in double precision by this thread
 
     const int tid = threadIdx.x, lane = tid & 31;
     // this launch's items: [chunk_begin(chunk), chunk_begin(chunk + 1)); only thread 0 needs the first (it
@@ -318,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
         const float* __restrict__ Hg = Jp->H;
         const NbrView* __restrict__ nbrs = Jp->nbrs;
         const int nh = N * LBa;
-        for (int e = tid; e < nh; e += kThreads) {
+        for (int e = tid; e < (KIND == kKindPrecise ? 0 : nh); e += kThreads) {
             const int n = e / LBa, l = e - n * LBa;
             const float* src = &Hg[((int64_t)n * L + d0 + l) * 9];
             HEntry& E = sH[e];
@@ -390,7 +475,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
         // Only the projective-only instantiation does this: on a rectified rig an out-of-view sample is
         // already cheap, and there the test cost more than it saved (1920x1080 linear 8-view rig: 7.8 % of
         // the evaluations culled, 31.1 against 30.9 ms).
-        if constexpr (KIND == kKindProjective) {  // every thread takes the same way through the barriers
+        // FP64-precision units stage their entries here, once the box is known (stage_precise), and move the
+        // pixels into the box's local frame.
+        int fx0 = 0, fy0 = 0;  // local-frame origin (kKindPrecise)
+        if constexpr (KIND == kKindProjective || KIND == kKindPrecise) {  // uniform way through the barriers
             int bx0 = INT_MAX, bx1 = INT_MIN, by0 = INT_MAX, by1 = INT_MIN;
 #pragma unroll
             for (int j = 0; j < kPPT; ++j)
@@ -411,16 +499,42 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                 atomicMax(&s_box[3], by1);
             }
             __syncthreads();
-            if (s_box[0] <= s_box[1]) {
-                const float fx0 = (float)s_box[0], fx1 = (float)s_box[1], fy0 = (float)s_box[2], fy1 = (float)s_box[3];
-                for (int e = tid; e < nh; e += kThreads) {
-                    HEntry& E = sH[e];
-                    if ((E.pm >> 28) == kGeneral &&
-                        box_out_of_view(E.h, fx0, fx1, fy0, fy1, (float)E.w, (float)E.h_)) {
-                        E.pm = (E.pm & kPitchMask) | ((uint32_t)kOut << 28);
-                        atomicAdd(&s_culled, 1);
+            if constexpr (KIND == kKindProjective) {
+                if (s_box[0] <= s_box[1]) {
+                    const float bx0f = (float)s_box[0], bx1f = (float)s_box[1], by0f = (float)s_box[2],
+                                by1f = (float)s_box[3];
+                    for (int e = tid; e < nh; e += kThreads) {
+                        HEntry& E = sH[e];
+                        if ((E.pm >> 28) == kGeneral &&
+                            box_out_of_view(E.h, bx0f, bx1f, by0f, by1f, (float)E.w, (float)E.h_)) {
+                            E.pm = (E.pm & kPitchMask) | ((uint32_t)kOut << 28);
+                            atomicAdd(&s_culled, 1);
+                        }
                     }
                 }
+            } else {
+                const bool any = s_box[0] <= s_box[1];  // a tile always holds a pixel; kept for safety
+                fx0 = any ? (s_box[0] + s_box[1]) >> 1 : 0;
+                fy0 = any ? (s_box[2] + s_box[3]) >> 1 : 0;
+                const int rx = any ? max(fx0 - s_box[0], s_box[1] - fx0) : 0;
+                const int ry = any ? max(fy0 - s_box[2], s_box[3] - fy0) : 0;
+                for (int e = tid; e < nh; e += kThreads) {
+                    const int n = e / LBa, l = e - n * LBa;
+                    HEntry& E = sH[e];
+                    const int wv = nbrs[n].w, hv = nbrs[n].h;
+                    const uint32_t mode = stage_precise(&Jp->H64[((int64_t)n * L + d0 + l) * 9], fx0, fy0, rx, ry, wv,
+                                                        hv, E.h, sP[e]);
+                    E.w = (uint32_t)wv;
+                    E.h_ = (uint32_t)hv;
+                    E.pm = (uint32_t)nbrs[n].pitch | (mode << 28);
+                    if (mode == kOut) atomicAdd(&s_culled, 1);
+                }
+#pragma unroll
+                for (int j = 0; j < kPPT; ++j)
+                    if (key[j] != kSentinel) {
+                        px[j] = (float)((int)px[j] - fx0);
+                        py[j] = (float)(iy[j] - fy0);
+                    }
             }
             __syncthreads();
             if (tid == 0 && s_culled > 0) atomicAdd(&plan->culled, (unsigned long long)s_culled * (unsigned)(w1 - w0));
@@ -440,7 +554,50 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                 const int pitch = (int)(pm & kPitchMask);
                 // a projective-only launch (no entry with h6 = h7 = 0) keeps the general path alone; a
                 // rectified-only instantiation measured slower than this mixed loop, so there is none
-                if (KIND == kKindMixed && mode == kRect) {
+                if (KIND == kKindPrecise) {
+                    const double* h64 = &Jp->H64[((int64_t)n * L + d0 + l) * 9];
+                    const int wv = __float_as_int(hc.y), hv = __float_as_int(hc.z);
+                    if (mode == kOut) {
+                        if (!(COMB == FTV_COMBINE_MIN && PF)) {
+#pragma unroll
+                            for (int j = 0; j < kPPT; ++j)
+                                m[j] = (COMB == FTV_COMBINE_MIN) ? min(m[j], penalty) : m[j] + penalty;
+                        }
+                    } else if (mode == kSlow) {
+#pragma unroll
+                        for (int j = 0; j < kPPT; ++j) {
+                            int ui = 0, vi = 0;
+                            const bool ok = project_fp64(h64, (int)px[j] + fx0, iy[j], wv, hv, &ui, &vi);
+                            n_recomputed += key[j] != kSentinel;
+                            accumulate<FMT, COMB, PF>(m[j], ok, tex, vi * pitch + ui, ra[j], rb[j], rc[j], penalty);
+                        }
+                    } else {
+                        const float4 ha = e4[0], hb = e4[1];
+                        const float4 pe = reinterpret_cast<const float4*>(sP)[n * LBa + l];
+                        const int u0 = __float_as_int(pe.x), v0 = __float_as_int(pe.y);
+#pragma unroll
+                        for (int j = 0; j < kPPT; ++j) {
+                            const float X = __fmaf_rn(ha.x, px[j], __fmaf_rn(ha.y, py[j], ha.z));
+                            const float Yh = __fmaf_rn(ha.w, px[j], __fmaf_rn(hb.x, py[j], hb.y));
+                            const float Wz = __fmaf_rn(hb.z, px[j], __fmaf_rn(hb.w, py[j], hc.x));
+                            const float r = contract_rcp<FAST_RCP>(Wz);
+                            const float tu = __fadd_rn(__fmul_rn(X, r), 0.5f);
+                            const float tv = __fadd_rn(__fmul_rn(Yh, r), 0.5f);
+                            const float fu = floorf(tu), fv = floorf(tv);
+                            const bool near = fabsf(__fsub_rn(__fsub_rn(tu, fu), 0.5f)) >= pe.z ||
+                                              fabsf(__fsub_rn(__fsub_rn(tv, fv), 0.5f)) >= pe.w;
+                            int ui = __float2int_rz(fu) + u0, vi = __float2int_rz(fv) + v0;
+                            bool ok;
+                            if (near) {
+                                ok = project_fp64(h64, (int)px[j] + fx0, iy[j], wv, hv, &ui, &vi);
+                                n_recomputed += key[j] != kSentinel;
+                            } else {
+                                ok = ((unsigned)ui < (unsigned)wv) & ((unsigned)vi < (unsigned)hv);
+                            }
+                            accumulate<FMT, COMB, PF>(m[j], ok, tex, vi * pitch + ui, ra[j], rb[j], rc[j], penalty);
+                        }
+                    }
+                } else if (KIND == kKindMixed && mode == kRect) {
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
                         int idx;
@@ -536,6 +693,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
             else atomicAdd(dst, v);
         }
     }
+    if constexpr (KIND == kKindPrecise) {
+        const unsigned n = __reduce_add_sync(kFull, n_recomputed);
+        if (lane == 0 && n) atomicAdd(&plan->recomputed, (unsigned long long)n);
+    }
 }
 
 template <int FMT, int COMB, bool FAST>
@@ -605,7 +766,9 @@ namespace {
 
 template <int FMT, int COMB, bool FAST, bool PF>
 void launch_kind(const RefJob* jobs, Plan* p, int kind, int ck, int nck, int grid, cudaStream_t s) {
-    if (kind == kKindProjective)
+    if (kind == kKindPrecise)
+        cost_kernel<FMT, COMB, FAST, PF, kKindPrecise><<<grid, kThreads, 0, s>>>(jobs, p, ck, nck);
+    else if (kind == kKindProjective)
         cost_kernel<FMT, COMB, FAST, PF, kKindProjective><<<grid, kThreads, 0, s>>>(jobs, p, ck, nck);
     else cost_kernel<FMT, COMB, FAST, PF, kKindMixed><<<grid, kThreads, 0, s>>>(jobs, p, ck, nck);
 }

@@ -207,6 +207,7 @@ __global__ void plan_kernel(const __grid_constant__ PlanArgs<CAP> args, int n_jo
         for (int k = 0; k < kMaxChunks; ++k) plan->counter[k] = 0;
         plan->n_jobs = n_jobs;
         plan->culled = 0;
+        plan->recomputed = 0;
     }
 }
 
@@ -226,6 +227,7 @@ __global__ void plan_device_kernel(RefJob* jobs, const int32_t* n_jobs_ptr, Plan
         for (int k = 0; k < kMaxChunks; ++k) plan->counter[k] = 0;
         plan->n_jobs = n_jobs;
         plan->culled = 0;
+        plan->recomputed = 0;
     }
 }
 

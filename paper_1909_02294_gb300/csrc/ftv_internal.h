@@ -54,6 +54,7 @@ struct RefJob {
     const int32_t* n_listed;   // device length of `list` (nullptr with list == nullptr)
     int32_t* woffs;            // scratch [S + 1]: prefix of listed segment sizes (written by plan)
     const float* H;            // [N][L][9]
+    const double* H64;         // [N][L][9] unrounded table (FP64-precision units; else nullptr)
     const NbrView* nbrs;       // [N]
     int32_t* cost;             // [S][L]
     int32_t W, S, N, L, LB, nLB, penalty, fmt;
@@ -69,6 +70,7 @@ struct Plan {
     int32_t total_items;
     int32_t n_jobs;            // units in the launch
     unsigned long long culled; // evaluations decided without sampling: the tile is out of that view
+    unsigned long long recomputed;  // FP64-precision evaluations computed in double precision
     int32_t counter[kMaxChunks];  // next item of each chunk, relative to the chunk's first (persistent CTAs)
 };
 
@@ -78,6 +80,7 @@ struct RefState {
     int32_t n_nbrs;
     std::vector<int32_t> nbrs;
     float* d_H = nullptr;      // [N][L][9]
+    double* d_H64 = nullptr;   // [N][L][9] unrounded table (FP64-precision contexts only)
     NbrView* d_nbrs = nullptr; // [N]
     int32_t* d_offs = nullptr;   // [max_segments + 1]
     int32_t* d_cursor = nullptr; // [max_segments]
@@ -87,6 +90,7 @@ struct RefState {
     int2* d_centre = nullptr;    // [max_segments] segment centres (centre table)
     const int32_t** d_nbr_labels = nullptr;  // [N] neighbour label maps (centre table)
     std::vector<float> h_H;      // host copy of the table
+    std::vector<double> h_H64;   // the table before its rounding to FP32
 };
 
 // Resident per-stream state of one reference view (ftv_stream_init).
@@ -122,6 +126,7 @@ struct ftv_ctx {
     int cost_blocks_per_sm = 0;
     int32_t n_views = 0, n_refs = 0, L = 0, plane_mode = 0, centre = 0;
     int32_t sample_bytes = 1, bit_depth = 8, penalty = 0, combine = 0, max_segments = 0, fmt = 0;
+    int32_t precision = 0;       // FTV_PRECISION_*
     bool fast_rcp = false;
     bool penalty_floor = false;  // penalty >= 3 (2^bit_depth - 1)
     int kind = 0;                // entry classification for the cost kernel (kKind*)
@@ -177,8 +182,9 @@ int cost_blocks_per_sm(int fmt, int combine, bool fast_rcp);
 // pf: the penalty is at least the largest possible sample cost (lets the min combination skip
 // out-of-view samples; see accumulate() in ftv_cost.cu).
 // kind: kKindProjective when no homography entry of the launch is affine (h6 = h7 = 0), else kKindMixed;
-// the projective instantiation of the cost kernel has the general path alone.
-enum : int { kKindMixed = 0, kKindProjective = 1 };
+// the projective instantiation of the cost kernel has the general path alone. kKindPrecise: the units
+// take their sample positions from the FP64 projection (FTV_PRECISION_FP64; every unit has H64).
+enum : int { kKindMixed = 0, kKindProjective = 1, kKindPrecise = 2 };
 // chunk, chunks: this launch takes items [total * chunk / chunks, total * (chunk + 1) / chunks) of the plan
 // (chunks <= kMaxChunks; a whole launch is chunk 0 of 1).
 cudaError_t launch_cost(const RefJob* jobs, const Plan* plan, int fmt, int combine, bool fast_rcp, bool pf, int kind,

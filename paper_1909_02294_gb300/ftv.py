@@ -25,6 +25,7 @@ FTV_PLANES_REF, FTV_PLANES_CENTRE = 0, 1
 FTV_COMBINE_MIN, FTV_COMBINE_SUM = 0, 1
 FTV_TM_Y_ONLY, FTV_TM_ALL_YUV = 0, 1
 FTV_MASK_CHANGED, FTV_MASK_REUSE_P, FTV_MASK_REUSE_I = 0, 1, 2
+FTV_PRECISION_FP32, FTV_PRECISION_FP64 = 0, 1
 
 
 class FtvError(RuntimeError):
@@ -46,7 +47,7 @@ class ftv_config(ctypes.Structure):
                 ("plane_mode", ctypes.c_int32), ("centre_view", ctypes.c_int32),
                 ("sample_bytes", ctypes.c_int32), ("bit_depth", ctypes.c_int32),
                 ("oob_penalty", ctypes.c_int32), ("combine", ctypes.c_int32),
-                ("max_segments", ctypes.c_int32)]
+                ("max_segments", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
 class ftv_segmenter_config(ctypes.Structure):
@@ -65,6 +66,7 @@ def _load() -> ctypes.CDLL:
         "ftv_depth_init": [ctypes.POINTER(ftv_config), ctypes.POINTER(vp)],
         "ftv_depth_destroy": [vp],
         "ftv_get_homographies": [vp, i32, vp],
+        "ftv_get_homographies_f64": [vp, i32, vp],
         "ftv_compute_homographies": [ctypes.POINTER(ftv_config), i32, vp],
         "ftv_get_neighbours": [vp, i32, vp, vp],
         "ftv_get_label_depths": [vp, vp],
@@ -74,6 +76,7 @@ def _load() -> ctypes.CDLL:
         "ftv_wta_depth": [vp, i32, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp],
         "ftv_check": [vp, vp],
         "ftv_culled_evaluations": [vp, vp, vp],
+        "ftv_fp64_recomputed": [vp, vp, vp],
         "ftv_set_profiling": [vp, i32],
         "ftv_stream_init": [vp, vp, vp, i32, i32, i32, vp],
         "ftv_stream_footprint": [vp, vp, vp],
@@ -119,7 +122,8 @@ def _load() -> ctypes.CDLL:
 
 lib = _load()
 
-EXPORTED = ["ftv_depth_init", "ftv_depth_destroy", "ftv_compute_homographies", "ftv_get_homographies", "ftv_get_neighbours",
+EXPORTED = ["ftv_depth_init", "ftv_depth_destroy", "ftv_compute_homographies", "ftv_get_homographies",
+            "ftv_get_homographies_f64", "ftv_fp64_recomputed", "ftv_get_neighbours",
             "ftv_get_label_depths", "ftv_segment_index", "ftv_cost_volume", "ftv_temporal_mask",
             "ftv_wta_depth", "ftv_check", "ftv_culled_evaluations", "ftv_launch_count", "ftv_status_str", "ftv_set_profiling",
             "ftv_last_kernel_ms", "ftv_temporal_mask_static", "ftv_stream_init", "ftv_stream_footprint",
@@ -187,7 +191,7 @@ class Context:
 
 
 def _config(cams, ref_views, n_labels, z_near, z_far, nbr_lists, plane_mode, centre_view, sample_bytes,
-            bit_depth, oob_penalty, combine, max_segments):
+            bit_depth, oob_penalty, combine, max_segments, precision=FTV_PRECISION_FP32):
     cam_arr = (ftv_camera * len(cams))(*[camera_struct(c) for c in cams])
     refs = _arr(ctypes.c_int32, ref_views)
     cfg = ftv_config()
@@ -207,16 +211,16 @@ def _config(cams, ref_views, n_labels, z_near, z_far, nbr_lists, plane_mode, cen
     cfg.n_labels, cfg.z_near, cfg.z_far = n_labels, z_near, z_far
     cfg.plane_mode, cfg.centre_view = plane_mode, centre_view
     cfg.sample_bytes, cfg.bit_depth, cfg.oob_penalty = sample_bytes, bit_depth, oob_penalty
-    cfg.combine, cfg.max_segments = combine, max_segments
+    cfg.combine, cfg.max_segments, cfg.precision = combine, max_segments, precision
     return cfg, keep
 
 
 def ftv_depth_init(cams, ref_views, n_labels: int, z_near: float, z_far: float, *, nbr_lists=None,
                    plane_mode: int = FTV_PLANES_REF, centre_view: int = 0, sample_bytes: int = 1,
                    bit_depth: int = 8, oob_penalty: int = -1, combine: int = FTV_COMBINE_MIN,
-                   max_segments: int = 1) -> Context:
+                   max_segments: int = 1, precision: int = FTV_PRECISION_FP32) -> Context:
     cfg, keep = _config(cams, ref_views, n_labels, z_near, z_far, nbr_lists, plane_mode, centre_view, sample_bytes,
-                        bit_depth, oob_penalty, combine, max_segments)
+                        bit_depth, oob_penalty, combine, max_segments, precision)
     h = ctypes.c_void_p()
     _ok(lib.ftv_depth_init(ctypes.byref(cfg), ctypes.byref(h)), "ftv_depth_init")
     return Context(h.value, len(ref_views), n_labels, list(ref_views))
@@ -243,6 +247,15 @@ def ftv_get_homographies(ctx: Context, ref_index: int) -> np.ndarray:
     _ok(lib.ftv_get_neighbours(ctx.handle, ref_index, ctypes.byref(n), None), "ftv_get_neighbours")
     out = np.empty((n.value, ctx.n_labels, 9), np.float32)
     _ok(lib.ftv_get_homographies(ctx.handle, ref_index, out.ctypes.data), "ftv_get_homographies")
+    return out
+
+
+def ftv_get_homographies_f64(ctx: Context, ref_index: int) -> np.ndarray:
+    """The FP64 table before its rounding (the FP64 projection's homographies)."""
+    n = ctypes.c_int32()
+    _ok(lib.ftv_get_neighbours(ctx.handle, ref_index, ctypes.byref(n), None), "ftv_get_neighbours")
+    out = np.empty((n.value, ctx.n_labels, 9), np.float64)
+    _ok(lib.ftv_get_homographies_f64(ctx.handle, ref_index, out.ctypes.data), "ftv_get_homographies_f64")
     return out
 
 
@@ -325,6 +338,14 @@ def ftv_culled_evaluations(ctx: Context, stream=None) -> int:
     a neighbour's view); waits for the stream."""
     n = ctypes.c_int64()
     _ok(lib.ftv_culled_evaluations(ctx.handle, _stream(stream), ctypes.byref(n)), "ftv_culled_evaluations")
+    return int(n.value)
+
+
+def ftv_fp64_recomputed(ctx: Context, stream=None) -> int:
+    """Evaluations of the most recent ftv_cost_volume call of an FP64-precision context that were computed
+    in double precision (near a rounding boundary, or no error bound); waits for the stream."""
+    n = ctypes.c_int64()
+    _ok(lib.ftv_fp64_recomputed(ctx.handle, _stream(stream), ctypes.byref(n)), "ftv_fp64_recomputed")
     return int(n.value)
 
 

@@ -13,7 +13,7 @@ def dev(a, device="cuda"):
 
 class Run:
     def __init__(self, wl, *, combine=None, plane_mode=0, centre=0, nbr_lists=None, max_segments=None,
-                 penalty=None):
+                 penalty=None, precision=ftv.FTV_PRECISION_FP32):
         self.wl = wl
         self.combine = combine or wl.combine
         self.S = [wl.labels(r)[1] for r in wl.ref_views]
@@ -23,7 +23,7 @@ class Run:
             centre_view=centre, sample_bytes=wl.sample_bytes, bit_depth=wl.bit_depth,
             oob_penalty=wl.oob_penalty if penalty is None else penalty,
             combine=ftv.FTV_COMBINE_MIN if self.combine == "min" else ftv.FTV_COMBINE_SUM,
-            max_segments=max_segments or max(self.S))
+            max_segments=max_segments or max(self.S), precision=precision)
         self.labels = [dev(wl.labels(r)[0]) for r in wl.ref_views]
 
     def planes(self, frame=0):
