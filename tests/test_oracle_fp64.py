@@ -185,3 +185,21 @@ def test_fp64_behind_the_camera_is_out_of_view():
     assert np.array_equal(got, np.repeat((n * 765)[:, None], 3, 1))
     want, _, n_in = _brute_volume(cams, views, 1, [3], H64, 3, lab, S, 765)
     assert n_in == 0 and np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("name,lo,hi", [("tiny", 0.0, 0.0), ("serving_small", 0.0, 0.0), ("hd8", 1e-3, 4e-3),
+                                        ("uhd15", 5e-5, 2e-4)])
+def test_fp32_contract_mismatch_fraction_per_workload(name, lo, hi):
+    """The reported figure: the fraction of evaluations whose FP32-contract sample (or in/out decision)
+    differs from the FP64 projection, on 20,000 seeded pixels of the first reference x every label x every
+    neighbour. The 1920x1080 rectified rig concentrates it in the few (label, view) pairs whose disparity
+    lies within FP32 resolution of a half-integer; the 3840x2160 convergent rig spreads it thinly. The
+    FP64 projection mode has none by construction. Printed with -s."""
+    from synth.configs import make_workload
+    wl = make_workload(name)
+    r = wl.ref_views[0]
+    c = wl.cams[r]
+    pix = np.random.default_rng(7).integers(0, c.width * c.height, 20000).astype(np.int32)
+    bad, tot = oracle.fp64_mismatch(wl.cams, r, wl.neighbours(r), wl.n_labels, wl.z_near, wl.z_far, pix=pix)
+    print(f"{name}: FP32-contract vs FP64-projection sample mismatch {bad} of {tot} = {bad / tot:.3e}")
+    assert lo <= bad / tot <= hi
