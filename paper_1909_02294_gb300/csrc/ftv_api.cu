@@ -199,7 +199,7 @@ ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out) {
         for (const auto& r : c->refs)
             for (size_t e = 0; e < r.h_H.size(); e += 9) any_affine = any_affine || (r.h_H[e + 6] == 0.0f && r.h_H[e + 7] == 0.0f);
         c->kind = any_affine ? kKindMixed : kKindProjective;
-        if (c->precision == FTV_PRECISION_FP64) c->kind = kKindPrecise;
+        if (c->precision == FTV_PRECISION_FP64) c->kind = any_affine ? kKindPreciseMixed : kKindPrecise;
     }
 
     // device scratch (all host-side validation is done by now)

@@ -594,7 +594,9 @@ ftv_status ftv_batch_prepare(ftv_batch* b, const ftv_frame_job* jobs, int32_t n_
         fmt = J.ctx->fmt;
         combine = J.ctx->combine;
         pf_all = pf_all && J.ctx->penalty_floor;
-        kind = j == 0 ? J.ctx->kind : (kind == J.ctx->kind ? kind : kKindMixed);
+        // contexts of one batch share a precision; differing entry classes take the mixed instantiation
+        if (j == 0) kind = J.ctx->kind;
+        else if (kind != J.ctx->kind) kind = precise_kind(kind) ? kKindPreciseMixed : kKindMixed;
         n_views += J.ctx->n_views;
         n_units += J.ctx->n_refs;
         for (int v = 0; v < J.ctx->n_views; ++v)

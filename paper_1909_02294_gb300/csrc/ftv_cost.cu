@@ -251,7 +251,8 @@ __device__ __forceinline__ bool box_out_of_view(const float* h, float x0, float 
 //   (3 * 2^-53 (A_X + |u| A_W) / W + 2 * 2^-53 (|u| + 1)),
 // doubled. Where t = u' + 0.5 computed in FP32 lies farther than delta from every integer, floor(t) + U0
 // is the FP64 projection's column (both floors see the same side of the same integer); otherwise the
-// evaluation is redone in FP64. Returns kGeneral (that test applies), kOut (the FP64 projection puts no
+// evaluation is redone in FP64. Returns kGeneral (that test applies), kRect (the same, rectified: below),
+// kOut (the FP64 projection puts no
 // pixel of the box in view: behind the camera, or wholly beyond one image edge by more than the bound) or
 // kSlow (no bound: W may come near zero in the box, or delta is large; every evaluation in FP64).
 __device__ uint32_t stage_precise(const double* __restrict__ hg, int x0, int y0, int rx, int ry, int wv, int hv,
@@ -308,6 +309,13 @@ __device__ uint32_t stage_precise(const double* __restrict__ hg, int x0, int y0,
     // near a tie when |frac(t) - 0.5| >= thr; 2^-22 more covers the FP32 rounding of that test itself
     P.thr_u = __double2float_rd(0.5 - du - 0x1p-22);
     P.thr_v = __double2float_rd(0.5 - dv - 0x1p-22);
+    // Rectified local frame (linear rigs with parallel axes): with a0 = b1 = c2 = 1 and a1 = b0 = c0 = c1 = 0
+    // the general evaluation computes exactly t_u = (x' + a2) + 0.5 (both rounded) and W = r = 1, so the
+    // bound above holds for that shorter sequence; and when |b2| + delta_v < 0.5 every pixel's row decision
+    // is floor(y' + b2 + 0.5 +- delta_v) = y', i.e. the row is y' + V0 with no test.
+    if (h[0] == 1.0f && h[1] == 0.0f && h[3] == 0.0f && h[4] == 1.0f && h[6] == 0.0f && h[7] == 0.0f &&
+        h[8] == 1.0f && fabs((double)h[5]) + dv < 0.49)
+        return kRect;
     return kGeneral;
 }
 
@@ -364,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
     __shared__ int sWoffs[kLocCache + 1];
     __shared__ int s_item, s_k0, s_k1, s_culled;
     __shared__ int s_box[4];  // the tile's pixel box: x min, x max, y min, y max
-    __shared__ PEntry sP[KIND == kKindPrecise ? kHEntries : 1];
+    __shared__ PEntry sP[precise_kind(KIND) ? kHEntries : 1];
     unsigned n_recomputed = 0;  // FP64-precision evaluations computed in double precision by this thread
 
     const int tid = threadIdx.x, lane = tid & 31;
@@ -403,7 +411,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
         const float* __restrict__ Hg = Jp->H;
         const NbrView* __restrict__ nbrs = Jp->nbrs;
         const int nh = N * LBa;
-        for (int e = tid; e < (KIND == kKindPrecise ? 0 : nh); e += kThreads) {
+        for (int e = tid; e < (precise_kind(KIND) ? 0 : nh); e += kThreads) {
             const int n = e / LBa, l = e - n * LBa;
             const float* src = &Hg[((int64_t)n * L + d0 + l) * 9];
             HEntry& E = sH[e];
@@ -478,7 +486,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
         // FP64-precision units stage their entries here, once the box is known (stage_precise), and move the
         // pixels into the box's local frame.
         int fx0 = 0, fy0 = 0;  // local-frame origin (kKindPrecise)
-        if constexpr (KIND == kKindProjective || KIND == kKindPrecise) {  // uniform way through the barriers
+        if constexpr (KIND == kKindProjective || precise_kind(KIND)) {  // uniform way through the barriers
             int bx0 = INT_MAX, bx1 = INT_MIN, by0 = INT_MAX, by1 = INT_MIN;
 #pragma unroll
             for (int j = 0; j < kPPT; ++j)
@@ -554,7 +562,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                 const int pitch = (int)(pm & kPitchMask);
                 // a projective-only launch (no entry with h6 = h7 = 0) keeps the general path alone; a
                 // rectified-only instantiation measured slower than this mixed loop, so there is none
-                if (KIND == kKindPrecise) {
+                if (precise_kind(KIND)) {
                     const double* h64 = &Jp->H64[((int64_t)n * L + d0 + l) * 9];
                     const int wv = __float_as_int(hc.y), hv = __float_as_int(hc.z);
                     if (mode == kOut) {
@@ -569,6 +577,24 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                             int ui = 0, vi = 0;
                             const bool ok = project_fp64(h64, (int)px[j] + fx0, iy[j], wv, hv, &ui, &vi);
                             n_recomputed += key[j] != kSentinel;
+                            accumulate<FMT, COMB, PF>(m[j], ok, tex, vi * pitch + ui, ra[j], rb[j], rc[j], penalty);
+                        }
+                    } else if (KIND == kKindPreciseMixed && mode == kRect) {
+                        const float a2 = e4[0].z;
+                        const float4 pe = reinterpret_cast<const float4*>(sP)[n * LBa + l];
+                        const int u0 = __float_as_int(pe.x), dv0 = __float_as_int(pe.y) - fy0;
+#pragma unroll
+                        for (int j = 0; j < kPPT; ++j) {
+                            const float tu = __fadd_rn(__fadd_rn(px[j], a2), 0.5f);
+                            const float fu = floorf(tu);
+                            int ui = __float2int_rz(fu) + u0, vi = iy[j] + dv0;
+                            bool ok;
+                            if (fabsf(__fsub_rn(__fsub_rn(tu, fu), 0.5f)) >= pe.z) {
+                                ok = project_fp64(h64, (int)px[j] + fx0, iy[j], wv, hv, &ui, &vi);
+                                n_recomputed += key[j] != kSentinel;
+                            } else {
+                                ok = ((unsigned)ui < (unsigned)wv) & ((unsigned)vi < (unsigned)hv);
+                            }
                             accumulate<FMT, COMB, PF>(m[j], ok, tex, vi * pitch + ui, ra[j], rb[j], rc[j], penalty);
                         }
                     } else {
@@ -693,7 +719,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
             else atomicAdd(dst, v);
         }
     }
-    if constexpr (KIND == kKindPrecise) {
+    if constexpr (precise_kind(KIND)) {
         const unsigned n = __reduce_add_sync(kFull, n_recomputed);
         if (lane == 0 && n) atomicAdd(&plan->recomputed, (unsigned long long)n);
     }
@@ -768,6 +794,8 @@ template <int FMT, int COMB, bool FAST, bool PF>
 void launch_kind(const RefJob* jobs, Plan* p, int kind, int ck, int nck, int grid, cudaStream_t s) {
     if (kind == kKindPrecise)
         cost_kernel<FMT, COMB, FAST, PF, kKindPrecise><<<grid, kThreads, 0, s>>>(jobs, p, ck, nck);
+    else if (kind == kKindPreciseMixed)
+        cost_kernel<FMT, COMB, FAST, PF, kKindPreciseMixed><<<grid, kThreads, 0, s>>>(jobs, p, ck, nck);
     else if (kind == kKindProjective)
         cost_kernel<FMT, COMB, FAST, PF, kKindProjective><<<grid, kThreads, 0, s>>>(jobs, p, ck, nck);
     else cost_kernel<FMT, COMB, FAST, PF, kKindMixed><<<grid, kThreads, 0, s>>>(jobs, p, ck, nck);

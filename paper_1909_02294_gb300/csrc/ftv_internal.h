@@ -182,9 +182,14 @@ int cost_blocks_per_sm(int fmt, int combine, bool fast_rcp);
 // pf: the penalty is at least the largest possible sample cost (lets the min combination skip
 // out-of-view samples; see accumulate() in ftv_cost.cu).
 // kind: kKindProjective when no homography entry of the launch is affine (h6 = h7 = 0), else kKindMixed;
-// the projective instantiation of the cost kernel has the general path alone. kKindPrecise: the units
-// take their sample positions from the FP64 projection (FTV_PRECISION_FP64; every unit has H64).
-enum : int { kKindMixed = 0, kKindProjective = 1, kKindPrecise = 2 };
+// the projective instantiation of the cost kernel has the general path alone. kKindPrecise and
+// kKindPreciseMixed: the units take their sample positions from the FP64 projection (FTV_PRECISION_FP64;
+// every unit has H64); the mixed one adds the rectified local-frame path, for rigs with affine entries.
+enum : int { kKindMixed = 0, kKindProjective = 1, kKindPrecise = 2, kKindPreciseMixed = 3 };
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr bool precise_kind(int kind) { return kind == kKindPrecise || kind == kKindPreciseMixed; }
 // chunk, chunks: this launch takes items [total * chunk / chunks, total * (chunk + 1) / chunks) of the plan
 // (chunks <= kMaxChunks; a whole launch is chunk 0 of 1).
 cudaError_t launch_cost(const RefJob* jobs, const Plan* plan, int fmt, int combine, bool fast_rcp, bool pf, int kind,
