@@ -415,6 +415,7 @@ ftv_status ftv_cost_volume(ftv_ctx* ctx, const void* const* d_planes, const int6
         J.nbrs = r.d_nbrs;
         J.cost = d_cost[i];
         J.W = r.W;
+        J.Href = r.H;
         J.S = S;
         J.N = r.n_nbrs;
         J.L = ctx->L;

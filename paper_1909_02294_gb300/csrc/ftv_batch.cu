@@ -680,6 +680,7 @@ ftv_status ftv_batch_prepare(ftv_batch* b, const ftv_frame_job* jobs, int32_t n_
             q.nbrs = S.d_nbrs_ring[cur];
             q.cost = S.d_cost;
             q.W = r.W;
+            q.Href = r.H;
             q.S = S.S;
             q.N = r.n_nbrs;
             q.L = c->L;

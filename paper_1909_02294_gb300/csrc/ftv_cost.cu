@@ -93,6 +93,15 @@ struct TexelOps<FMT_U16X4> {
 //   kRect     unit with h0 = 1, h1 = 0, h3 = 0, h4 = 1, |h5| < 0.25 (rectified rigs: the row is kept):
 //             X = fma(1, x, fma(0, y, h2)) is x + h2 rounded once, and Y = y + h5 rounded once lies
 //             within 0.25 + 2^-9 of the integer y < 2^15, so floor(Y + 0.5) is exactly y;
+//   kShift    rectified, and the column is x + D for every x < 2^15 with D = floor(h2 + 0.5): s = x + h2
+//             rounded is within 2^-24 (|x| + |h2|) of x + h2; when h2 + 0.5 lies more than twice that
+//             from every integer (checked at staging with |x| < 2^15, |h2| < 2^20), s + 0.5 lies more than
+//             2^-24 from every integer, where rounding s + 0.5 cannot cross one (below 1 in magnitude its
+//             rounding error is at most 2^-24; above, s + 0.5 is exact or only crosses into a binade
+//             whose lower end is the integer below it), so floor((s + 0.5) rounded) = x + D. Used when the
+//             view's pitch is the reference width and its height at least the reference height: the
+//             sample's index is then the pixel's y * W + x plus D, the row needs no test, and the column
+//             test is -D <= x < w - D, staged as floats (h[6], h[7]) with D in h[8];
 //   kOut      affine with 1/h8 not finite and positive, or no pixel of the item's tile can reach the view
 //             (box_out_of_view): every sample is out of view.
 // All of them give bit-identical results to the general sequence; they only skip work whose result
@@ -101,7 +110,7 @@ struct __align__(16) HEntry {
     float h[9];
     uint32_t w, h_, pm;
 };
-enum : uint32_t { kGeneral = 0, kAffine = 1, kUnit = 2, kOut = 3, kRect = 4, kSlow = 5 };
+enum : uint32_t { kGeneral = 0, kAffine = 1, kUnit = 2, kOut = 3, kRect = 4, kSlow = 5, kShift = 6 };
 
 // FP64-projection entries (kKindPrecise) stage local-frame coefficients in HEntry::h (stage_precise) and
 // this alongside: the integer column u0 and row v0 the frame is shifted by, and the tie-test thresholds.
@@ -426,6 +435,16 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                     mode = kRect;
                 E.h[6] = r;
                 E.h[8] = E.h[2];  // Wz is not needed any more; a rectified entry then reads one float4
+                if (mode == kRect && nbrs[n].pitch == W && nbrs[n].h >= Jp->Href) {
+                    const double h2 = (double)E.h[2];
+                    const double D = floor(h2 + 0.5), g = h2 + 0.5 - D;
+                    if (fabs(h2) < 0x1p20 && fmin(g, 1.0 - g) > 0x1p-23 * (32768.0 + fabs(h2))) {
+                        mode = kShift;
+                        E.h[6] = (float)(-D);
+                        E.h[7] = (float)((double)nbrs[n].w - D);
+                        E.h[8] = __int_as_float((int)D);
+                    }
+                }
             }
             E.w = (uint32_t)nbrs[n].w;
             E.h_ = (uint32_t)nbrs[n].h;
@@ -455,11 +474,16 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
         // this thread's pixels
         float px[kPPT], py[kPPT];
         int ra[kPPT], rb[kPPT], rc[kPPT], key[kPPT], iy[kPPT];
+        int rowx[kPPT];  // y * W + x (kShift entries of the mixed kernel)
+        // The float row: kept in registers except in the mixed kernel, which needs registers for rowx and,
+        // on the rigs it serves, rarely takes the general or affine paths that read it (exact conversion).
+        auto row_f = [&](int j) { return KIND == kKindMixed ? (float)iy[j] : py[j]; };
 #pragma unroll
         for (int j = 0; j < kPPT; ++j) {
             const int w = w0 + j * kThreads + tid;
             key[j] = kSentinel;
             iy[j] = 0;
+            rowx[j] = 0;
             px[j] = py[j] = 0.0f;
             ra[j] = rb[j] = rc[j] = 0;
             if (w < w1) {
@@ -473,6 +497,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                 px[j] = (float)x;
                 py[j] = (float)y;
                 iy[j] = y;
+                rowx[j] = y * W + x;
                 TexelOps<FMT>::unpack_ref(ref_tex, (int64_t)y * W + x, ra[j], rb[j], rc[j]);
                 key[j] = k - k0;
             }
@@ -623,6 +648,14 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                             accumulate<FMT, COMB, PF>(m[j], ok, tex, vi * pitch + ui, ra[j], rb[j], rc[j], penalty);
                         }
                     }
+                } else if (KIND == kKindMixed && mode == kShift) {
+                    const float4 hb = e4[1];  // (h4, h5, -D, w - D)
+                    const int D = __float_as_int(hc.x);
+#pragma unroll
+                    for (int j = 0; j < kPPT; ++j) {
+                        const bool ok = (px[j] >= hb.z) & (px[j] < hb.w);
+                        accumulate<FMT, COMB, false>(m[j], ok, tex, rowx[j] + D, ra[j], rb[j], rc[j], penalty);
+                    }
                 } else if (KIND == kKindMixed && mode == kRect) {
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
@@ -641,7 +674,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
                         int idx;
-                        const bool ok = pos_general<FAST_RCP>(ha, hb, hc, pitch, px[j], py[j], idx);
+                        const bool ok = pos_general<FAST_RCP>(ha, hb, hc, pitch, px[j], row_f(j), idx);
                         accumulate<FMT, COMB, PF>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty);
                     }
                 } else if (KIND == kKindMixed && mode == kUnit) {
@@ -649,7 +682,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
                         int idx;
-                        const bool ok = pos_affine<true>(ha, hb, hc, 1.0f, pitch, px[j], py[j], idx);
+                        const bool ok = pos_affine<true>(ha, hb, hc, 1.0f, pitch, px[j], row_f(j), idx);
                         accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty);
                     }
                 } else if (KIND == kKindMixed && mode == kAffine) {
@@ -657,7 +690,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
                         int idx;
-                        const bool ok = pos_affine<false>(ha, hb, hc, hb.z, pitch, px[j], py[j], idx);
+                        const bool ok = pos_affine<false>(ha, hb, hc, hb.z, pitch, px[j], row_f(j), idx);
                         accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty);
                     }
                 } else if (KIND == kKindMixed && !(COMB == FTV_COMBINE_MIN && PF)) {

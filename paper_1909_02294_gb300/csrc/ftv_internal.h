@@ -58,6 +58,7 @@ struct RefJob {
     const NbrView* nbrs;       // [N]
     int32_t* cost;             // [S][L]
     int32_t W, S, N, L, LB, nLB, penalty, fmt;
+    int32_t Href;              // reference height
     // plan outputs
     int32_t n_work;            // listed segments
     int32_t n_rec;             // listed pixels

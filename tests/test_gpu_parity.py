@@ -149,6 +149,25 @@ def test_affine_and_out_of_view_homography_modes():
     run.close()
 
 
+def test_rectified_shift_path_and_its_fallbacks():
+    """Rectified neighbours take the kernel's integer-shift path (column x + D, row kept) when the view's
+    pitch is the reference width and its height at least the reference height; a shorter view (rows
+    beyond it out of view) and a narrower one (another pitch) keep the float sequence. All must equal
+    the contract, with min and sum."""
+    wl = make_workload("tiny")
+    base = wl.cams[1]
+    for C, (w, h) in (([0.037, 0.0, 0.0], (480, 200)), ([-0.021, 0.0, 0.0], (400, 270)),
+                      ([0.013, 0.0, 0.0], (480, 300))):
+        wl.cams.append(synth.Camera(base.K.copy(), np.eye(3), -np.array(C), w, h))
+    lists = [[0, 3, 4, 5, 2]]
+    for combine in ("min", "sum"):
+        run = Run(wl, nbr_lists=lists, combine=combine)
+        costs = run.volumes()
+        assert run.check() == 0
+        _assert_equal(costs[0], _oracle_all(wl, combine=combine, nbr_lists=lists)[0], f"shift path ({combine})")
+        run.close()
+
+
 def test_projective_entries_whose_denominator_changes_sign():
     """A neighbour rotated 75 degrees about the vertical axis: Wz = 0 crosses the reference image, so
     part of every candidate plane is behind it (the kernel's general entries with the guarded
