@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kCentreThreads) centre_table_kernel(CentreArgs
                         }
                         int q[3];
                         texel(nv.texels, a.fmt, qrow + qx, q);
-                        m += abs(sref[i][0] - q[0]) + abs(sref[i][1] - q[1]) + abs(sref[i][2] - q[2]);
+                        m += (int)__sad(sref[i][0], q[0], __sad(sref[i][1], q[1], __sad(sref[i][2], q[2], 0u)));
                     }
                 }
             }
