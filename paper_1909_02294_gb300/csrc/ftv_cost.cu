@@ -36,7 +36,10 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kSentinel = INT_MAX;
-constexpr int kLocCache = kTile + 1;
+// Segments of a tile whose listed-pixel offsets are cached in shared memory (more: binary search in
+// global memory). Together with kSegAcc this keeps a CTA near 30 KB of shared memory, so that four CTAs
+// leave about half of the SM's 256 KB L1 to the neighbour-view gathers (prefer_l1).
+constexpr int kLocCache = 257;
 
 // cost(): |dY| + |dCb| + |dCr| as a chain of __sad (|x - y| + z, unsigned accumulate; exact here, as every
 // term and the sum are below 2^18), which measured 12.5 % fewer instructions per evaluation than separate
@@ -826,15 +829,36 @@ int cost_blocks_per_sm(int fmt, int combine, bool fast) {
 
 namespace {
 
+// Shared-memory carveout hint: the smallest split that still holds kMinBlocks CTAs of this kernel, so
+// that the rest of the SM's L1 caches the neighbour-view gathers. Once per instantiation and process.
+template <typename Kernel>
+bool prefer_l1(Kernel kernel) {
+    cudaFuncAttributes a{};
+    int dev = 0, smem_sm = 0;
+    if (cudaFuncGetAttributes(&a, kernel) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+        smem_sm > 0) {
+        const size_t need = (size_t)kMinBlocks * (a.sharedSizeBytes + 1024);
+        const int pct = (int)std::min<size_t>(100, (need * 100 + smem_sm - 1) / smem_sm);
+        cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    }
+    cudaGetLastError();  // a hint only
+    return true;
+}
+
+template <int FMT, int COMB, bool FAST, bool PF, int KIND>
+void launch_one(const RefJob* jobs, Plan* p, int ck, int nck, int grid, cudaStream_t s) {
+    static const bool hinted = prefer_l1(cost_kernel<FMT, COMB, FAST, PF, KIND>);
+    (void)hinted;
+    cost_kernel<FMT, COMB, FAST, PF, KIND><<<grid, kThreads, 0, s>>>(jobs, p, ck, nck);
+}
+
 template <int FMT, int COMB, bool FAST, bool PF>
 void launch_kind(const RefJob* jobs, Plan* p, int kind, int ck, int nck, int grid, cudaStream_t s) {
-    if (kind == kKindPrecise)
-        cost_kernel<FMT, COMB, FAST, PF, kKindPrecise><<<grid, kThreads, 0, s>>>(jobs, p, ck, nck);
-    else if (kind == kKindPreciseMixed)
-        cost_kernel<FMT, COMB, FAST, PF, kKindPreciseMixed><<<grid, kThreads, 0, s>>>(jobs, p, ck, nck);
-    else if (kind == kKindProjective)
-        cost_kernel<FMT, COMB, FAST, PF, kKindProjective><<<grid, kThreads, 0, s>>>(jobs, p, ck, nck);
-    else cost_kernel<FMT, COMB, FAST, PF, kKindMixed><<<grid, kThreads, 0, s>>>(jobs, p, ck, nck);
+    if (kind == kKindPrecise) launch_one<FMT, COMB, FAST, PF, kKindPrecise>(jobs, p, ck, nck, grid, s);
+    else if (kind == kKindPreciseMixed) launch_one<FMT, COMB, FAST, PF, kKindPreciseMixed>(jobs, p, ck, nck, grid, s);
+    else if (kind == kKindProjective) launch_one<FMT, COMB, FAST, PF, kKindProjective>(jobs, p, ck, nck, grid, s);
+    else launch_one<FMT, COMB, FAST, PF, kKindMixed>(jobs, p, ck, nck, grid, s);
 }
 
 template <int FMT, int COMB>

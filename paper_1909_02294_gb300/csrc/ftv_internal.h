@@ -37,7 +37,7 @@ constexpr int kMinBlocks = FTV_MINB;  // resident CTAs per SM the register budge
 constexpr int kTile = kThreads * kPPT;
 constexpr int kMaxLB = 64;          // labels per block
 constexpr int kHEntries = 512;      // shared-memory capacity for N x LB staged homographies
-constexpr int kSegAcc = 64;         // per-tile segment accumulators in shared memory
+constexpr int kSegAcc = 16;         // per-tile segment accumulators in shared memory (more: global atomics)
 
 // Geometry of a neighbour view as the cost kernel sees it.
 struct NbrView {
