@@ -177,6 +177,125 @@ __global__ void __launch_bounds__(kCentreThreads) centre_table_kernel(CentreArgs
     }
 }
 
+// Texel of a packed view with the format fixed at compile time.
+template <int FMT>
+__device__ __forceinline__ void texel_t(const void* base, int64_t i, int& p, int& q, int& r) {
+    if (FMT == FMT_U16X4) {
+        const uint2 t = __ldg(static_cast<const uint2*>(base) + i);
+        p = t.x & 0xffff;
+        q = t.x >> 16;
+        r = t.y;
+    } else {
+        const uint32_t t = __ldg(static_cast<const uint32_t*>(base) + i);
+        constexpr int sh = FMT == FMT_P10 ? 10 : 8;
+        constexpr uint32_t mk = (1u << sh) - 1u;
+        p = t & mk;
+        q = (t >> sh) & mk;
+        r = t >> (2 * sh);
+    }
+}
+
+// The paper's 3x3 window (FMT at compile time). Same results as centre_table_kernel; per segment the 27
+// reference samples move from shared memory into registers (every entry of the segment reads them), and
+// an entry whose two windows lie inside both images, the common case, sums its nine pixel pairs with no
+// per-pixel test. Entry j of a segment is (neighbour k, label d) with j = k L + d, so its homography is
+// the table's entry j.
+template <int FMT>
+__global__ void __launch_bounds__(kCentreThreads) centre_table3_kernel(CentreArgs a) {
+    __shared__ int sref[9][3];
+    __shared__ NbrView snb[FTV_MAX_NBRS];
+    __shared__ const int32_t* slab[FTV_MAX_NBRS];
+    const int tid = threadIdx.x;
+    for (int k = tid; k < a.N; k += kCentreThreads) {
+        snb[k] = a.nbrs[k];
+        slab[k] = a.labels_v[k];
+    }
+    const int nent = a.L * a.N;
+    for (int s = blockIdx.x; s < a.S; s += gridDim.x) {
+        const int2 c = a.centre[s];
+        __syncthreads();  // the previous segment's window is no longer read
+        if (tid < 9) {
+            const int rx = c.x - 1 + tid % 3, ry = c.y - 1 + tid / 3;
+            if (c.x >= 0 && rx >= 0 && rx < a.W && ry >= 0 && ry < a.H_) {
+                texel_t<FMT>(a.ref_tex, (int64_t)ry * a.W + rx, sref[tid][0], sref[tid][1], sref[tid][2]);
+            } else {
+                sref[tid][0] = -1;
+            }
+        }
+        __syncthreads();
+        int rv[9][3];
+        bool ref_in = true;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            rv[i][0] = sref[i][0];
+            rv[i][1] = sref[i][1];
+            rv[i][2] = sref[i][2];
+            ref_in = ref_in && rv[i][0] >= 0;
+        }
+        int32_t* mrow = a.m + (int64_t)s * nent;
+        int32_t* srow = a.sp + (int64_t)s * nent;
+        for (int j = tid; j < nent; j += kCentreThreads) {
+            const int k = a.L == 1 ? j : (int)__umulhi((uint32_t)j, a.l_magic), d = j - k * a.L;
+            const int64_t out = (int64_t)d * a.N + k;
+            const NbrView nv = snb[k];
+            bool in = c.x >= 0;
+            int ui = 0, vi = 0;
+            if (in && a.H64) {
+                in = project_fp64(a.H64 + (int64_t)j * 9, c.x, c.y, nv.w, nv.h, &ui, &vi);
+            } else if (in) {
+                const float* h = a.H + (int64_t)j * 9;
+                const float x = (float)c.x, y = (float)c.y;
+                const float X = __fmaf_rn(__ldg(&h[0]), x, __fmaf_rn(__ldg(&h[1]), y, __ldg(&h[2])));
+                const float Yh = __fmaf_rn(__ldg(&h[3]), x, __fmaf_rn(__ldg(&h[4]), y, __ldg(&h[5])));
+                const float Wz = __fmaf_rn(__ldg(&h[6]), x, __fmaf_rn(__ldg(&h[7]), y, __ldg(&h[8])));
+                in = Wz > 0.0f;
+                if (in) {
+                    const float r = __frcp_rn(Wz);
+                    const float fu = floorf(__fadd_rn(__fmul_rn(X, r), 0.5f));
+                    const float fv = floorf(__fadd_rn(__fmul_rn(Yh, r), 0.5f));
+                    in = fu >= 0.0f && fu <= (float)(nv.w - 1) && fv >= 0.0f && fv <= (float)(nv.h - 1);
+                    if (in) {
+                        ui = (int)fu;
+                        vi = (int)fv;
+                    }
+                }
+            }
+            int m = 0;
+            if (!in) {
+                m = 9 * a.penalty;
+            } else if (ref_in && ui >= 1 && ui + 1 < nv.w && vi >= 1 && vi + 1 < nv.h) {
+                const int64_t base = (int64_t)(vi - 1) * nv.pitch + (ui - 1);
+#pragma unroll
+                for (int wy = 0; wy < 3; ++wy)
+#pragma unroll
+                    for (int wx = 0; wx < 3; ++wx) {
+                        int p, q, r;
+                        texel_t<FMT>(nv.texels, base + (int64_t)wy * nv.pitch + wx, p, q, r);
+                        const int i = wy * 3 + wx;
+                        m += (int)__sad(rv[i][0], p, __sad(rv[i][1], q, __sad(rv[i][2], r, 0u)));
+                    }
+            } else {
+#pragma unroll
+                for (int wy = 0; wy < 3; ++wy)
+#pragma unroll
+                    for (int wx = 0; wx < 3; ++wx) {
+                        const int i = wy * 3 + wx, qx = ui - 1 + wx, qy = vi - 1 + wy;
+                        if (rv[i][0] < 0 || qx < 0 || qx >= nv.w || qy < 0 || qy >= nv.h) {
+                            m += a.penalty;
+                            continue;
+                        }
+                        int p, q, r;
+                        texel_t<FMT>(nv.texels, (int64_t)qy * nv.pitch + qx, p, q, r);
+                        m += (int)__sad(rv[i][0], p, __sad(rv[i][1], q, __sad(rv[i][2], r, 0u)));
+                    }
+            }
+            mrow[out] = m;
+            const int32_t* lv = slab[k];
+            srow[out] = (in && lv) ? lv[(int64_t)vi * nv.w + ui] : -1;
+        }
+    }
+}
+
 }  // namespace
 }  // namespace ftv
 
@@ -249,7 +368,10 @@ extern "C" ftv_status ftv_centre_table(ftv_ctx* ctx, const void* const* d_planes
         const int64_t total = (int64_t)S * ctx->L * r.n_nbrs;
         const int blocks = std::max(1, std::min(S, ctx->n_sm * 8));
         if (total > 0) {
-            if (window == 3) centre_table_kernel<3><<<blocks, kCentreThreads, 0, s>>>(a);
+            if (window == 3 && ctx->fmt == FMT_P10) centre_table3_kernel<FMT_P10><<<blocks, kCentreThreads, 0, s>>>(a);
+            else if (window == 3 && ctx->fmt == FMT_U8X4)
+                centre_table3_kernel<FMT_U8X4><<<blocks, kCentreThreads, 0, s>>>(a);
+            else if (window == 3) centre_table3_kernel<FMT_U16X4><<<blocks, kCentreThreads, 0, s>>>(a);
             else centre_table_kernel<0><<<blocks, kCentreThreads, 0, s>>>(a);
             ctx->launches++;
         }

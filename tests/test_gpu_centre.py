@@ -17,9 +17,14 @@ if not torch.cuda.is_available():
 from gpu_runs import Run, dev  # noqa: E402
 
 
-@pytest.mark.parametrize("name,window,drop", [("tiny", 3, None), ("tiny", 5, 0), ("hd8", 3, 2), ("uhd15", 3, 1)])
+@pytest.mark.parametrize("name,window,drop", [("tiny", 3, None), ("tiny", 5, 0), ("hd8", 3, 2), ("uhd15", 3, 1),
+                                              ("hd8@12", 3, None)])
 def test_centre_table_bit_exact(name, window, drop):
-    wl = make_workload(name, reduced=(name != "tiny"))
+    """8-bit (tiny), 10-bit (hd8, uhd15) and, declared as 12-bit, the wide 16-bit-field texels."""
+    wl = make_workload(name.split("@")[0], reduced=(name != "tiny"))
+    if name.endswith("@12"):
+        wl.bit_depth = 12
+        wl.ref_views = [0, 5]
     run = Run(wl)
     labels_h = [wl.labels(v)[0] for v in range(wl.n_views)]
     if drop is not None and drop not in wl.ref_views:
