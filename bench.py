@@ -666,6 +666,15 @@ def main():
         for i in range(R):
             ftv.ftv_wta_depth(ctx, i, costs[i], S[i], wins[i])
 
+    # launch shape of the cost kernel: the autotuner's choice for this job class (cached per machine), chosen
+    # before the untimed warm-up steps
+    from paper_1909_02294_gb300 import tune
+    key = tune.job_class(wl.cams, wl.ref_views, [len(wl.neighbours(r)) for r in wl.ref_views], L, wl.sample_bytes,
+                         wl.bit_depth, ftv.FTV_COMBINE_MIN, ftv.FTV_PRECISION_FP64 if fp64 else ftv.FTV_PRECISION_FP32,
+                         torch.cuda.get_device_name(dev))
+    shape_rec = tune.apply_or_tune(ctx, key, planes, labels, S, costs, reps=2)
+    shape_now = ftv.ftv_get_launch_shape(ctx)
+
     for _ in range(args.warmup):
         step()
     st = ftv.ftv_check(ctx)
@@ -746,6 +755,9 @@ def main():
                        "cost_kernel_ms": kms, "evaluations_per_step": evals,
                        "culled_evaluations_per_step": culled, "culled_fraction": culled / evals,
                        "precision": "FP64 projection" if fp64 else "FP32 contract",
+                       "launch_shape": {"label_block": shape_now["label_block"],
+                                        "ctas_per_sm": shape_now["ctas_per_sm"], "chosen_by": shape_rec["source"],
+                                        "autotune_grid_ms": shape_rec.get("grid_ms")},
                        **({"fp64_recomputed_per_step": recomputed, "fp64_recomputed_fraction": recomputed / evals}
                           if fp64 else {})},
             "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Tops/s",

@@ -499,6 +499,37 @@ FTV_API ftv_status ftv_set_profiling(ftv_ctx* ctx, int32_t enable);
  * stop event. FTV_ERR_STATE if no timed launch happened. */
 FTV_API ftv_status ftv_last_kernel_ms(ftv_ctx* ctx, float* ms);
 
+/*
+ * Launch shape of the context's cost kernel (no paper counterpart: the GPU's work decomposition). A work
+ * item is one tile of the kernel's compile-time pixel count times one block of consecutive labels;
+ * label_block caps the labels per block (the labels are split into equal blocks of at most that many,
+ * 1 <= label_block <= the stage's limit for the context's neighbour count), and ctas_per_sm sets the
+ * persistent grid (1 up to the occupancy limit; 0 = the occupancy limit). Every shape gives the same
+ * volume. Set between calls, not while a call of the context is being issued. The batch path
+ * (ftv_batch_*) uses a context's label block and its own occupancy-sized grid.
+ */
+FTV_API ftv_status ftv_set_launch_shape(ftv_ctx* ctx, int32_t label_block, int32_t ctas_per_sm);
+
+/* The effective shape (the label block in use, CTAs per SM in use) and the limits for this context. Any
+ * output pointer may be NULL. */
+FTV_API ftv_status ftv_get_launch_shape(const ftv_ctx* ctx, int32_t* label_block, int32_t* ctas_per_sm,
+                                        int32_t* max_label_block, int32_t* max_ctas_per_sm);
+
+/*
+ * Autotuner: for every candidate shape (label_blocks[i], ctas[j]) runs ftv_cost_volume on the given
+ * inputs `reps` times, times the cost kernel with the context's events (ftv_set_profiling), and keeps the
+ * fastest shape on the context (best_* may be NULL). ms_out (host, may be NULL) receives the minimum
+ * kernel milliseconds per candidate, [n_label_blocks][n_ctas]. The first run indexes d_labels (NULL:
+ * the cached index); d_cost receives the volume (identical for every shape). Synchronous (waits for each
+ * timed launch). Errors: FTV_ERR_INVALID_ARG for a candidate outside the limits of
+ * ftv_get_launch_shape; any error of ftv_cost_volume, after which the previous shape is restored.
+ */
+FTV_API ftv_status ftv_autotune(ftv_ctx* ctx, const void* const* d_planes, const int64_t* pitch_bytes,
+                                const int32_t* const* d_labels, const int32_t* n_segments, int32_t* const* d_cost,
+                                const int32_t* label_blocks, int32_t n_label_blocks, const int32_t* ctas,
+                                int32_t n_ctas, int32_t reps, ftv_stream stream, float* ms_out,
+                                int32_t* best_label_block, int32_t* best_ctas_per_sm);
+
 /* Kernel launches this context has enqueued since creation (for accounting). */
 FTV_API int64_t ftv_launch_count(const ftv_ctx* ctx);
 

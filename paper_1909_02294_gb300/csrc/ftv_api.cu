@@ -164,6 +164,7 @@ ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out) {
     // label blocking: N x LB x 9 homography floats must fit the kernel's shared-memory stage
     int lb_max = std::min(kMaxLB, kHEntries / std::max(1, max_n));
     lb_max = std::max(1, std::min(lb_max, c->L));
+    c->lb_max = lb_max;
     c->nLB = (c->L + lb_max - 1) / lb_max;
     c->LB = (c->L + c->nLB - 1) / c->nLB;
 
@@ -430,8 +431,9 @@ ftv_status ftv_cost_volume(ftv_ctx* ctx, const void* const* d_planes, const int6
     }
     if (e == cudaSuccess && ctx->profiling) e = cudaEventRecord(ctx->ev_start, s);
     if (e == cudaSuccess) {
+        const int per_sm = ctx->ctas_per_sm > 0 ? ctx->ctas_per_sm : ctx->cost_blocks_per_sm;
         e = launch_cost(ctx->d_jobs, ctx->d_plan, ctx->fmt, ctx->combine, ctx->fast_rcp, ctx->penalty_floor, ctx->kind,
-                        0, 1, ctx->n_sm * ctx->cost_blocks_per_sm, s);
+                        0, 1, ctx->n_sm * per_sm, s);
         ctx->launches++;
     }
     if (e == cudaSuccess && ctx->profiling) {
@@ -538,6 +540,72 @@ ftv_status ftv_set_profiling(ftv_ctx* ctx, int32_t enable) {
     }
     ctx->profiling = enable != 0;
     return FTV_OK;
+}
+
+ftv_status ftv_set_launch_shape(ftv_ctx* ctx, int32_t label_block, int32_t ctas_per_sm) {
+    if (!ctx || label_block < 1 || label_block > ctx->lb_max) return FTV_ERR_INVALID_ARG;
+    if (ctas_per_sm < 0 || ctas_per_sm > ctx->cost_blocks_per_sm) return FTV_ERR_INVALID_ARG;
+    ctx->nLB = (ctx->L + label_block - 1) / label_block;
+    ctx->LB = (ctx->L + ctx->nLB - 1) / ctx->nLB;  // equal blocks of at most label_block labels
+    ctx->ctas_per_sm = ctas_per_sm;
+    return FTV_OK;
+}
+
+ftv_status ftv_get_launch_shape(const ftv_ctx* ctx, int32_t* label_block, int32_t* ctas_per_sm,
+                                int32_t* max_label_block, int32_t* max_ctas_per_sm) {
+    if (!ctx) return FTV_ERR_INVALID_ARG;
+    if (label_block) *label_block = ctx->LB;
+    if (ctas_per_sm) *ctas_per_sm = ctx->ctas_per_sm > 0 ? ctx->ctas_per_sm : ctx->cost_blocks_per_sm;
+    if (max_label_block) *max_label_block = ctx->lb_max;
+    if (max_ctas_per_sm) *max_ctas_per_sm = ctx->cost_blocks_per_sm;
+    return FTV_OK;
+}
+
+ftv_status ftv_autotune(ftv_ctx* ctx, const void* const* d_planes, const int64_t* pitch_bytes,
+                        const int32_t* const* d_labels, const int32_t* n_segments, int32_t* const* d_cost,
+                        const int32_t* label_blocks, int32_t n_label_blocks, const int32_t* ctas, int32_t n_ctas,
+                        int32_t reps, ftv_stream stream, float* ms_out, int32_t* best_label_block,
+                        int32_t* best_ctas_per_sm) {
+    if (!ctx || !label_blocks || !ctas || n_label_blocks < 1 || n_ctas < 1 || reps < 1 || !d_cost)
+        return FTV_ERR_INVALID_ARG;
+    for (int i = 0; i < n_label_blocks; ++i)
+        if (label_blocks[i] < 1 || label_blocks[i] > ctx->lb_max) return FTV_ERR_INVALID_ARG;
+    for (int j = 0; j < n_ctas; ++j)
+        if (ctas[j] < 0 || ctas[j] > ctx->cost_blocks_per_sm) return FTV_ERR_INVALID_ARG;
+    const int32_t keep_lb = ctx->LB, keep_ctas = ctx->ctas_per_sm;
+    const bool keep_profiling = ctx->profiling;
+    ftv_status st = ftv_set_profiling(ctx, 1);
+    float best = 0.0f;
+    int bi = -1, bj = -1;
+    for (int i = 0; i < n_label_blocks && st == FTV_OK; ++i)
+        for (int j = 0; j < n_ctas && st == FTV_OK; ++j) {
+            st = ftv_set_launch_shape(ctx, label_blocks[i], ctas[j]);
+            float t_min = 0.0f;
+            for (int r = 0; r < reps && st == FTV_OK; ++r) {
+                // the first call indexes the label maps; later ones reuse the cached index
+                st = ftv_cost_volume(ctx, d_planes, pitch_bytes, (i == 0 && j == 0 && r == 0) ? d_labels : nullptr,
+                                     n_segments, nullptr, nullptr, d_cost, stream);
+                float ms = 0.0f;
+                if (st == FTV_OK) st = ftv_last_kernel_ms(ctx, &ms);
+                if (st == FTV_OK && (r == 0 || ms < t_min)) t_min = ms;
+            }
+            if (st != FTV_OK) break;
+            if (ms_out) ms_out[i * n_ctas + j] = t_min;
+            if (bi < 0 || t_min < best) {
+                best = t_min;
+                bi = i;
+                bj = j;
+            }
+        }
+    ctx->profiling = keep_profiling;
+    if (st != FTV_OK) {
+        ftv_set_launch_shape(ctx, keep_lb, keep_ctas);
+        return st;
+    }
+    st = ftv_set_launch_shape(ctx, label_blocks[bi], ctas[bj]);
+    if (best_label_block) *best_label_block = label_blocks[bi];
+    if (best_ctas_per_sm) *best_ctas_per_sm = ctas[bj];
+    return st;
 }
 
 ftv_status ftv_last_kernel_ms(ftv_ctx* ctx, float* ms) {

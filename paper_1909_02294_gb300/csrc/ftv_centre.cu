@@ -87,9 +87,8 @@ constexpr int kMaxWindow = 15;
 // One CTA per segment (grid-stride): the segment's reference window is unpacked once into shared memory
 // (-1 marks a pixel outside the reference image), then the CTA's threads take the segment's (label,
 // neighbour) entries, label fastest: a warp then works on consecutive labels of one neighbour, whose
-// windows lie a few pixels apart in that view and share its cache lines.
-// WIN: the window side at compile time (3, the paper's, unrolls completely), or 0 for a.window at run time.
-template <int WIN>
+// windows lie a few pixels apart in that view and share its cache lines. Any odd window up to 15; the
+// paper's 3x3 takes centre_table3_kernel.
 __global__ void __launch_bounds__(kCentreThreads) centre_table_kernel(CentreArgs a) {
     __shared__ int sref[kMaxWindow * kMaxWindow][3];
     __shared__ NbrView snb[FTV_MAX_NBRS];
@@ -99,7 +98,7 @@ __global__ void __launch_bounds__(kCentreThreads) centre_table_kernel(CentreArgs
         snb[k] = a.nbrs[k];
         slab[k] = a.labels_v[k];
     }
-    const int win = WIN > 0 ? WIN : a.window;
+    const int win = a.window;
     const int half = win / 2, ww = win * win, nent = a.L * a.N;
     for (int s = blockIdx.x; s < a.S; s += gridDim.x) {
         const int2 c = a.centre[s];
@@ -151,14 +150,10 @@ __global__ void __launch_bounds__(kCentreThreads) centre_table_kernel(CentreArgs
                 m = ww * a.penalty;
             } else {
                 const bool inside = ui >= half && ui + half < nv.w && vi >= half && vi + half < nv.h;
-#pragma unroll
-                for (int wy = 0; wy < (WIN > 0 ? WIN : kMaxWindow); ++wy) {
-                    if (WIN == 0 && wy >= win) break;
+                for (int wy = 0; wy < win; ++wy) {
                     const int qy = vi - half + wy;
                     const int64_t qrow = (int64_t)qy * nv.pitch;
-#pragma unroll
-                    for (int wx = 0; wx < (WIN > 0 ? WIN : kMaxWindow); ++wx) {
-                        if (WIN == 0 && wx >= win) break;
+                    for (int wx = 0; wx < win; ++wx) {
                         const int i = wy * win + wx, qx = ui - half + wx;
                         if (sref[i][0] < 0 || (!inside && (qx < 0 || qx >= nv.w || qy < 0 || qy >= nv.h))) {
                             m += a.penalty;
@@ -374,7 +369,7 @@ extern "C" ftv_status ftv_centre_table(ftv_ctx* ctx, const void* const* d_planes
             else if (window == 3 && ctx->fmt == FMT_U8X4)
                 centre_table3_kernel<FMT_U8X4><<<blocks, kCentreThreads, 0, s>>>(a);
             else if (window == 3) centre_table3_kernel<FMT_U16X4><<<blocks, kCentreThreads, 0, s>>>(a);
-            else centre_table_kernel<0><<<blocks, kCentreThreads, 0, s>>>(a);
+            else centre_table_kernel<<<blocks, kCentreThreads, 0, s>>>(a);
             ctx->launches++;
         }
         e = cudaGetLastError();

@@ -132,6 +132,8 @@ struct ftv_ctx {
     bool penalty_floor = false;  // penalty >= 3 (2^bit_depth - 1)
     int kind = 0;                // entry classification for the cost kernel (kKind*)
     int32_t LB = 0, nLB = 0;
+    int32_t lb_max = 0;          // largest label block the kernel's stage holds for this context's neighbours
+    int32_t ctas_per_sm = 0;     // cost-kernel CTAs per SM (0: the occupancy limit, cost_blocks_per_sm)
     double z_near = 0, z_far = 0;
     std::vector<ftv_camera> cams;
     std::vector<ftv::RefState> refs;

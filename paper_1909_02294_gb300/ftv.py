@@ -77,6 +77,9 @@ def _load() -> ctypes.CDLL:
         "ftv_check": [vp, vp],
         "ftv_culled_evaluations": [vp, vp, vp],
         "ftv_fp64_recomputed": [vp, vp, vp],
+        "ftv_set_launch_shape": [vp, i32, i32],
+        "ftv_get_launch_shape": [vp, vp, vp, vp, vp],
+        "ftv_autotune": [vp, vp, vp, vp, vp, vp, vp, i32, vp, i32, i32, vp, vp, vp, vp],
         "ftv_set_profiling": [vp, i32],
         "ftv_stream_init": [vp, vp, vp, i32, i32, i32, vp],
         "ftv_stream_footprint": [vp, vp, vp],
@@ -123,7 +126,8 @@ def _load() -> ctypes.CDLL:
 lib = _load()
 
 EXPORTED = ["ftv_depth_init", "ftv_depth_destroy", "ftv_compute_homographies", "ftv_get_homographies",
-            "ftv_get_homographies_f64", "ftv_fp64_recomputed", "ftv_get_neighbours",
+            "ftv_get_homographies_f64", "ftv_fp64_recomputed", "ftv_set_launch_shape", "ftv_get_launch_shape",
+            "ftv_autotune", "ftv_get_neighbours",
             "ftv_get_label_depths", "ftv_segment_index", "ftv_cost_volume", "ftv_temporal_mask",
             "ftv_wta_depth", "ftv_check", "ftv_culled_evaluations", "ftv_launch_count", "ftv_status_str", "ftv_set_profiling",
             "ftv_last_kernel_ms", "ftv_temporal_mask_static", "ftv_stream_init", "ftv_stream_footprint",
@@ -300,6 +304,38 @@ def ftv_cost_volume(ctx: Context, planes, labels, n_segments, costs, seg_lists=N
     assert len(costs) == R
     _ok(lib.ftv_cost_volume(ctx.handle, p_arr, pitch_arr, lab_arr, nseg, sl, nl, c_arr, _stream(stream)),
         "ftv_cost_volume")
+
+
+def ftv_set_launch_shape(ctx: Context, label_block: int, ctas_per_sm: int = 0) -> None:
+    _ok(lib.ftv_set_launch_shape(ctx.handle, int(label_block), int(ctas_per_sm)), "ftv_set_launch_shape")
+
+
+def ftv_get_launch_shape(ctx: Context) -> dict:
+    """{'label_block', 'ctas_per_sm', 'max_label_block', 'max_ctas_per_sm'} of the context's cost kernel."""
+    v = [ctypes.c_int32() for _ in range(4)]
+    _ok(lib.ftv_get_launch_shape(ctx.handle, *[ctypes.byref(x) for x in v]), "ftv_get_launch_shape")
+    return dict(zip(("label_block", "ctas_per_sm", "max_label_block", "max_ctas_per_sm"), (x.value for x in v)))
+
+
+def ftv_autotune(ctx: Context, planes, labels, n_segments, costs, label_blocks, ctas, reps: int = 3,
+                 stream=None) -> tuple[int, int, np.ndarray]:
+    """Times the cost kernel for every (label block, CTAs per SM) candidate on these inputs and keeps the
+    fastest on the context. Returns (label_block, ctas_per_sm, ms [len(label_blocks)][len(ctas)])."""
+    ptrs, pitches = [], []
+    for trip in planes:
+        for t in trip:
+            ptrs.append(_ptr(t))
+            pitches.append(int(t.stride(0)) * t.element_size())
+    lab_arr = _arr(ctypes.c_void_p, [_ptr(l) if l is not None else None for l in labels]) if labels is not None else None
+    nseg = _arr(ctypes.c_int32, n_segments) if n_segments is not None else None
+    c_arr = _arr(ctypes.c_void_p, [_ptr(c) for c in costs])
+    lbs, cts = _arr(ctypes.c_int32, list(label_blocks)), _arr(ctypes.c_int32, list(ctas))
+    ms = np.zeros((len(label_blocks), len(ctas)), np.float32)
+    b_lb, b_ct = ctypes.c_int32(), ctypes.c_int32()
+    _ok(lib.ftv_autotune(ctx.handle, _arr(ctypes.c_void_p, ptrs), _arr(ctypes.c_int64, pitches), lab_arr, nseg,
+                         c_arr, lbs, len(label_blocks), cts, len(ctas), int(reps), _stream(stream),
+                         ms.ctypes.data, ctypes.byref(b_lb), ctypes.byref(b_ct)), "ftv_autotune")
+    return b_lb.value, b_ct.value, ms
 
 
 def _trip(planes):
