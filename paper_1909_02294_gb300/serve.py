@@ -323,14 +323,40 @@ def _stats(streams, reqs) -> dict:
             "p99_ms_by_shape": {k: float(np.percentile(v, 99)) for k, v in sorted(by_shape.items())}}
 
 
-def make_streams(per_shape: int, gop: int, n_frames: int, keep_labels: bool = False, shapes=None):
+def tune_streams(streams: list[Stream], reps: int = 1) -> dict:
+    """One autotuner run per stream shape (on its first stream's first frame, or the JSON cache of
+    tune.py), the chosen launch shape applied to every stream of that shape. Returns {shape: record}."""
+    from . import tune
+    chosen = {}
+    for st in streams:
+        if st.shape not in chosen:
+            wl = st.wl
+            planes = st.upload(0, torch.cuda.current_stream())
+            labels = [torch.from_numpy(wl.labels(r)[0]).cuda() for r in wl.ref_views]
+            costs = [torch.empty((n, wl.n_labels), dtype=torch.int32, device="cuda") for n in st.S]
+            key = tune.job_class(wl.cams, wl.ref_views, [len(wl.neighbours(r)) for r in wl.ref_views], wl.n_labels,
+                                 wl.sample_bytes, wl.bit_depth, ftv.FTV_COMBINE_MIN, ftv.FTV_PRECISION_FP32,
+                                 torch.cuda.get_device_name())
+            chosen[st.shape] = tune.apply_or_tune(st.ctx, key, planes, labels, st.S, costs, reps=reps)
+        rec = chosen[st.shape]
+        ftv.ftv_set_launch_shape(st.ctx, rec["label_block"], rec["ctas_per_sm"])
+    torch.cuda.synchronize()
+    return {f"{k[0]}x{k[1]}/{k[2]}v/{k[3]}L": {"label_block": v["label_block"], "ctas_per_sm": v["ctas_per_sm"],
+                                              "source": v["source"]} for k, v in chosen.items()}
+
+
+def make_streams(per_shape: int, gop: int, n_frames: int, keep_labels: bool = False, shapes=None,
+                 tune: bool = False):
     import synth.configs as configs
     wls = configs.serving_streams(per_shape)
     if shapes is not None:
         wls = [w for w in wls if any(w.name.startswith(p) for p in shapes)]
     dev = torch.device("cuda")
-    return [Stream(w, n_frames if w.cams[0].width < 3840 else max(2, n_frames // 2), gop, dev, keep_labels)
-            for w in wls]
+    streams = [Stream(w, n_frames if w.cams[0].width < 3840 else max(2, n_frames // 2), gop, dev, keep_labels)
+               for w in wls]
+    if tune:
+        tune_streams(streams)
+    return streams
 
 
 def main(argv=None):
@@ -349,6 +375,8 @@ def main(argv=None):
     ap.add_argument("--heavy-chunks", type=int, default=HEAVY_CHUNKS,
                     help="cost-kernel launches per heavy batch (1: one persistent launch)")
     ap.add_argument("--sequence", default=None, help="run one stream of this workload (e.g. temporal) over --frames")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default launch shapes (no autotuner run or cache lookup per stream shape)")
     args = ap.parse_args(argv)
     shapes = args.shapes.split(",") if args.shapes else None
     if args.sequence:
@@ -359,7 +387,7 @@ def main(argv=None):
         return res
 
     def fresh():
-        return make_streams(args.per_shape, args.gop, args.frames, shapes=shapes)
+        return make_streams(args.per_shape, args.gop, args.frames, shapes=shapes, tune=not args.no_tune)
 
     budget = int(args.budget_gb * (1 << 30))
     n_cap = args.capacity_jobs or args.jobs
@@ -389,6 +417,7 @@ def main(argv=None):
         for s in streams:
             s.close()
     results["config"] = {"streams": len(streams), "jobs": args.jobs, "class_batches": not args.mixed_batches,
+                         "launch_shapes": "autotuned per stream shape (tune.py)" if not args.no_tune else "defaults",
                          "gop": args.gop, "slots": args.slots, "budget_gb": args.budget_gb,
                          "rate_frac": args.rate_frac, "shapes": "960x540/3v/64L, 1920x1080/8v/250L, 3840x2160/15v/400L"}
     print(json.dumps(results), flush=True)

@@ -39,3 +39,23 @@ def test_sequence_runner_reports_skipped_fraction():
     res = serve.run_sequence(make_workload("temporal", reduced=True), 4, 4)
     assert res["frames"] == 4 and res["depth_maps"] == 32
     assert 0.0 < res["changed_fraction_p_frames"] < 1.0
+
+
+def test_tuned_launch_shapes_serve_the_same_labels(tmp_path, monkeypatch):
+    """Streams whose contexts take the autotuner's launch shape (one tuning per stream shape, cached in a
+    JSON file) give the same labels as streams with the default shape."""
+    monkeypatch.setenv("FTV_TUNE_CACHE", str(tmp_path / "shapes.json"))
+    kw = dict(per_shape=2, gop=3, n_frames=2, keep_labels=True, shapes=["s540"])
+    a = serve.make_streams(**kw, tune=True)
+    chosen = serve.tune_streams(a)  # the second time from the cache
+    assert all(v["source"] == "cache" for v in chosen.values()) and len(chosen) == 1
+    b = serve.make_streams(**kw)
+    for streams in (a, b):
+        serve.run_plain(streams, serve.poisson_trace(len(streams), 8, 4000.0, 5))
+    for sa, sb in zip(a, b):
+        assert len(sa.history) == len(sb.history) > 0
+        for fa, fb in zip(sa.history, sb.history):
+            for x, y in zip(fa, fb):
+                assert np.array_equal(x, y)
+    for s in a + b:
+        s.close()
