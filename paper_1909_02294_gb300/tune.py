@@ -18,8 +18,9 @@ CACHE_ENV = "FTV_TUNE_CACHE"
 
 
 def default_cache_path() -> str:
-    """$FTV_TUNE_CACHE, else ~/.cache/ftv/tuned_shapes.json."""
-    return os.environ.get(CACHE_ENV) or os.path.join(os.path.expanduser("~"), ".cache", "ftv", "tuned_shapes.json")
+    """$FTV_TUNE_CACHE, else .tune_cache/tuned_shapes.json beside the package (a machine-local file)."""
+    here = os.path.dirname(os.path.abspath(__file__))
+    return os.environ.get(CACHE_ENV) or os.path.join(os.path.dirname(here), ".tune_cache", "tuned_shapes.json")
 
 
 def job_class(cams, ref_views, nbr_counts, n_labels: int, sample_bytes: int, bit_depth: int, combine: int,
