@@ -412,9 +412,15 @@ def _part_line(args, world, metric, unit, value, total_s, extra_config, roofline
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
 
 
+# Temporal test thresholds for 10-bit samples: the paper's 8-bit T_P = 3, T_I = 1 scaled by 4.
+TEMPORAL_T_P, TEMPORAL_T_I = 12, 4
+
+
 def run_part(args, rank, world, local):
     """--part centre: one step = the centre table of every reference (ftv_centre_table, one call).
     --part adjacency: one step = adjacency and beta of every reference (ftv_adjacency per reference).
+    --part temporal: one step = the temporal test of every reference (ftv_temporal_mask, luma mode) of
+    the temporal workload's frame 1 against frame 0 as the previous P and the I frame.
     The roofline is taken over the whole call (pack, segment index and the part's kernels)."""
     import torch
     import torch.distributed as dist
@@ -422,7 +428,7 @@ def run_part(args, rank, world, local):
     import synth
     import oracle
 
-    wl = synth.make_workload(args.workload)
+    wl = synth.make_workload("temporal" if args.part == "temporal" and args.workload == WORKLOAD else args.workload)
     dev = torch.device("cuda", local)
     R, L = len(wl.ref_views), wl.n_labels
     S = [wl.labels(r)[1] for r in wl.ref_views]
@@ -444,6 +450,25 @@ def run_part(args, rank, world, local):
 
         def step():
             ftv.ftv_centre_table(ctx, planes, labels, S, CENTRE_WINDOW, m_out, sp_out)
+        outs = m_out
+    elif args.part == "temporal":
+        # a step's new input is the current frame (the previous and I frames are resident from earlier
+        # steps); luma mode reads one plane of each
+        cur_host = [torch.from_numpy(np.ascontiguousarray(wl.view(r, 1).Y)).pin_memory() for r in wl.ref_views]
+        cur = [t.to(dev) for t in cur_host]
+        ref_prev = [planes[r][0] for r in wl.ref_views]  # frame 0
+        masks = [torch.empty(S[i], dtype=torch.uint8, device=dev) for i in range(R)]
+        changed = [torch.empty(S[i], dtype=torch.int32, device=dev) for i in range(R)]
+        n_changed = [torch.zeros(1, dtype=torch.int32, device=dev) for _ in range(R)]
+        host_out = [torch.empty(S[i], dtype=torch.uint8).pin_memory() for i in range(R)]
+        units = sum(wl.cams[r].width * wl.cams[r].height for r in wl.ref_views)
+
+        def step():
+            for i, r in enumerate(wl.ref_views):
+                ftv.ftv_temporal_mask(ctx, i, (cur[i], None, None), (ref_prev[i], None, None),
+                                      (ref_prev[i], None, None), labels[r], S[i], TEMPORAL_T_P, TEMPORAL_T_I,
+                                      ftv.FTV_TM_Y_ONLY, masks[i], changed[i], n_changed[i])
+        outs = masks
     else:
         cap = [8 * S[i] + 64 for i in range(R)]
         es = [torch.empty(c, dtype=torch.int32, device=dev) for c in cap]
@@ -456,6 +481,7 @@ def run_part(args, rank, world, local):
         def step():
             for i, r in enumerate(wl.ref_views):
                 ftv.ftv_adjacency(ctx, i, planes[r], labels[r], S[i], 4, 1.0, 1.0, es[i], et[i], beta[i], ne[i])
+        outs = beta
 
     for _ in range(args.warmup):
         step()
@@ -481,10 +507,14 @@ def run_part(args, rank, world, local):
     value = whole_job_rate(world, units * args.steps, total_s)
     if ftv.ftv_check(ctx) != 0:
         raise RuntimeError("device status")
-    # end to end: planes and label maps up, the part's result down, every step
-    h2d = sum(t.numel() * t.element_size() for trip in host_planes for t in trip)
-    h2d += sum(t.numel() * t.element_size() for t in host_labels)
-    outs = m_out if args.part == "centre" else beta
+    # end to end: the step's inputs up (planes and label maps; the temporal test: the current frame), the
+    # part's result down, every step
+    if args.part == "temporal":
+        uploads = list(zip(cur_host, cur))
+    else:
+        uploads = [(th, td) for trip_h, trip_d in zip(host_planes, planes) for th, td in zip(trip_h, trip_d)]
+        uploads += list(zip(host_labels, labels))
+    h2d = sum(th.numel() * th.element_size() for th, _ in uploads)
     d2h = sum(t.numel() * t.element_size() for t in host_out)
     e2e_ev = []
     torch.cuda.synchronize()
@@ -492,10 +522,7 @@ def run_part(args, rank, world, local):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for trip_h, trip_d in zip(host_planes, planes):
-            for th, td in zip(trip_h, trip_d):
-                td.copy_(th, non_blocking=True)
-        for th, td in zip(host_labels, labels):
+        for th, td in uploads:
             td.copy_(th, non_blocking=True)
         step()
         for th, td in zip(host_out, outs):
@@ -521,6 +548,18 @@ def run_part(args, rank, world, local):
             metric, unit = "centre-table entries/s", "entries/s"
             extra = {"window": CENTRE_WINDOW, "entries_per_step": units, "labels": L,
                      "neighbours": len(nbrs[0])}
+        elif args.part == "temporal":
+            peak, peak_kind = _peaks()
+            byts = units * (3 * wl.sample_bytes + 4) + sum(S) * 5
+            roof = {"bound": "hbm", "achieved": byts / mean_s / 1e9, "peak": peak, "unit": "GB/s",
+                    "frac": byts / mean_s / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
+                    "algorithmic_bytes_per_step": byts,
+                    "definition": "per pixel its label and three luma samples (current, previous, I) read "
+                                  "once, per segment its mask byte and list entry written",
+                    "kernel": "the whole ftv_temporal_mask calls (accumulate and finalize kernels)"}
+            metric, unit = "temporal-test pixels/s", "px/s"
+            extra = {"mode": "luma, previous P and I frame", "t_p": TEMPORAL_T_P, "t_i": TEMPORAL_T_I,
+                     "changed_per_step": sum(int(t.item()) for t in n_changed)}
         else:
             peak, peak_kind = _peaks()
             n_edges = sum(int(t.item()) for t in ne)
@@ -550,6 +589,15 @@ def run_part(args, rank, world, local):
                 line["cpu_baseline"] = {"value": n / dt, "unit": unit, "cores": 1, "kind": "oracle",
                                         "sample": f"oracle, 1 thread: the table of reference {r0} for labels "
                                                   f"0..{Lsub - 1} ({n} entries)"}
+            elif args.part == "temporal":
+                t = time.perf_counter()
+                oracle.temporal_mask(lab0, S0, wl.view(r0, 1), wl.view(r0, 0), wl.view(r0, 0), wl.sample_bytes,
+                                     TEMPORAL_T_P, TEMPORAL_T_I, 0)
+                dt = time.perf_counter() - t
+                n = lab0.size
+                line["cpu_baseline"] = {"value": n / dt, "unit": unit, "cores": 1, "kind": "oracle",
+                                        "sample": f"oracle, 1 thread: the temporal test of reference {r0} "
+                                                  f"({n} pixels)"}
             else:
                 t = time.perf_counter()
                 oracle.adjacency(lab0, S0, views[r0], wl.sample_bytes, 4, 1.0, 1.0)
@@ -613,9 +661,10 @@ def main():
                     help="synthetic workload (default: the 1920x1080 8-view configuration; others for profiling)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="sample positions of the depth part: the FP32 contract (default) or the FP64 projection")
-    ap.add_argument("--part", default="depth", choices=["depth", "segmentation", "centre", "adjacency"],
+    ap.add_argument("--part", default="depth", choices=["depth", "segmentation", "centre", "adjacency", "temporal"],
                     help="depth: the cost-volume hot path (default); segmentation: superpixels of every view; "
-                         "centre: the centre table of every reference; adjacency: adjacency and beta")
+                         "centre: the centre table of every reference; adjacency: adjacency and beta; "
+                         "temporal: the temporal test of every reference (temporal workload)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
