@@ -139,6 +139,10 @@ FTV_API ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out);
  * laid out [n_nbrs][n_labels][9] into host_out (same arithmetic, no device needed). */
 FTV_API ftv_status ftv_compute_homographies(const ftv_config* cfg, int32_t ref_index, float* host_out);
 
+/* Host-only: the same table before its rounding to FP32 (FP64 entries, [n_nbrs][n_labels][9]), i.e. the
+ * homographies of the FTV_PRECISION_FP64 projection. */
+FTV_API ftv_status ftv_compute_homographies_f64(const ftv_config* cfg, int32_t ref_index, double* host_out);
+
 /* Release a context and its device scratch. Waits for the device. NULL is accepted. */
 FTV_API ftv_status ftv_depth_destroy(ftv_ctx* ctx);
 

@@ -76,6 +76,37 @@ int64_t max_pixel_cost(const ftv_ctx* c, int n_nbrs) {
 
 }  // namespace
 
+// The host-only tables of ftv_compute_homographies[_f64]: the same arithmetic as ftv_depth_init.
+template <typename T>
+static ftv_status compute_homographies(const ftv_config* cfg, int32_t ref_index, T* host_out) {
+    if (!cfg || !host_out || !cfg->cams || !cfg->ref_views) return FTV_ERR_INVALID_ARG;
+    if (cfg->n_views < 1 || cfg->n_views > FTV_MAX_VIEWS || ref_index < 0 || ref_index >= cfg->n_refs)
+        return FTV_ERR_INVALID_ARG;
+    if (cfg->plane_mode == FTV_PLANES_CENTRE && (cfg->centre_view < 0 || cfg->centre_view >= cfg->n_views))
+        return FTV_ERR_INVALID_ARG;
+    std::vector<double> iz;
+    if (!label_inv_depths(cfg->n_labels, cfg->z_near, cfg->z_far, iz)) return FTV_ERR_INVALID_ARG;
+    const int ref = cfg->ref_views[ref_index];
+    if (ref < 0 || ref >= cfg->n_views) return FTV_ERR_INVALID_ARG;
+    std::vector<int> nbrs;
+    if (cfg->nbr_offsets) {
+        for (int k = cfg->nbr_offsets[ref_index]; k < cfg->nbr_offsets[ref_index + 1]; ++k) nbrs.push_back(cfg->nbr_views[k]);
+    } else {
+        for (int v = 0; v < cfg->n_views; ++v)
+            if (v != ref) nbrs.push_back(v);
+    }
+    const ftv_camera* cc = cfg->plane_mode == FTV_PLANES_CENTRE ? &cfg->cams[cfg->centre_view] : nullptr;
+    for (size_t k = 0; k < nbrs.size(); ++k) {
+        if (nbrs[k] < 0 || nbrs[k] >= cfg->n_views) return FTV_ERR_INVALID_ARG;
+        for (int d = 0; d < cfg->n_labels; ++d) {
+            double H[9];
+            if (plane_homography(cfg->cams[ref], cfg->cams[nbrs[k]], cc, iz[d], H) != 0) return FTV_ERR_INVALID_ARG;
+            for (int e = 0; e < 9; ++e) host_out[(k * cfg->n_labels + d) * 9 + e] = (T)H[e];
+        }
+    }
+    return FTV_OK;
+}
+
 extern "C" {
 
 const char* ftv_status_str(ftv_status s) {
@@ -269,32 +300,11 @@ ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out) {
 }
 
 ftv_status ftv_compute_homographies(const ftv_config* cfg, int32_t ref_index, float* host_out) {
-    if (!cfg || !host_out || !cfg->cams || !cfg->ref_views) return FTV_ERR_INVALID_ARG;
-    if (cfg->n_views < 1 || cfg->n_views > FTV_MAX_VIEWS || ref_index < 0 || ref_index >= cfg->n_refs)
-        return FTV_ERR_INVALID_ARG;
-    if (cfg->plane_mode == FTV_PLANES_CENTRE && (cfg->centre_view < 0 || cfg->centre_view >= cfg->n_views))
-        return FTV_ERR_INVALID_ARG;
-    std::vector<double> iz;
-    if (!label_inv_depths(cfg->n_labels, cfg->z_near, cfg->z_far, iz)) return FTV_ERR_INVALID_ARG;
-    const int ref = cfg->ref_views[ref_index];
-    if (ref < 0 || ref >= cfg->n_views) return FTV_ERR_INVALID_ARG;
-    std::vector<int> nbrs;
-    if (cfg->nbr_offsets) {
-        for (int k = cfg->nbr_offsets[ref_index]; k < cfg->nbr_offsets[ref_index + 1]; ++k) nbrs.push_back(cfg->nbr_views[k]);
-    } else {
-        for (int v = 0; v < cfg->n_views; ++v)
-            if (v != ref) nbrs.push_back(v);
-    }
-    const ftv_camera* cc = cfg->plane_mode == FTV_PLANES_CENTRE ? &cfg->cams[cfg->centre_view] : nullptr;
-    for (size_t k = 0; k < nbrs.size(); ++k) {
-        if (nbrs[k] < 0 || nbrs[k] >= cfg->n_views) return FTV_ERR_INVALID_ARG;
-        for (int d = 0; d < cfg->n_labels; ++d) {
-            double H[9];
-            if (plane_homography(cfg->cams[ref], cfg->cams[nbrs[k]], cc, iz[d], H) != 0) return FTV_ERR_INVALID_ARG;
-            for (int e = 0; e < 9; ++e) host_out[(k * cfg->n_labels + d) * 9 + e] = (float)H[e];
-        }
-    }
-    return FTV_OK;
+    return compute_homographies(cfg, ref_index, host_out);
+}
+
+ftv_status ftv_compute_homographies_f64(const ftv_config* cfg, int32_t ref_index, double* host_out) {
+    return compute_homographies(cfg, ref_index, host_out);
 }
 
 ftv_status ftv_depth_destroy(ftv_ctx* ctx) {

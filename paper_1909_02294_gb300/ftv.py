@@ -68,6 +68,7 @@ def _load() -> ctypes.CDLL:
         "ftv_get_homographies": [vp, i32, vp],
         "ftv_get_homographies_f64": [vp, i32, vp],
         "ftv_compute_homographies": [ctypes.POINTER(ftv_config), i32, vp],
+        "ftv_compute_homographies_f64": [ctypes.POINTER(ftv_config), i32, vp],
         "ftv_get_neighbours": [vp, i32, vp, vp],
         "ftv_get_label_depths": [vp, vp],
         "ftv_segment_index": [vp, i32, vp, i32, vp],
@@ -126,7 +127,7 @@ def _load() -> ctypes.CDLL:
 lib = _load()
 
 EXPORTED = ["ftv_depth_init", "ftv_depth_destroy", "ftv_compute_homographies", "ftv_get_homographies",
-            "ftv_get_homographies_f64", "ftv_fp64_recomputed", "ftv_set_launch_shape", "ftv_get_launch_shape",
+            "ftv_get_homographies_f64", "ftv_compute_homographies_f64", "ftv_fp64_recomputed", "ftv_set_launch_shape", "ftv_get_launch_shape",
             "ftv_autotune", "ftv_get_neighbours",
             "ftv_get_label_depths", "ftv_segment_index", "ftv_cost_volume", "ftv_temporal_mask",
             "ftv_wta_depth", "ftv_check", "ftv_culled_evaluations", "ftv_launch_count", "ftv_status_str", "ftv_set_profiling",
@@ -239,6 +240,18 @@ def ftv_compute_homographies(cams, ref_views, ref_index: int, n_labels: int, z_n
     n = len(nbr_lists[ref_index]) if nbr_lists is not None else len(cams) - 1
     out = np.empty((n, n_labels, 9), np.float32)
     _ok(lib.ftv_compute_homographies(ctypes.byref(cfg), ref_index, out.ctypes.data), "ftv_compute_homographies")
+    return out
+
+
+def ftv_compute_homographies_f64(cams, ref_views, ref_index: int, n_labels: int, z_near: float, z_far: float, *,
+                                 nbr_lists=None, plane_mode: int = FTV_PLANES_REF, centre_view: int = 0) -> np.ndarray:
+    """Host-only FP64 homography table [n_nbrs][n_labels][9] of reference ref_index (before the FP32 rounding)."""
+    cfg, keep = _config(cams, ref_views, n_labels, z_near, z_far, nbr_lists, plane_mode, centre_view, 1, 8, -1,
+                        FTV_COMBINE_MIN, 1)
+    n = len(nbr_lists[ref_index]) if nbr_lists is not None else len(cams) - 1
+    out = np.empty((n, n_labels, 9), np.float64)
+    _ok(lib.ftv_compute_homographies_f64(ctypes.byref(cfg), ref_index, out.ctypes.data),
+        "ftv_compute_homographies_f64")
     return out
 
 

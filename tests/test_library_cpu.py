@@ -53,6 +53,27 @@ def test_homography_table_bit_identical_to_oracle(ftv, name, reduced):
         assert np.array_equal(mine.view(np.uint32), ref.view(np.uint32))
 
 
+@pytest.mark.parametrize("name,reduced", [("tiny", False), ("hd8", False), ("uhd15", False)])
+def test_fp64_homography_table_bit_identical_to_oracle(ftv, name, reduced):
+    """The FP64 projection mode's table (before the FP32 rounding), computed by the library's host code,
+    equals the oracle's byte for byte, and rounds to the FP32 table."""
+    wl = make_workload(name, reduced=reduced)
+    for i, r in enumerate(wl.ref_views[:4]):
+        mine = ftv.ftv_compute_homographies_f64(wl.cams, wl.ref_views, i, wl.n_labels, wl.z_near, wl.z_far)
+        ref = oracle.homography_table_f64(wl.cams, r, wl.neighbours(r), wl.n_labels, wl.z_near, wl.z_far)
+        assert mine.dtype == np.float64 and mine.shape == ref.shape
+        assert mine.tobytes() == ref.tobytes()
+        f32 = ftv.ftv_compute_homographies(wl.cams, wl.ref_views, i, wl.n_labels, wl.z_near, wl.z_far)
+        assert np.array_equal(mine.astype(np.float32).view(np.uint32), f32.view(np.uint32))
+    r0 = wl.ref_views[0]
+    two = wl.neighbours(r0)[:2]
+    lists = [two] + [wl.neighbours(r)[:1] for r in wl.ref_views[1:]]
+    mine = ftv.ftv_compute_homographies_f64(wl.cams, wl.ref_views, 0, 7, wl.z_near, wl.z_far, nbr_lists=lists,
+                                            plane_mode=ftv.FTV_PLANES_CENTRE, centre_view=1)
+    ref = oracle.homography_table_f64(wl.cams, r0, two, 7, wl.z_near, wl.z_far, plane_mode=1, centre=1)
+    assert mine.tobytes() == ref.tobytes()
+
+
 def test_homography_table_centre_planes_and_neighbour_lists(ftv):
     wl = make_workload("uhd15", reduced=True)
     lists = [[1, 2], [6, 8, 0], [13]]
