@@ -70,7 +70,10 @@ def stage(h, x0, y0, rx, ry, wv, hv, tie_test=True):
         return "slow", None
     if not tie_test:
         return "general", (c, int(U0), int(V0), np.float32(1.0), np.float32(1.0))
-    return "general", (c, int(U0), int(V0), f32_down(0.5 - du - 2.0 ** -22), f32_down(0.5 - dv - 2.0 ** -22))
+    rect = (c[0] == 1 and c[1] == 0 and c[3] == 0 and c[4] == 1 and c[6] == 0 and c[7] == 0 and c[8] == 1
+            and abs(float(c[5])) + dv < 0.49)
+    return ("rect" if rect else "general"), (c, int(U0), int(V0), f32_down(0.5 - du - 2.0 ** -22),
+                                             f32_down(0.5 - dv - 2.0 ** -22))
 
 
 def fast(c, U0, V0, thr_u, thr_v, xl, yl):
@@ -125,7 +128,7 @@ def test_fp32_local_frame_decisions_equal_the_fp64_projection():
                 continue
             if mode == "slow":
                 continue
-            n_general += 1
+            n_general += 1  # general or rect: the general evaluation decides both
             c, U0, V0, thr_u, thr_v = st
             near, ui, vi = fast(c, U0, V0, thr_u, thr_v, (xs - x0).astype(np.float32), (ys - y0).astype(np.float32))
             dec = ~near
@@ -177,6 +180,18 @@ def _mismatches(h, W, H, x0b, y0b, bw, bh, tie_test):
         return 0, 0
     c, U0, V0, thr_u, thr_v = st
     near, ui, vi = fast(c, U0, V0, thr_u, thr_v, (xs - x0).astype(np.float32), (ys - y0).astype(np.float32))
+    if mode == "rect":
+        # the rectified path: t_u = (x' + a2) + 0.5 rounded twice, the row y' + V0 with no test; it must
+        # decide exactly what the general evaluation decides
+        tu = (((xs - x0).astype(np.float32) + c[2]).astype(np.float32) + np.float32(0.5)).astype(np.float32)
+        fu = np.floor(tu)
+        near_r = np.abs(((tu - fu).astype(np.float32) - np.float32(0.5)).astype(np.float32)) >= thr_u
+        ui_r, vi_r = fu.astype(np.int64) + U0, (ys - y0).astype(np.int64) + V0
+        dec_r = ~near_r
+        assert np.array_equal(near_r, near)  # the row is never near a rounding boundary here
+        ok_r = (ui_r >= 0) & (ui_r < W) & (vi_r >= 0) & (vi_r < H)
+        bad_r = (ok_r != ok64) | (ok64 & ((ui_r != fu64.astype(np.int64)) | (vi_r != fv64.astype(np.int64))))
+        assert not np.any(bad_r & dec_r)
     dec = ~near
     ok32 = (ui >= 0) & (ui < W) & (vi >= 0) & (vi < H)
     bad = (ok32 != ok64) | (ok64 & ((ui != fu64.astype(np.int64)) | (vi != fv64.astype(np.int64))))
@@ -189,6 +204,8 @@ def test_bound_holds_where_every_sample_is_near_a_rounding_boundary_and_is_neede
     boxes = [(int(rng.integers(0, W - 128)), int(rng.integers(0, H - 16)), int(rng.integers(8, 128)),
               int(rng.integers(1, 16))) for _ in range(12)]
     n_near = wrong_untested = 0
+    r0 = stage([float(v) for v in table[0, 0]], 100, 10, 20, 4, W, H)[0]
+    assert r0 == "rect"  # the rig's entries take the rectified local frame
     for d in range(table.shape[1]):
         h = [float(v) for v in table[0, d]]
         for box in boxes:
