@@ -19,6 +19,9 @@
  *    Wz = fma(h6,x,fma(h7,y,h8)) in FP32; it is out of the view unless Wz > 0; otherwise
  *    r = 1/Wz, u = X*r, v = Y*r (each IEEE FP32 round-to-nearest), and the nearest sample is
  *    (floor(u + 0.5), floor(v + 0.5)), which must lie inside the view.
+ *  - FP64 projection mode: the same decision in IEEE double with the unrounded FP64 table
+ *    (or_homography_table_f64): X = (h0*x + h1*y) + h2 etc., each operation rounded on its own,
+ *    out unless Wz > 0, (floor(X/Wz + 0.5), floor(Y/Wz + 0.5)) (project_f64).
  *  - The sample cost is the L1 distance of the integer (Y, Cb, Cr) vectors (Eq. 4 with a one-pixel
  *    window and without the 1/size(W) scaling), or a fixed penalty when the sample is out of view.
  *  - Per pixel the costs of the neighbouring views are combined by their minimum (or their sum, the
