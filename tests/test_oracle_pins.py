@@ -181,6 +181,52 @@ def test_cost_volume_against_fp64_ray_path(name, combine):
     assert n_eq / n_tot > 0.99, (n_eq, n_tot)
 
 
+@pytest.mark.parametrize("name,combine", [("tiny", "min"), ("tiny", "sum"), ("uhd15", "min"), ("uhd15", "sum")])
+def test_cost_entries_equal_the_volume_rows(name, combine):
+    """The single-entry checker (or_cost_entries, used at sizes where the whole volume is too slow) returns,
+    for every requested (segment, label) pair in any order, that entry of the volume, and the volume itself
+    is pinned to the FP64 ray path above. Pairs are drawn so that segment and label indices differ (a
+    swapped index or a wrong row stride would read another entry), with repeats, the last segment and the
+    last label, and segments that own no pixel (cost 0)."""
+    wl = make_workload(name, reduced=(name != "tiny"))
+    wl.combine = combine
+    r = wl.ref_views[-1]
+    vol = oracle_runs.volume(wl, r)
+    S, L = vol.shape
+    rng = np.random.default_rng(7)
+    seg = np.concatenate([rng.integers(0, S, 400), [S - 1, 0, S - 1], rng.integers(0, S, 5)]).astype(np.int32)
+    lab = np.concatenate([rng.integers(0, L, 400), [L - 1, L - 1, 0], rng.integers(0, L, 5)]).astype(np.int32)
+    got = oracle_runs.entries(wl, r, seg, lab)
+    np.testing.assert_array_equal(got, vol[seg, lab])
+    # a whole label column and a whole segment row
+    col = oracle_runs.entries(wl, r, np.arange(S, dtype=np.int32), np.full(S, L // 2, np.int32))
+    np.testing.assert_array_equal(col, vol[:, L // 2])
+    row = oracle_runs.entries(wl, r, np.full(L, S // 3, np.int32), np.arange(L, dtype=np.int32))
+    np.testing.assert_array_equal(row, vol[S // 3])
+
+
+def test_cost_entries_against_fp64_ray_path():
+    """or_cost_entries on whole label columns against the FP64 ray path directly (the same >99 % agreement
+    the volume has; the rest differ only where an FP32 sample position differs from FP64's)."""
+    wl = make_workload("tiny")
+    r = wl.ref_views[0]
+    lab, S = wl.labels(r)
+    for d in (0, 17, wl.n_labels - 1):
+        got = oracle_runs.entries(wl, r, np.arange(S, dtype=np.int32), np.full(S, d, np.int32)).astype(np.int64)
+        ref = _cost_fp64(wl, r, d)
+        assert np.mean(got == ref) > 0.99
+        assert np.all(np.abs(got - ref) <= 4 * wl.oob_penalty)
+
+
+def test_cost_entries_reject_out_of_range_pairs():
+    wl = make_workload("tiny")
+    r = wl.ref_views[0]
+    lab, S = wl.labels(r)
+    for seg, lb in (([S], [0]), ([-1], [0]), ([0], [wl.n_labels]), ([0], [-1])):
+        with pytest.raises(RuntimeError):
+            oracle_runs.entries(wl, r, np.array(seg, np.int32), np.array(lb, np.int32))
+
+
 def _painted_tiny():
     wl = make_workload("tiny", painted=True)
     r = wl.ref_views[0]
