@@ -239,10 +239,13 @@ FTV_API ftv_status ftv_temporal_mask(ftv_ctx* ctx, int32_t ref_index, const void
  * Scratch: the per-segment accumulators live in one statically sized device array inside this library
  * (FTV_STATIC_MAX_SEGMENTS x 64 bytes = 4 MiB), which every GPU that loads the library holds until the
  * process exits. n_segments above FTV_STATIC_MAX_SEGMENTS is rejected with FTV_ERR_INVALID_ARG.
- * The first call on a device looks up the array's device address (once per device, with that device
- * current); make that first call before any stream capture. Every call on a device shares the same
- * array and clears it on its stream before use: calls whose work overlaps on the GPU (different
- * streams without ordering between them) race and give wrong results. Asynchronous on `stream`.
+ * The work runs on the current device: every device pointer argument must be memory of that device, else
+ * FTV_ERR_INVALID_ARG before anything is launched. Each call looks up the array's device address with the
+ * current device (no address is cached, so a device reset leaves nothing stale); the first call on a
+ * device also loads the library's device code there, so make it before any stream capture. Every call on
+ * a device shares the same array and clears it on its stream before use: calls whose work overlaps on the
+ * GPU (different streams without ordering between them) race and give wrong results. Asynchronous on
+ * `stream`.
  */
 #define FTV_STATIC_MAX_SEGMENTS 65536
 FTV_API ftv_status ftv_temporal_mask_static(int32_t width, int32_t height, int32_t sample_bytes,
@@ -311,6 +314,11 @@ FTV_API ftv_status ftv_stream_labels(const ftv_ctx* ctx, int32_t ref_index, cons
 FTV_API ftv_status ftv_stream_mask(const ftv_ctx* ctx, int32_t ref_index, const uint8_t** d_mask,
                                    const int32_t** d_n_changed);
 
+/* Device pointer to a stream's list of the segments its last frame of reference ref_index re-estimated
+ * (int32, in increasing order, *d_n_changed entries as reported by ftv_stream_mask; every segment for an I
+ * frame). Sec. III-E: only these segments' costs are computed. Valid after that frame's batch completes. */
+FTV_API ftv_status ftv_stream_changed(const ftv_ctx* ctx, int32_t ref_index, const int32_t** d_changed);
+
 /* A batch executor with room for max_jobs frames, max_units (job, reference) units (<= 240) and
  * max_views views in total; owns a device descriptor block and a pinned staging copy of it. */
 FTV_API ftv_status ftv_batch_create(int32_t max_jobs, int32_t max_units, int32_t max_views, ftv_batch** out);
@@ -346,11 +354,49 @@ FTV_API ftv_status ftv_batch_set_chunks(ftv_batch* b, int32_t chunks);
 /* Non-blocking completion test of the last launch: FTV_OK when done, FTV_ERR_BUSY while running. */
 FTV_API ftv_status ftv_batch_query(ftv_batch* b);
 
-/* Wait for the last launch; returns and clears device-found errors of the batch. */
+/* Wait for the last launch; returns the device-found errors of its jobs (the OR of their statuses). */
 FTV_API ftv_status ftv_batch_wait(ftv_batch* b);
 
 /* Kernel launches this batch object has enqueued (for accounting). */
 FTV_API int64_t ftv_batch_launch_count(const ftv_batch* b);
+
+/*
+ * Job-level boundary of the batched and served forms (the paper has no serving system; these calls carry
+ * its per-view I/P depth frames of Sec. III-E for many camera streams at once).
+ *
+ * ftv_job_footprint: device bytes one camera stream of configuration cfg needs, with at most n_segments_max
+ * segments per reference (0: cfg->max_segments): the context ftv_depth_init allocates (packed views,
+ * homography tables, segment index, scratch), the resident state ftv_stream_init allocates (three packed
+ * frames, per-segment labels, mask, list, sums, the cost rows) and one frame of input planes. Host only;
+ * FTV_ERR_INVALID_ARG for an invalid configuration.
+ *
+ * ftv_batch_set_budget: admission budget of a batch object in device bytes (0, the default: none).
+ *
+ * ftv_batch_submit: queue one frame of one stream (job->ctx after ftv_stream_init) for the batch's next
+ * launch and return its ticket (> 0). The job's arrays are copied; its device buffers must stay valid
+ * until the ticket completes. Synchronous argument errors: FTV_ERR_INVALID_ARG (as ftv_batch_prepare),
+ * FTV_ERR_STATE (a P frame before the stream's first I frame). Admission: FTV_ERR_BUSY when the stream
+ * already has a queued frame, when the queued jobs would exceed the batch's capacity or differ in precision,
+ * sample format or combination rule, or when the footprints (ftv_job_footprint of each job's stream) of the
+ * queued jobs plus those of the launch in flight would exceed the budget: retry after a ticket completes.
+ * FTV_ERR_OUT_OF_MEMORY when the job alone exceeds the budget.
+ *
+ * ftv_batch_flush: launch every queued job as one batch on `stream` (the captured graph of
+ * ftv_batch_replay). FTV_OK with nothing queued; FTV_ERR_BUSY while the previous launch of this batch
+ * object runs (the queue is kept: retry).
+ *
+ * ftv_batch_poll: non-blocking. FTV_ERR_BUSY while the ticket's job is queued or running; FTV_OK once it
+ * has completed, with *job_status that job's own result: FTV_OK, FTV_ERR_INVALID_ARG (a sample above the
+ * bit depth, or a label outside [0, S) in its stream's label maps), FTV_ERR_OVERFLOW (a segment too large
+ * for int32 sums) or FTV_ERR_CUDA. Every job of a launch has its own device status word, so a failed job
+ * does not fail the others. FTV_ERR_INVALID_ARG for a ticket never issued or older than the last 4096.
+ * ftv_batch_wait after a flush waits for the launch and returns the OR of its jobs' statuses.
+ */
+FTV_API ftv_status ftv_job_footprint(const ftv_config* cfg, int32_t n_segments_max, int64_t* bytes);
+FTV_API ftv_status ftv_batch_set_budget(ftv_batch* b, int64_t hbm_budget_bytes);
+FTV_API ftv_status ftv_batch_submit(ftv_batch* b, const ftv_frame_job* job, uint64_t* ticket);
+FTV_API ftv_status ftv_batch_flush(ftv_batch* b, ftv_stream stream);
+FTV_API ftv_status ftv_batch_poll(ftv_batch* b, uint64_t ticket, ftv_status* job_status);
 
 /*
  * Centre table (Sec. III-C as written): Eq. 4 on a window around each segment's centre and the
@@ -475,7 +521,9 @@ FTV_API ftv_status ftv_segmenter_kernel_ms(ftv_segmenter* sg, float* assign_ms, 
 
 FTV_API ftv_status ftv_segmenter_destroy(ftv_segmenter* sg);
 
-/* Wait for `stream`, then return and clear the context's device status word (FTV_OK if clean). */
+/* Wait for `stream`, then return and clear the context's device status word (FTV_OK if clean). Errors
+ * found building a stream's resident state (ftv_stream_init: a label outside [0, S), a segment too large
+ * for int32 sums) are included and not cleared: they hold for every frame of that stream. */
 FTV_API ftv_status ftv_check(ftv_ctx* ctx, ftv_stream stream);
 
 /* Wait for `stream`, then report in *culled how many pixel x label x neighbour evaluations of the context's

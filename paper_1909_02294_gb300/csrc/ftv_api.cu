@@ -526,6 +526,12 @@ ftv_status ftv_check(ftv_ctx* ctx, ftv_stream stream) {
     uint32_t st = 0;
     if (cudaMemcpy(&st, ctx->d_status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return FTV_ERR_CUDA;
     if (st && cudaMemset(ctx->d_status, 0, sizeof(st)) != cudaSuccess) return FTV_ERR_CUDA;
+    // errors found building a stream's resident state stay with the stream (every job of it reports them)
+    if (ctx->stream.d_status) {
+        uint32_t ss = 0;
+        if (cudaMemcpy(&ss, ctx->stream.d_status, sizeof(ss), cudaMemcpyDeviceToHost) != cudaSuccess) return FTV_ERR_CUDA;
+        st |= ss;
+    }
     if (cudaGetLastError() != cudaSuccess) return FTV_ERR_CUDA;
     if (st & (ST_BAD_LABEL | ST_BAD_SAMPLE)) return FTV_ERR_INVALID_ARG;
     if (st & ST_OVERFLOW) return FTV_ERR_OVERFLOW;

@@ -32,6 +32,7 @@ struct PackTask {
     const void* planes[3];
     int64_t pitch[3];
     void* out;
+    uint32_t* status;  // the job's status word
     int32_t W, H, sb, fmt;
     uint32_t maxv;
     int32_t row_base;  // first row of this task in the flattened row space
@@ -46,6 +47,8 @@ struct TempUnit {
     uint8_t* mask;
     int32_t* changed;
     int32_t* n_changed;
+    uint32_t* status;              // the job's status word
+    const uint32_t* stream_status; // errors of the stream's resident state (its label maps' index)
     int32_t W, H, S, t_p, t_i, nch, fmt, is_i;
     int32_t row_base;   // rows of P-frame units, flattened (I-frame units have no rows)
     int32_t stat_base;  // stats words of P-frame units, flattened
@@ -60,6 +63,7 @@ struct WtaUnit {
     const int32_t* labels;
     float* depth;
     const float* label_z;
+    uint32_t* status;  // the job's status word
     int32_t S, L, W, H, is_i;
     int32_t seg_base;    // segments, flattened
     int32_t depth_base;  // rows of units with depth maps, flattened (units without depth own no rows)
@@ -111,7 +115,7 @@ __device__ __forceinline__ uint32_t load_plane(const void* plane, int64_t pitch,
     return sb == 1 ? (uint32_t)reinterpret_cast<const uint8_t*>(row)[x] : (uint32_t)reinterpret_cast<const uint16_t*>(row)[x];
 }
 
-__global__ void pack_multi_kernel(const Header* __restrict__ hdr, const PackTask* __restrict__ tasks, uint32_t* status) {
+__global__ void pack_multi_kernel(const Header* __restrict__ hdr, const PackTask* __restrict__ tasks) {
     const int rows = hdr->pack_rows, n = hdr->n_pack;
     for (int g = blockIdx.x; g < rows; g += gridDim.x) {
         const int t = find_base(&tasks[0].row_base, sizeof(PackTask), n, g);
@@ -122,7 +126,7 @@ __global__ void pack_multi_kernel(const Header* __restrict__ hdr, const PackTask
             uint32_t b = load_plane(T.planes[1], T.pitch[1], T.sb, x, y);
             uint32_t c = load_plane(T.planes[2], T.pitch[2], T.sb, x, y);
             if (a > T.maxv || b > T.maxv || c > T.maxv) {
-                atomicOr(status, ST_BAD_SAMPLE);
+                atomicOr(T.status, ST_BAD_SAMPLE);
                 a = min(a, T.maxv);
                 b = min(b, T.maxv);
                 c = min(c, T.maxv);
@@ -163,8 +167,7 @@ __global__ void temporal_zero_multi_kernel(const Header* __restrict__ hdr, const
 
 // Per-segment sums of cur - prev and cur - I (rows of P-frame units flattened; one block per row at a
 // time). Lanes with the same label are reduced in the warp first.
-__global__ void temporal_accumulate_multi_kernel(const Header* __restrict__ hdr, const TempUnit* __restrict__ units,
-                                                 uint32_t* status) {
+__global__ void temporal_accumulate_multi_kernel(const Header* __restrict__ hdr, const TempUnit* __restrict__ units) {
     const int rows = hdr->temp_rows, n = hdr->n_units;
     const int lane = threadIdx.x & 31;
     for (int g = blockIdx.x; g < rows; g += gridDim.x) {
@@ -176,7 +179,7 @@ __global__ void temporal_accumulate_multi_kernel(const Header* __restrict__ hdr,
             const bool in = x < T.W;
             const int l = in ? T.labels[(int64_t)y * T.W + x] : -1;
             const bool ok = in && (unsigned)l < (unsigned)T.S;
-            if (in && !ok) atomicOr(status, ST_BAD_LABEL);
+            if (in && !ok) atomicOr(T.status, ST_BAD_LABEL);
             int dp[3] = {0, 0, 0}, di[3] = {0, 0, 0};
             if (ok) {
                 int a[3], b[3], c[3];
@@ -243,10 +246,16 @@ __device__ int block_scan_1024(int v, int* total) {
 __device__ __forceinline__ int64_t iabs64(int64_t v) { return v < 0 ? -v : v; }
 
 // One block of 1024 threads per unit: masks and the ordered changed list. I-frame units list every
-// segment (Sec. III-E: all segments of an I-type frame are estimated).
+// segment (Sec. III-E: all segments of an I-type frame are estimated). Errors found when the stream's
+// resident state was built (a label outside [0, S), a segment too large for int32 sums) are reported by
+// every job of that stream.
 __global__ void temporal_finalize_multi_kernel(const Header* __restrict__ hdr, const TempUnit* __restrict__ units) {
     for (int u = blockIdx.x; u < hdr->n_units; u += gridDim.x) {
         const TempUnit& T = units[u];
+        if (threadIdx.x == 0 && T.stream_status) {
+            const uint32_t e = *T.stream_status;
+            if (e) atomicOr(T.status, e);
+        }
         const int S = T.S;
         const int per = (S + blockDim.x - 1) / blockDim.x;
         const int b = threadIdx.x * per, e = min(S, b + per);
@@ -329,7 +338,7 @@ __global__ void wta_multi_kernel(const Header* __restrict__ hdr, const WtaUnit* 
     }
 }
 
-__global__ void depth_multi_kernel(const Header* __restrict__ hdr, const WtaUnit* __restrict__ units, uint32_t* status) {
+__global__ void depth_multi_kernel(const Header* __restrict__ hdr, const WtaUnit* __restrict__ units) {
     const int rows = hdr->depth_rows, n = hdr->n_units;
     for (int g = blockIdx.x; g < rows; g += gridDim.x) {
         const int u = find_base(&units[0].depth_base, sizeof(WtaUnit), n, g);
@@ -340,7 +349,7 @@ __global__ void depth_multi_kernel(const Header* __restrict__ hdr, const WtaUnit
             const int s = T.labels[p];
             float z = 0.0f;
             if ((unsigned)s < (unsigned)T.S && T.prev_label[s] < T.L) z = T.label_z[T.prev_label[s]];
-            else atomicOr(status, ST_BAD_LABEL);
+            else atomicOr(T.status, ST_BAD_LABEL);
             T.depth[p] = z;
         }
     }
@@ -353,6 +362,20 @@ cudaError_t dalloc(T** p, size_t count) {
 
 }  // namespace
 
+// A job submitted with ftv_batch_submit and not yet launched: the caller's arrays copied.
+struct QueuedJob {
+    ftv_ctx* ctx = nullptr;
+    int32_t frame_type = 0;
+    std::vector<const void*> planes;
+    std::vector<int64_t> pitch;
+    std::vector<uint16_t*> label_out;
+    std::vector<float*> depth_out;
+    bool has_label_out = false, has_depth_out = false;
+    int64_t footprint = 0;
+};
+
+constexpr int kTicketRing = 4096;  // completed tickets whose status ftv_batch_poll still reports
+
 struct ftv_batch {
     int device = 0;
     int n_sm = 0;
@@ -361,7 +384,18 @@ struct ftv_batch {
     char* d_desc = nullptr;     // device descriptor block
     char* h_stage = nullptr;    // pinned staging copy
     ftv::Plan* d_plan = nullptr;
-    uint32_t* d_status = nullptr;
+    uint32_t* d_job_status = nullptr;  // [max_jobs] one status word per job of a launch
+    uint32_t* h_job_status = nullptr;  // pinned copy, written back by the launch's last step
+    int32_t prepared_jobs = 0, launched_jobs = 0;
+    // ticketed submission (ftv_batch_submit / ftv_batch_flush / ftv_batch_poll)
+    std::vector<QueuedJob> queue;
+    uint64_t next_ticket = 1;
+    uint64_t launch_first = 0;          // tickets [launch_first, launch_first + launch_n) are in the last launch
+    int32_t launch_n = 0;
+    bool harvested = true;              // their statuses are in `ring`
+    int64_t launch_footprint = 0;       // footprint of the jobs of the launch in flight
+    int64_t budget = 0;                 // admission budget in device bytes (0: none)
+    std::vector<int8_t> ring;           // status of ticket t at t % kTicketRing
     int32_t fmt = -1, combine = -1;
     bool fast_rcp = false;
     bool penalty_floor = false;
@@ -399,6 +433,8 @@ void free_stream_state(ftv_ctx* c) {
         cudaFree(p);
         p = nullptr;
     }
+    cudaFree(st.d_status);
+    st.d_status = nullptr;
     st.ready = false;
 }
 
@@ -406,18 +442,67 @@ void free_stream_state(ftv_ctx* c) {
 
 namespace {
 
-int64_t stream_bytes(const ftv_ctx* c, const int32_t* n_segments) {
-    int64_t b = 0;
-    size_t packed = 0;
-    for (int v = 0; v < c->n_views; ++v)
-        packed += (((size_t)c->cams[v].width * c->cams[v].height * c->texel_bytes) + 255) & ~(size_t)255;
-    b += 3 * (int64_t)packed;
-    for (int i = 0; i < c->n_refs; ++i) {
-        const int64_t S = n_segments[i];
-        const auto& r = c->refs[i];
-        b += S * (2 + 2 + 1 + 4 + 64) + S * c->L * 4 + (int64_t)r.W * r.H * 4 + 3 * (int64_t)r.n_nbrs * sizeof(NbrView);
+// A job's (or a batch's) device status bits as the ABI's status.
+ftv_status status_of(uint32_t st) {
+    if (st & ST_OVERFLOW) return FTV_ERR_OVERFLOW;
+    if (st) return FTV_ERR_INVALID_ARG;
+    return FTV_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Geometry of one reference for the footprint formulas.
+struct RefDims {
+    int64_t W, H, N, S;
+};
+
+// Device bytes ftv_stream_init allocates: the status word, three packed frames, and per reference its
+// labels of the previous and the I frame, mask, changed list and count, temporal sums, cost rows, label
+// map copy and the neighbour geometry into each ring slot.
+int64_t stream_bytes_of(size_t packed, const std::vector<RefDims>& refs, int64_t L) {
+    int64_t b = sizeof(uint32_t) + 3 * (int64_t)packed;
+    for (const RefDims& r : refs)
+        b += r.S * (2 + 2 + 1 + 4 + 8 * kStat) + 4 + r.S * L * 4 + r.W * r.H * 4 + 3 * r.N * (int64_t)sizeof(NbrView);
+    return b;
+}
+
+// Device bytes ftv_depth_init allocates (max_segments MS): packed views, status, unit descriptors, plan,
+// temporal and adjacency scratch, label depths, and per reference its tables, neighbour geometry, segment
+// index, centres and neighbour label pointers.
+int64_t context_bytes_of(size_t packed, const std::vector<RefDims>& refs, int64_t L, int64_t MS, bool fp64) {
+    int64_t b = (int64_t)packed + sizeof(uint32_t) + kMaxUnits * (int64_t)sizeof(RefJob) + sizeof(Plan);
+    b += MS * 8 * 8 + L * 4 + MS * 4 + MS * 32 * 4 + MS * 4;
+    for (const RefDims& r : refs) {
+        b += r.N * L * 9 * 4 + (fp64 ? r.N * L * 9 * 8 : 0) + r.N * (int64_t)sizeof(NbrView);
+        b += 2 * (MS + 1) * 4 + MS * 4 + r.W * r.H * 4 + MS * 8 + std::max<int64_t>(1, r.N) * 8;
     }
     return b;
+}
+
+int64_t stream_bytes(const ftv_ctx* c, const int32_t* n_segments) {
+    size_t packed = 0;
+    for (int v = 0; v < c->n_views; ++v) packed += align256((size_t)c->cams[v].width * c->cams[v].height * c->texel_bytes);
+    std::vector<RefDims> refs;
+    for (int i = 0; i < c->n_refs; ++i)
+        refs.push_back({c->refs[i].W, c->refs[i].H, c->refs[i].n_nbrs, n_segments[i]});
+    return stream_bytes_of(packed, refs, c->L);
+}
+
+// A stream's whole footprint, as ftv_job_footprint states it: its context, its resident stream state and
+// one frame of input planes.
+int64_t job_bytes(const ftv_ctx* c) {
+    size_t packed = 0;
+    int64_t input = 0;
+    for (int v = 0; v < c->n_views; ++v) {
+        packed += align256((size_t)c->cams[v].width * c->cams[v].height * c->texel_bytes);
+        input += 3 * (int64_t)c->cams[v].width * c->cams[v].height * c->sample_bytes;
+    }
+    std::vector<RefDims> refs;
+    for (int i = 0; i < c->n_refs; ++i)
+        refs.push_back({c->refs[i].W, c->refs[i].H, c->refs[i].n_nbrs,
+                        c->stream.ready ? c->stream.refs[i].S : c->max_segments});
+    return context_bytes_of(packed, refs, c->L, c->max_segments, c->precision == FTV_PRECISION_FP64) +
+           stream_bytes_of(packed, refs, c->L) + input;
 }
 
 }  // namespace
@@ -444,7 +529,7 @@ ftv_status ftv_stream_init(ftv_ctx* ctx, const int32_t* const* d_labels, const i
     size_t packed = 0;
     for (int v = 0; v < ctx->n_views; ++v)
         packed += (((size_t)ctx->cams[v].width * ctx->cams[v].height * ctx->texel_bytes) + 255) & ~(size_t)255;
-    bool ok = true;
+    bool ok = dalloc(&st.d_status, 1) == cudaSuccess && cudaMemsetAsync(st.d_status, 0, sizeof(uint32_t), s) == cudaSuccess;
     for (auto& p : st.d_ring) ok = ok && cudaMalloc(&p, packed) == cudaSuccess;
     st.refs.resize(ctx->n_refs);
     for (int i = 0; i < ctx->n_refs && ok; ++i) {
@@ -492,7 +577,7 @@ ftv_status ftv_stream_init(ftv_ctx* ctx, const int32_t* const* d_labels, const i
         const int64_t one = std::max<int64_t>(ctx->penalty, 3LL * ((1LL << ctx->bit_depth) - 1));
         const int64_t mpc = ctx->combine == FTV_COMBINE_MIN ? one : one * std::max(1, r.n_nbrs);
         e = launch_segment_index(st.refs[i].d_labels, r.W, r.H, n_segments[i], mpc, r.d_offs, r.d_cursor, r.d_pix,
-                                 ctx->d_status, s, &ctx->launches);
+                                 st.d_status, s, &ctx->launches);
         r.S_indexed = n_segments[i];
     }
     if (prev_dev >= 0 && prev_dev != ctx->device) cudaSetDevice(prev_dev);
@@ -522,6 +607,13 @@ ftv_status ftv_stream_mask(const ftv_ctx* ctx, int32_t ref_index, const uint8_t*
     return FTV_OK;
 }
 
+ftv_status ftv_stream_changed(const ftv_ctx* ctx, int32_t ref_index, const int32_t** d_changed) {
+    if (!ctx || !d_changed || !ctx->stream.ready || ref_index < 0 || ref_index >= ctx->n_refs)
+        return FTV_ERR_INVALID_ARG;
+    *d_changed = ctx->stream.refs[ref_index].d_changed;
+    return FTV_OK;
+}
+
 ftv_status ftv_batch_create(int32_t max_jobs, int32_t max_units, int32_t max_views, ftv_batch** out) {
     if (!out || max_jobs < 1 || max_units < 1 || max_views < 1 || max_units > kMaxUnits) return FTV_ERR_INVALID_ARG;
     *out = nullptr;
@@ -540,16 +632,23 @@ ftv_status ftv_batch_create(int32_t max_jobs, int32_t max_units, int32_t max_vie
     bool ok = cudaMalloc(reinterpret_cast<void**>(&b->d_desc), b->lay.total) == cudaSuccess;
     ok = ok && cudaMallocHost(reinterpret_cast<void**>(&b->h_stage), b->lay.total) == cudaSuccess;
     ok = ok && cudaMalloc(reinterpret_cast<void**>(&b->d_plan), sizeof(Plan)) == cudaSuccess;
-    ok = ok && cudaMalloc(reinterpret_cast<void**>(&b->d_status), sizeof(uint32_t)) == cudaSuccess;
-    ok = ok && cudaMemset(b->d_status, 0, sizeof(uint32_t)) == cudaSuccess;
+    ok = ok && cudaMalloc(reinterpret_cast<void**>(&b->d_job_status), sizeof(uint32_t) * max_jobs) == cudaSuccess;
+    ok = ok && cudaMemset(b->d_job_status, 0, sizeof(uint32_t) * max_jobs) == cudaSuccess;
+    ok = ok && cudaMallocHost(reinterpret_cast<void**>(&b->h_job_status), sizeof(uint32_t) * max_jobs) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess;
-    if (ok) std::memset(b->h_stage, 0, b->lay.total);
+    if (ok) {
+        std::memset(b->h_stage, 0, b->lay.total);
+        std::memset(b->h_job_status, 0, sizeof(uint32_t) * max_jobs);
+        b->ring.assign(kTicketRing, (int8_t)FTV_OK);
+        b->queue.reserve(max_jobs);
+    }
     if (!ok) {
         cudaGetLastError();
         cudaFree(b->d_desc);
         cudaFreeHost(b->h_stage);
         cudaFree(b->d_plan);
-        cudaFree(b->d_status);
+        cudaFree(b->d_job_status);
+        cudaFreeHost(b->h_job_status);
         if (b->done) cudaEventDestroy(b->done);
         delete b;
         return FTV_ERR_OUT_OF_MEMORY;
@@ -566,7 +665,8 @@ ftv_status ftv_batch_destroy(ftv_batch* b) {
     cudaFree(b->d_desc);
     cudaFreeHost(b->h_stage);
     cudaFree(b->d_plan);
-    cudaFree(b->d_status);
+    cudaFree(b->d_job_status);
+    cudaFreeHost(b->h_job_status);
     cudaEventDestroy(b->done);
     delete b;
     return FTV_OK;
@@ -637,6 +737,7 @@ ftv_status ftv_batch_prepare(ftv_batch* b, const ftv_frame_job* jobs, int32_t n_
             t.sb = c->sample_bytes;
             t.fmt = c->fmt;
             t.maxv = maxv;
+            t.status = b->d_job_status + j;
             t.row_base = pack_rows;
             pack_rows += t.H;
         }
@@ -653,6 +754,8 @@ ftv_status ftv_batch_prepare(ftv_batch* b, const ftv_frame_job* jobs, int32_t n_
             t.mask = S.d_mask;
             t.changed = S.d_changed;
             t.n_changed = S.d_n_changed;
+            t.status = b->d_job_status + j;
+            t.stream_status = st.d_status;
             t.W = r.W;
             t.H = is_i ? 0 : r.H;
             t.S = S.S;
@@ -697,6 +800,7 @@ ftv_status ftv_batch_prepare(ftv_batch* b, const ftv_frame_job* jobs, int32_t n_
             w.labels = S.d_labels;
             w.depth = J.d_depth_out ? J.d_depth_out[i] : nullptr;
             w.label_z = c->d_label_z;
+            w.status = b->d_job_status + j;
             w.S = S.S;
             w.L = c->L;
             w.W = r.W;
@@ -740,6 +844,7 @@ ftv_status ftv_batch_prepare(ftv_batch* b, const ftv_frame_job* jobs, int32_t n_
         b->kind = kind;
     }
     b->prepared_units = pu;
+    b->prepared_jobs = n_jobs;
     return FTV_OK;
 }
 
@@ -751,10 +856,11 @@ static cudaError_t enqueue(ftv_batch* b, cudaStream_t s) {
     const WtaUnit* wta = reinterpret_cast<const WtaUnit*>(b->d_desc + b->lay.wta);
     const int g = b->n_sm * 4;
     cudaError_t e = cudaMemcpyAsync(b->d_desc, b->h_stage, b->lay.total, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_job_status, 0, sizeof(uint32_t) * b->max_jobs, s);
     if (e != cudaSuccess) return e;
-    pack_multi_kernel<<<g, 256, 0, s>>>(hdr, pack, b->d_status);
+    pack_multi_kernel<<<g, 256, 0, s>>>(hdr, pack);
     temporal_zero_multi_kernel<<<g, 256, 0, s>>>(hdr, temp);
-    temporal_accumulate_multi_kernel<<<g, 256, 0, s>>>(hdr, temp, b->d_status);
+    temporal_accumulate_multi_kernel<<<g, 256, 0, s>>>(hdr, temp);
     temporal_finalize_multi_kernel<<<std::min(b->max_units, 1024), 1024, 0, s>>>(hdr, temp);
     zero_changed_rows_kernel<<<dim3(64, std::min(b->max_units, 65535)), 256, 0, s>>>(hdr, jobs);
     e = launch_plan_device(jobs, &hdr->n_units, b->d_plan, s);
@@ -767,9 +873,14 @@ static cudaError_t enqueue(ftv_batch* b, cudaStream_t s) {
                         b->cost_grid, s);
     if (e != cudaSuccess) return e;
     wta_multi_kernel<<<g, 256, 0, s>>>(hdr, wta);
-    depth_multi_kernel<<<g, 256, 0, s>>>(hdr, wta, b->d_status);
+    depth_multi_kernel<<<g, 256, 0, s>>>(hdr, wta);
     b->launches += 8 + b->chunks;
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    // every job's status word back to pinned host memory, read by ftv_batch_wait / ftv_batch_poll once the
+    // launch's completion event has fired
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->h_job_status, b->d_job_status, sizeof(uint32_t) * b->max_jobs, cudaMemcpyDeviceToHost, s);
+    return e;
 }
 
 ftv_status ftv_batch_launch(ftv_batch* b, ftv_stream stream) {
@@ -780,6 +891,7 @@ ftv_status ftv_batch_launch(ftv_batch* b, ftv_stream stream) {
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = enqueue(b, s);
     if (e == cudaSuccess) e = cudaEventRecord(b->done, s);
+    if (e == cudaSuccess) b->launched_jobs = b->prepared_jobs;
     if (prev_dev >= 0 && prev_dev != b->device) cudaSetDevice(prev_dev);
     return e == cudaSuccess ? FTV_OK : FTV_ERR_CUDA;
 }
@@ -823,6 +935,7 @@ ftv_status ftv_batch_replay(ftv_batch* b, ftv_stream stream) {
         b->launches += 8 + b->chunks;
         e = cudaEventRecord(b->done, s);
     }
+    if (e == cudaSuccess) b->launched_jobs = b->prepared_jobs;
     if (prev_dev >= 0 && prev_dev != b->device) cudaSetDevice(prev_dev);
     return e == cudaSuccess ? FTV_OK : FTV_ERR_CUDA;
 }
@@ -846,14 +959,153 @@ ftv_status ftv_batch_wait(ftv_batch* b) {
     if (!b) return FTV_ERR_INVALID_ARG;
     if (cudaEventSynchronize(b->done) != cudaSuccess) return FTV_ERR_CUDA;
     uint32_t st = 0;
-    if (cudaMemcpy(&st, b->d_status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return FTV_ERR_CUDA;
-    if (st) {
-        cudaMemset(b->d_status, 0, sizeof(st));
-        return (st & ST_OVERFLOW) ? FTV_ERR_OVERFLOW : FTV_ERR_INVALID_ARG;
-    }
-    return FTV_OK;
+    for (int j = 0; j < b->launched_jobs; ++j) st |= b->h_job_status[j];
+    return status_of(st);
 }
 
 int64_t ftv_batch_launch_count(const ftv_batch* b) { return b ? b->launches : 0; }
+
+ftv_status ftv_job_footprint(const ftv_config* cfg, int32_t n_segments_max, int64_t* bytes) {
+    if (!cfg || !bytes || n_segments_max < 0) return FTV_ERR_INVALID_ARG;
+    if (cfg->n_views < 1 || cfg->n_views > FTV_MAX_VIEWS || !cfg->cams) return FTV_ERR_INVALID_ARG;
+    if (cfg->n_refs < 1 || cfg->n_refs > cfg->n_views || !cfg->ref_views) return FTV_ERR_INVALID_ARG;
+    if (cfg->n_labels < 1 || cfg->n_labels > FTV_MAX_LABELS || cfg->max_segments < 1) return FTV_ERR_INVALID_ARG;
+    if (cfg->sample_bytes != 1 && cfg->sample_bytes != 2) return FTV_ERR_INVALID_ARG;
+    if (cfg->bit_depth < 1 || cfg->bit_depth > 8 * cfg->sample_bytes) return FTV_ERR_INVALID_ARG;
+    const size_t tb = (cfg->sample_bytes == 1 || cfg->bit_depth <= 10) ? 4 : 8;
+    size_t packed = 0;
+    int64_t input = 0;
+    for (int v = 0; v < cfg->n_views; ++v) {
+        const int64_t w = cfg->cams[v].width, h = cfg->cams[v].height;
+        if (w < 1 || h < 1 || w > FTV_MAX_DIM || h > FTV_MAX_DIM) return FTV_ERR_INVALID_ARG;
+        packed += align256((size_t)(w * h) * tb);
+        input += 3 * w * h * cfg->sample_bytes;
+    }
+    const int64_t S = n_segments_max > 0 ? n_segments_max : cfg->max_segments;
+    std::vector<RefDims> refs;
+    for (int i = 0; i < cfg->n_refs; ++i) {
+        const int r = cfg->ref_views[i];
+        if (r < 0 || r >= cfg->n_views) return FTV_ERR_INVALID_ARG;
+        int64_t N = cfg->n_views - 1;
+        if (cfg->nbr_offsets) {
+            N = cfg->nbr_offsets[i + 1] - cfg->nbr_offsets[i];
+            if (N < 0 || N > FTV_MAX_NBRS) return FTV_ERR_INVALID_ARG;
+        }
+        refs.push_back({cfg->cams[r].width, cfg->cams[r].height, N, S});
+    }
+    *bytes = context_bytes_of(packed, refs, cfg->n_labels, cfg->max_segments, cfg->precision == FTV_PRECISION_FP64) +
+             stream_bytes_of(packed, refs, cfg->n_labels) + input;
+    return FTV_OK;
+}
+
+ftv_status ftv_batch_set_budget(ftv_batch* b, int64_t hbm_budget_bytes) {
+    if (!b || hbm_budget_bytes < 0) return FTV_ERR_INVALID_ARG;
+    b->budget = hbm_budget_bytes;
+    return FTV_OK;
+}
+
+namespace {
+
+// Records the statuses of the last launch's tickets once it has completed; false while it runs.
+bool harvest(ftv_batch* b) {
+    if (b->harvested) return true;
+    const cudaError_t e = cudaEventQuery(b->done);
+    if (e == cudaErrorNotReady) return false;
+    for (int k = 0; k < b->launch_n; ++k)
+        b->ring[(b->launch_first + k) % kTicketRing] =
+            (int8_t)(e == cudaSuccess ? status_of(b->h_job_status[k]) : FTV_ERR_CUDA);
+    if (e != cudaSuccess) cudaGetLastError();
+    b->harvested = true;
+    b->launch_footprint = 0;
+    return true;
+}
+
+}  // namespace
+
+ftv_status ftv_batch_submit(ftv_batch* b, const ftv_frame_job* job, uint64_t* ticket) {
+    if (!b || !job || !ticket) return FTV_ERR_INVALID_ARG;
+    ftv_ctx* c = job->ctx;
+    if (!c || !c->stream.ready || !job->d_planes || !job->pitch_bytes) return FTV_ERR_INVALID_ARG;
+    const int64_t footprint_bytes = job_bytes(c);
+    if (job->frame_type != FTV_FRAME_I && job->frame_type != FTV_FRAME_P) return FTV_ERR_INVALID_ARG;
+    if (c->device != b->device) return FTV_ERR_INVALID_ARG;
+    for (int v = 0; v < c->n_views; ++v)
+        for (int k = 0; k < 3; ++k) {
+            if (!job->d_planes[3 * v + k]) return FTV_ERR_INVALID_ARG;
+            if (job->pitch_bytes[3 * v + k] < (int64_t)c->cams[v].width * c->sample_bytes) return FTV_ERR_INVALID_ARG;
+        }
+    if (b->budget > 0 && footprint_bytes > b->budget) return FTV_ERR_OUT_OF_MEMORY;  // can never be admitted
+    // capacity, one frame per stream per launch, one precision, sample format and combination per launch
+    int units = c->n_refs, views = c->n_views;
+    int64_t queued = footprint_bytes;
+    bool stream_has_i = c->stream.prev >= 0;
+    for (const QueuedJob& q : b->queue) {
+        if (q.ctx == c) return FTV_ERR_BUSY;
+        if (q.ctx->precision != c->precision || q.ctx->fmt != c->fmt || q.ctx->combine != c->combine)
+            return FTV_ERR_BUSY;
+        units += q.ctx->n_refs;
+        views += q.ctx->n_views;
+        queued += q.footprint;
+    }
+    if (job->frame_type == FTV_FRAME_P && !stream_has_i) return FTV_ERR_STATE;
+    if ((int)b->queue.size() >= b->max_jobs || units > b->max_units || views > b->max_views) return FTV_ERR_BUSY;
+    harvest(b);
+    if (b->budget > 0 && queued + b->launch_footprint > b->budget) return FTV_ERR_BUSY;  // admission by footprint
+    QueuedJob q;
+    q.ctx = c;
+    q.frame_type = job->frame_type;
+    q.planes.assign(job->d_planes, job->d_planes + 3 * c->n_views);
+    q.pitch.assign(job->pitch_bytes, job->pitch_bytes + 3 * c->n_views);
+    q.has_label_out = job->d_label_out != nullptr;
+    q.has_depth_out = job->d_depth_out != nullptr;
+    if (q.has_label_out) q.label_out.assign(job->d_label_out, job->d_label_out + c->n_refs);
+    if (q.has_depth_out) q.depth_out.assign(job->d_depth_out, job->d_depth_out + c->n_refs);
+    q.footprint = footprint_bytes;
+    b->queue.push_back(std::move(q));
+    *ticket = b->next_ticket++;
+    return FTV_OK;
+}
+
+ftv_status ftv_batch_flush(ftv_batch* b, ftv_stream stream) {
+    if (!b) return FTV_ERR_INVALID_ARG;
+    if (b->queue.empty()) return FTV_OK;
+    if (!harvest(b)) return FTV_ERR_BUSY;  // the previous launch still reads the staging block
+    const int n = (int)b->queue.size();
+    std::vector<ftv_frame_job> jobs(n);
+    int64_t footprint = 0;
+    for (int j = 0; j < n; ++j) {
+        QueuedJob& q = b->queue[j];
+        jobs[j].ctx = q.ctx;
+        jobs[j].d_planes = q.planes.data();
+        jobs[j].pitch_bytes = q.pitch.data();
+        jobs[j].frame_type = q.frame_type;
+        jobs[j].d_label_out = q.has_label_out ? q.label_out.data() : nullptr;
+        jobs[j].d_depth_out = q.has_depth_out ? q.depth_out.data() : nullptr;
+        footprint += q.footprint;
+    }
+    const uint64_t first = b->next_ticket - (uint64_t)n;
+    ftv_status st = ftv_batch_prepare(b, jobs.data(), n);
+    if (st == FTV_OK) st = ftv_batch_replay(b, stream);
+    b->queue.clear();
+    if (st != FTV_OK) {
+        for (int k = 0; k < n; ++k) b->ring[(first + k) % kTicketRing] = (int8_t)st;
+        return st;
+    }
+    b->launch_first = first;
+    b->launch_n = n;
+    b->harvested = false;
+    b->launch_footprint = footprint;
+    return FTV_OK;
+}
+
+ftv_status ftv_batch_poll(ftv_batch* b, uint64_t ticket, ftv_status* job_status) {
+    if (!b || !job_status || ticket == 0 || ticket >= b->next_ticket) return FTV_ERR_INVALID_ARG;
+    if (ticket + kTicketRing < b->next_ticket) return FTV_ERR_INVALID_ARG;  // no longer kept
+    if (ticket > b->next_ticket - 1 - b->queue.size()) return FTV_ERR_BUSY;  // submitted, not yet flushed
+    if (ticket >= b->launch_first && ticket < b->launch_first + (uint64_t)b->launch_n && !harvest(b))
+        return FTV_ERR_BUSY;
+    *job_status = (ftv_status)b->ring[ticket % kTicketRing];
+    return FTV_OK;
+}
 
 }  // extern "C"

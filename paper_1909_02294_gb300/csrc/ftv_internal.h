@@ -112,6 +112,7 @@ struct StreamRef {
 // label states, so that consecutive frames of one camera stream can skip unchanged segments.
 struct StreamState {
     bool ready = false;
+    uint32_t* d_status = nullptr;  // errors found building the resident state (reported by every job)
     int32_t t_p = 0, t_i = 0, mode = 0;
     void* d_ring[3] = {nullptr, nullptr, nullptr};
     int32_t prev = -1, iframe = -1;

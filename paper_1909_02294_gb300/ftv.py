@@ -86,6 +86,7 @@ def _load() -> ctypes.CDLL:
         "ftv_stream_footprint": [vp, vp, vp],
         "ftv_stream_labels": [vp, i32, vp],
         "ftv_stream_mask": [vp, i32, vp, vp],
+        "ftv_stream_changed": [vp, i32, vp],
         "ftv_reciprocal_check": [vp, vp],
         "ftv_centre_table": [vp, vp, vp, vp, vp, i32, vp, vp, vp],
         "ftv_adjacency": [vp, i32, vp, vp, vp, i32, i32, ctypes.c_double, ctypes.c_double, i32, vp, vp, vp, vp,
@@ -98,6 +99,11 @@ def _load() -> ctypes.CDLL:
         "ftv_batch_set_chunks": [vp, i32],
         "ftv_batch_query": [vp],
         "ftv_batch_wait": [vp],
+        "ftv_job_footprint": [ctypes.POINTER(ftv_config), i32, vp],
+        "ftv_batch_set_budget": [vp, i64],
+        "ftv_batch_submit": [vp, vp, vp],
+        "ftv_batch_flush": [vp, vp],
+        "ftv_batch_poll": [vp, ctypes.c_uint64, vp],
         "ftv_temporal_mask_static": [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp,
                                      vp],
         "ftv_last_kernel_ms": [vp, vp],
@@ -132,8 +138,9 @@ EXPORTED = ["ftv_depth_init", "ftv_depth_destroy", "ftv_compute_homographies", "
             "ftv_get_label_depths", "ftv_segment_index", "ftv_cost_volume", "ftv_temporal_mask",
             "ftv_wta_depth", "ftv_check", "ftv_culled_evaluations", "ftv_launch_count", "ftv_status_str", "ftv_set_profiling",
             "ftv_last_kernel_ms", "ftv_temporal_mask_static", "ftv_stream_init", "ftv_stream_footprint",
-            "ftv_stream_labels", "ftv_stream_mask", "ftv_reciprocal_check", "ftv_centre_table", "ftv_adjacency", "ftv_batch_create", "ftv_batch_destroy", "ftv_batch_prepare", "ftv_batch_launch",
+            "ftv_stream_labels", "ftv_stream_mask", "ftv_stream_changed", "ftv_reciprocal_check", "ftv_centre_table", "ftv_adjacency", "ftv_batch_create", "ftv_batch_destroy", "ftv_batch_prepare", "ftv_batch_launch",
             "ftv_batch_replay", "ftv_batch_query", "ftv_batch_wait", "ftv_batch_launch_count", "ftv_batch_set_chunks",
+            "ftv_job_footprint", "ftv_batch_set_budget", "ftv_batch_submit", "ftv_batch_flush", "ftv_batch_poll",
             "ftv_segmenter_init", "ftv_segmenter_segments", "ftv_superpixels", "ftv_segmenter_check",
             "ftv_segmenter_launch_count", "ftv_segmenter_destroy", "ftv_segmenter_set_profiling",
             "ftv_segmenter_kernel_ms"]
@@ -423,13 +430,20 @@ def ftv_temporal_mask_static(width: int, height: int, sample_bytes: int, cur, pr
                              t_p: int, t_i: int, mode: int, mask, changed_list, n_changed, status=None,
                              stream=None) -> None:
     """The temporal test without a context and without any device allocation (statically sized scratch
-    inside the library, at most FTV_STATIC_MAX_SEGMENTS segments)."""
+    inside the library, at most FTV_STATIC_MAX_SEGMENTS segments). Runs on the label map's device; every
+    tensor argument must be on that device."""
+    import torch
+    args = [t for trip in (cur, prev, iframe) if trip is not None for t in trip if t is not None]
+    args += [t for t in (mask, changed_list, n_changed, status) if t is not None]
+    if any(getattr(t, "device", None) != labels.device for t in args):
+        raise FtvError(FTV_ERR_INVALID_ARG, "ftv_temporal_mask_static: tensors on different devices")
     cp, cpi = _trip(cur)
     pp, ppi = _trip(prev)
     ip, ipi = _trip(iframe)
-    _ok(lib.ftv_temporal_mask_static(width, height, sample_bytes, cp, cpi, pp, ppi, ip, ipi, _ptr(labels), n_segments,
-                                     t_p, t_i, mode, _ptr(mask), _ptr(changed_list), _ptr(n_changed), _ptr(status),
-                                     _stream(stream)), "ftv_temporal_mask_static")
+    with torch.cuda.device(labels.device):
+        _ok(lib.ftv_temporal_mask_static(width, height, sample_bytes, cp, cpi, pp, ppi, ip, ipi, _ptr(labels),
+                                         n_segments, t_p, t_i, mode, _ptr(mask), _ptr(changed_list), _ptr(n_changed),
+                                         _ptr(status), _stream(stream)), "ftv_temporal_mask_static")
 
 
 FTV_FRAME_I, FTV_FRAME_P = 0, 1
@@ -467,6 +481,13 @@ def ftv_stream_mask(ctx: Context, ref_index: int) -> tuple[int, int]:
     return int(m.value), int(n.value)
 
 
+def ftv_stream_changed(ctx: Context, ref_index: int) -> int:
+    """Device pointer of the int32 list of segments the last frame re-estimated (length: ftv_stream_mask)."""
+    p = ctypes.c_void_p()
+    _ok(lib.ftv_stream_changed(ctx.handle, ref_index, ctypes.byref(p)), "ftv_stream_changed")
+    return int(p.value)
+
+
 def ctx_void():
     return ctypes.c_void_p()
 
@@ -495,9 +516,7 @@ def ftv_batch_create(max_jobs: int, max_units: int, max_views: int) -> Batch:
     return Batch(max_jobs, max_units, max_views)
 
 
-def ftv_batch_prepare(batch: Batch, jobs) -> int:
-    """jobs: list of dicts {ctx, planes (per view (Y, Cb, Cr) tensors), frame_type, label_out (list or
-    None), depth_out (list or None)}. Returns the status code (FTV_ERR_BUSY while the batch is in use)."""
+def _frame_jobs(jobs):
     keep = []
     arr = (ftv_frame_job * max(1, len(jobs)))()
     for k, j in enumerate(jobs):
@@ -516,7 +535,51 @@ def ftv_batch_prepare(batch: Batch, jobs) -> int:
         arr[k].frame_type = j["frame_type"]
         arr[k].d_label_out = ctypes.cast(lo, ctypes.c_void_p) if lo is not None else None
         arr[k].d_depth_out = ctypes.cast(do, ctypes.c_void_p) if do is not None else None
+    return arr, keep
+
+
+def ftv_batch_prepare(batch: Batch, jobs) -> int:
+    """jobs: list of dicts {ctx, planes (per view (Y, Cb, Cr) tensors), frame_type, label_out (list or
+    None), depth_out (list or None)}. Returns the status code (FTV_ERR_BUSY while the batch is in use)."""
+    arr, keep = _frame_jobs(jobs)
     return int(lib.ftv_batch_prepare(batch.handle, arr, len(jobs)))
+
+
+def ftv_job_footprint(cams, ref_views, n_labels: int, z_near: float, z_far: float, n_segments_max: int = 0, *,
+                      nbr_lists=None, sample_bytes: int = 1, bit_depth: int = 8, max_segments: int = 1,
+                      precision: int = FTV_PRECISION_FP32) -> int:
+    """Device bytes of one camera stream of this configuration: context, resident stream state and one
+    input frame (host only)."""
+    cfg, keep = _config(cams, ref_views, n_labels, z_near, z_far, nbr_lists, FTV_PLANES_REF, 0, sample_bytes,
+                        bit_depth, -1, FTV_COMBINE_MIN, max_segments, precision)
+    out = ctypes.c_int64()
+    _ok(lib.ftv_job_footprint(ctypes.byref(cfg), n_segments_max, ctypes.byref(out)), "ftv_job_footprint")
+    return int(out.value)
+
+
+def ftv_batch_set_budget(batch: Batch, budget_bytes: int) -> None:
+    _ok(lib.ftv_batch_set_budget(batch.handle, int(budget_bytes)), "ftv_batch_set_budget")
+
+
+def ftv_batch_submit(batch: Batch, job) -> tuple[int, int]:
+    """Queue one job (a dict as in ftv_batch_prepare). Returns (status, ticket); status FTV_ERR_BUSY means
+    not admitted now (retry after a ticket completes)."""
+    arr, keep = _frame_jobs([job])
+    t = ctypes.c_uint64()
+    rc = int(lib.ftv_batch_submit(batch.handle, arr, ctypes.byref(t)))
+    return rc, int(t.value)
+
+
+def ftv_batch_flush(batch: Batch, stream=None) -> int:
+    """Launch the queued jobs; returns the status (FTV_ERR_BUSY while the previous launch runs)."""
+    return int(lib.ftv_batch_flush(batch.handle, _stream(stream)))
+
+
+def ftv_batch_poll(batch: Batch, ticket: int) -> tuple[int, int]:
+    """Non-blocking: (FTV_OK, the job's own status) once it completed, (FTV_ERR_BUSY, -1) while pending."""
+    st = ctypes.c_int32(-1)
+    rc = int(lib.ftv_batch_poll(batch.handle, ctypes.c_uint64(ticket), ctypes.byref(st)))
+    return rc, int(st.value)
 
 
 def ftv_batch_launch(batch: Batch, stream=None) -> None:

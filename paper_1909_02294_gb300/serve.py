@@ -7,12 +7,17 @@ segments whose colour changed (Sec. III-E; 9 P frames between I frames as in the
 
 Served mode: up to `slots` batches are in flight on separate CUDA streams. Whenever a slot is free,
 every request that has arrived, whose stream has no frame in flight (in-stream order is kept) and whose
-input frame fits the HBM admission budget is admitted into one batch: its planes are copied from pinned
-host memory on the slot's stream and the batch's captured graph is replayed (ftv_batch_prepare +
-ftv_batch_replay). Requests that arrive while others are on the GPU join the next free slot.
+footprint fits the HBM admission budget is admitted into one batch: its planes are copied from pinned
+host memory on the slot's stream, the job is queued with ftv_batch_submit (one ticket per job) and the
+batch is launched through its captured graph (ftv_batch_flush); each job completes when
+ftv_batch_poll reports its ticket done, with that job's own status. Requests that arrive while others are
+on the GPU join the next free slot. A job's footprint is ftv_job_footprint of its stream: the stream's
+context, its resident state (frames, per-segment labels, cost rows) and one input frame.
 
 Plain mode (the comparison): the same requests in arrival order, one job at a time, each launched on
-its own (ftv_batch_launch of a single job, no graph) and completed before the next starts.
+its own (ftv_batch_launch of a single job, no graph) and completed before the next starts. Its GPU-busy
+fraction (the jobs' launch sequences timed with CUDA events, summed, over the run's wall time) bounds
+what any batching can gain over it: at most 1 / busy.
 
 Both modes run the same kernels on the same stream states and produce bit-identical labels.
 """
@@ -61,6 +66,9 @@ class Stream:
             wl.drop_frame(k)
         self.frame_bytes = sum(t.numel() * t.element_size() for trip in self.frames[0] for t in trip) \
             if self.frames else 0
+        self.footprint = ftv.ftv_job_footprint(wl.cams, wl.ref_views, wl.n_labels, wl.z_near, wl.z_far, max(self.S),
+                                               sample_bytes=wl.sample_bytes, bit_depth=wl.bit_depth,
+                                               max_segments=max(self.S))
         self.out = [torch.zeros(s, dtype=torch.int16, device=device) for s in self.S]
         self.keep = keep_labels
         self.history = []
@@ -108,6 +116,7 @@ class Slot:
     lo: object      # low-priority stream (batches of heavy shapes)
     cur: object = None
     reqs: list = field(default_factory=list)
+    tickets: list = field(default_factory=list)
     inputs: list = field(default_factory=list)
     bytes: int = 0
     heavy: bool = False
@@ -117,7 +126,7 @@ HEAVY_EVALS = 1e11  # a stream whose full frame is this many evaluations saturat
 HEAVY_CHUNKS = 16   # cost-kernel launches per heavy batch: light work can start between two of them
 
 
-def run_served(streams: list[Stream], reqs: list[Request], slots: int = 3, budget_bytes: int = 8 << 30,
+def run_served(streams: list[Stream], reqs: list[Request], slots: int = 3, budget_bytes: int = 16 << 30,
                max_jobs: int = 32, by_class: bool = True, heavy_exclusive: bool = True,
                heavy_chunks: int = HEAVY_CHUNKS) -> dict:
     """by_class: a batch only takes jobs of one stream shape (the shape of the earliest admissible
@@ -142,10 +151,13 @@ def run_served(streams: list[Stream], reqs: list[Request], slots: int = 3, budge
         now = time.perf_counter() - t0
         progressed = False
         for sl in pool:
-            if sl.reqs and ftv.ftv_batch_query(sl.cur) == 0:
-                st = ftv.ftv_batch_wait(sl.cur)
-                if st != 0:
-                    raise RuntimeError(f"batch failed: {ftv.ftv_status_str(st)}")
+            if not sl.reqs:
+                continue
+            polls = [ftv.ftv_batch_poll(sl.cur, t) for t in sl.tickets]
+            if all(rc == 0 for rc, _ in polls):
+                bad = [ftv.ftv_status_str(st) for _, st in polls if st != 0]
+                if bad:
+                    raise RuntimeError(f"job failed: {bad[0]}")
                 t_done = time.perf_counter() - t0
                 for r in sl.reqs:
                     r.done = t_done
@@ -153,7 +165,7 @@ def run_served(streams: list[Stream], reqs: list[Request], slots: int = 3, budge
                     streams[r.sid].record()
                 done += len(sl.reqs)
                 inflight_bytes -= sl.bytes
-                sl.reqs, sl.inputs, sl.bytes = [], [], 0
+                sl.reqs, sl.tickets, sl.inputs, sl.bytes = [], [], [], 0
                 progressed = True
         free = [sl for sl in pool if not sl.reqs]
         heavy_busy = heavy_exclusive and any(sl.reqs and sl.heavy for sl in pool)
@@ -168,8 +180,8 @@ def run_served(streams: list[Stream], reqs: list[Request], slots: int = 3, budge
                 seen.add(r.sid)
                 if s.busy:
                     continue
-                if inflight_bytes + add_bytes + s.frame_bytes > budget_bytes and (inflight_bytes or chosen):
-                    continue  # admission by HBM footprint: wait until in-flight inputs free up (a job
+                if inflight_bytes + add_bytes + s.footprint > budget_bytes and (inflight_bytes or chosen):
+                    continue  # admission by HBM footprint: wait until in-flight jobs free up (a job
                     # larger than the whole budget still runs, alone, when nothing else is in flight)
                 if len(chosen) >= max_jobs or units + s.n_refs > max_units or views + s.n_views > max_views:
                     continue
@@ -181,7 +193,7 @@ def run_served(streams: list[Stream], reqs: list[Request], slots: int = 3, budge
                 chosen.append(r)
                 units += s.n_refs
                 views += s.n_views
-                add_bytes += s.frame_bytes
+                add_bytes += s.footprint
             if chosen:
                 sl = free[0]
                 heavy = any(streams[r.sid].heavy for r in chosen)
@@ -192,20 +204,22 @@ def run_served(streams: list[Stream], reqs: list[Request], slots: int = 3, budge
                     sl.batches[key] = b
                 sl.cur = sl.batches[key]
                 stream = sl.lo if heavy else sl.hi
-                jobs = []
+                tickets = []
                 for r in chosen:
                     s = streams[r.sid]
                     planes = s.upload(r.seq, stream)
                     sl.inputs.append(planes)
-                    jobs.append(s.job(r.seq, planes))
+                    rc, t = ftv.ftv_batch_submit(sl.cur, s.job(r.seq, planes))
+                    if rc != 0:
+                        raise RuntimeError(f"submit failed: {ftv.ftv_status_str(rc)}")
+                    tickets.append(t)
                     s.busy = True
                     r.admitted = now
                     pending.remove(r)
-                rc = ftv.ftv_batch_prepare(sl.cur, jobs)
+                rc = ftv.ftv_batch_flush(sl.cur, stream)
                 if rc != 0:
-                    raise RuntimeError(f"prepare failed: {ftv.ftv_status_str(rc)}")
-                ftv.ftv_batch_replay(sl.cur, stream)
-                sl.reqs, sl.bytes = chosen, add_bytes
+                    raise RuntimeError(f"flush failed: {ftv.ftv_status_str(rc)}")
+                sl.reqs, sl.tickets, sl.bytes = chosen, tickets, add_bytes
                 sl.heavy = heavy
                 inflight_bytes += add_bytes
                 batches += 1
@@ -228,6 +242,8 @@ def run_plain(streams: list[Stream], reqs: list[Request]) -> dict:
     st = torch.cuda.Stream(dev)
     batch = ftv.ftv_batch_create(1, max(s.n_refs for s in streams), max(s.n_views for s in streams))
     per_job = []
+    gpu_ms = 0.0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for r in reqs:
@@ -239,8 +255,12 @@ def run_plain(streams: list[Stream], reqs: list[Request]) -> dict:
         rc = ftv.ftv_batch_prepare(batch, [s.job(r.seq, planes)])
         if rc != 0:
             raise RuntimeError(f"prepare failed: {ftv.ftv_status_str(rc)}")
+        ev0.record(st)
         ftv.ftv_batch_launch(batch, st)
+        ev1.record(st)
         rc = ftv.ftv_batch_wait(batch)
+        ev1.synchronize()
+        gpu_ms += ev0.elapsed_time(ev1)
         if rc != 0:
             raise RuntimeError(f"batch failed: {ftv.ftv_status_str(rc)}")
         r.done = time.perf_counter() - t0
@@ -253,7 +273,8 @@ def run_plain(streams: list[Stream], reqs: list[Request]) -> dict:
     service = {}
     for shape, ftype, ms in per_job:
         service.setdefault(f"{shape} {ftype}", []).append(ms)
-    out.update({"mode": "plain", "gpu_launches": launches,
+    out.update({"mode": "plain", "gpu_launches": launches, "gpu_busy_ms": gpu_ms,
+                "gpu_busy_fraction": gpu_ms / 1e3 / out["wall_s"],
                 "service_ms_by_shape_and_type": {k: float(np.mean(v)) for k, v in sorted(service.items())}})
     return out
 
@@ -366,7 +387,8 @@ def main(argv=None):
     ap.add_argument("--gop", type=int, default=10, help="frames per I frame (paper: 9 P frames between I frames)")
     ap.add_argument("--frames", type=int, default=4, help="distinct frames rendered per stream (cycled)")
     ap.add_argument("--slots", type=int, default=3)
-    ap.add_argument("--budget-gb", type=float, default=8.0, help="HBM admission budget for in-flight inputs")
+    ap.add_argument("--budget-gb", type=float, default=16.0,
+                    help="HBM admission budget: footprints (ftv_job_footprint) of the jobs in flight")
     ap.add_argument("--rate-frac", type=float, default=0.7, help="arrival rate as a fraction of measured capacity")
     ap.add_argument("--capacity-jobs", type=int, default=0, help="jobs of the saturated capacity run (0: --jobs)")
     ap.add_argument("--seed", type=int, default=1)

@@ -243,6 +243,32 @@ def serving_streams(per_shape: int = 4) -> list[Workload]:
     return streams
 
 
+def serving_streams_reduced(per_shape: int = 1) -> list[Workload]:
+    """The serving workload's three stream shapes at sizes the CPU oracle finishes in seconds (parity tests):
+    per_shape streams each of a 3-view linear rig (320x180, 64 labels), an 8-view linear rig (244x138, 40
+    labels, references 0, 3 and 7) and the 15-view convergent arc (390x218, 24 labels, references 0, 7
+    and 14), each with moving planes and sensor noise, 10-bit 4:4:4 in uint16."""
+    streams = []
+    for i in range(per_shape):
+        seed = BASE_SEED + 5 + 1000 * (i + 1)
+        cams = linear_rig(3, 0.10, 250.0, 320, 180)
+        rng = np.random.default_rng(seed)
+        planes = _layered(cams[1], 250.0, 8, 4.0, 12.0, 18.0, seed, rng) + _movers(cams[1], 250.0, seed)
+        streams.append(Workload(f"r540_{i}", cams, [0, 1, 2], 64, 1.0, 20.0, 10, planes, cell=8, seed=seed,
+                                noise_sigma=2.0))
+    for i in range(per_shape):
+        seed = BASE_SEED + 5 + 1000 * (i + 1) + 1
+        streams.append(_temporal(seed, W=244, H=138, f=190.0, L=40, refs=[0, 3, 7], name=f"r1080_{i}"))
+    for i in range(per_shape):
+        seed = BASE_SEED + 5 + 1000 * (i + 1) + 2
+        wl = _uhd15(seed, W=390, H=218, f=304.0, L=24, refs=[0, 7, 14], cell=7, name=f"r2160_{i}")
+        wl.planes = wl.planes + _movers(wl.cams[7], 304.0, seed)
+        wl.noise_sigma = 2.0
+        wl.specular_frac = 0.0
+        streams.append(wl)
+    return streams
+
+
 def make_workload(name: str, reduced: bool = False, painted: bool = False) -> Workload:
     """Build a named workload. `reduced` gives a small variant of the same structure (rig type,
     bit depth, chroma handling, noise, all references) that the CPU oracle finishes in seconds while

@@ -43,3 +43,16 @@ class Run:
 
     def close(self):
         self.ctx.close()
+
+
+class _DeviceArray:
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3}
+
+
+def from_device_pointer(ptr: int, n: int, typestr: str) -> np.ndarray:
+    """Host copy of n elements at a device pointer the library returned (typestr: '|u1', '<i4', '<u2')."""
+    if n == 0:
+        return np.zeros(0, np.dtype(typestr))
+    return torch.as_tensor(_DeviceArray(ptr, (n,), typestr), device="cuda").cpu().numpy().copy()

@@ -203,3 +203,114 @@ def test_chunked_cost_launches_give_identical_results():
             for sa, sb in zip(fa, fb):
                 for a, c in zip(sa, sb):
                     assert np.array_equal(a, c), chunks
+
+
+def _poll_until_done(batch, ticket, limit_s=60.0):
+    import time
+    t0 = time.time()
+    while True:
+        rc, st = ftv.ftv_batch_poll(batch, ticket)
+        if rc == 0:
+            return st
+        assert rc == ftv.FTV_ERR_BUSY, rc
+        assert time.time() - t0 < limit_s, "ticket did not complete"
+        time.sleep(1e-3)
+
+
+def test_ticketed_batch_reports_each_job_on_its_own():
+    """ftv_batch_submit / flush / poll: three streams in one launch, one of whose label maps holds a label
+    outside [0, S) (made on the host). Only that job's ticket reports FTV_ERR_INVALID_ARG, frame after frame;
+    the other two equal the oracle's I/P procedure (Sec. III-E)."""
+    wls = _streams()
+    good = [Stream(w) for w in wls]
+    bad_wl = make_workload("temporal", reduced=True)
+    lab_bad = [bad_wl.labels(r)[0].copy() for r in bad_wl.ref_views]
+    S_bad = [bad_wl.labels(r)[1] for r in bad_wl.ref_views]
+    lab_bad[1][3, 5] = S_bad[1]  # one pixel of reference 1 labelled S
+    bad_ctx = ftv.ftv_depth_init(bad_wl.cams, bad_wl.ref_views, bad_wl.n_labels, bad_wl.z_near, bad_wl.z_far,
+                                 sample_bytes=bad_wl.sample_bytes, bit_depth=bad_wl.bit_depth,
+                                 oob_penalty=bad_wl.oob_penalty, max_segments=max(S_bad))
+    ftv.ftv_stream_init(bad_ctx, [dev(l) for l in lab_bad], S_bad, T_P, T_I, 0)
+    bad_out = [torch.zeros(s, dtype=torch.int16, device="cuda") for s in S_bad]
+    refs = [OracleStream(w) for w in wls]
+    batch = ftv.ftv_batch_create(4, 64, 64)
+    for frame, ftype in SCHEDULE:
+        tickets, jobs = [], []  # the jobs' device buffers must stay valid until their tickets complete
+        for s in good:
+            jobs.append(s.job(frame, ftype))
+            rc, t = ftv.ftv_batch_submit(batch, jobs[-1])
+            assert rc == 0 and t > 0
+            tickets.append(t)
+        planes = [(dev(v.Y), dev(v.U), dev(v.V)) for v in bad_wl.views(frame)]
+        rc, t_bad = ftv.ftv_batch_submit(batch, {"ctx": bad_ctx, "planes": planes, "frame_type": ftype,
+                                                 "label_out": bad_out})
+        assert rc == 0
+        # a second frame of a queued stream waits for the next launch; a queued ticket is pending
+        assert ftv.ftv_batch_submit(batch, good[0].job(frame, ftype))[0] == ftv.FTV_ERR_BUSY
+        assert ftv.ftv_batch_poll(batch, t_bad)[0] == ftv.FTV_ERR_BUSY
+        assert ftv.ftv_batch_flush(batch) == 0
+        assert _poll_until_done(batch, t_bad) == ftv.FTV_ERR_INVALID_ARG
+        for t in tickets:
+            assert _poll_until_done(batch, t) == 0
+        for s, o in zip(good, refs):
+            for r, (g, w) in enumerate(zip(s.labels(), o.step(frame, ftype))):
+                assert np.array_equal(g, w), (s.wl.name, frame, r)
+        assert ftv.ftv_batch_wait(batch) == ftv.FTV_ERR_INVALID_ARG  # the OR over the launch's jobs
+    # unknown tickets
+    assert ftv.ftv_batch_poll(batch, 0)[0] == ftv.FTV_ERR_INVALID_ARG
+    assert ftv.ftv_batch_poll(batch, 10 ** 9)[0] == ftv.FTV_ERR_INVALID_ARG
+    assert ftv.ftv_batch_flush(batch) == 0  # nothing queued
+    batch.close()
+    bad_ctx.close()
+    for s in good:
+        s.ctx.close()
+
+
+def test_ticketed_admission_by_footprint():
+    """A batch with an HBM budget admits jobs while the footprints (ftv_job_footprint) of the queued and
+    in-flight jobs fit: with room for one stream's footprint, a second job waits (FTV_ERR_BUSY) until the
+    first has completed, and a budget below one job's footprint refuses it outright."""
+    wls = _streams()
+    streams = [Stream(w) for w in wls]
+    fp = [ftv.ftv_job_footprint(w.cams, w.ref_views, w.n_labels, w.z_near, w.z_far, max(s.S),
+                                sample_bytes=w.sample_bytes, bit_depth=w.bit_depth, max_segments=max(s.S))
+          for w, s in zip(wls, streams)]
+    batch = ftv.ftv_batch_create(4, 64, 64)
+    ftv.ftv_batch_set_budget(batch, max(fp) + min(fp) // 2)
+    j0, j1 = streams[0].job(0, 0), streams[1].job(0, 0)  # kept alive until their tickets complete
+    rc, t0 = ftv.ftv_batch_submit(batch, j0)
+    assert rc == 0
+    assert ftv.ftv_batch_submit(batch, j1)[0] == ftv.FTV_ERR_BUSY  # queued + new > budget
+    assert ftv.ftv_batch_flush(batch) == 0
+    assert _poll_until_done(batch, t0) == 0
+    rc, t1 = ftv.ftv_batch_submit(batch, j1)  # the first has completed: room again
+    assert rc == 0
+    assert ftv.ftv_batch_flush(batch) == 0
+    assert _poll_until_done(batch, t1) == 0
+    ftv.ftv_batch_set_budget(batch, min(fp) - 1)
+    assert ftv.ftv_batch_submit(batch, streams[0].job(1, 1))[0] == ftv.FTV_ERR_OUT_OF_MEMORY
+    batch.close()
+    for s in streams:
+        s.ctx.close()
+
+
+def test_job_footprint_covers_the_device_allocations():
+    """The device memory taken by creating a stream's context and resident state is what ftv_job_footprint
+    states for them (its input-frame part excluded), up to the allocator's rounding of each allocation."""
+    wl = make_workload("hd8")
+    S = [wl.labels(r)[1] for r in wl.ref_views]
+    fp = ftv.ftv_job_footprint(wl.cams, wl.ref_views, wl.n_labels, wl.z_near, wl.z_far, max(S),
+                               sample_bytes=wl.sample_bytes, bit_depth=wl.bit_depth, max_segments=max(S))
+    input_bytes = sum(3 * c.width * c.height * wl.sample_bytes for c in wl.cams)
+    labels = [dev(wl.labels(r)[0]) for r in wl.ref_views]
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    ctx = ftv.ftv_depth_init(wl.cams, wl.ref_views, wl.n_labels, wl.z_near, wl.z_far, sample_bytes=wl.sample_bytes,
+                             bit_depth=wl.bit_depth, oob_penalty=wl.oob_penalty, max_segments=max(S))
+    ftv.ftv_stream_init(ctx, labels, [max(S)] * len(S), T_P, T_I, 0)
+    torch.cuda.synchronize()
+    used = free0 - torch.cuda.mem_get_info()[0]
+    n_allocs = 10 + 10 * len(S) + 3 + 11 * len(S)
+    assert fp - input_bytes <= used + (2 << 20), (fp - input_bytes, used)
+    assert used <= fp - input_bytes + n_allocs * (2 << 20), (fp - input_bytes, used)
+    ctx.close()

@@ -145,3 +145,58 @@ def test_label_split_by_reciprocal_multiply_is_exact_at_every_label_count():
         j = np.concatenate([k * L - 1, (k - 1) * L]).astype(np.uint64)
         got = (j * np.uint64(magic)) >> np.uint64(32)
         assert np.array_equal(got, j // np.uint64(L)), L
+
+
+def test_job_footprint_on_the_host(ftv):
+    """ftv_job_footprint needs no device: it grows with the segment count, an FP64-precision stream adds
+    exactly its FP64 homography tables (8 bytes x 9 per neighbour and label of every reference), and an
+    invalid configuration is refused."""
+    wl = make_workload("hd8")
+    S = max(wl.labels(r)[1] for r in wl.ref_views)
+    args = (wl.cams, wl.ref_views, wl.n_labels, wl.z_near, wl.z_far)
+    kw = dict(sample_bytes=wl.sample_bytes, bit_depth=wl.bit_depth, max_segments=S)
+    a = ftv.ftv_job_footprint(*args, S, **kw)
+    b = ftv.ftv_job_footprint(*args, S + 1000, **kw)
+    assert 0 < a < b
+    c = ftv.ftv_job_footprint(*args, S, precision=ftv.FTV_PRECISION_FP64, **kw)
+    nbrs = sum(len(wl.neighbours(r)) for r in wl.ref_views)
+    assert c - a == nbrs * wl.n_labels * 9 * 8
+    # more than the views' input planes and the int32 cost volume alone
+    inputs = sum(3 * cm.width * cm.height * wl.sample_bytes for cm in wl.cams)
+    assert a > inputs + len(wl.ref_views) * S * wl.n_labels * 4
+    with pytest.raises(ftv.FtvError):
+        ftv.ftv_job_footprint(*args, -1, **kw)
+    with pytest.raises(ftv.FtvError):
+        ftv.ftv_job_footprint(wl.cams, wl.ref_views, 0, wl.z_near, wl.z_far, S, **kw)
+
+
+def test_static_temporal_mask_refuses_tensors_on_another_device(ftv, monkeypatch):
+    """The allocation-free temporal test runs on its label map's device; an output or a frame on another
+    device is refused on the host before the library is called (no launch)."""
+    import torch
+
+    class Fake:
+        def __init__(self, device):
+            self.device = torch.device(device)
+
+        def data_ptr(self):
+            return 4096
+
+        def stride(self, k):
+            return 16
+
+        def element_size(self):
+            return 2
+
+    called = []
+    monkeypatch.setattr(ftv.ftv.lib, "ftv_temporal_mask_static", lambda *a: called.append(a) or 0, raising=False)
+    frame = (Fake("cuda:0"), Fake("cuda:0"), Fake("cuda:0"))
+    for odd in ("mask", "frame", "status"):
+        mask = Fake("cuda:1" if odd == "mask" else "cuda:0")
+        cur = (Fake("cuda:1"), frame[1], frame[2]) if odd == "frame" else frame
+        status = Fake("cuda:1") if odd == "status" else None
+        with pytest.raises(ftv.FtvError) as e:
+            ftv.ftv_temporal_mask_static(16, 8, 2, cur, frame, None, Fake("cuda:0"), 4, 12, 4, 0, mask,
+                                         Fake("cuda:0"), Fake("cuda:0"), status=status)
+        assert e.value.code == ftv.FTV_ERR_INVALID_ARG
+    assert called == []
