@@ -7,37 +7,40 @@
 // accumulators in a fixed, statically sized device array instead, and calls no allocator.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "ftv_internal.h"
 
 namespace {
 
 constexpr int kStatWords = 8;     // int64 accumulators per segment, the layout the temporal kernels use
 constexpr int kSpareWords = 32;   // tail of the array: the status word when the caller passes none
-constexpr int kMaxDevices = 64;
 
 // Accumulators of ftv_temporal_mask_static: FTV_STATIC_MAX_SEGMENTS x 8 int64 (4 MiB for 65536
 // segments) plus a spare tail. Every GPU that loads this library holds it until the process exits.
 static __device__ __align__(256) int64_t g_tm_scratch[FTV_STATIC_MAX_SEGMENTS * kStatWords + kSpareWords];
 
-std::mutex g_mutex;
-int64_t* g_scratch_ptr[kMaxDevices] = {};
-
 // Device address of g_tm_scratch on the current device. In host code the symbol's name is only a
-// host-side stand-in, so the address is looked up once per device (with that device current) and
-// cached.
+// host-side stand-in, so the address is looked up with the device current. The lookup runs on every call:
+// it allocates nothing, and no address is kept that a device reset could leave stale.
 ftv_status scratch_for_current_device(int64_t** out) {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FTV_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (g_scratch_ptr[dev] == nullptr) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_tm_scratch) != cudaSuccess || p == nullptr) return FTV_ERR_CUDA;
-        g_scratch_ptr[dev] = static_cast<int64_t*>(p);
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_tm_scratch) != cudaSuccess || p == nullptr) {
+        cudaGetLastError();
+        return FTV_ERR_CUDA;
     }
-    *out = g_scratch_ptr[dev];
+    *out = static_cast<int64_t*>(p);
     return FTV_OK;
+}
+
+// True when p is device memory of device `dev` (or managed memory): the kernels run on the current device
+// with the current device's scratch, so an argument on another device, or in host memory, is refused
+// before anything is launched.
+bool on_device(const void* p, int dev) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 }  // namespace
@@ -63,6 +66,14 @@ extern "C" ftv_status ftv_temporal_mask_static(int32_t width, int32_t height, in
         if (!d_cur[c] || !d_prev[c] || cur_pitch[c] < row || prev_pitch[c] < row) return FTV_ERR_INVALID_ARG;
         if (d_iframe && (!d_iframe[c] || iframe_pitch[c] < row)) return FTV_ERR_INVALID_ARG;
     }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FTV_ERR_CUDA;
+    if (!on_device(d_labels, dev) || !on_device(d_mask, dev) || !on_device(d_changed_list, dev) ||
+        !on_device(d_n_changed, dev) || (d_status && !on_device(d_status, dev)))
+        return FTV_ERR_INVALID_ARG;
+    for (int c = 0; c < nch; ++c)
+        if (!on_device(d_cur[c], dev) || !on_device(d_prev[c], dev) || (d_iframe && !on_device(d_iframe[c], dev)))
+            return FTV_ERR_INVALID_ARG;
     int64_t* scratch = nullptr;
     const ftv_status st = scratch_for_current_device(&scratch);
     if (st != FTV_OK) return st;

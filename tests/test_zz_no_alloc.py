@@ -65,3 +65,52 @@ def test_static_scratch_rejects_too_many_segments():
         ftv.ftv_temporal_mask_static(wl.cams[r].width, wl.cams[r].height, 2, dev, dev, None,
                                      torch.from_numpy(lab).cuda(), big, 12, 4, 0, m, c, n)
     assert e.value.code == ftv.FTV_ERR_INVALID_ARG
+
+
+def test_static_scratch_without_status_word_and_with_a_bad_label():
+    """Without a caller status word (d_status NULL) the results are unchanged; with one pixel labelled S the
+    call reports the bad label in the caller's word and leaves that pixel out, as the context version does."""
+    wl = make_workload("temporal", reduced=True)
+    run = Run(wl)
+    r_index, r = 2, wl.ref_views[2]
+    lab, S = wl.labels(r)
+    frames = [run.planes(f)[r] for f in range(2)]
+    cam = wl.cams[r]
+    bad = lab.copy()
+    bad[4, 9] = S
+    for lab_k, expect_bad in ((lab, False), (bad, True)):
+        labels = torch.from_numpy(lab_k).cuda()
+        m_a, c_a, n_a = _outputs(S)
+        ftv.ftv_temporal_mask(run.ctx, r_index, frames[1], frames[0], None, labels, S, 12, 4, ftv.FTV_TM_ALL_YUV,
+                              m_a, c_a, n_a)
+        assert run.check() == (ftv.FTV_ERR_INVALID_ARG if expect_bad else 0)
+        for with_status in (False, True):
+            status = torch.zeros(1, dtype=torch.int32, device="cuda") if with_status else None
+            m_b, c_b, n_b = _outputs(S)
+            ftv.ftv_temporal_mask_static(cam.width, cam.height, wl.sample_bytes, frames[1], frames[0], None, labels, S,
+                                         12, 4, ftv.FTV_TM_ALL_YUV, m_b, c_b, n_b, status=status)
+            torch.cuda.synchronize()
+            n = int(n_a.item())
+            assert int(n_b.item()) == n
+            assert torch.equal(m_a, m_b) and torch.equal(c_a[:n], c_b[:n])
+            if with_status:
+                assert (int(status.item()) & 1) == (1 if expect_bad else 0)  # the bad-label bit
+    run.close()
+
+
+def test_static_scratch_refuses_host_memory_before_launching():
+    """A label map in host memory (not memory of the current device) is refused with FTV_ERR_INVALID_ARG by
+    the argument check, before anything is launched."""
+    import ctypes
+    wl = make_workload("temporal", reduced=True)
+    r = wl.ref_views[0]
+    lab, S = wl.labels(r)
+    planes = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (wl.view(r).Y, wl.view(r).U, wl.view(r).V)]
+    host_labels = torch.from_numpy(lab).pin_memory()
+    m, c, n = _outputs(S)
+    cp = (ctypes.c_void_p * 3)(*[t.data_ptr() for t in planes])
+    pitch = (ctypes.c_int64 * 3)(*[t.stride(0) * t.element_size() for t in planes])
+    rc = ftv.ftv.lib.ftv_temporal_mask_static(wl.cams[r].width, wl.cams[r].height, 2, cp, pitch, cp, pitch, None,
+                                              None, host_labels.data_ptr(), S, 12, 4, 0, m.data_ptr(), c.data_ptr(),
+                                              n.data_ptr(), None, torch.cuda.current_stream().cuda_stream)
+    assert rc == ftv.FTV_ERR_INVALID_ARG
