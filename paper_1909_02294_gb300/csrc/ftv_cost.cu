@@ -99,7 +99,8 @@ struct TexelOps<FMT_U16X4> {
 //   kRect     unit with h0 = 1, h1 = 0, h3 = 0, h4 = 1, |h5| < 0.25 (rectified rigs: the row is kept):
 //             X = fma(1, x, fma(0, y, h2)) is x + h2 rounded once, and Y = y + h5 rounded once lies
 //             within 0.25 + 2^-9 of the integer y < 2^15, so floor(Y + 0.5) is exactly y;
-//   kShift    rectified, and the column is x + D for every x < 2^15 with D = floor(h2 + 0.5): s = x + h2
+//   kShift    rectified, and the column is x + D for every x < 2^15 with D = floor(h2 + 0.5) (FP64-precision
+//             units: see shift_fp64; the FP32 contract: s = x + h2
 //             rounded is within 2^-24 (|x| + |h2|) of x + h2; when h2 + 0.5 lies more than twice that
 //             from every integer (checked at staging with |x| < 2^15, |h2| < 2^20), s + 0.5 lies more than
 //             2^-24 from every integer, where rounding s + 0.5 cannot cross one (below 1 in magnitude its
@@ -109,14 +110,19 @@ struct TexelOps<FMT_U16X4> {
 //             sample's index is then the pixel's y * W + x plus D, the row needs no test, and the column
 //             test is -D <= x < w - D, staged as floats (h[6], h[7]) with D in h[8];
 //   kOut      affine with 1/h8 not finite and positive, or no pixel of the item's tile can reach the view
-//             (box_out_of_view): every sample is out of view.
+//             (box_class): every sample is out of view;
+//   kIn       projective, and at every pixel of the item's tile Wz > 2^-92 and the sample rounds into the
+//             view (box_class): r = 1/Wz is a normal reciprocal (no subnormal scaling) and neither the
+//             finite-reciprocal test nor a range test can fail, so none is made;
+//   kFront    projective, Wz > 2^-92 at every pixel of the tile (box_class): the reciprocal needs no
+//             subnormal scaling and is finite and positive; the range tests remain.
 // All of them give bit-identical results to the general sequence; they only skip work whose result
 // is known exactly.
 struct __align__(16) HEntry {
     float h[9];
     uint32_t w, h_, pm;
 };
-enum : uint32_t { kGeneral = 0, kAffine = 1, kUnit = 2, kOut = 3, kRect = 4, kSlow = 5, kShift = 6 };
+enum : uint32_t { kGeneral = 0, kAffine = 1, kUnit = 2, kOut = 3, kRect = 4, kSlow = 5, kShift = 6, kIn = 7, kFront = 8 };
 
 // FP64-projection entries (kKindPrecise) stage local-frame coefficients in HEntry::h (stage_precise) and
 // this alongside: the integer column u0 and row v0 the frame is shifted by, and the tie-test thresholds.
@@ -128,34 +134,6 @@ constexpr uint32_t kPitchMask = (1u << 28) - 1u;
 
 __device__ __forceinline__ bool finite_positive(float r) {
     return (unsigned)(__float_as_int(r) - 1) < 0x7f7fffffu;
-}
-
-// The contract's r = 1/w is the IEEE round-to-nearest reciprocal. On devices where an exhaustive
-// start-up comparison found it equal, for every float w in [2^-126, 2^126), to one Newton-Raphson step
-// on the hardware estimate r0 ~ 1/w, namely r = r0 + r0 (1 - w r0) with both steps fused multiply-adds
-// (Markstein's method), the kernel uses that step:
-//   rcp_newton: exact for w in [2^-126, 2^126);
-//   rcp_scaled: any w. Positive subnormal w (and w <= 0) are first scaled by 2^64, which is exact,
-//               and the result scaled back; 1/w = 2^64 / (2^64 w) and power-of-two scaling commutes
-//               with round-to-nearest, including the overflow to infinity of 1/w for w < 2^-128. For
-//               w <= 0 or NaN the result is non-positive or NaN, which the in-view test rejects, as it
-//               rejects the IEEE reciprocal of such w.
-// w >= 2^126 cannot occur: the host bounds |h| <= 2^100, so |Wz| < 2^117.
-__device__ __forceinline__ float rcp_newton(float w) {
-    float r0;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(w));
-    return __fmaf_rn(r0, __fmaf_rn(-w, r0, 1.0f), r0);
-}
-
-__device__ __forceinline__ float rcp_scaled(float w) {
-    const bool small = w < 0x1p-126f;
-    const float r = rcp_newton(small ? w * 0x1p64f : w);
-    return small ? r * 0x1p64f : r;
-}
-
-template <bool FAST>
-__device__ __forceinline__ float contract_rcp(float w) {
-    return FAST ? rcp_scaled(w) : __frcp_rn(w);
 }
 
 // Position of one sample: reference pixel (x, y) through homography e.h into one neighbour view.
@@ -217,20 +195,34 @@ __device__ __forceinline__ void accumulate(int& m, bool ok, const void* tex, int
     }
 }
 
-// True when no pixel of the box [x0, x1] x [y0, y1] can sample the wv x hv view under the FP32 contract.
-// At every corner the homography must put the point left of u = -1 (X + Wz < 0), right of u = wv
-// (X - wv Wz > 0), above v = -1 or below v = hv (the same with Y), or behind the camera (Wz < 0), each
-// with a margin of 2^-20 times the magnitude of its terms. The contract's FP32 evaluation at any pixel
-// of the box is within 2^-23 of those magnitudes of the exact value, and each condition together with
-// that error bound is convex in the pixel position, so holding at the four corners it holds at every
-// pixel of the box: there a point left of u = -1 has u + 0.5 < 0 after rounding (a column below 0), one
-// right of u = wv rounds to a column of at least wv (likewise for rows), and one behind the camera has
-// Wz <= 0, which the contract counts as out of view. |h| <= 2^100 keeps every term finite; an overflow
-// or a NaN fails the comparisons and keeps the box.
-__device__ __forceinline__ bool box_out_of_view(const float* h, float x0, float x1, float y0, float y1, float wv,
-                                                float hv) {
+// Classifies a projective entry for the pixel box [x0, x1] x [y0, y1] (x, y >= 0) under the FP32 contract,
+// from the homography evaluated at the box's four corners:
+//   kOut     no pixel can sample the wv x hv view. At every corner the point lies left of u = -1 (X + Wz < 0),
+//            right of u = wv (X - wv Wz > 0), above v = -1 or below v = hv (the same with Y), or behind the
+//            camera (Wz < 0);
+//   kIn      at every pixel Wz > 2^-92 and the sample rounds into the view. At every corner Wz is positive
+//            (and above 2^-90), X and Y are positive, and (wv - 1) Wz - X and (hv - 1) Wz - Y are positive;
+//   kFront   at every pixel Wz > 2^-92 (the corners as for kIn, Wz only);
+//   kGeneral otherwise.
+// Each corner condition carries a margin of 2^-20 times the magnitude of its terms (sx = |h0| x + |h1| y +
+// |h2|, likewise sy, sz). Why the conclusions hold at every pixel: the contract's two fused multiply-adds
+// put X, Y and Wz within 2^-23 of those magnitudes of their exact values, at any pixel and at the corners.
+// With the margin, each corner condition implies, in exact arithmetic, a condition linear (convex, for
+// kOut) in the pixel position with half the margin (for Wz: Wz - 2^-22 sz - 2^-92 > 0), which therefore
+// holds at every pixel of the box, and there the FP32 value keeps the sign the conclusion needs:
+//   Wz_f32 > 2^-92, so r = 1/Wz is finite, positive and the reciprocal of a normal float;
+//   X_f32 >= 0, so u = X r >= 0 and floor(u + 0.5) >= 0;
+//   X_f32 <= (wv - 1) Wz_f32, so u <= (wv - 1)(1 + 2^-23) < wv - 1 + 2^-7 (wv <= 2^15), u + 0.5 rounds
+//   below wv and floor(u + 0.5) <= wv - 1 (the same for rows);
+//   for kOut as before: a point left of u = -1 has u + 0.5 < 0 after rounding, one right of u = wv rounds to
+//   a column of at least wv, one behind the camera has Wz <= 0.
+// |h| <= 2^100 keeps every term finite; an overflow or a NaN fails the comparisons and gives kGeneral.
+__device__ __forceinline__ uint32_t box_class(const float* h, float x0, float x1, float y0, float y1, float wv,
+                                              float hv) {
     const float m = 0x1p-20f;
+    const float wv1 = wv - 1.0f, hv1 = hv - 1.0f;
     bool left = true, right = true, top = true, bottom = true, behind = true;
+    bool front = true, inside = true;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const float x = (k & 1) ? x1 : x0, y = (k & 2) ? y1 : y0;  // x, y >= 0
@@ -247,8 +239,37 @@ __device__ __forceinline__ bool box_out_of_view(const float* h, float x0, float 
         top = top && tt < -m * (sy + sz + fabsf(tt));
         bottom = bottom && tb > m * (sy + hv * sz + fabsf(tb));
         behind = behind && Z < -m * (sz + fabsf(Z));
+        front = front && Z > fmaxf(m * (sz + fabsf(Z)), 0x1p-90f);
+        const float ir = __fmaf_rn(wv1, Z, -X), ib = __fmaf_rn(hv1, Z, -Y);
+        inside = inside && X > m * (sx + fabsf(X)) && Y > m * (sy + fabsf(Y)) &&
+                 ir > m * (sx + wv1 * sz + fabsf(ir)) && ib > m * (sy + hv1 * sz + fabsf(ib));
     }
-    return left || right || top || bottom || behind;
+    if (left || right || top || bottom || behind) return kOut;
+    if (front) return inside ? kIn : kFront;
+    return kGeneral;
+}
+
+// Integer-shift entries of the FP64 projection (linear rigs with parallel axes): the unrounded homography
+// is exactly [[1, 0, h2], [0, 1, h5], [0, 0, 1]] with |h5| < 0.49 and |h2| < 2^20. The FP64 projection then
+// computes X = x + h2 (one rounding; 1 * x and 0 * y are exact), Wz = 1 and X / Wz = X exactly, and
+// floor(X + 0.5) rounded once more; likewise the row from y + h5. g = h2 + 0.5 is exact (|h2| < 2^20), and
+// with D = floor(g):
+//   g an integer: x + h2 = x + D - 0.5 and x + D are exact, so the column is x + D;
+//   otherwise the two roundings move x + h2 + 0.5 by less than 2^-31 (|x + h2 + 0.5| < 2^21, unit roundoff
+//   2^-53), so when g lies more than 2^-30 from every integer the column is floor(x + g) = x + D.
+// The row is y: y + h5 + 0.5 lies in (y + 0.01, y + 0.99) and moves by less than 2^-35.
+// Then every pixel's sample is (x + D, y), in view exactly when 0 <= x + D < wv (the view being at least as
+// tall as the reference). Returns whether the entry has this form, with D.
+__device__ __forceinline__ bool shift_fp64(const double* __restrict__ hg, int& D) {
+    const double h0 = __ldg(&hg[0]), h1 = __ldg(&hg[1]), h2 = __ldg(&hg[2]), h3 = __ldg(&hg[3]), h4 = __ldg(&hg[4]),
+                 h5 = __ldg(&hg[5]), h6 = __ldg(&hg[6]), h7 = __ldg(&hg[7]), h8 = __ldg(&hg[8]);
+    if (!(h0 == 1.0 && h1 == 0.0 && h3 == 0.0 && h4 == 1.0 && h6 == 0.0 && h7 == 0.0 && h8 == 1.0 && fabs(h5) < 0.49 &&
+          fabs(h2) < 0x1p20))
+        return false;
+    const double g = h2 + 0.5, f = floor(g), r = g - f;
+    if (!(r == 0.0 || fmin(r, 1.0 - r) > 0x1p-30)) return false;
+    D = (int)f;
+    return true;
 }
 
 // Stages one (neighbour, label) entry of an FP64-precision unit for a tile whose pixels lie in the box
@@ -388,6 +409,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
     __shared__ int s_item, s_k0, s_k1, s_culled;
     __shared__ int s_box[4];  // the tile's pixel box: x min, x max, y min, y max
     __shared__ PEntry sP[precise_kind(KIND) ? kHEntries : 1];
+    __shared__ uint8_t sOrd[KIND == kKindProjective ? kHEntries : 1];  // per label: neighbours to visit
+    __shared__ int sCnt[KIND == kKindProjective ? kMaxLB : 1];         // per label: kIn | kFront << 8 | kGeneral << 16
     unsigned n_recomputed = 0;  // FP64-precision evaluations computed in double precision by this thread
 
     const int tid = threadIdx.x, lane = tid & 31;
@@ -509,9 +532,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
             }
         }
 
-        // An entry whose neighbour view no pixel of the tile can reach (box_out_of_view, on the staged
-        // coefficients) takes the penalty for every pixel, without sampling: it becomes an all-out entry.
-        // Only the projective-only instantiation does this: on a rectified rig an out-of-view sample is
+        // An entry whose neighbour view no pixel of the tile can reach (box_class, on the staged coefficients)
+        // takes the penalty for every pixel, without sampling: it becomes an all-out entry, which the pixel
+        // loop does not visit. box_class also marks the entries whose samples all land in view (kIn) or in
+        // front of the camera (kFront), which skip the tests they cannot fail. Only the projective-only
+        // instantiation does this: on a rectified rig an out-of-view sample is
         // already cheap, and there the test cost more than it saved (1920x1080 linear 8-view rig: 7.8 % of
         // the evaluations culled, 31.1 against 30.9 ms).
         // FP64-precision units stage their entries here, once the box is known (stage_precise), and move the
@@ -542,12 +567,21 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                 if (s_box[0] <= s_box[1]) {
                     const float bx0f = (float)s_box[0], bx1f = (float)s_box[1], by0f = (float)s_box[2],
                                 by1f = (float)s_box[3];
+                    // Slots past the end of the unit's last tile hold no pixel (their result is discarded);
+                    // they take the box's first corner, so that every slot lies in the box and the kIn
+                    // path's unchecked gathers stay inside the view for them too.
+#pragma unroll
+                    for (int j = 0; j < kPPT; ++j)
+                        if (key[j] == kSentinel) {
+                            px[j] = bx0f;
+                            py[j] = by0f;
+                        }
                     for (int e = tid; e < nh; e += kThreads) {
                         HEntry& E = sH[e];
-                        if ((E.pm >> 28) == kGeneral &&
-                            box_out_of_view(E.h, bx0f, bx1f, by0f, by1f, (float)E.w, (float)E.h_)) {
-                            E.pm = (E.pm & kPitchMask) | ((uint32_t)kOut << 28);
-                            atomicAdd(&s_culled, 1);
+                        if ((E.pm >> 28) == kGeneral) {
+                            const uint32_t cls = box_class(E.h, bx0f, bx1f, by0f, by1f, (float)E.w, (float)E.h_);
+                            E.pm = (E.pm & kPitchMask) | (cls << 28);
+                            if (cls == kOut) atomicAdd(&s_culled, 1);
                         }
                     }
                 }
@@ -561,22 +595,52 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                     const int n = e / LBa, l = e - n * LBa;
                     HEntry& E = sH[e];
                     const int wv = nbrs[n].w, hv = nbrs[n].h;
-                    const uint32_t mode = stage_precise(&Jp->H64[((int64_t)n * L + d0 + l) * 9], fx0, fy0, rx, ry, wv,
-                                                        hv, E.h, sP[e]);
+                    const double* hg = &Jp->H64[((int64_t)n * L + d0 + l) * 9];
+                    int D = 0;
+                    uint32_t mode;
+                    if (KIND == kKindPreciseMixed && nbrs[n].pitch == W && hv >= Jp->Href && shift_fp64(hg, D)) {
+                        // every pixel's FP64 column is x + D and its row y: bounds on the local x' = x - fx0
+                        mode = kShift;
+                        E.h[6] = (float)(-D - fx0);
+                        E.h[7] = (float)(wv - D - fx0);
+                        E.h[8] = __int_as_float(D);
+                    } else {
+                        mode = stage_precise(hg, fx0, fy0, rx, ry, wv, hv, E.h, sP[e]);
+                    }
                     E.w = (uint32_t)wv;
                     E.h_ = (uint32_t)hv;
                     E.pm = (uint32_t)nbrs[n].pitch | (mode << 28);
                     if (mode == kOut) atomicAdd(&s_culled, 1);
                 }
+                // every slot, an empty one too (pixel (0, 0), rowx 0), so that its local coordinates, its row
+                // index and the FP64 projection's arguments name the same pixel of the reference
 #pragma unroll
-                for (int j = 0; j < kPPT; ++j)
-                    if (key[j] != kSentinel) {
-                        px[j] = (float)((int)px[j] - fx0);
-                        py[j] = (float)(iy[j] - fy0);
-                    }
+                for (int j = 0; j < kPPT; ++j) {
+                    px[j] = (float)((int)px[j] - fx0);
+                    py[j] = (float)(iy[j] - fy0);
+                }
             }
             __syncthreads();
             if (tid == 0 && s_culled > 0) atomicAdd(&plan->culled, (unsigned long long)s_culled * (unsigned)(w1 - w0));
+            if constexpr (KIND == kKindProjective) {
+                // per label, the neighbours to visit grouped by class (kIn, then kFront, then kGeneral; kOut
+                // entries are left out): one warp per label, N <= 32
+                for (int l = tid >> 5; l < LBa; l += kThreads / 32) {
+                    const uint32_t mode = lane < N ? (sH[lane * LBa + l].pm >> 28) : (uint32_t)kOut;
+                    const unsigned mi = __ballot_sync(kFull, mode == kIn);
+                    const unsigned mf = __ballot_sync(kFull, mode == kFront);
+                    const unsigned mg = __ballot_sync(kFull, mode == kGeneral);
+                    const unsigned lt = (1u << lane) - 1u;
+                    const int ci = __popc(mi), cf = __popc(mf);
+                    int pos = -1;
+                    if (mode == kIn) pos = __popc(mi & lt);
+                    else if (mode == kFront) pos = ci + __popc(mf & lt);
+                    else if (mode == kGeneral) pos = ci + cf + __popc(mg & lt);
+                    if (pos >= 0) sOrd[l * N + pos] = (uint8_t)lane;
+                    if (lane == 0) sCnt[l] = ci | (cf << 8) | (__popc(mg) << 16);
+                }
+                __syncthreads();
+            }
         }
 
         for (int l = 0; l < LBa; ++l) {
@@ -584,7 +648,66 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
 #pragma unroll
             for (int j = 0; j < kPPT; ++j)
                 m[j] = (COMB == FTV_COMBINE_MIN && N > 0) ? (PF ? penalty : INT_MAX) : 0;
-            for (int n = 0; n < N; ++n) {
+            if constexpr (KIND == kKindProjective) {
+                const int cnt = sCnt[l];
+                const int ci = cnt & 0xff, cf = ci + ((cnt >> 8) & 0xff), cg = cf + (cnt >> 16);
+                const uint8_t* ord = &sOrd[l * N];
+                for (int k = 0; k < ci; ++k) {  // every pixel's sample is in view
+                    const int n = ord[k];
+                    const float4* e4 = reinterpret_cast<const float4*>(&sH[n * LBa + l]);
+                    const float4 ha = e4[0], hb = e4[1], hc = e4[2];
+                    const void* tex = sBase[n];
+                    const int pitch = (int)(__float_as_uint(hc.w) & kPitchMask);
+#pragma unroll
+                    for (int j = 0; j < kPPT; ++j) {
+                        const float X = __fmaf_rn(ha.x, px[j], __fmaf_rn(ha.y, py[j], ha.z));
+                        const float Yh = __fmaf_rn(ha.w, px[j], __fmaf_rn(hb.x, py[j], hb.y));
+                        const float Wz = __fmaf_rn(hb.z, px[j], __fmaf_rn(hb.w, py[j], hc.x));
+                        const float r = contract_rcp_normal<FAST_RCP>(Wz);
+                        const int ui = __float2int_rd(__fadd_rn(__fmul_rn(X, r), 0.5f));
+                        const int vi = __float2int_rd(__fadd_rn(__fmul_rn(Yh, r), 0.5f));
+                        const int cst = TexelOps<FMT>::cost(tex, vi * pitch + ui, ra[j], rb[j], rc[j]);
+                        m[j] = COMB == FTV_COMBINE_MIN ? min(m[j], cst) : m[j] + cst;
+                    }
+                }
+                for (int k = ci; k < cf; ++k) {  // Wz proven positive and normal: range tests only
+                    const int n = ord[k];
+                    const float4* e4 = reinterpret_cast<const float4*>(&sH[n * LBa + l]);
+                    const float4 ha = e4[0], hb = e4[1], hc = e4[2];
+                    const void* tex = sBase[n];
+                    const int pitch = (int)(__float_as_uint(hc.w) & kPitchMask);
+#pragma unroll
+                    for (int j = 0; j < kPPT; ++j) {
+                        const float X = __fmaf_rn(ha.x, px[j], __fmaf_rn(ha.y, py[j], ha.z));
+                        const float Yh = __fmaf_rn(ha.w, px[j], __fmaf_rn(hb.x, py[j], hb.y));
+                        const float Wz = __fmaf_rn(hb.z, px[j], __fmaf_rn(hb.w, py[j], hc.x));
+                        const float r = contract_rcp_normal<FAST_RCP>(Wz);
+                        const int ui = __float2int_rd(__fadd_rn(__fmul_rn(X, r), 0.5f));
+                        const int vi = __float2int_rd(__fadd_rn(__fmul_rn(Yh, r), 0.5f));
+                        const bool ok = ((unsigned)ui < __float_as_uint(hc.y)) & ((unsigned)vi < __float_as_uint(hc.z));
+                        accumulate<FMT, COMB, PF>(m[j], ok, tex, vi * pitch + ui, ra[j], rb[j], rc[j], penalty);
+                    }
+                }
+                for (int k = cf; k < cg; ++k) {  // the contract's sequence as written
+                    const int n = ord[k];
+                    const float4* e4 = reinterpret_cast<const float4*>(&sH[n * LBa + l]);
+                    const float4 ha = e4[0], hb = e4[1], hc = e4[2];
+                    const void* tex = sBase[n];
+                    const int pitch = (int)(__float_as_uint(hc.w) & kPitchMask);
+#pragma unroll
+                    for (int j = 0; j < kPPT; ++j) {
+                        int idx;
+                        const bool ok = pos_general<FAST_RCP>(ha, hb, hc, pitch, px[j], py[j], idx);
+                        accumulate<FMT, COMB, PF>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty);
+                    }
+                }
+                if (!(COMB == FTV_COMBINE_MIN && PF) && cg < N) {  // entries out of view: the penalty each
+#pragma unroll
+                    for (int j = 0; j < kPPT; ++j)
+                        m[j] = (COMB == FTV_COMBINE_MIN) ? min(m[j], penalty) : m[j] + (N - cg) * penalty;
+                }
+            }
+            for (int n = 0; n < (KIND == kKindProjective ? 0 : N); ++n) {
                 const float4* e4 = reinterpret_cast<const float4*>(&sH[n * LBa + l]);
                 const float4 hc = e4[2];
                 const void* tex = sBase[n];
@@ -605,10 +728,18 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                     } else if (mode == kSlow) {
 #pragma unroll
                         for (int j = 0; j < kPPT; ++j) {
-                            int ui = 0, vi = 0;
-                            const bool ok = project_fp64(h64, (int)px[j] + fx0, iy[j], wv, hv, &ui, &vi);
+                            const long long q = project_fp64_packed(h64, (int)px[j] + fx0, iy[j], wv, hv);
                             n_recomputed += key[j] != kSentinel;
-                            accumulate<FMT, COMB, PF>(m[j], ok, tex, vi * pitch + ui, ra[j], rb[j], rc[j], penalty);
+                            const int idx = (int)(q >> 32) * pitch + (int)(unsigned)q;
+                            accumulate<FMT, COMB, PF>(m[j], q >= 0, tex, idx, ra[j], rb[j], rc[j], penalty);
+                        }
+                    } else if (KIND == kKindPreciseMixed && mode == kShift) {
+                        const float4 hb = e4[1];  // (h4, h5, lower and upper bound of x')
+                        const int D = __float_as_int(hc.x);
+#pragma unroll
+                        for (int j = 0; j < kPPT; ++j) {
+                            const bool ok = (px[j] >= hb.z) & (px[j] < hb.w);
+                            accumulate<FMT, COMB, PF>(m[j], ok, tex, rowx[j] + D, ra[j], rb[j], rc[j], penalty);
                         }
                     } else if (KIND == kKindPreciseMixed && mode == kRect) {
                         const float a2 = e4[0].z;
@@ -621,7 +752,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                             int ui = __float2int_rz(fu) + u0, vi = iy[j] + dv0;
                             bool ok;
                             if (fabsf(__fsub_rn(__fsub_rn(tu, fu), 0.5f)) >= pe.z) {
-                                ok = project_fp64(h64, (int)px[j] + fx0, iy[j], wv, hv, &ui, &vi);
+                                const long long q = project_fp64_packed(h64, (int)px[j] + fx0, iy[j], wv, hv);
+                                ok = q >= 0;
+                                ui = (int)(unsigned)q;
+                                vi = (int)(q >> 32);
                                 n_recomputed += key[j] != kSentinel;
                             } else {
                                 ok = ((unsigned)ui < (unsigned)wv) & ((unsigned)vi < (unsigned)hv);
@@ -646,7 +780,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                             int ui = __float2int_rz(fu) + u0, vi = __float2int_rz(fv) + v0;
                             bool ok;
                             if (near) {
-                                ok = project_fp64(h64, (int)px[j] + fx0, iy[j], wv, hv, &ui, &vi);
+                                const long long q = project_fp64_packed(h64, (int)px[j] + fx0, iy[j], wv, hv);
+                                ok = q >= 0;
+                                ui = (int)(unsigned)q;
+                                vi = (int)(q >> 32);
                                 n_recomputed += key[j] != kSentinel;
                             } else {
                                 ok = ((unsigned)ui < (unsigned)wv) & ((unsigned)vi < (unsigned)hv);
@@ -670,12 +807,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                                                  idx);
                         accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty);
                     }
-                } else if (KIND == kKindProjective && mode == kOut) {
-                    if (!(COMB == FTV_COMBINE_MIN && PF)) {
-#pragma unroll
-                        for (int j = 0; j < kPPT; ++j) m[j] = (COMB == FTV_COMBINE_MIN) ? min(m[j], penalty) : m[j] + penalty;
-                    }
-                } else if (KIND == kKindProjective || (KIND == kKindMixed && mode == kGeneral)) {
+                } else if (KIND == kKindMixed && mode == kGeneral) {
                     const float4 ha = e4[0], hb = e4[1];
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {

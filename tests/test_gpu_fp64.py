@@ -45,14 +45,16 @@ def _assert_equal(got, ref, what):
     assert bad == 0, f"{what}: {bad} of {ref.size} entries differ"
 
 
-def _near_tie(W=256, H=48, L=8):
+def _near_tie(W=256, H=48, L=8, wide=False):
     """Two cameras 0.1 m apart, f = 100 px; depths put every label's disparity 1e-7 beyond a half-integer
-    (10 iz_d = 10.5000001 + d), where the FP32 contract rounds the other way."""
+    (10 iz_d = 10.5000001 + d), where the FP32 contract rounds the other way. wide: the neighbour image is 8
+    columns wider (its principal point 4 px further right, so the offsets stay 1e-7 beyond half-integers)."""
     f, B = 100.0, 0.1
+    Wv = W + 8 if wide else W
     cams = [synth.Camera(synth.intrinsics(f, W, H), np.eye(3), np.zeros(3), W, H),
-            synth.Camera(synth.intrinsics(f, W, H), np.eye(3), -np.array([B, 0.0, 0.0]), W, H)]
+            synth.Camera(synth.intrinsics(f, Wv, H), np.eye(3), -np.array([B, 0.0, 0.0]), Wv, H)]
     rng = np.random.default_rng(11)
-    views = [synth.View(*(rng.integers(0, 256, (H, W), dtype=np.uint8) for _ in range(3))) for _ in cams]
+    views = [synth.View(*(rng.integers(0, 256, (H, c.width), dtype=np.uint8) for _ in range(3))) for c in cams]
     lab, S = synth.grid_labels(W, H, 8, 2, seed=12)
     return cams, views, lab, S, L, 1.0 / ((10.5000001 + L - 1) / (f * B)), 1.0 / (10.5000001 / (f * B))
 
@@ -84,11 +86,13 @@ def test_fp64_volumes_bit_exact(name, reduced, combine):
     run.close()
 
 
-@pytest.mark.parametrize("combine", ["min", "sum"])
-def test_fp64_on_half_integer_disparities(combine):
-    """Every evaluation lies 1e-7 from a rounding boundary, far inside the FP32 bound: all of them go
-    through the FP64 path, and the volume differs from the FP32 contract's."""
-    cams, views, lab, S, L, zn, zf = _near_tie()
+@pytest.mark.parametrize("combine,wide", [("min", False), ("sum", False), ("min", True), ("sum", True)])
+def test_fp64_on_half_integer_disparities(combine, wide):
+    """Every evaluation lies 1e-7 from a rounding boundary, far inside the FP32 bound, and the volume differs
+    from the FP32 contract's. With equal image widths every entry is an exact FP64 integer shift (its offset
+    is more than 2^-30 from a half-integer): nothing is recomputed. With a wider neighbour image the shift
+    does not apply (the neighbour's row pitch differs), and every evaluation goes through the FP64 path."""
+    cams, views, lab, S, L, zn, zf = _near_tie(wide=wide)
     comb = ftv.FTV_COMBINE_MIN if combine == "min" else ftv.FTV_COMBINE_SUM
     vols = {}
     for prec in (ftv.FTV_PRECISION_FP32, FP64):
@@ -100,7 +104,10 @@ def test_fp64_on_half_integer_disparities(combine):
         vols[prec] = cost.cpu().numpy()
         if prec == FP64:
             n_rec, n_cull = ftv.ftv_fp64_recomputed(ctx), ftv.ftv_culled_evaluations(ctx)
-            assert n_rec + n_cull == lab.size * L and n_rec > 0.9 * lab.size * L
+            if wide:
+                assert n_rec + n_cull == lab.size * L and n_rec > 0.9 * lab.size * L
+            else:
+                assert n_rec == 0
         else:
             assert ftv.ftv_fp64_recomputed(ctx) == 0
         ctx.close()
