@@ -293,6 +293,144 @@ __global__ void __launch_bounds__(kCentreThreads, 4) centre_table3_kernel(Centre
     }
 }
 
+// One 3x3 window pair's sum for 4-byte texels: t[i] the neighbour's packed texels (Y | Cb << sh | Cr << 2 sh),
+// ref[i] the reference's samples (Y, Cb, Cr, unused), read from shared memory (one broadcast load each).
+template <int FMT>
+__device__ __forceinline__ int window_sum(const uint32_t* t, const int4* ref) {
+    constexpr int sh = FMT == FMT_P10 ? 10 : 8;
+    constexpr uint32_t mk = (1u << sh) - 1u;
+    unsigned m = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int4 r = ref[i];
+        m = __sad(t[i] & mk, (unsigned)r.x, __sad((t[i] >> sh) & mk, (unsigned)r.y, __sad(t[i] >> (2 * sh), (unsigned)r.z, m)));
+    }
+    return (int)m;
+}
+
+// Projection of a segment centre through entry j of the FP32 table (the contract): (ui, vi) and whether the
+// centre is in view.
+template <bool FAST>
+__device__ __forceinline__ bool project_centre(const CentreArgs& a, int j, int2 c, const NbrView& nv, int& ui,
+                                               int& vi) {
+    if (c.x < 0) return false;
+    const float* h = a.H + (int64_t)j * 9;
+    const float x = (float)c.x, y = (float)c.y;
+    const float X = __fmaf_rn(__ldg(&h[0]), x, __fmaf_rn(__ldg(&h[1]), y, __ldg(&h[2])));
+    const float Yh = __fmaf_rn(__ldg(&h[3]), x, __fmaf_rn(__ldg(&h[4]), y, __ldg(&h[5])));
+    const float Wz = __fmaf_rn(__ldg(&h[6]), x, __fmaf_rn(__ldg(&h[7]), y, __ldg(&h[8])));
+    if (!(Wz > 0.0f)) return false;
+    const float r = contract_rcp<FAST>(Wz);
+    const float fu = floorf(__fadd_rn(__fmul_rn(X, r), 0.5f));
+    const float fv = floorf(__fadd_rn(__fmul_rn(Yh, r), 0.5f));
+    if (!(fu >= 0.0f && fu <= (float)(nv.w - 1) && fv >= 0.0f && fv <= (float)(nv.h - 1))) return false;
+    ui = (int)fu;
+    vi = (int)fv;
+    return true;
+}
+
+// The paper's 3x3 window for 4-byte texels (8- and 10-bit samples) in FP32-contract contexts: the results
+// of centre_table_kernel. The kernel is latency-bound (each entry is a dependent chain: homography,
+// projection, nine gathers), so each thread software-pipelines its entries: the next entry's homography
+// loads and projection are issued while the current entry's nine gathers are in flight. The segment's
+// reference samples stay in shared memory (27 values, read by broadcast loads), which leaves registers for
+// the pipeline. The reciprocal is the Newton-Raphson step where the start-up check found it exact (FAST).
+// Windows that touch an image border take the checked loop.
+struct CentreProj {
+    int j, k, ui, vi;
+    bool in, fast;
+};
+
+template <bool FAST>
+__device__ __forceinline__ CentreProj centre_proj(const CentreArgs& a, const NbrView* snb, int j, int nent, int2 c,
+                                                  bool ref_in) {
+    CentreProj p{j, 0, 0, 0, false, false};
+    if (j >= nent) return p;
+    p.k = a.L == 1 ? j : (int)__umulhi((uint32_t)j, a.l_magic);
+    const NbrView& nv = snb[p.k];
+    p.in = project_centre<FAST>(a, j, c, nv, p.ui, p.vi);
+    p.fast = p.in && ref_in && p.ui >= 1 && p.ui + 1 < nv.w && p.vi >= 1 && p.vi + 1 < nv.h;
+    return p;
+}
+
+template <int FMT, bool FAST>
+__global__ void __launch_bounds__(kCentreThreads, 4) centre_table3p_kernel(CentreArgs a) {
+    __shared__ int4 sref[9];
+    __shared__ int s_refin;
+    __shared__ NbrView snb[FTV_MAX_NBRS];
+    __shared__ const int32_t* slab[FTV_MAX_NBRS];
+    constexpr int sh = FMT == FMT_P10 ? 10 : 8;
+    constexpr uint32_t mk = (1u << sh) - 1u;
+    const int tid = threadIdx.x;
+    for (int k = tid; k < a.N; k += kCentreThreads) {
+        snb[k] = a.nbrs[k];
+        slab[k] = a.labels_v[k];
+    }
+    const int nent = a.L * a.N;
+    const uint32_t* tex_ref = static_cast<const uint32_t*>(a.ref_tex);
+    for (int s = blockIdx.x; s < a.S; s += gridDim.x) {
+        const int2 c = a.centre[s];
+        __syncthreads();  // the previous segment's window is no longer read
+        if (tid < 32) {
+            bool in = false;
+            if (tid < 9) {
+                const int rx = c.x - 1 + tid % 3, ry = c.y - 1 + tid / 3;
+                in = c.x >= 0 && rx >= 0 && rx < a.W && ry >= 0 && ry < a.H_;
+                const uint32_t w = in ? __ldg(tex_ref + (int64_t)ry * a.W + rx) : 0u;
+                sref[tid] = make_int4((int)(w & mk), (int)((w >> sh) & mk), (int)(w >> (2 * sh)), 0);
+            }
+            const unsigned inside = __ballot_sync(kFull, in);
+            if (tid == 0) s_refin = inside == 0x1ffu;
+        }
+        __syncthreads();
+        const bool ref_in = s_refin != 0;
+        int32_t* mrow = a.m + (int64_t)s * nent;
+        int32_t* srow = a.sp + (int64_t)s * nent;
+        CentreProj cur = centre_proj<FAST>(a, snb, tid, nent, c, ref_in);
+        while (cur.j < nent) {
+            const NbrView& nv = snb[cur.k];
+            uint32_t t[9];
+            if (cur.fast) {
+                const uint32_t* base = static_cast<const uint32_t*>(nv.texels) + ((int64_t)(cur.vi - 1) * nv.pitch + (cur.ui - 1));
+#pragma unroll
+                for (int wy = 0; wy < 3; ++wy)
+#pragma unroll
+                    for (int wx = 0; wx < 3; ++wx) t[wy * 3 + wx] = __ldg(base + (int64_t)wy * nv.pitch + wx);
+            }
+            // the next entry's homography and projection while the gathers are in flight
+            const CentreProj nxt = centre_proj<FAST>(a, snb, cur.j + kCentreThreads, nent, c, ref_in);
+            int m;
+            if (cur.fast) {
+                m = window_sum<FMT>(t, sref);
+            } else if (!cur.in) {
+                m = 9 * a.penalty;
+            } else {
+                m = 0;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const int qx = cur.ui - 1 + i % 3, qy = cur.vi - 1 + i / 3;
+                    const int rx = c.x - 1 + i % 3, ry = c.y - 1 + i / 3;
+                    const bool rin = rx >= 0 && rx < a.W && ry >= 0 && ry < a.H_;
+                    if (!rin || qx < 0 || qx >= nv.w || qy < 0 || qy >= nv.h) {
+                        m += a.penalty;
+                        continue;
+                    }
+                    const uint32_t q = __ldg(static_cast<const uint32_t*>(nv.texels) + (int64_t)qy * nv.pitch + qx);
+                    const int4 r = sref[i];
+                    m += (int)__sad(q & mk, (unsigned)r.x, __sad((q >> sh) & mk, (unsigned)r.y,
+                                                                  __sad(q >> (2 * sh), (unsigned)r.z, 0u)));
+                }
+            }
+            const int d = cur.j - cur.k * a.L;
+            const int64_t out = (int64_t)d * a.N + cur.k;
+            mrow[out] = m;
+            const int32_t* lv = slab[cur.k];
+            srow[out] = (cur.in && lv) ? lv[(int64_t)cur.vi * nv.w + cur.ui] : -1;
+            cur = nxt;
+        }
+    }
+}
+
 }  // namespace
 }  // namespace ftv
 
@@ -318,6 +456,7 @@ extern "C" ftv_status ftv_centre_table(ftv_ctx* ctx, const void* const* d_planes
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != ctx->device) cudaSetDevice(ctx->device);
+    NvtxRange range("ftv_centre_table");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
     for (int v = 0; v < ctx->n_views && e == cudaSuccess; ++v) {
@@ -365,9 +504,18 @@ extern "C" ftv_status ftv_centre_table(ftv_ctx* ctx, const void* const* d_planes
         const int64_t total = (int64_t)S * ctx->L * r.n_nbrs;
         const int blocks = std::max(1, std::min(S, ctx->n_sm * 8));
         if (total > 0) {
-            if (window == 3 && ctx->fmt == FMT_P10) centre_table3_kernel<FMT_P10><<<blocks, kCentreThreads, 0, s>>>(a);
-            else if (window == 3 && ctx->fmt == FMT_U8X4)
+            const bool fast = ctx->fast_rcp, fp32 = ctx->precision == FTV_PRECISION_FP32;
+            if (window == 3 && !fp32 && ctx->fmt == FMT_P10) centre_table3_kernel<FMT_P10><<<blocks, kCentreThreads, 0, s>>>(a);
+            else if (window == 3 && !fp32 && ctx->fmt == FMT_U8X4)
                 centre_table3_kernel<FMT_U8X4><<<blocks, kCentreThreads, 0, s>>>(a);
+            else if (window == 3 && ctx->fmt == FMT_P10 && fast)
+                centre_table3p_kernel<FMT_P10, true><<<blocks, kCentreThreads, 0, s>>>(a);
+            else if (window == 3 && ctx->fmt == FMT_P10)
+                centre_table3p_kernel<FMT_P10, false><<<blocks, kCentreThreads, 0, s>>>(a);
+            else if (window == 3 && ctx->fmt == FMT_U8X4 && fast)
+                centre_table3p_kernel<FMT_U8X4, true><<<blocks, kCentreThreads, 0, s>>>(a);
+            else if (window == 3 && ctx->fmt == FMT_U8X4)
+                centre_table3p_kernel<FMT_U8X4, false><<<blocks, kCentreThreads, 0, s>>>(a);
             else if (window == 3) centre_table3_kernel<FMT_U16X4><<<blocks, kCentreThreads, 0, s>>>(a);
             else centre_table_kernel<<<blocks, kCentreThreads, 0, s>>>(a);
             ctx->launches++;
