@@ -114,33 +114,55 @@ __device__ int block_exclusive_scan(int v, int* total) {
 
 __device__ __forceinline__ int64_t abs64(int64_t v) { return v < 0 ? -v : v; }
 
-// One block of 1024 threads: decide each segment's mask and compact the changed ones in order.
-__global__ void temporal_finalize_kernel(const int64_t* __restrict__ stats, int S, int nch, bool has_i, int t_p,
-                                         int t_i, uint8_t* __restrict__ mask, int32_t* __restrict__ changed,
-                                         int32_t* n_changed) {
-    const int per = (S + blockDim.x - 1) / blockDim.x;
-    const int b = threadIdx.x * per, e = min(S, b + per);
-    int cnt = 0;
-    for (int s = b; s < e; ++s) {
-        const int64_t* st = stats + (int64_t)s * kStat;
-        const int64_t n = st[0];
-        int m = FTV_MASK_CHANGED;
-        if (n > 0) {
-            bool okp = true, oki = has_i;
-            for (int c = 0; c < nch; ++c) {
-                okp = okp && abs64(st[1 + c]) < (int64_t)t_p * n;
-                oki = oki && abs64(st[4 + c]) < (int64_t)t_i * n;
-            }
-            m = okp ? FTV_MASK_REUSE_P : (oki ? FTV_MASK_REUSE_I : FTV_MASK_CHANGED);
+// The masks and the ordered list of changed segments, in two passes over blocks of kChunk segments.
+// decide: one thread per segment sets its mask; each block's count of changed segments goes to the spare
+// word (index 7) of the stats of its first segment. compact: each block adds up the counts of the blocks
+// before it, scans its own changed flags and writes their positions; the last block writes the total.
+constexpr int kChunk = 1024;
+
+__device__ __forceinline__ int decide(const int64_t* st, int nch, bool has_i, int t_p, int t_i) {
+    const int64_t n = st[0];
+    int m = FTV_MASK_CHANGED;
+    if (n > 0) {
+        bool okp = true, oki = has_i;
+        for (int c = 0; c < nch; ++c) {
+            okp = okp && abs64(st[1 + c]) < (int64_t)t_p * n;
+            oki = oki && abs64(st[4 + c]) < (int64_t)t_i * n;
         }
-        mask[s] = (uint8_t)m;
-        cnt += m == FTV_MASK_CHANGED;
+        m = okp ? FTV_MASK_REUSE_P : (oki ? FTV_MASK_REUSE_I : FTV_MASK_CHANGED);
     }
+    return m;
+}
+
+__global__ void __launch_bounds__(kChunk) temporal_decide_kernel(int64_t* __restrict__ stats, int S, int nch, bool has_i,
+                                                                 int t_p, int t_i, uint8_t* __restrict__ mask) {
+    const int s = blockIdx.x * kChunk + threadIdx.x;
+    int m = FTV_MASK_CHANGED;
+    if (s < S) {
+        m = decide(stats + (int64_t)s * kStat, nch, has_i, t_p, t_i);
+        mask[s] = (uint8_t)m;
+    }
+    const int cnt = __syncthreads_count(s < S && m == FTV_MASK_CHANGED);
+    if (threadIdx.x == 0) stats[(int64_t)blockIdx.x * kChunk * kStat + 7] = cnt;
+}
+
+__global__ void __launch_bounds__(kChunk) temporal_compact_kernel(const int64_t* __restrict__ stats, int S,
+                                                                  const uint8_t* __restrict__ mask,
+                                                                  int32_t* __restrict__ changed, int32_t* n_changed) {
+    __shared__ int s_base;
+    if (threadIdx.x == 0) s_base = 0;
+    __syncthreads();
+    int before = 0;  // changed segments of the blocks before this one
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += kChunk) before += (int)stats[(int64_t)b * kChunk * kStat + 7];
+    before = __reduce_add_sync(kFull, before);
+    if ((threadIdx.x & 31) == 0 && before) atomicAdd(&s_base, before);
+    __syncthreads();
+    const int s = blockIdx.x * kChunk + threadIdx.x;
+    const int flag = s < S && mask[s] == FTV_MASK_CHANGED;
     int total;
-    int run = block_exclusive_scan(cnt, &total);
-    for (int s = b; s < e; ++s)
-        if (mask[s] == FTV_MASK_CHANGED) changed[run++] = s;
-    if (threadIdx.x == 0) *n_changed = total;
+    const int pos = block_exclusive_scan(flag, &total);
+    if (flag) changed[s_base + pos] = s;
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *n_changed = s_base + total;
 }
 
 // One warp per listed segment: least-cost label, smallest on ties; masked segments adopt.
@@ -230,8 +252,10 @@ cudaError_t launch_temporal(const void* const* cur, const int64_t* cur_pitch, co
         *launches += 1;
     }
 #undef FTV_T
-    temporal_finalize_kernel<<<1, 1024, 0, s>>>(stats, S, nch, hi, t_p, t_i, mask, changed, n_changed);
-    *launches += 1;
+    const int chunks = std::max(1, (S + kChunk - 1) / kChunk);
+    if (S > 0) temporal_decide_kernel<<<chunks, kChunk, 0, s>>>(stats, S, nch, hi, t_p, t_i, mask);
+    temporal_compact_kernel<<<chunks, kChunk, 0, s>>>(stats, S, mask, changed, n_changed);
+    *launches += S > 0 ? 2 : 1;
     return cudaGetLastError();
 }
 

@@ -106,3 +106,33 @@ def test_temporal_sequence_at_full_size_through_the_stream_path():
     assert 0.03 < changed_total / (p_frames * sum(S)) < 0.4
     batch.close()
     ctx.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_temporal_mask_at_full_size(mode):
+    """ftv_temporal_mask on two 1920x1080 references of the temporal workload (20736 segments: the mask is
+    decided and the list compacted over many blocks), frame 1 against frame 0 as the previous P and as the
+    I frame, and without an I frame: mask, ordered list and count equal the oracle's (Sec. III-E)."""
+    wl = make_workload("temporal")
+    run = Run(wl)
+    for i in (0, 5):
+        r = wl.ref_views[i]
+        lab, S = wl.labels(r)
+        labels = dev(lab)
+        cur = [dev(a) for a in (wl.view(r, 1).Y, wl.view(r, 1).U, wl.view(r, 1).V)]
+        prev = [dev(a) for a in (wl.view(r, 0).Y, wl.view(r, 0).U, wl.view(r, 0).V)]
+        for with_i in (True, False):
+            mask = torch.empty(S, dtype=torch.uint8, device="cuda")
+            changed = torch.empty(S, dtype=torch.int32, device="cuda")
+            n = torch.empty(1, dtype=torch.int32, device="cuda")
+            ftv.ftv_temporal_mask(run.ctx, i, cur, prev, prev if with_i else None, labels, S, T_P, T_I, mode, mask,
+                                  changed, n)
+            assert run.check() == 0
+            m_ref, ch_ref, n_ref = oracle.temporal_mask(lab, S, wl.view(r, 1), wl.view(r, 0),
+                                                        wl.view(r, 0) if with_i else None, wl.sample_bytes, T_P, T_I,
+                                                        mode)
+            assert S > 4096 and 0 < n_ref < S
+            assert int(n.item()) == n_ref
+            assert np.array_equal(mask.cpu().numpy(), m_ref)
+            assert np.array_equal(changed.cpu().numpy()[:n_ref], ch_ref)
+    run.close()
