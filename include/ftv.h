@@ -314,6 +314,22 @@ FTV_API ftv_status ftv_stream_labels(const ftv_ctx* ctx, int32_t ref_index, cons
 FTV_API ftv_status ftv_stream_mask(const ftv_ctx* ctx, int32_t ref_index, const uint8_t** d_mask,
                                    const int32_t** d_n_changed);
 
+/*
+ * Checkpoint and resume of a stream's resident temporal state (Sec. III-E: the previous P and the I depth
+ * frame of every view, with the colours the temporal test compares against). The checkpoint holds the
+ * previous frame's and the I frame's packed views and, per reference, the per-segment labels of both.
+ * ftv_stream_state_bytes: size of the checkpoint of ctx's stream now (host only).
+ * ftv_stream_state_save: copy it into host_buf (bytes at least that size; pinned memory keeps the copy
+ * asynchronous) on `stream`; valid once the stream's work up to the call, and the copy, have completed.
+ * ftv_stream_state_load: restore it into a stream made by ftv_stream_init with the same cameras, references,
+ * label count, texel format and segment counts (the label maps themselves are ftv_stream_init's input);
+ * the next frame may then be a P frame. FTV_ERR_INVALID_ARG for a checkpoint of another shape or a short
+ * buffer. Asynchronous on `stream`; host_buf must stay valid until the copy completes.
+ */
+FTV_API ftv_status ftv_stream_state_bytes(const ftv_ctx* ctx, int64_t* bytes);
+FTV_API ftv_status ftv_stream_state_save(const ftv_ctx* ctx, void* host_buf, int64_t bytes, ftv_stream stream);
+FTV_API ftv_status ftv_stream_state_load(ftv_ctx* ctx, const void* host_buf, int64_t bytes, ftv_stream stream);
+
 /* Device pointer to a stream's list of the segments its last frame of reference ref_index re-estimated
  * (int32, in increasing order, *d_n_changed entries as reported by ftv_stream_mask; every segment for an I
  * frame). Sec. III-E: only these segments' costs are computed. Valid after that frame's batch completes. */

@@ -202,6 +202,7 @@ extern "C" ftv_status ftv_adjacency(ftv_ctx* ctx, int32_t ref_index, const void*
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != ctx->device) cudaSetDevice(ctx->device);
+    NvtxRange range("ftv_adjacency");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t one = std::max<int64_t>(ctx->penalty, 3LL * ((1LL << ctx->bit_depth) - 1));
     const int64_t mpc = ctx->combine == FTV_COMBINE_MIN ? one : one * std::max(1, r.n_nbrs);

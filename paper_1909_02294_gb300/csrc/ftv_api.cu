@@ -386,9 +386,11 @@ ftv_status ftv_cost_volume(ftv_ctx* ctx, const void* const* d_planes, const int6
         if (d_seg_list && d_seg_list[i] && (!d_n_listed || !d_n_listed[i])) return FTV_ERR_INVALID_ARG;
     }
     DeviceGuard g(ctx->device);
+    NvtxRange range("ftv_cost_volume");
     cudaError_t e = cudaSuccess;
     for (int v = 0; v < ctx->n_views && e == cudaSuccess; ++v) {
         if (!used[v]) continue;
+        NvtxRange stage("pack");
         e = launch_pack(d_planes + 3 * v, pitch_bytes + 3 * v, ctx->sample_bytes, ctx->bit_depth, ctx->fmt,
                         ctx->cams[v].width, ctx->cams[v].height,
                         static_cast<char*>(ctx->d_packed) + ctx->view_offset_bytes[v], ctx->d_status, s);
@@ -398,6 +400,7 @@ ftv_status ftv_cost_volume(ftv_ctx* ctx, const void* const* d_planes, const int6
     for (int i = 0; i < ctx->n_refs && e == cudaSuccess; ++i) {
         RefState& r = ctx->refs[i];
         if (d_labels && d_labels[i]) {
+            NvtxRange stage("segment index");
             e = launch_segment_index(d_labels[i], r.W, r.H, n_segments[i], max_pixel_cost(ctx, r.n_nbrs), r.d_offs,
                                      r.d_cursor, r.d_pix, ctx->d_status, s, &ctx->launches);
             r.S_indexed = n_segments[i];
@@ -436,11 +439,13 @@ ftv_status ftv_cost_volume(ftv_ctx* ctx, const void* const* d_planes, const int6
         J.fmt = ctx->fmt;
     }
     if (e == cudaSuccess) {
+        NvtxRange stage("plan");
         e = launch_plan(jobs.data(), ctx->n_refs, ctx->d_jobs, ctx->d_plan, s);
         ctx->launches++;
     }
     if (e == cudaSuccess && ctx->profiling) e = cudaEventRecord(ctx->ev_start, s);
     if (e == cudaSuccess) {
+        NvtxRange stage("cost kernel");
         const int per_sm = ctx->ctas_per_sm > 0 ? ctx->ctas_per_sm : ctx->cost_blocks_per_sm;
         e = launch_cost(ctx->d_jobs, ctx->d_plan, ctx->fmt, ctx->combine, ctx->fast_rcp, ctx->penalty_floor, ctx->kind,
                         0, 1, ctx->n_sm * per_sm, s);
@@ -472,6 +477,7 @@ ftv_status ftv_temporal_mask(ftv_ctx* ctx, int32_t ref_index, const void* const*
         if (d_iframe && (!d_iframe[c] || iframe_pitch[c] < row)) return FTV_ERR_INVALID_ARG;
     }
     DeviceGuard g(ctx->device);
+    NvtxRange range("ftv_temporal_mask");
     const cudaError_t e =
         launch_temporal(d_cur, cur_pitch, d_prev, prev_pitch, d_iframe, iframe_pitch, ctx->sample_bytes, d_labels, r.W,
                         r.H, n_segments, t_p, t_i, mode, ctx->d_tstats, d_mask, d_changed_list, d_n_changed,
@@ -488,6 +494,7 @@ ftv_status ftv_wta_depth(ftv_ctx* ctx, int32_t ref_index, const int32_t* d_cost,
     if (d_seg_list && !d_n_listed) return FTV_ERR_INVALID_ARG;
     if ((d_labels_pix == nullptr) != (d_depth_map == nullptr)) return FTV_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
+    NvtxRange range("ftv_wta_depth");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = launch_wta(d_cost, n_segments, ctx->L, d_mask, d_prev_label, d_iframe_label, d_seg_list,
                                d_n_listed, d_label_out, s);

@@ -607,6 +607,142 @@ ftv_status ftv_stream_mask(const ftv_ctx* ctx, int32_t ref_index, const uint8_t*
     return FTV_OK;
 }
 
+namespace {
+
+// Checkpoint layout of a stream's resident state: this header, the per-reference segment counts, then the
+// previous P frame's packed views (if any), the I frame's packed views (if any and different), and per
+// reference the previous and the I frame's per-segment labels (uint16 each).
+struct StateHeader {
+    char magic[4];        // "FTVS"
+    int32_t version;      // 1
+    int32_t n_refs, n_views, L, fmt;
+    int32_t has_prev, has_i, i_is_prev, pad;
+    int64_t packed_bytes, frames;
+};
+
+size_t packed_bytes_of(const ftv_ctx* c) {
+    size_t packed = 0;
+    for (int v = 0; v < c->n_views; ++v) packed += align256((size_t)c->cams[v].width * c->cams[v].height * c->texel_bytes);
+    return packed;
+}
+
+int64_t state_bytes(const ftv_ctx* c) {
+    const StreamState& st = c->stream;
+    int64_t b = sizeof(StateHeader) + sizeof(int32_t) * c->n_refs;
+    const bool has_prev = st.prev >= 0, has_i = st.iframe >= 0 && st.iframe != st.prev;
+    b += (int64_t)packed_bytes_of(c) * ((has_prev ? 1 : 0) + (has_i ? 1 : 0));
+    for (const StreamRef& r : st.refs) b += 2 * (int64_t)sizeof(uint16_t) * r.S;
+    return b;
+}
+
+}  // namespace
+
+ftv_status ftv_stream_state_bytes(const ftv_ctx* ctx, int64_t* bytes) {
+    if (!ctx || !bytes || !ctx->stream.ready) return FTV_ERR_INVALID_ARG;
+    *bytes = state_bytes(ctx);
+    return FTV_OK;
+}
+
+ftv_status ftv_stream_state_save(const ftv_ctx* ctx, void* host_buf, int64_t bytes, ftv_stream stream) {
+    if (!ctx || !host_buf || !ctx->stream.ready || bytes < state_bytes(ctx)) return FTV_ERR_INVALID_ARG;
+    NvtxRange range("ftv_stream_state_save");
+    const StreamState& st = ctx->stream;
+    char* h = static_cast<char*>(host_buf);
+    StateHeader hd{};
+    std::memcpy(hd.magic, "FTVS", 4);
+    hd.version = 1;
+    hd.n_refs = ctx->n_refs;
+    hd.n_views = ctx->n_views;
+    hd.L = ctx->L;
+    hd.fmt = ctx->fmt;
+    hd.has_prev = st.prev >= 0;
+    hd.i_is_prev = st.iframe >= 0 && st.iframe == st.prev;
+    hd.has_i = st.iframe >= 0 && !hd.i_is_prev;
+    hd.packed_bytes = (int64_t)packed_bytes_of(ctx);
+    hd.frames = st.frames;
+    std::memcpy(h, &hd, sizeof(hd));
+    h += sizeof(hd);
+    for (int i = 0; i < ctx->n_refs; ++i) {
+        std::memcpy(h, &st.refs[i].S, sizeof(int32_t));
+        h += sizeof(int32_t);
+    }
+    int prev_dev = -1;
+    cudaGetDevice(&prev_dev);
+    if (prev_dev != ctx->device) cudaSetDevice(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (hd.has_prev) {
+        e = cudaMemcpyAsync(h, st.d_ring[st.prev], hd.packed_bytes, cudaMemcpyDeviceToHost, s);
+        h += hd.packed_bytes;
+    }
+    if (e == cudaSuccess && hd.has_i) {
+        e = cudaMemcpyAsync(h, st.d_ring[st.iframe], hd.packed_bytes, cudaMemcpyDeviceToHost, s);
+        h += hd.packed_bytes;
+    }
+    for (int i = 0; i < ctx->n_refs && e == cudaSuccess; ++i) {
+        const StreamRef& r = st.refs[i];
+        e = cudaMemcpyAsync(h, r.d_prev_label, sizeof(uint16_t) * r.S, cudaMemcpyDeviceToHost, s);
+        h += sizeof(uint16_t) * r.S;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, r.d_i_label, sizeof(uint16_t) * r.S, cudaMemcpyDeviceToHost, s);
+        h += sizeof(uint16_t) * r.S;
+    }
+    if (prev_dev >= 0 && prev_dev != ctx->device) cudaSetDevice(prev_dev);
+    return e == cudaSuccess ? FTV_OK : FTV_ERR_CUDA;
+}
+
+ftv_status ftv_stream_state_load(ftv_ctx* ctx, const void* host_buf, int64_t bytes, ftv_stream stream) {
+    if (!ctx || !host_buf || !ctx->stream.ready || bytes < (int64_t)sizeof(StateHeader)) return FTV_ERR_INVALID_ARG;
+    StreamState& st = ctx->stream;
+    const char* h = static_cast<const char*>(host_buf);
+    StateHeader hd;
+    std::memcpy(&hd, h, sizeof(hd));
+    h += sizeof(hd);
+    // the checkpoint must come from a stream of the same shape (views, references, labels, texel format)
+    if (std::memcmp(hd.magic, "FTVS", 4) != 0 || hd.version != 1 || hd.n_refs != ctx->n_refs ||
+        hd.n_views != ctx->n_views || hd.L != ctx->L || hd.fmt != ctx->fmt ||
+        hd.packed_bytes != (int64_t)packed_bytes_of(ctx) || (hd.i_is_prev && !hd.has_prev) ||
+        (hd.has_i && !hd.has_prev))
+        return FTV_ERR_INVALID_ARG;
+    int64_t need = sizeof(StateHeader) + sizeof(int32_t) * ctx->n_refs +
+                   hd.packed_bytes * ((hd.has_prev ? 1 : 0) + (hd.has_i ? 1 : 0));
+    for (int i = 0; i < ctx->n_refs; ++i) {
+        int32_t S;
+        std::memcpy(&S, h + sizeof(int32_t) * i, sizeof(S));
+        if (S != st.refs[i].S) return FTV_ERR_INVALID_ARG;
+        need += 2 * (int64_t)sizeof(uint16_t) * S;
+    }
+    if (bytes < need) return FTV_ERR_INVALID_ARG;
+    h += sizeof(int32_t) * ctx->n_refs;
+    NvtxRange range("ftv_stream_state_load");
+    int prev_dev = -1;
+    cudaGetDevice(&prev_dev);
+    if (prev_dev != ctx->device) cudaSetDevice(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    // previous P frame into ring slot 0, a separate I frame into slot 1
+    if (hd.has_prev) {
+        e = cudaMemcpyAsync(st.d_ring[0], h, hd.packed_bytes, cudaMemcpyHostToDevice, s);
+        h += hd.packed_bytes;
+    }
+    if (e == cudaSuccess && hd.has_i) {
+        e = cudaMemcpyAsync(st.d_ring[1], h, hd.packed_bytes, cudaMemcpyHostToDevice, s);
+        h += hd.packed_bytes;
+    }
+    for (int i = 0; i < ctx->n_refs && e == cudaSuccess; ++i) {
+        StreamRef& r = st.refs[i];
+        e = cudaMemcpyAsync(r.d_prev_label, h, sizeof(uint16_t) * r.S, cudaMemcpyHostToDevice, s);
+        h += sizeof(uint16_t) * r.S;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(r.d_i_label, h, sizeof(uint16_t) * r.S, cudaMemcpyHostToDevice, s);
+        h += sizeof(uint16_t) * r.S;
+    }
+    if (prev_dev >= 0 && prev_dev != ctx->device) cudaSetDevice(prev_dev);
+    if (e != cudaSuccess) return FTV_ERR_CUDA;
+    st.prev = hd.has_prev ? 0 : -1;
+    st.iframe = hd.has_i ? 1 : (hd.i_is_prev ? 0 : -1);
+    st.frames = hd.frames;
+    return FTV_OK;
+}
+
 ftv_status ftv_stream_changed(const ftv_ctx* ctx, int32_t ref_index, const int32_t** d_changed) {
     if (!ctx || !d_changed || !ctx->stream.ready || ref_index < 0 || ref_index >= ctx->n_refs)
         return FTV_ERR_INVALID_ARG;
@@ -677,6 +813,7 @@ ftv_status ftv_batch_prepare(ftv_batch* b, const ftv_frame_job* jobs, int32_t n_
     // the staging block must not be rewritten while a launch that reads it is pending
     if (cudaEventQuery(b->done) == cudaErrorNotReady) return FTV_ERR_BUSY;
     cudaGetLastError();
+    NvtxRange range("ftv_batch_prepare");
     int n_views = 0, n_units = 0, fmt = -1, combine = -1;
     bool pf_all = true;
     int kind = kKindMixed;
@@ -888,6 +1025,7 @@ ftv_status ftv_batch_launch(ftv_batch* b, ftv_stream stream) {
     int prev_dev = -1;
     cudaGetDevice(&prev_dev);
     if (prev_dev != b->device) cudaSetDevice(b->device);
+    NvtxRange range("ftv_batch_launch");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = enqueue(b, s);
     if (e == cudaSuccess) e = cudaEventRecord(b->done, s);
@@ -901,6 +1039,7 @@ ftv_status ftv_batch_replay(ftv_batch* b, ftv_stream stream) {
     int prev_dev = -1;
     cudaGetDevice(&prev_dev);
     if (prev_dev != b->device) cudaSetDevice(b->device);
+    NvtxRange range("ftv_batch_replay");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
     if (!b->exec || b->graph_fmt != b->fmt || b->graph_combine != b->combine || b->graph_pf != b->penalty_floor ||
@@ -1068,6 +1207,7 @@ ftv_status ftv_batch_submit(ftv_batch* b, const ftv_frame_job* job, uint64_t* ti
 
 ftv_status ftv_batch_flush(ftv_batch* b, ftv_stream stream) {
     if (!b) return FTV_ERR_INVALID_ARG;
+    NvtxRange range("ftv_batch_flush");
     if (b->queue.empty()) return FTV_OK;
     if (!harvest(b)) return FTV_ERR_BUSY;  // the previous launch still reads the staging block
     const int n = (int)b->queue.size();

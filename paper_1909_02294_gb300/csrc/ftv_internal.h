@@ -6,9 +6,21 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ftv.h"
 
 namespace ftv {
+
+// A host-side NVTX range over one stage of an entry point ("ftv_cost_volume", "cost kernel", ...): a profiler
+// that records NVTX ranges (Nsight Systems) shows the pipeline's stages and their launches; with no profiler
+// attached the calls return at once.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Packed texel formats: one load fetches the three samples of a pixel.
 enum TexelFormat : int32_t {

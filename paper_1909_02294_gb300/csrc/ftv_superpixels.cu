@@ -37,7 +37,7 @@
 #include <numeric>
 #include <vector>
 
-#include "ftv.h"
+#include "ftv_internal.h"
 
 namespace {
 
@@ -886,6 +886,7 @@ extern "C" ftv_status ftv_superpixels(ftv_segmenter* g, const void* const* d_pla
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != g->device) cudaSetDevice(g->device);
+    ftv::NvtxRange range("ftv_superpixels");
     cudaStream_t st = (cudaStream_t)stream;
     // the staging copy of the previous call must have left before it is rewritten
     if (cudaEventSynchronize(g->staged) != cudaSuccess) {

@@ -87,6 +87,9 @@ def _load() -> ctypes.CDLL:
         "ftv_stream_labels": [vp, i32, vp],
         "ftv_stream_mask": [vp, i32, vp, vp],
         "ftv_stream_changed": [vp, i32, vp],
+        "ftv_stream_state_bytes": [vp, vp],
+        "ftv_stream_state_save": [vp, vp, i64, vp],
+        "ftv_stream_state_load": [vp, vp, i64, vp],
         "ftv_reciprocal_check": [vp, vp],
         "ftv_centre_table": [vp, vp, vp, vp, vp, i32, vp, vp, vp],
         "ftv_adjacency": [vp, i32, vp, vp, vp, i32, i32, ctypes.c_double, ctypes.c_double, i32, vp, vp, vp, vp,
@@ -138,7 +141,8 @@ EXPORTED = ["ftv_depth_init", "ftv_depth_destroy", "ftv_compute_homographies", "
             "ftv_get_label_depths", "ftv_segment_index", "ftv_cost_volume", "ftv_temporal_mask",
             "ftv_wta_depth", "ftv_check", "ftv_culled_evaluations", "ftv_launch_count", "ftv_status_str", "ftv_set_profiling",
             "ftv_last_kernel_ms", "ftv_temporal_mask_static", "ftv_stream_init", "ftv_stream_footprint",
-            "ftv_stream_labels", "ftv_stream_mask", "ftv_stream_changed", "ftv_reciprocal_check", "ftv_centre_table", "ftv_adjacency", "ftv_batch_create", "ftv_batch_destroy", "ftv_batch_prepare", "ftv_batch_launch",
+            "ftv_stream_labels", "ftv_stream_mask", "ftv_stream_changed", "ftv_stream_state_bytes", "ftv_stream_state_save",
+            "ftv_stream_state_load", "ftv_reciprocal_check", "ftv_centre_table", "ftv_adjacency", "ftv_batch_create", "ftv_batch_destroy", "ftv_batch_prepare", "ftv_batch_launch",
             "ftv_batch_replay", "ftv_batch_query", "ftv_batch_wait", "ftv_batch_launch_count", "ftv_batch_set_chunks",
             "ftv_job_footprint", "ftv_batch_set_budget", "ftv_batch_submit", "ftv_batch_flush", "ftv_batch_poll",
             "ftv_segmenter_init", "ftv_segmenter_segments", "ftv_superpixels", "ftv_segmenter_check",
@@ -486,6 +490,21 @@ def ftv_stream_changed(ctx: Context, ref_index: int) -> int:
     p = ctypes.c_void_p()
     _ok(lib.ftv_stream_changed(ctx.handle, ref_index, ctypes.byref(p)), "ftv_stream_changed")
     return int(p.value)
+
+
+def ftv_stream_state_save(ctx: Context, stream=None):
+    """Checkpoint of the stream's resident temporal state as a pinned uint8 tensor (valid after a sync)."""
+    import torch
+    n = ctypes.c_int64()
+    _ok(lib.ftv_stream_state_bytes(ctx.handle, ctypes.byref(n)), "ftv_stream_state_bytes")
+    buf = torch.empty(int(n.value), dtype=torch.uint8).pin_memory()
+    _ok(lib.ftv_stream_state_save(ctx.handle, buf.data_ptr(), buf.numel(), _stream(stream)), "ftv_stream_state_save")
+    return buf
+
+
+def ftv_stream_state_load(ctx: Context, buf, stream=None) -> None:
+    """Restore a checkpoint (from ftv_stream_state_save) into a stream of the same shape."""
+    _ok(lib.ftv_stream_state_load(ctx.handle, buf.data_ptr(), buf.numel(), _stream(stream)), "ftv_stream_state_load")
 
 
 def ctx_void():

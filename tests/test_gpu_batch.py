@@ -314,3 +314,35 @@ def test_job_footprint_covers_the_device_allocations():
     assert fp - input_bytes <= used + (2 << 20), (fp - input_bytes, used)
     assert used <= fp - input_bytes + n_allocs * (2 << 20), (fp - input_bytes, used)
     ctx.close()
+
+
+def test_stream_state_checkpoint_and_resume():
+    """A stream's resident state saved after an I and two P frames and loaded into a fresh stream of the same
+    shape: the next P frame gives the oracle's labels on both the original and the restored stream. A
+    checkpoint of another shape, or a short buffer, is refused."""
+    wls = _streams()
+    w = wls[0]
+    a = Stream(w)
+    o = OracleStream(w)
+    batch = ftv.ftv_batch_create(2, 32, 32)
+    for frame, ftype in SCHEDULE[:3]:
+        _run(batch, [a.job(frame, ftype)])
+        o.step(frame, ftype)
+    buf = ftv.ftv_stream_state_save(a.ctx)
+    torch.cuda.synchronize()
+    b = Stream(w)
+    ftv.ftv_stream_state_load(b.ctx, buf)
+    frame, ftype = SCHEDULE[3]
+    want = o.step(frame, ftype)
+    for s in (a, b):
+        _run(batch, [s.job(frame, ftype)])
+        for r, (g, x) in enumerate(zip(s.labels(), want)):
+            assert np.array_equal(g, x), r
+    other = Stream(wls[1])
+    with pytest.raises(ftv.FtvError):
+        ftv.ftv_stream_state_load(other.ctx, buf)
+    with pytest.raises(ftv.FtvError):
+        ftv.ftv_stream_state_load(b.ctx, buf[: buf.numel() // 2])
+    batch.close()
+    for s in (a, b, other):
+        s.ctx.close()
