@@ -399,6 +399,7 @@ def main(argv=None):
     ap.add_argument("--sequence", default=None, help="run one stream of this workload (e.g. temporal) over --frames")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch shapes (no autotuner run or cache lookup per stream shape)")
+    ap.add_argument("--capacity-only", action="store_true", help="only the capacity runs (no Poisson arrivals)")
     args = ap.parse_args(argv)
     shapes = args.shapes.split(",") if args.shapes else None
     if args.sequence:
@@ -427,7 +428,7 @@ def main(argv=None):
     results["served_vs_plain_depth_maps_per_s"] = (results["capacity_served"]["depth_maps_per_s"] /
                                                    results["capacity_plain"]["depth_maps_per_s"])
     # latency under Poisson arrivals at rate_frac of each mode's own capacity
-    for mode in ("served", "plain"):
+    for mode in (() if args.capacity_only else ("served", "plain")):
         rate = args.rate_frac * results[f"capacity_{mode}"]["jobs_per_s"]
         streams = fresh()
         trace = poisson_trace(len(streams), args.jobs, rate, args.seed + 7)
@@ -439,6 +440,7 @@ def main(argv=None):
         for s in streams:
             s.close()
     results["config"] = {"streams": len(streams), "jobs": args.jobs, "class_batches": not args.mixed_batches,
+                         "heavy_chunks": args.heavy_chunks,
                          "launch_shapes": "autotuned per stream shape (tune.py)" if not args.no_tune else "defaults",
                          "gop": args.gop, "slots": args.slots, "budget_gb": args.budget_gb,
                          "rate_frac": args.rate_frac, "shapes": "960x540/3v/64L, 1920x1080/8v/250L, 3840x2160/15v/400L"}
