@@ -397,7 +397,10 @@ __global__ void __launch_bounds__(kCentreThreads, 4) centre_table3p_kernel(Centr
 #pragma unroll
                     for (int wx = 0; wx < 3; ++wx) t[wy * 3 + wx] = __ldg(base + (int64_t)wy * nv.pitch + wx);
             }
-            // the next entry's homography and projection while the gathers are in flight
+            // the correspondence s' and the next entry's homography and projection while the gathers are in
+            // flight
+            const int32_t* lv0 = slab[cur.k];
+            const int spv = (cur.in && lv0) ? __ldg(lv0 + (int64_t)cur.vi * nv.w + cur.ui) : -1;
             const CentreProj nxt = centre_proj<FAST>(a, snb, cur.j + kCentreThreads, nent, c, ref_in);
             int m;
             if (cur.fast) {
@@ -424,8 +427,7 @@ __global__ void __launch_bounds__(kCentreThreads, 4) centre_table3p_kernel(Centr
             const int d = cur.j - cur.k * a.L;
             const int64_t out = (int64_t)d * a.N + cur.k;
             mrow[out] = m;
-            const int32_t* lv = slab[cur.k];
-            srow[out] = (cur.in && lv) ? lv[(int64_t)cur.vi * nv.w + cur.ui] : -1;
+            srow[out] = spv;
             cur = nxt;
         }
     }
