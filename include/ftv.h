@@ -48,7 +48,9 @@ typedef enum ftv_status {
     FTV_ERR_OVERFLOW = 4,      /* a segment is large enough that its int32 cost sum could overflow */
     FTV_ERR_TIMEOUT = 5,       /* reserved: a bounded device wait gave up */
     FTV_ERR_BUSY = 6,          /* batch admission refused: over the HBM budget or out of slots */
-    FTV_ERR_STATE = 7          /* call out of order (e.g. no segment index built yet) */
+    FTV_ERR_STATE = 7,         /* call out of order (e.g. no segment index built yet) */
+    FTV_ERR_CHECKED = 8        /* checked builds (FTV_CHECKED) only: a cost-kernel gather index fell outside
+                                  its view and was skipped; regular builds never report it */
 } ftv_status;
 
 typedef void* ftv_stream; /* cudaStream_t */

@@ -119,6 +119,7 @@ const char* ftv_status_str(ftv_status s) {
         case FTV_ERR_TIMEOUT: return "device wait timed out";
         case FTV_ERR_BUSY: return "busy: admission refused";
         case FTV_ERR_STATE: return "call out of order";
+        case FTV_ERR_CHECKED: return "checked build: a gather index outside its view was skipped";
     }
     return "unknown status";
 }
@@ -533,6 +534,13 @@ ftv_status ftv_check(ftv_ctx* ctx, ftv_stream stream) {
     uint32_t st = 0;
     if (cudaMemcpy(&st, ctx->d_status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return FTV_ERR_CUDA;
     if (st && cudaMemset(ctx->d_status, 0, sizeof(st)) != cudaSuccess) return FTV_ERR_CUDA;
+#ifdef FTV_CHECKED
+    {  // the last cost-kernel launch's out-of-view gathers (checked builds)
+        uint32_t ck = 0;
+        if (cudaMemcpy(&ck, &ctx->d_plan->checked, sizeof(ck), cudaMemcpyDeviceToHost) != cudaSuccess) return FTV_ERR_CUDA;
+        st |= ck;
+    }
+#endif
     // errors found building a stream's resident state stay with the stream (every job of it reports them)
     if (ctx->stream.d_status) {
         uint32_t ss = 0;
@@ -540,6 +548,7 @@ ftv_status ftv_check(ftv_ctx* ctx, ftv_stream stream) {
         st |= ss;
     }
     if (cudaGetLastError() != cudaSuccess) return FTV_ERR_CUDA;
+    if (st & ST_CHECKED) return FTV_ERR_CHECKED;
     if (st & (ST_BAD_LABEL | ST_BAD_SAMPLE)) return FTV_ERR_INVALID_ARG;
     if (st & ST_OVERFLOW) return FTV_ERR_OVERFLOW;
     return FTV_OK;

@@ -444,6 +444,7 @@ namespace {
 
 // A job's (or a batch's) device status bits as the ABI's status.
 ftv_status status_of(uint32_t st) {
+    if (st & ST_CHECKED) return FTV_ERR_CHECKED;
     if (st & ST_OVERFLOW) return FTV_ERR_OVERFLOW;
     if (st) return FTV_ERR_INVALID_ARG;
     return FTV_OK;
@@ -455,6 +456,18 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 struct RefDims {
     int64_t W, H, N, S;
 };
+
+// Checked builds: the last launch's out-of-view gathers (recorded in its plan), reported by all its jobs.
+uint32_t checked_bits(const ftv_batch* b) {
+#ifdef FTV_CHECKED
+    uint32_t ck = 0;
+    if (cudaMemcpy(&ck, &b->d_plan->checked, sizeof(ck), cudaMemcpyDeviceToHost) != cudaSuccess) return ST_CHECKED;
+    return ck;
+#else
+    (void)b;
+    return 0;
+#endif
+}
 
 // Device bytes ftv_stream_init allocates: the status word, three packed frames, and per reference its
 // labels of the previous and the I frame, mask, changed list and count, temporal sums, cost rows, label
@@ -1097,7 +1110,7 @@ ftv_status ftv_batch_query(ftv_batch* b) {
 ftv_status ftv_batch_wait(ftv_batch* b) {
     if (!b) return FTV_ERR_INVALID_ARG;
     if (cudaEventSynchronize(b->done) != cudaSuccess) return FTV_ERR_CUDA;
-    uint32_t st = 0;
+    uint32_t st = checked_bits(b);
     for (int j = 0; j < b->launched_jobs; ++j) st |= b->h_job_status[j];
     return status_of(st);
 }
@@ -1150,9 +1163,10 @@ bool harvest(ftv_batch* b) {
     if (b->harvested) return true;
     const cudaError_t e = cudaEventQuery(b->done);
     if (e == cudaErrorNotReady) return false;
+    const uint32_t ck = e == cudaSuccess ? checked_bits(b) : 0;
     for (int k = 0; k < b->launch_n; ++k)
         b->ring[(b->launch_first + k) % kTicketRing] =
-            (int8_t)(e == cudaSuccess ? status_of(b->h_job_status[k]) : FTV_ERR_CUDA);
+            (int8_t)(e == cudaSuccess ? status_of(b->h_job_status[k] | ck) : FTV_ERR_CUDA);
     if (e != cudaSuccess) cudaGetLastError();
     b->harvested = true;
     b->launch_footprint = 0;

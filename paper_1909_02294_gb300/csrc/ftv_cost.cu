@@ -183,9 +183,29 @@ __device__ __forceinline__ bool pos_rect(float h2, uint32_t wv, uint32_t hv, int
 // samples update it (PF here), which pays off where many samples fall outside (wide convergent
 // baselines), while the rectified and affine paths keep the select form, measured faster there. Both
 // forms give the minimum over in-view costs and penalties of the contract.
+//
+// Checked builds (FTV_CHECKED): every gather is first tested against the neighbour view's texel count lim;
+// an index outside it is recorded in the launch's plan (ST_CHECKED) and the sample is skipped, so a path
+// whose in-view claim were wrong shows up as a status instead of an out-of-bounds read. Regular builds drop
+// the test (lim and status are unused).
+__device__ __forceinline__ bool checked_gather(bool ok, int idx, unsigned lim, uint32_t* status) {
+#ifdef FTV_CHECKED
+    if (ok && (unsigned)idx >= lim) {
+        atomicOr(status, ST_CHECKED);
+        return false;
+    }
+#else
+    (void)idx;
+    (void)lim;
+    (void)status;
+#endif
+    return ok;
+}
+
 template <int FMT, int COMB, bool PF>
 __device__ __forceinline__ void accumulate(int& m, bool ok, const void* tex, int idx, int a, int b, int c,
-                                           int penalty) {
+                                           int penalty, unsigned lim, uint32_t* status) {
+    ok = checked_gather(ok, idx, lim, status);
     if (COMB == FTV_COMBINE_MIN && PF) {
         if (ok) m = min(m, TexelOps<FMT>::cost(tex, idx, a, b, c));
     } else {
@@ -658,6 +678,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                     const float4 ha = e4[0], hb = e4[1], hc = e4[2];
                     const void* tex = sBase[n];
                     const int pitch = (int)(__float_as_uint(hc.w) & kPitchMask);
+                    const unsigned lim = (unsigned)pitch * __float_as_uint(hc.z);  // texels of the view
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
                         const float X = __fmaf_rn(ha.x, px[j], __fmaf_rn(ha.y, py[j], ha.z));
@@ -666,8 +687,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                         const float r = contract_rcp_normal<FAST_RCP>(Wz);
                         const int ui = __float2int_rd(__fadd_rn(__fmul_rn(X, r), 0.5f));
                         const int vi = __float2int_rd(__fadd_rn(__fmul_rn(Yh, r), 0.5f));
+#ifdef FTV_CHECKED
+                        accumulate<FMT, COMB, false>(m[j], true, tex, vi * pitch + ui, ra[j], rb[j], rc[j], penalty, lim,
+                                                     &plan->checked);
+#else
                         const int cst = TexelOps<FMT>::cost(tex, vi * pitch + ui, ra[j], rb[j], rc[j]);
                         m[j] = COMB == FTV_COMBINE_MIN ? min(m[j], cst) : m[j] + cst;
+#endif
                     }
                 }
                 for (int k = ci; k < cf; ++k) {  // Wz proven positive and normal: range tests only
@@ -676,6 +702,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                     const float4 ha = e4[0], hb = e4[1], hc = e4[2];
                     const void* tex = sBase[n];
                     const int pitch = (int)(__float_as_uint(hc.w) & kPitchMask);
+                    const unsigned lim = (unsigned)pitch * __float_as_uint(hc.z);  // texels of the view
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
                         const float X = __fmaf_rn(ha.x, px[j], __fmaf_rn(ha.y, py[j], ha.z));
@@ -685,7 +712,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                         const int ui = __float2int_rd(__fadd_rn(__fmul_rn(X, r), 0.5f));
                         const int vi = __float2int_rd(__fadd_rn(__fmul_rn(Yh, r), 0.5f));
                         const bool ok = ((unsigned)ui < __float_as_uint(hc.y)) & ((unsigned)vi < __float_as_uint(hc.z));
-                        accumulate<FMT, COMB, PF>(m[j], ok, tex, vi * pitch + ui, ra[j], rb[j], rc[j], penalty);
+                        accumulate<FMT, COMB, PF>(m[j], ok, tex, vi * pitch + ui, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
                     }
                 }
                 for (int k = cf; k < cg; ++k) {  // the contract's sequence as written
@@ -694,11 +721,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                     const float4 ha = e4[0], hb = e4[1], hc = e4[2];
                     const void* tex = sBase[n];
                     const int pitch = (int)(__float_as_uint(hc.w) & kPitchMask);
+                    const unsigned lim = (unsigned)pitch * __float_as_uint(hc.z);  // texels of the view
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
                         int idx;
                         const bool ok = pos_general<FAST_RCP>(ha, hb, hc, pitch, px[j], py[j], idx);
-                        accumulate<FMT, COMB, PF>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty);
+                        accumulate<FMT, COMB, PF>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
                     }
                 }
                 if (!(COMB == FTV_COMBINE_MIN && PF) && cg < N) {  // entries out of view: the penalty each
@@ -714,6 +742,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                 const uint32_t pm = __float_as_uint(hc.w);
                 const uint32_t mode = pm >> 28;
                 const int pitch = (int)(pm & kPitchMask);
+                const unsigned lim = (unsigned)pitch * __float_as_uint(hc.z);  // texels of the view
                 // a projective-only launch (no entry with h6 = h7 = 0) keeps the general path alone; a
                 // rectified-only instantiation measured slower than this mixed loop, so there is none
                 if (precise_kind(KIND)) {
@@ -731,7 +760,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                             const long long q = project_fp64_packed(h64, (int)px[j] + fx0, iy[j], wv, hv);
                             n_recomputed += key[j] != kSentinel;
                             const int idx = (int)(q >> 32) * pitch + (int)(unsigned)q;
-                            accumulate<FMT, COMB, PF>(m[j], q >= 0, tex, idx, ra[j], rb[j], rc[j], penalty);
+                            accumulate<FMT, COMB, PF>(m[j], q >= 0, tex, idx, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
                         }
                     } else if (KIND == kKindPreciseMixed && mode == kShift) {
                         const float4 hb = e4[1];  // (h4, h5, lower and upper bound of x')
@@ -739,7 +768,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
 #pragma unroll
                         for (int j = 0; j < kPPT; ++j) {
                             const bool ok = (px[j] >= hb.z) & (px[j] < hb.w);
-                            accumulate<FMT, COMB, PF>(m[j], ok, tex, rowx[j] + D, ra[j], rb[j], rc[j], penalty);
+                            accumulate<FMT, COMB, PF>(m[j], ok, tex, rowx[j] + D, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
                         }
                     } else if (KIND == kKindPreciseMixed && mode == kRect) {
                         const float a2 = e4[0].z;
@@ -760,7 +789,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                             } else {
                                 ok = ((unsigned)ui < (unsigned)wv) & ((unsigned)vi < (unsigned)hv);
                             }
-                            accumulate<FMT, COMB, PF>(m[j], ok, tex, vi * pitch + ui, ra[j], rb[j], rc[j], penalty);
+                            accumulate<FMT, COMB, PF>(m[j], ok, tex, vi * pitch + ui, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
                         }
                     } else {
                         const float4 ha = e4[0], hb = e4[1];
@@ -788,7 +817,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                             } else {
                                 ok = ((unsigned)ui < (unsigned)wv) & ((unsigned)vi < (unsigned)hv);
                             }
-                            accumulate<FMT, COMB, PF>(m[j], ok, tex, vi * pitch + ui, ra[j], rb[j], rc[j], penalty);
+                            accumulate<FMT, COMB, PF>(m[j], ok, tex, vi * pitch + ui, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
                         }
                     }
                 } else if (KIND == kKindMixed && mode == kShift) {
@@ -797,7 +826,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
                         const bool ok = (px[j] >= hb.z) & (px[j] < hb.w);
-                        accumulate<FMT, COMB, false>(m[j], ok, tex, rowx[j] + D, ra[j], rb[j], rc[j], penalty);
+                        accumulate<FMT, COMB, false>(m[j], ok, tex, rowx[j] + D, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
                     }
                 } else if (KIND == kKindMixed && mode == kRect) {
 #pragma unroll
@@ -805,7 +834,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                         int idx;
                         const bool ok = pos_rect(hc.x, __float_as_uint(hc.y), __float_as_uint(hc.z), pitch, px[j], iy[j],
                                                  idx);
-                        accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty);
+                        accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
                     }
                 } else if (KIND == kKindMixed && mode == kGeneral) {
                     const float4 ha = e4[0], hb = e4[1];
@@ -813,7 +842,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                     for (int j = 0; j < kPPT; ++j) {
                         int idx;
                         const bool ok = pos_general<FAST_RCP>(ha, hb, hc, pitch, px[j], row_f(j), idx);
-                        accumulate<FMT, COMB, PF>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty);
+                        accumulate<FMT, COMB, PF>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
                     }
                 } else if (KIND == kKindMixed && mode == kUnit) {
                     const float4 ha = e4[0], hb = e4[1];
@@ -821,7 +850,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                     for (int j = 0; j < kPPT; ++j) {
                         int idx;
                         const bool ok = pos_affine<true>(ha, hb, hc, 1.0f, pitch, px[j], row_f(j), idx);
-                        accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty);
+                        accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
                     }
                 } else if (KIND == kKindMixed && mode == kAffine) {
                     const float4 ha = e4[0], hb = e4[1];
@@ -829,7 +858,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                     for (int j = 0; j < kPPT; ++j) {
                         int idx;
                         const bool ok = pos_affine<false>(ha, hb, hc, hb.z, pitch, px[j], row_f(j), idx);
-                        accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty);
+                        accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
                     }
                 } else if (KIND == kKindMixed && !(COMB == FTV_COMBINE_MIN && PF)) {
 #pragma unroll

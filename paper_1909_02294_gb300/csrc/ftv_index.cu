@@ -208,6 +208,7 @@ __global__ void plan_kernel(const __grid_constant__ PlanArgs<CAP> args, int n_jo
         plan->n_jobs = n_jobs;
         plan->culled = 0;
         plan->recomputed = 0;
+        plan->checked = 0;
     }
 }
 
@@ -228,6 +229,7 @@ __global__ void plan_device_kernel(RefJob* jobs, const int32_t* n_jobs_ptr, Plan
         plan->n_jobs = n_jobs;
         plan->culled = 0;
         plan->recomputed = 0;
+        plan->checked = 0;
     }
 }
 

@@ -30,7 +30,8 @@ enum TexelFormat : int32_t {
 };
 
 // Device status bits (OR-ed by kernels, read and cleared by ftv_check).
-enum StatusBits : uint32_t { ST_BAD_LABEL = 1u, ST_BAD_SAMPLE = 2u, ST_OVERFLOW = 4u };
+// ST_CHECKED: a checked build (FTV_CHECKED) found a gather index outside its view and skipped it.
+enum StatusBits : uint32_t { ST_BAD_LABEL = 1u, ST_BAD_SAMPLE = 2u, ST_OVERFLOW = 4u, ST_CHECKED = 8u };
 
 // Cost-kernel tiling: each work item is one tile of kTile consecutive segment pixels (in listed-segment
 // order) times one block of consecutive labels. kThreads threads own kPPT pixels each.
@@ -84,6 +85,7 @@ struct Plan {
     int32_t n_jobs;            // units in the launch
     unsigned long long culled; // evaluations decided without sampling: the tile is out of that view
     unsigned long long recomputed;  // FP64-precision evaluations computed in double precision
+    uint32_t checked;          // checked builds: ST_CHECKED when a gather index fell outside its view
     int32_t counter[kMaxChunks];  // next item of each chunk, relative to the chunk's first (persistent CTAs)
 };
 

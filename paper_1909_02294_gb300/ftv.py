@@ -18,7 +18,7 @@ LIB_PATH = os.environ.get("FTV_LIBRARY") or os.path.join(_HERE, "libftv.so")
 
 FTV_OK = 0
 FTV_ERR_INVALID_ARG, FTV_ERR_OUT_OF_MEMORY, FTV_ERR_CUDA, FTV_ERR_OVERFLOW = 1, 2, 3, 4
-FTV_ERR_TIMEOUT, FTV_ERR_BUSY, FTV_ERR_STATE = 5, 6, 7
+FTV_ERR_TIMEOUT, FTV_ERR_BUSY, FTV_ERR_STATE, FTV_ERR_CHECKED = 5, 6, 7, 8
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
           4: "segment cost may overflow int32", 5: "device wait timed out", 6: "busy", 7: "call out of order"}
 FTV_PLANES_REF, FTV_PLANES_CENTRE = 0, 1

@@ -1,10 +1,10 @@
 """Whole-volume GPU parity at the benchmark workloads' full sizes, with the CPU oracle run on every host core
 as the checker (tests/oracle_runs.py: volume_all_cores).
 
-  - one whole reference of the 1920x1080 8-view workload (20736 segments x 250 labels) and one of the
+  - every reference of the 1920x1080 8-view workload (20736 segments x 250 labels each) and two of the
     3840x2160 15-view workload (49432 x 400): every entry of the cost volume (Eq. 4 summed over the segment,
     min over the neighbouring views) and the winner-take-all labels, in the default launch shape (the one
-    the autotuner keeps for both on GB300);
+    the autotuner keeps for both on GB300); a whole 1080p reference in the FP64 projection mode;
   - the whole 30-frame 1920x1080 8-view temporal sequence through the stream/batch path: per frame and
     reference the temporal mask, the ordered list of re-estimated segments and the labels, against the
     oracle's I/P procedure of Sec. III-E (I frames at frames 0 and 15, P frames between).
@@ -31,23 +31,42 @@ from gpu_runs import Run, dev, from_device_pointer  # noqa: E402
 T_P, T_I = 12, 4  # the paper's 8-bit T_P = 3, T_I = 1 scaled to 10-bit samples
 
 
-@pytest.mark.parametrize("name,ref", [("hd8", 3), ("uhd15", 7)])
-def test_whole_reference_volume_at_full_size(name, ref):
+@pytest.mark.parametrize("name,refs", [("hd8", [0, 1, 2, 3, 4, 5, 6, 7]), ("uhd15", [0, 7])])
+def test_whole_reference_volume_at_full_size(name, refs):
+    """Every reference of the 1080p workload and an end and the middle reference of the 4K arc (the most
+    and the fewest culled tiles), each whole volume computed in one launch with all references."""
     wl = make_workload(name)
     run = Run(wl)
     costs = run.volumes()
     assert run.check() == 0
-    idx = wl.ref_views.index(ref)
-    S = run.S[idx]
-    got = costs[idx].cpu().numpy()
-    want = oracle_runs.volume_all_cores(wl, ref)
-    assert got.shape == want.shape == (S, wl.n_labels)
-    bad = np.argwhere(got != want)
-    assert len(bad) == 0, (name, ref, len(bad), bad[:5].tolist())
-    win = torch.empty(S, dtype=torch.int16, device="cuda")
-    ftv.ftv_wta_depth(run.ctx, idx, costs[idx], S, win)
+    for ref in refs:
+        idx = wl.ref_views.index(ref)
+        S = run.S[idx]
+        got = costs[idx].cpu().numpy()
+        want = oracle_runs.volume_all_cores(wl, ref)
+        assert got.shape == want.shape == (S, wl.n_labels)
+        bad = np.argwhere(got != want)
+        assert len(bad) == 0, (name, ref, len(bad), bad[:5].tolist())
+        win = torch.empty(S, dtype=torch.int16, device="cuda")
+        ftv.ftv_wta_depth(run.ctx, idx, costs[idx], S, win)
+        assert run.check() == 0
+        assert np.array_equal(win.cpu().numpy().view(np.uint16), oracle.wta(want))
+    run.close()
+
+
+def test_whole_reference_volume_at_full_size_fp64_projection():
+    """FP64 projection mode on a whole 1080p reference (integer-shift entries, the local frame and its tie
+    test), against the oracle's FP64 mode."""
+    wl = make_workload("hd8")
+    run = Run(wl, precision=ftv.FTV_PRECISION_FP64)
+    costs = run.volumes()
     assert run.check() == 0
-    assert np.array_equal(win.cpu().numpy().view(np.uint16), oracle.wta(want))
+    for ref in (4,):
+        idx = wl.ref_views.index(ref)
+        H64 = oracle.homography_table_f64(wl.cams, ref, wl.neighbours(ref), wl.n_labels, wl.z_near, wl.z_far)
+        want = oracle_runs.volume_all_cores(wl, ref, table_=H64)
+        got = costs[idx].cpu().numpy()
+        assert np.array_equal(got, want), (ref, int((got != want).sum()))
     run.close()
 
 
