@@ -128,18 +128,18 @@ class ClockSampler:
 
 
 def _traffic_for_current_kernel(workload_key: str, table: str = "cost_kernel_traffic.txt",
-                                source: str = "ftv_cost.cu"):
-    """DRAM bytes per launch of a kernel from the committed ncu summary table, if it was taken on the
-    current source of that kernel (hash match); otherwise None."""
+                                source: str = "ftv_cost.cu", column: int = 2):
+    """Bytes per launch of a kernel from the committed ncu summary table (column 2: DRAM read + write; column
+    3, where given: L2 bytes), if it was taken on the current source of that kernel (hash match); else None."""
     path = os.path.join(ROOT, "profiles", table)
     src = os.path.join(ROOT, "paper_1909_02294_gb300", "csrc", source)
     if not os.path.exists(path):
         return None
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     for line in open(path):
-        parts = line.split()
-        if len(parts) >= 3 and parts[0] == workload_key and parts[1] == h:
-            return float(parts[2])
+        parts = line.split("#")[0].split()
+        if len(parts) > column and parts[0] == workload_key and parts[1] == h:
+            return float(parts[column])
     return None
 
 
@@ -815,6 +815,7 @@ def main():
         kms = statistics.mean(kernel_ms)
         achieved = (ev_bytes + comp_bytes) / (kms / 1000.0) / 1e9
         traffic = _traffic_for_current_kernel(args.workload + ("_fp64" if fp64 else ""))
+        l2_bytes = _traffic_for_current_kernel(args.workload + ("_fp64" if fp64 else ""), column=3)
         clk = clocks.summary()
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         sm_mhz = clk["sm_mhz"] if clk else 2070.0
@@ -845,6 +846,8 @@ def main():
                          "compulsory_bytes_per_launch": comp_bytes,
                          "compulsory_floor_ms": comp_bytes / (peak * 1e9) * 1e3,
                          "dram_fraction_of_algorithmic": (traffic / (ev_bytes + comp_bytes)) if traffic else None,
+                         "ncu_dram_gbs": (traffic / (kms / 1000.0) / 1e9) if traffic else None,
+                         "ncu_l2_gbs": (l2_bytes / (kms / 1000.0) / 1e9) if l2_bytes else None,
                          "note": "a notional gather rate: most gathers hit L1/L2, and the DRAM traffic (traffic) "
                                  "is a small fraction of the algorithmic bytes; the kernel is issue/ALU-bound"},
             "alu_roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Tops/s",
