@@ -469,6 +469,22 @@ uint32_t checked_bits(const ftv_batch* b) {
 #endif
 }
 
+// Records the statuses of the last launch's tickets once it has completed; false while it runs.
+bool harvest(ftv_batch* b) {
+    if (b->harvested) return true;
+    const cudaError_t e = cudaEventQuery(b->done);
+    if (e == cudaErrorNotReady) return false;
+    const uint32_t ck = e == cudaSuccess ? checked_bits(b) : 0;
+    for (int k = 0; k < b->launch_n; ++k)
+        b->ring[(b->launch_first + k) % kTicketRing] =
+            (int8_t)(e == cudaSuccess ? status_of(b->h_job_status[k] | ck) : FTV_ERR_CUDA);
+    if (e != cudaSuccess) cudaGetLastError();
+    b->harvested = true;
+    b->launch_footprint = 0;
+    return true;
+}
+
+
 // Device bytes ftv_stream_init allocates: the status word, three packed frames, and per reference its
 // labels of the previous and the I frame, mask, changed list and count, temporal sums, cost rows, label
 // map copy and the neighbour geometry into each ring slot.
@@ -826,6 +842,7 @@ ftv_status ftv_batch_prepare(ftv_batch* b, const ftv_frame_job* jobs, int32_t n_
     // the staging block must not be rewritten while a launch that reads it is pending
     if (cudaEventQuery(b->done) == cudaErrorNotReady) return FTV_ERR_BUSY;
     cudaGetLastError();
+    harvest(b);  // a completed ticketed launch keeps its jobs' statuses before this launch overwrites them
     NvtxRange range("ftv_batch_prepare");
     int n_views = 0, n_units = 0, fmt = -1, combine = -1;
     bool pf_all = true;
@@ -1156,24 +1173,6 @@ ftv_status ftv_batch_set_budget(ftv_batch* b, int64_t hbm_budget_bytes) {
     return FTV_OK;
 }
 
-namespace {
-
-// Records the statuses of the last launch's tickets once it has completed; false while it runs.
-bool harvest(ftv_batch* b) {
-    if (b->harvested) return true;
-    const cudaError_t e = cudaEventQuery(b->done);
-    if (e == cudaErrorNotReady) return false;
-    const uint32_t ck = e == cudaSuccess ? checked_bits(b) : 0;
-    for (int k = 0; k < b->launch_n; ++k)
-        b->ring[(b->launch_first + k) % kTicketRing] =
-            (int8_t)(e == cudaSuccess ? status_of(b->h_job_status[k] | ck) : FTV_ERR_CUDA);
-    if (e != cudaSuccess) cudaGetLastError();
-    b->harvested = true;
-    b->launch_footprint = 0;
-    return true;
-}
-
-}  // namespace
 
 ftv_status ftv_batch_submit(ftv_batch* b, const ftv_frame_job* job, uint64_t* ticket) {
     if (!b || !job || !ticket) return FTV_ERR_INVALID_ARG;

@@ -26,6 +26,7 @@ FTV_COMBINE_MIN, FTV_COMBINE_SUM = 0, 1
 FTV_TM_Y_ONLY, FTV_TM_ALL_YUV = 0, 1
 FTV_MASK_CHANGED, FTV_MASK_REUSE_P, FTV_MASK_REUSE_I = 0, 1, 2
 FTV_PRECISION_FP32, FTV_PRECISION_FP64 = 0, 1
+FTV_MAX_VIEWS, FTV_MAX_NBRS, FTV_MAX_LABELS, FTV_MAX_DIM = 64, 32, 4096, 32767  # include/ftv.h
 
 
 class FtvError(RuntimeError):

@@ -392,3 +392,53 @@ def test_full_size_sampled_entries(name):
         rows = costs[idx][torch.from_numpy(seg).long().cuda()].cpu().numpy()
         assert np.array_equal(win.cpu().numpy().view(np.uint16)[seg], rows.argmin(1).astype(np.uint16))
     run.close()
+
+
+def _random_views(cams, seed, bits=8):
+    rng = np.random.default_rng(seed)
+    hi = (1 << bits)
+    dt = np.uint8 if bits <= 8 else np.uint16
+    return [synth.View(*(rng.integers(0, hi, (c.height, c.width), dtype=dt) for _ in range(3))) for c in cams]
+
+
+@pytest.mark.parametrize("combine,penalty", [("min", None), ("min", 100), ("sum", None)])
+def test_thirty_two_neighbours_on_a_convergent_arc(combine, penalty):
+    """FTV_MAX_NBRS = 32 neighbours of one reference on a convergent arc (projective entries): the per-label
+    neighbour lists are built by one warp with one lane per neighbour, so the last lane is used; the label
+    block is 512 / 32 = 16 labels."""
+    W, H, L = 200, 120, 24
+    cams = synth.arc_rig(33, 3.0, 3.0, 260.0, W, H, seed=5, roll_deg=2.0)
+    views = _random_views(cams, 6)
+    lab, S = synth.grid_labels(W, H, 9, 2, seed=7)
+    nb = [v for v in range(33) if v != 16]
+    comb = ftv.FTV_COMBINE_MIN if combine == "min" else ftv.FTV_COMBINE_SUM
+    pen = 765 if penalty is None else penalty
+    ctx = ftv.ftv_depth_init(cams, [16], L, 0.8, 15.0, sample_bytes=1, bit_depth=8, oob_penalty=pen, combine=comb,
+                             max_segments=S)
+    assert ftv.ftv_get_launch_shape(ctx)["max_label_block"] == 16
+    cost = torch.empty((S, L), dtype=torch.int32, device="cuda")
+    ftv.ftv_cost_volume(ctx, [(dev(v.Y), dev(v.U), dev(v.V)) for v in views], [dev(lab)], [S], [cost])
+    assert ftv.ftv_check(ctx) == 0
+    Ht = oracle.homography_table(cams, 16, nb, L, 0.8, 15.0)
+    want = oracle.cost_volume(cams, views, 1, 16, nb, Ht, L, lab, S, pen, combine)
+    _assert_equal(cost, want, f"32 neighbours ({combine}, penalty {pen})")
+    ctx.close()
+
+
+def test_maximum_label_count():
+    """FTV_MAX_LABELS = 4096 candidate depths on a small linear rig (64 label blocks of 64 per tile)."""
+    W, H, L = 96, 40, ftv.FTV_MAX_LABELS
+    cams = synth.linear_rig(3, 0.05, 120.0, W, H)
+    views = _random_views(cams, 8, bits=10)
+    lab, S = synth.grid_labels(W, H, 8, 1, seed=9)
+    ctx = ftv.ftv_depth_init(cams, [1], L, 0.5, 20.0, sample_bytes=2, bit_depth=10, max_segments=S)
+    cost = torch.empty((S, L), dtype=torch.int32, device="cuda")
+    ftv.ftv_cost_volume(ctx, [(dev(v.Y), dev(v.U), dev(v.V)) for v in views], [dev(lab)], [S], [cost])
+    win = torch.empty(S, dtype=torch.int16, device="cuda")
+    ftv.ftv_wta_depth(ctx, 0, cost, S, win)
+    assert ftv.ftv_check(ctx) == 0
+    Ht = oracle.homography_table(cams, 1, [0, 2], L, 0.5, 20.0)
+    want = oracle.cost_volume(cams, views, 2, 1, [0, 2], Ht, L, lab, S, 3 * 1023)
+    _assert_equal(cost, want, "4096 labels")
+    assert np.array_equal(win.cpu().numpy().view(np.uint16), oracle.wta(want))
+    ctx.close()

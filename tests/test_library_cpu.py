@@ -200,3 +200,14 @@ def test_static_temporal_mask_refuses_tensors_on_another_device(ftv, monkeypatch
                                          Fake("cuda:0"), Fake("cuda:0"), status=status)
         assert e.value.code == ftv.FTV_ERR_INVALID_ARG
     assert called == []
+
+
+def test_binding_constants_match_the_header(ftv):
+    txt = open(os.path.join(ROOT, "include", "ftv.h")).read()
+    for name in ("FTV_MAX_VIEWS", "FTV_MAX_NBRS", "FTV_MAX_LABELS", "FTV_MAX_DIM", "FTV_STATIC_MAX_SEGMENTS",
+                 "FTV_MAX_BATCH_CHUNKS"):
+        m = re.search(r"#define\s+" + name + r"\s+(\d+)", txt)
+        assert m and int(m.group(1)) == getattr(ftv, name), name
+    codes = dict(re.findall(r"(FTV_(?:OK|ERR_\w+))\s*=\s*(\d+)", txt))
+    for name, value in codes.items():
+        assert getattr(ftv, name) == int(value), name
