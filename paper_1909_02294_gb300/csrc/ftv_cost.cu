@@ -432,6 +432,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
     __shared__ uint8_t sOrd[KIND == kKindProjective ? kHEntries : 1];  // per label: neighbours to visit
     __shared__ int sCnt[KIND == kKindProjective ? kMaxLB : 1];         // per label: kIn | kFront << 8 | kGeneral << 16
     unsigned n_recomputed = 0;  // FP64-precision evaluations computed in double precision by this thread
+    uint32_t* const ck = &plan->checked;  // out-of-view gathers of checked builds
 
     const int tid = threadIdx.x, lane = tid & 31;
     // this launch's items: [chunk_begin(chunk), chunk_begin(chunk + 1)); only thread 0 needs the first (it
@@ -632,10 +633,17 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                     E.pm = (uint32_t)nbrs[n].pitch | (mode << 28);
                     if (mode == kOut) atomicAdd(&s_culled, 1);
                 }
-                // every slot, an empty one too (pixel (0, 0), rowx 0), so that its local coordinates, its row
-                // index and the FP64 projection's arguments name the same pixel of the reference
+                // every slot into the local frame; an empty slot (past the end of the unit's last tile, its
+                // result discarded) takes the box's centre pixel, row and row index, so that every slot lies
+                // in the box the entries were staged for and its local coordinates, row index and FP64
+                // projection arguments name the same reference pixel
 #pragma unroll
                 for (int j = 0; j < kPPT; ++j) {
+                    if (key[j] == kSentinel) {
+                        px[j] = (float)fx0;
+                        iy[j] = fy0;
+                        rowx[j] = fy0 * W + fx0;
+                    }
                     px[j] = (float)((int)px[j] - fx0);
                     py[j] = (float)(iy[j] - fy0);
                 }
@@ -701,7 +709,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                         const int vi = __float2int_rd(__fadd_rn(__fmul_rn(Yh, r), 0.5f));
 #ifdef FTV_CHECKED
                         accumulate<FMT, COMB, false>(m[j], true, tex, vi * pitch + ui, ra[j], rb[j], rc[j], penalty, lim,
-                                                     &plan->checked);
+                                                     ck);
 #else
                         const int cst = TexelOps<FMT>::cost(tex, vi * pitch + ui, ra[j], rb[j], rc[j]);
                         m[j] = COMB == FTV_COMBINE_MIN ? min(m[j], cst) : m[j] + cst;
@@ -724,7 +732,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                         const int ui = __float2int_rd(__fadd_rn(__fmul_rn(X, r), 0.5f));
                         const int vi = __float2int_rd(__fadd_rn(__fmul_rn(Yh, r), 0.5f));
                         const bool ok = ((unsigned)ui < __float_as_uint(hc.y)) & ((unsigned)vi < __float_as_uint(hc.z));
-                        accumulate<FMT, COMB, PF>(m[j], ok, tex, vi * pitch + ui, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
+                        accumulate<FMT, COMB, PF>(m[j], ok, tex, vi * pitch + ui, ra[j], rb[j], rc[j], penalty, lim, ck);
                     }
                 }
                 for (int k = cf; k < cg; ++k) {  // the contract's sequence as written
@@ -738,7 +746,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                     for (int j = 0; j < kPPT; ++j) {
                         int idx;
                         const bool ok = pos_general<FAST_RCP>(ha, hb, hc, pitch, px[j], py[j], idx);
-                        accumulate<FMT, COMB, PF>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
+                        accumulate<FMT, COMB, PF>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty, lim, ck);
                     }
                 }
                 if (!(COMB == FTV_COMBINE_MIN && PF) && cg < N) {  // entries out of view: the penalty each
@@ -772,7 +780,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                             const long long q = project_fp64_packed(h64, (int)px[j] + fx0, iy[j], wv, hv);
                             n_recomputed += key[j] != kSentinel;
                             const int idx = (int)(q >> 32) * pitch + (int)(unsigned)q;
-                            accumulate<FMT, COMB, PF>(m[j], q >= 0, tex, idx, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
+                            accumulate<FMT, COMB, PF>(m[j], q >= 0, tex, idx, ra[j], rb[j], rc[j], penalty, lim, ck);
                         }
                     } else if (KIND == kKindPreciseMixed && mode == kShift) {
                         const float4 hb = e4[1];  // (h4, h5, lower and upper bound of x')
@@ -780,7 +788,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
 #pragma unroll
                         for (int j = 0; j < kPPT; ++j) {
                             const bool ok = (px[j] >= hb.z) & (px[j] < hb.w);
-                            accumulate<FMT, COMB, PF>(m[j], ok, tex, rowx[j] + D, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
+                            accumulate<FMT, COMB, PF>(m[j], ok, tex, rowx[j] + D, ra[j], rb[j], rc[j], penalty, lim, ck);
                         }
                     } else if (KIND == kKindPreciseMixed && mode == kRect) {
                         const float a2 = e4[0].z;
@@ -801,7 +809,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                             } else {
                                 ok = ((unsigned)ui < (unsigned)wv) & ((unsigned)vi < (unsigned)hv);
                             }
-                            accumulate<FMT, COMB, PF>(m[j], ok, tex, vi * pitch + ui, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
+                            accumulate<FMT, COMB, PF>(m[j], ok, tex, vi * pitch + ui, ra[j], rb[j], rc[j], penalty, lim, ck);
                         }
                     } else {
                         const float4 ha = e4[0], hb = e4[1];
@@ -829,7 +837,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                             } else {
                                 ok = ((unsigned)ui < (unsigned)wv) & ((unsigned)vi < (unsigned)hv);
                             }
-                            accumulate<FMT, COMB, PF>(m[j], ok, tex, vi * pitch + ui, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
+                            accumulate<FMT, COMB, PF>(m[j], ok, tex, vi * pitch + ui, ra[j], rb[j], rc[j], penalty, lim, ck);
                         }
                     }
                 } else if (KIND == kKindMixed && mode == kShift) {
@@ -838,7 +846,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
                         const bool ok = (px[j] >= hb.z) & (px[j] < hb.w);
-                        accumulate<FMT, COMB, false>(m[j], ok, tex, rowx[j] + D, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
+                        accumulate<FMT, COMB, false>(m[j], ok, tex, rowx[j] + D, ra[j], rb[j], rc[j], penalty, lim, ck);
                     }
                 } else if (KIND == kKindMixed && mode == kRect) {
 #pragma unroll
@@ -846,7 +854,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                         int idx;
                         const bool ok = pos_rect(hc.x, __float_as_uint(hc.y), __float_as_uint(hc.z), pitch, px[j], iy[j],
                                                  idx);
-                        accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
+                        accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty, lim, ck);
                     }
                 } else if (KIND == kKindMixed && mode == kGeneral) {
                     const float4 ha = e4[0], hb = e4[1];
@@ -854,7 +862,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                     for (int j = 0; j < kPPT; ++j) {
                         int idx;
                         const bool ok = pos_general<FAST_RCP>(ha, hb, hc, pitch, px[j], row_f(j), idx);
-                        accumulate<FMT, COMB, PF>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
+                        accumulate<FMT, COMB, PF>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty, lim, ck);
                     }
                 } else if (KIND == kKindMixed && mode == kUnit) {
                     const float4 ha = e4[0], hb = e4[1];
@@ -862,7 +870,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                     for (int j = 0; j < kPPT; ++j) {
                         int idx;
                         const bool ok = pos_affine<true>(ha, hb, hc, 1.0f, pitch, px[j], row_f(j), idx);
-                        accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
+                        accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty, lim, ck);
                     }
                 } else if (KIND == kKindMixed && mode == kAffine) {
                     const float4 ha = e4[0], hb = e4[1];
@@ -870,7 +878,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cost_kernel(const RefJob
                     for (int j = 0; j < kPPT; ++j) {
                         int idx;
                         const bool ok = pos_affine<false>(ha, hb, hc, hb.z, pitch, px[j], row_f(j), idx);
-                        accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty, lim, &plan->checked);
+                        accumulate<FMT, COMB, false>(m[j], ok, tex, idx, ra[j], rb[j], rc[j], penalty, lim, ck);
                     }
                 } else if (KIND == kKindMixed && !(COMB == FTV_COMBINE_MIN && PF)) {
 #pragma unroll
