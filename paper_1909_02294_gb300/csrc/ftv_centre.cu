@@ -311,128 +311,159 @@ __device__ __forceinline__ int window_sum(const uint32_t* t, const int4* ref) {
     return (int)(m[0] + m[1] + m[2]);
 }
 
-// Projection of a segment centre through entry j of the FP32 table (the contract): (ui, vi) and whether the
-// centre is in view.
-template <bool FAST>
-__device__ __forceinline__ bool project_centre(const CentreArgs& a, int j, int2 c, const NbrView& nv, int& ui,
-                                               int& vi) {
-    if (c.x < 0) return false;
-    const float* h = a.H + (int64_t)j * 9;
-    const float x = (float)c.x, y = (float)c.y;
-    const float X = __fmaf_rn(__ldg(&h[0]), x, __fmaf_rn(__ldg(&h[1]), y, __ldg(&h[2])));
-    const float Yh = __fmaf_rn(__ldg(&h[3]), x, __fmaf_rn(__ldg(&h[4]), y, __ldg(&h[5])));
-    const float Wz = __fmaf_rn(__ldg(&h[6]), x, __fmaf_rn(__ldg(&h[7]), y, __ldg(&h[8])));
-    if (!(Wz > 0.0f)) return false;
-    const float r = contract_rcp<FAST>(Wz);
-    const float fu = floorf(__fadd_rn(__fmul_rn(X, r), 0.5f));
-    const float fv = floorf(__fadd_rn(__fmul_rn(Yh, r), 0.5f));
-    if (!(fu >= 0.0f && fu <= (float)(nv.w - 1) && fv >= 0.0f && fv <= (float)(nv.h - 1))) return false;
-    ui = (int)fu;
-    vi = (int)fv;
-    return true;
+// The paper's 3x3 window for 4-byte texels (8- and 10-bit samples) in FP32-contract contexts: the results
+// of centre_table_kernel, with the roles of entries and segments exchanged. A work item is (a chunk of 256
+// consecutive entries, a group of kGroup consecutive segments); each thread owns one entry of the chunk
+// (neighbour k, label d) and holds its homography and the neighbour view's geometry in registers, so the
+// per-(segment, entry) chain starts at the projection instead of at nine homography loads. The CTA stages
+// the group's centres and reference windows in shared memory; the next item's stage is loaded into
+// registers while the current group is worked on and stored to the other buffer afterwards (one barrier
+// per item). Within a group each thread software-pipelines its segments: the next segment's projection is
+// computed while the current window's nine gathers are in flight. Windows that touch an image border take
+// the checked loop. The reciprocal is the Newton-Raphson step where the start-up check found it exact.
+constexpr int kGroup = 16;
+static_assert(9 * kGroup <= kCentreThreads, "one stage sample per thread");
+
+struct CentreStage {
+    int4 ref[kGroup * 9];  // reference samples (Y, Cb, Cr, 0), segment-major
+    int2 c[kGroup];        // centres; (-1, -1) for an empty segment
+    int inside[kGroup];    // the segment's 3x3 window lies inside the reference image
+};
+
+// One thread's share of a group's stage: thread t < 9 kGroup loads sample t % 9 of segment t / 9.
+struct StageLoad {
+    int2 c;
+    uint32_t w;
+    bool valid;
+};
+
+template <int FMT>
+__device__ __forceinline__ StageLoad load_stage(const CentreArgs& a, int group, int tid) {
+    StageLoad r{make_int2(-1, -1), 0u, false};
+    const int g = tid / 9, i = tid - 9 * g, s = group * kGroup + g;
+    if (tid < 9 * kGroup && s < a.S) {
+        r.valid = true;
+        r.c = __ldg(a.centre + s);
+        const int rx = r.c.x - 1 + i % 3, ry = r.c.y - 1 + i / 3;
+        if (r.c.x >= 0 && rx >= 0 && rx < a.W && ry >= 0 && ry < a.H_)
+            r.w = __ldg(static_cast<const uint32_t*>(a.ref_tex) + (int64_t)ry * a.W + rx);
+    }
+    return r;
 }
 
-// The paper's 3x3 window for 4-byte texels (8- and 10-bit samples) in FP32-contract contexts: the results
-// of centre_table_kernel. The kernel is latency-bound (each entry is a dependent chain: homography,
-// projection, nine gathers), so each thread software-pipelines its entries: the next entry's homography
-// loads and projection are issued while the current entry's nine gathers are in flight. The segment's
-// reference samples stay in shared memory (27 values, read by broadcast loads), which leaves registers for
-// the pipeline. The reciprocal is the Newton-Raphson step where the start-up check found it exact (FAST).
-// Windows that touch an image border take the checked loop.
+template <int FMT>
+__device__ __forceinline__ void store_stage(const CentreArgs& a, CentreStage& st, const StageLoad& r, int tid) {
+    constexpr int sh = FMT == FMT_P10 ? 10 : 8;
+    constexpr uint32_t mk = (1u << sh) - 1u;
+    if (!r.valid) return;
+    const int g = tid / 9;
+    st.ref[tid] = make_int4((int)(r.w & mk), (int)((r.w >> sh) & mk), (int)(r.w >> (2 * sh)), 0);
+    if (tid - 9 * g == 0) {
+        st.c[g] = r.c;
+        st.inside[g] = r.c.x >= 1 && r.c.x + 1 < a.W && r.c.y >= 1 && r.c.y + 1 < a.H_;
+    }
+}
+
+// The projection of a segment centre through one entry (the contract's FP32 sequence) and the fast-path test.
 struct CentreProj {
-    int j, k, ui, vi;
+    int2 c;
+    int ui, vi;
     bool in, fast;
 };
 
 template <bool FAST>
-__device__ __forceinline__ CentreProj centre_proj(const CentreArgs& a, const NbrView* snb, int j, int nent, int2 c,
-                                                  bool ref_in) {
-    CentreProj p{j, 0, 0, 0, false, false};
-    if (j >= nent) return p;
-    p.k = a.L == 1 ? j : (int)__umulhi((uint32_t)j, a.l_magic);
-    const NbrView& nv = snb[p.k];
-    p.in = project_centre<FAST>(a, j, c, nv, p.ui, p.vi);
-    p.fast = p.in && ref_in && p.ui >= 1 && p.ui + 1 < nv.w && p.vi >= 1 && p.vi + 1 < nv.h;
+__device__ __forceinline__ CentreProj project_entry(const float (&h)[9], const CentreStage& st, int g, int w,
+                                                    int hgt) {
+    CentreProj p{st.c[g], 0, 0, false, false};
+    if (p.c.x < 0) return p;
+    const float x = (float)p.c.x, y = (float)p.c.y;
+    const float X = __fmaf_rn(h[0], x, __fmaf_rn(h[1], y, h[2]));
+    const float Yh = __fmaf_rn(h[3], x, __fmaf_rn(h[4], y, h[5]));
+    const float Wz = __fmaf_rn(h[6], x, __fmaf_rn(h[7], y, h[8]));
+    if (!(Wz > 0.0f)) return p;
+    const float r = contract_rcp<FAST>(Wz);
+    const float fu = floorf(__fadd_rn(__fmul_rn(X, r), 0.5f));
+    const float fv = floorf(__fadd_rn(__fmul_rn(Yh, r), 0.5f));
+    if (!(fu >= 0.0f && fu <= (float)(w - 1) && fv >= 0.0f && fv <= (float)(hgt - 1))) return p;
+    p.ui = (int)fu;
+    p.vi = (int)fv;
+    p.in = true;
+    p.fast = st.inside[g] && p.ui >= 1 && p.ui + 1 < w && p.vi >= 1 && p.vi + 1 < hgt;
     return p;
 }
 
 template <int FMT, bool FAST>
-__global__ void __launch_bounds__(kCentreThreads, 4) centre_table3p_kernel(CentreArgs a) {
-    __shared__ int4 sref[9];
-    __shared__ int s_refin;
-    __shared__ NbrView snb[FTV_MAX_NBRS];
-    __shared__ const int32_t* slab[FTV_MAX_NBRS];
+__global__ void __launch_bounds__(kCentreThreads, 4) centre_table3t_kernel(CentreArgs a, int chunks, int groups) {
+    __shared__ CentreStage st[2];
     constexpr int sh = FMT == FMT_P10 ? 10 : 8;
     constexpr uint32_t mk = (1u << sh) - 1u;
     const int tid = threadIdx.x;
-    for (int k = tid; k < a.N; k += kCentreThreads) {
-        snb[k] = a.nbrs[k];
-        slab[k] = a.labels_v[k];
-    }
     const int nent = a.L * a.N;
-    const uint32_t* tex_ref = static_cast<const uint32_t*>(a.ref_tex);
-    for (int s = blockIdx.x; s < a.S; s += gridDim.x) {
-        const int2 c = a.centre[s];
-        __syncthreads();  // the previous segment's window is no longer read
-        if (tid < 32) {
-            bool in = false;
-            if (tid < 9) {
-                const int rx = c.x - 1 + tid % 3, ry = c.y - 1 + tid / 3;
-                in = c.x >= 0 && rx >= 0 && rx < a.W && ry >= 0 && ry < a.H_;
-                const uint32_t w = in ? __ldg(tex_ref + (int64_t)ry * a.W + rx) : 0u;
-                sref[tid] = make_int4((int)(w & mk), (int)((w >> sh) & mk), (int)(w >> (2 * sh)), 0);
-            }
-            const unsigned inside = __ballot_sync(kFull, in);
-            if (tid == 0) s_refin = inside == 0x1ffu;
-        }
-        __syncthreads();
-        const bool ref_in = s_refin != 0;
-        int32_t* mrow = a.m + (int64_t)s * nent;
-        int32_t* srow = a.sp + (int64_t)s * nent;
-        CentreProj cur = centre_proj<FAST>(a, snb, tid, nent, c, ref_in);
-        while (cur.j < nent) {
-            const NbrView& nv = snb[cur.k];
-            uint32_t t[9];
-            if (cur.fast) {
-                const uint32_t* base = static_cast<const uint32_t*>(nv.texels) + ((int64_t)(cur.vi - 1) * nv.pitch + (cur.ui - 1));
+    const int64_t items = (int64_t)chunks * groups;
+    int64_t item = blockIdx.x;
+    int buf = 0;
+    if (item < items) store_stage<FMT>(a, st[0], load_stage<FMT>(a, (int)(item / chunks), tid), tid);
+    for (; item < items; item += gridDim.x, buf ^= 1) {
+        __syncthreads();  // st[buf] holds this item's group; st[buf ^ 1] is no longer read
+        const int64_t next = item + gridDim.x;
+        const StageLoad pre = next < items ? load_stage<FMT>(a, (int)(next / chunks), tid) : StageLoad{};
+        const int group = (int)(item / chunks), j = (int)(item - (int64_t)group * chunks) * kCentreThreads + tid;
+        if (j < nent) {
+            // this thread's entry: neighbour k, label d (j = k L + d), its homography and the neighbour view
+            const int k = a.L == 1 ? j : (int)__umulhi((uint32_t)j, a.l_magic), d = j - k * a.L;
+            float h[9];
 #pragma unroll
-                for (int wy = 0; wy < 3; ++wy)
+            for (int i = 0; i < 9; ++i) h[i] = __ldg(a.H + (int64_t)j * 9 + i);
+            const NbrView nv = a.nbrs[k];
+            const int32_t* lv = a.labels_v[k];
+            const uint32_t* tex = static_cast<const uint32_t*>(nv.texels);
+            const CentreStage& cs = st[buf];
+            const int s0 = group * kGroup, n = min(kGroup, a.S - s0);
+            int32_t* mp = a.m + (int64_t)s0 * nent + (int64_t)d * a.N + k;
+            int32_t* spp = a.sp + (int64_t)s0 * nent + (int64_t)d * a.N + k;
+            CentreProj cur = project_entry<FAST>(h, cs, 0, nv.w, nv.h);
+            for (int g = 0; g < n; ++g) {
+                uint32_t t[9];
+                if (cur.fast) {
+                    const uint32_t* base = tex + ((int64_t)(cur.vi - 1) * nv.pitch + (cur.ui - 1));
 #pragma unroll
-                    for (int wx = 0; wx < 3; ++wx) t[wy * 3 + wx] = __ldg(base + (int64_t)wy * nv.pitch + wx);
-            }
-            // the correspondence s' and the next entry's homography and projection while the gathers are in
-            // flight
-            const int32_t* lv0 = slab[cur.k];
-            const int spv = (cur.in && lv0) ? __ldg(lv0 + (int64_t)cur.vi * nv.w + cur.ui) : -1;
-            const CentreProj nxt = centre_proj<FAST>(a, snb, cur.j + kCentreThreads, nent, c, ref_in);
-            int m;
-            if (cur.fast) {
-                m = window_sum<FMT>(t, sref);
-            } else if (!cur.in) {
-                m = 9 * a.penalty;
-            } else {
-                m = 0;
+                    for (int wy = 0; wy < 3; ++wy)
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const int qx = cur.ui - 1 + i % 3, qy = cur.vi - 1 + i / 3;
-                    const int rx = c.x - 1 + i % 3, ry = c.y - 1 + i / 3;
-                    const bool rin = rx >= 0 && rx < a.W && ry >= 0 && ry < a.H_;
-                    if (!rin || qx < 0 || qx >= nv.w || qy < 0 || qy >= nv.h) {
-                        m += a.penalty;
-                        continue;
-                    }
-                    const uint32_t q = __ldg(static_cast<const uint32_t*>(nv.texels) + (int64_t)qy * nv.pitch + qx);
-                    const int4 r = sref[i];
-                    m += (int)__sad(q & mk, (unsigned)r.x, __sad((q >> sh) & mk, (unsigned)r.y,
-                                                                  __sad(q >> (2 * sh), (unsigned)r.z, 0u)));
+                        for (int wx = 0; wx < 3; ++wx) t[wy * 3 + wx] = __ldg(base + (int64_t)wy * nv.pitch + wx);
                 }
+                const int spv = (cur.in && lv) ? __ldg(lv + (int64_t)cur.vi * nv.w + cur.ui) : -1;
+                CentreProj nxt{};
+                if (g + 1 < n) nxt = project_entry<FAST>(h, cs, g + 1, nv.w, nv.h);
+                int m;
+                if (cur.fast) {
+                    m = window_sum<FMT>(t, cs.ref + 9 * g);
+                } else if (!cur.in) {
+                    m = 9 * a.penalty;
+                } else {
+                    m = 0;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        const int qx = cur.ui - 1 + i % 3, qy = cur.vi - 1 + i / 3;
+                        const int rx = cur.c.x - 1 + i % 3, ry = cur.c.y - 1 + i / 3;
+                        const bool rin = rx >= 0 && rx < a.W && ry >= 0 && ry < a.H_;
+                        if (!rin || qx < 0 || qx >= nv.w || qy < 0 || qy >= nv.h) {
+                            m += a.penalty;
+                            continue;
+                        }
+                        const uint32_t q = __ldg(tex + (int64_t)qy * nv.pitch + qx);
+                        const int4 r = cs.ref[9 * g + i];
+                        m += (int)__sad(q & mk, (unsigned)r.x, __sad((q >> sh) & mk, (unsigned)r.y,
+                                                                      __sad(q >> (2 * sh), (unsigned)r.z, 0u)));
+                    }
+                }
+                *mp = m;
+                *spp = spv;
+                mp += nent;
+                spp += nent;
+                cur = nxt;
             }
-            const int d = cur.j - cur.k * a.L;
-            const int64_t out = (int64_t)d * a.N + cur.k;
-            mrow[out] = m;
-            srow[out] = spv;
-            cur = nxt;
         }
+        if (next < items) store_stage<FMT>(a, st[buf ^ 1], pre, tid);
     }
 }
 
@@ -508,19 +539,22 @@ extern "C" ftv_status ftv_centre_table(ftv_ctx* ctx, const void* const* d_planes
         a.l_magic = ctx->L > 1 ? (uint32_t)((0x100000000ull + (uint64_t)ctx->L - 1) / (uint64_t)ctx->L) : 0u;
         const int64_t total = (int64_t)S * ctx->L * r.n_nbrs;
         const int blocks = std::max(1, std::min(S, ctx->n_sm * 8));
+        // centre_table3t_kernel: (entry chunk, segment group) items over four resident CTAs per SM
+        const int chunks = (ctx->L * r.n_nbrs + kCentreThreads - 1) / kCentreThreads, groups = (S + kGroup - 1) / kGroup;
+        const int tblocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)chunks * groups, ctx->n_sm * 4));
         if (total > 0) {
             const bool fast = ctx->fast_rcp, fp32 = ctx->precision == FTV_PRECISION_FP32;
             if (window == 3 && !fp32 && ctx->fmt == FMT_P10) centre_table3_kernel<FMT_P10><<<blocks, kCentreThreads, 0, s>>>(a);
             else if (window == 3 && !fp32 && ctx->fmt == FMT_U8X4)
                 centre_table3_kernel<FMT_U8X4><<<blocks, kCentreThreads, 0, s>>>(a);
             else if (window == 3 && ctx->fmt == FMT_P10 && fast)
-                centre_table3p_kernel<FMT_P10, true><<<blocks, kCentreThreads, 0, s>>>(a);
+                centre_table3t_kernel<FMT_P10, true><<<tblocks, kCentreThreads, 0, s>>>(a, chunks, groups);
             else if (window == 3 && ctx->fmt == FMT_P10)
-                centre_table3p_kernel<FMT_P10, false><<<blocks, kCentreThreads, 0, s>>>(a);
+                centre_table3t_kernel<FMT_P10, false><<<tblocks, kCentreThreads, 0, s>>>(a, chunks, groups);
             else if (window == 3 && ctx->fmt == FMT_U8X4 && fast)
-                centre_table3p_kernel<FMT_U8X4, true><<<blocks, kCentreThreads, 0, s>>>(a);
+                centre_table3t_kernel<FMT_U8X4, true><<<tblocks, kCentreThreads, 0, s>>>(a, chunks, groups);
             else if (window == 3 && ctx->fmt == FMT_U8X4)
-                centre_table3p_kernel<FMT_U8X4, false><<<blocks, kCentreThreads, 0, s>>>(a);
+                centre_table3t_kernel<FMT_U8X4, false><<<tblocks, kCentreThreads, 0, s>>>(a, chunks, groups);
             else if (window == 3) centre_table3_kernel<FMT_U16X4><<<blocks, kCentreThreads, 0, s>>>(a);
             else centre_table_kernel<<<blocks, kCentreThreads, 0, s>>>(a);
             ctx->launches++;

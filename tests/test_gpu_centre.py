@@ -47,10 +47,11 @@ def test_centre_table_bit_exact(name, window, drop):
     run.close()
 
 
-@pytest.mark.parametrize("window", [1, 15])
+@pytest.mark.parametrize("window", [1, 3, 15])
 def test_centre_table_single_neighbour_empty_segments_and_window_limits(window):
-    """One neighbour (the kernel's label/neighbour split has a special case there), the smallest and the
-    largest window, a one-pixel segment in the corner (its window leaves the image) and an empty segment."""
+    """One neighbour (the kernel's label/neighbour split has a special case there), the smallest, the paper's
+    and the largest window, a one-pixel segment in the corner (its window leaves the image) and an empty
+    segment."""
     wl = make_workload("tiny")
     r = wl.ref_views[0]
     lab, S0 = wl.labels(r)
