@@ -421,8 +421,8 @@ TEMPORAL_T_P, TEMPORAL_T_I = 12, 4
 def run_part(args, rank, world, local):
     """--part centre: one step = the centre table of every reference (ftv_centre_table, one call).
     --part adjacency: one step = adjacency and beta of every reference (ftv_adjacency per reference).
-    --part temporal: one step = the temporal test of every reference (ftv_temporal_mask, luma mode) of
-    the temporal workload's frame 1 against frame 0 as the previous P and the I frame.
+    --part temporal: one step = the temporal test of every reference (one ftv_temporal_mask_views call, luma
+    mode) of the temporal workload's frame 1 against frame 0 as the previous P and the I frame.
     The roofline is taken over the whole call (pack, segment index and the part's kernels)."""
     import torch
     import torch.distributed as dist
@@ -465,11 +465,14 @@ def run_part(args, rank, world, local):
         host_out = [torch.empty(S[i], dtype=torch.uint8).pin_memory() for i in range(R)]
         units = sum(wl.cams[r].width * wl.cams[r].height for r in wl.ref_views)
 
+        trips_cur = [(cur[i], None, None) for i in range(R)]
+        trips_prev = [(ref_prev[i], None, None) for i in range(R)]
+        ref_labels = [labels[r] for r in wl.ref_views]
+
         def step():
-            for i, r in enumerate(wl.ref_views):
-                ftv.ftv_temporal_mask(ctx, i, (cur[i], None, None), (ref_prev[i], None, None),
-                                      (ref_prev[i], None, None), labels[r], S[i], TEMPORAL_T_P, TEMPORAL_T_I,
-                                      ftv.FTV_TM_Y_ONLY, masks[i], changed[i], n_changed[i])
+            # every reference of the frame in one ftv_temporal_mask_views call (one launch sequence)
+            ftv.ftv_temporal_mask_views(ctx, list(range(R)), trips_cur, trips_prev, trips_prev, ref_labels, S,
+                                        TEMPORAL_T_P, TEMPORAL_T_I, ftv.FTV_TM_Y_ONLY, masks, changed, n_changed)
         outs = masks
     else:
         cap = [8 * S[i] + 64 for i in range(R)]
@@ -558,7 +561,7 @@ def run_part(args, rank, world, local):
                     "algorithmic_bytes_per_step": byts,
                     "definition": "per pixel its label and three luma samples (current, previous, I) read "
                                   "once, per segment its mask byte and list entry written",
-                    "kernel": "the whole ftv_temporal_mask calls (accumulate and finalize kernels)"}
+                    "kernel": "the whole ftv_temporal_mask_views call (accumulate, decide and compact kernels)"}
             metric, unit = "temporal-test pixels/s", "px/s"
             extra = {"mode": "luma, previous P and I frame", "t_p": TEMPORAL_T_P, "t_i": TEMPORAL_T_I,
                      "changed_per_step": sum(int(t.item()) for t in n_changed)}

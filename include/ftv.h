@@ -219,7 +219,10 @@ FTV_API ftv_status ftv_cost_volume(ftv_ctx* ctx, const void* const* d_planes, co
  * |S_cur - S_I| < t_i * n; else FTV_MASK_CHANGED (also for empty segments). This is the paper's test
  * on segment means (mean change < T) in exact integers. d_mask[n_segments] receives the mask,
  * d_changed_list the changed segments in increasing order and *d_n_changed their count (device).
- * The paper's thresholds are T_P = 3 and T_I = 1 for 8-bit samples. Asynchronous.
+ * The paper's thresholds are T_P = 3 and T_I = 1 for 8-bit samples. Asynchronous. The per-segment sums live
+ * in the context, one slot per reference (ftv_adjacency uses the same slot as scratch): calls for one
+ * reference whose work overlaps on the GPU (different streams without ordering between them) race.
+ * Device-found errors (a label outside [0, n_segments): the pixel is left out) are reported by ftv_check.
  */
 FTV_API ftv_status ftv_temporal_mask(ftv_ctx* ctx, int32_t ref_index, const void* const* d_cur,
                                      const int64_t* cur_pitch, const void* const* d_prev, const int64_t* prev_pitch,
@@ -227,6 +230,26 @@ FTV_API ftv_status ftv_temporal_mask(ftv_ctx* ctx, int32_t ref_index, const void
                                      const int32_t* d_labels, int32_t n_segments, int32_t t_p, int32_t t_i,
                                      int32_t mode, uint8_t* d_mask, int32_t* d_changed_list,
                                      int32_t* d_n_changed, ftv_stream stream);
+
+/*
+ * ftv_temporal_mask_views - ftv_temporal_mask for n distinct references of one context in one launch
+ * sequence (three kernel launches for up to 16 references), e.g. every view of a frame. Reference
+ * ref_indices[k] (host array [n]) takes d_cur[3k..3k+2], d_prev[3k..3k+2] and, when d_iframe is not NULL,
+ * d_iframe[3k..3k+2] (host arrays of device plane pointers, pitches in bytes alike; the I-frame test is
+ * made for all or none), d_labels[k] with n_segments[k] segments, and writes d_mask[k], d_changed_list[k]
+ * and *d_n_changed[k] (host arrays of device pointers). Each reference gets exactly the results of
+ * ftv_temporal_mask. Arguments are checked before anything is launched (FTV_ERR_INVALID_ARG: a repeated or
+ * out-of-range reference index, a NULL pointer, a short pitch, a segment count above max_segments).
+ * Asynchronous on `stream`.
+ */
+FTV_API ftv_status ftv_temporal_mask_views(ftv_ctx* ctx, int32_t n, const int32_t* ref_indices,
+                                           const void* const* d_cur, const int64_t* cur_pitch,
+                                           const void* const* d_prev, const int64_t* prev_pitch,
+                                           const void* const* d_iframe, const int64_t* iframe_pitch,
+                                           const int32_t* const* d_labels, const int32_t* n_segments, int32_t t_p,
+                                           int32_t t_i, int32_t mode, uint8_t* const* d_mask,
+                                           int32_t* const* d_changed_list, int32_t* const* d_n_changed,
+                                           ftv_stream stream);
 
 /*
  * ftv_temporal_mask_static - the temporal test of ftv_temporal_mask without any device allocation.

@@ -223,7 +223,10 @@ extern "C" ftv_status ftv_adjacency(ftv_ctx* ctx, int32_t ref_index, const void*
         a.S = n_segments;
         a.sb = ctx->sample_bytes;
         a.conn = connectivity;
-        a.stats = ctx->d_tstats;
+        // scratch: this reference's slot of the temporal sums, which is then no longer known to be zero
+        int64_t* const scratch = ctx->d_tstats + (size_t)ref_index * ctx->max_segments * 8;
+        ctx->tstats_zero[ref_index] = 0;
+        a.stats = scratch;
         a.deg = ctx->d_adj_deg;
         a.slots = ctx->d_adj_slots;
         a.status = ctx->d_status;
@@ -231,7 +234,7 @@ extern "C" ftv_status ftv_adjacency(ftv_ctx* ctx, int32_t ref_index, const void*
         neighbours_kernel<<<blocks, kWarps * 32, 0, s>>>(a);
         edge_offsets_kernel<<<1, 1024, 0, s>>>(ctx->d_adj_deg, n_segments, ctx->d_adj_offs, d_n_edges);
         edges_kernel<<<std::max(1, std::min(65535, (n_segments + 255) / 256)), 256, 0, s>>>(
-            ctx->d_adj_deg, ctx->d_adj_slots, ctx->d_adj_offs, ctx->d_tstats, n_segments, capacity, beta0, min_diff,
+            ctx->d_adj_deg, ctx->d_adj_slots, ctx->d_adj_offs, scratch, n_segments, capacity, beta0, min_diff,
             d_edge_s, d_edge_t, d_beta);
         ctx->launches += 3;
         e = cudaGetLastError();

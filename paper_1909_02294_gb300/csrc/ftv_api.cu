@@ -249,7 +249,8 @@ ftv_status ftv_depth_init(const ftv_config* cfg, ftv_ctx** out) {
     ok = ok && dalloc(&c->d_status, 1) == cudaSuccess;
     ok = ok && dalloc(&c->d_jobs, kMaxUnits) == cudaSuccess;
     ok = ok && dalloc(&c->d_plan, 1) == cudaSuccess;
-    ok = ok && dalloc(&c->d_tstats, (size_t)c->max_segments * 8) == cudaSuccess;
+    ok = ok && dalloc(&c->d_tstats, (size_t)std::max(1, c->n_refs) * c->max_segments * 8) == cudaSuccess;
+    c->tstats_zero.assign(c->n_refs, 0);
     ok = ok && dalloc(&c->d_label_z, (size_t)c->L) == cudaSuccess;
     ok = ok && dalloc(&c->d_adj_deg, (size_t)c->max_segments) == cudaSuccess;
     ok = ok && dalloc(&c->d_adj_slots, (size_t)c->max_segments * 32) == cudaSuccess;
@@ -459,31 +460,96 @@ ftv_status ftv_cost_volume(ftv_ctx* ctx, const void* const* d_planes, const int6
     return e == cudaSuccess ? FTV_OK : FTV_ERR_CUDA;
 }
 
+// The temporal test of n references of a context (ftv_temporal_mask and ftv_temporal_mask_views): arguments
+// checked, then one launch sequence per kMaxTemporalRefs references. Reference ref_indices[k] takes its own
+// slot of the context's sums, cleared first when the slot is not known to be zero.
+static ftv_status temporal_views(ftv_ctx* ctx, int32_t n, const int32_t* ref_indices, const void* const* d_cur,
+                                 const int64_t* cur_pitch, const void* const* d_prev, const int64_t* prev_pitch,
+                                 const void* const* d_iframe, const int64_t* iframe_pitch,
+                                 const int32_t* const* d_labels, const int32_t* n_segments, int32_t t_p, int32_t t_i,
+                                 int32_t mode, uint8_t* const* d_mask, int32_t* const* d_changed_list,
+                                 int32_t* const* d_n_changed, ftv_stream stream) {
+    if (!ctx || n < 0 || (n > 0 && (!ref_indices || !d_cur || !cur_pitch || !d_prev || !prev_pitch || !d_labels ||
+                                    !n_segments || !d_mask || !d_changed_list || !d_n_changed)))
+        return FTV_ERR_INVALID_ARG;
+    if (t_p < 0 || t_i < 0 || (mode != FTV_TM_Y_ONLY && mode != FTV_TM_ALL_YUV)) return FTV_ERR_INVALID_ARG;
+    if (d_iframe && !iframe_pitch) return FTV_ERR_INVALID_ARG;
+    const int nch = mode == FTV_TM_ALL_YUV ? 3 : 1;
+    std::vector<uint8_t> seen(ctx->n_refs, 0);
+    for (int k = 0; k < n; ++k) {
+        const int ri = ref_indices[k];
+        if (ri < 0 || ri >= ctx->n_refs || seen[ri]) return FTV_ERR_INVALID_ARG;
+        seen[ri] = 1;
+        if (!d_labels[k] || !d_mask[k] || !d_changed_list[k] || !d_n_changed[k]) return FTV_ERR_INVALID_ARG;
+        if (n_segments[k] < 0 || n_segments[k] > ctx->max_segments) return FTV_ERR_INVALID_ARG;
+        const int64_t row = (int64_t)ctx->refs[ri].W * ctx->sample_bytes;
+        for (int c = 0; c < nch; ++c) {
+            const int i = 3 * k + c;
+            if (!d_cur[i] || !d_prev[i] || cur_pitch[i] < row || prev_pitch[i] < row) return FTV_ERR_INVALID_ARG;
+            if (d_iframe && (!d_iframe[i] || iframe_pitch[i] < row)) return FTV_ERR_INVALID_ARG;
+        }
+    }
+    DeviceGuard g(ctx->device);
+    NvtxRange range("ftv_temporal_mask");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t slot = (size_t)ctx->max_segments * 8;  // int64 words per reference
+    cudaError_t e = cudaSuccess;
+    for (int k0 = 0; k0 < n && e == cudaSuccess; k0 += kMaxTemporalRefs) {
+        const int m = std::min(n - k0, kMaxTemporalRefs);
+        TemporalRef refs[kMaxTemporalRefs];
+        for (int j = 0; j < m && e == cudaSuccess; ++j) {
+            const int k = k0 + j, ri = ref_indices[k];
+            TemporalRef& r = refs[j];
+            r = TemporalRef{};
+            for (int c = 0; c < 3; ++c) {
+                const bool used = c < nch;
+                r.cur[c] = used ? d_cur[3 * k + c] : nullptr;
+                r.prev[c] = used ? d_prev[3 * k + c] : nullptr;
+                r.ifr[c] = used && d_iframe ? d_iframe[3 * k + c] : nullptr;
+                r.pc[c] = used ? cur_pitch[3 * k + c] : 0;
+                r.pp[c] = used ? prev_pitch[3 * k + c] : 0;
+                r.pi[c] = used && d_iframe ? iframe_pitch[3 * k + c] : 0;
+            }
+            r.labels = d_labels[k];
+            r.stats = ctx->d_tstats + ri * slot;
+            r.mask = d_mask[k];
+            r.changed = d_changed_list[k];
+            r.n_changed = d_n_changed[k];
+            r.W = ctx->refs[ri].W;
+            r.H = ctx->refs[ri].H;
+            r.S = n_segments[k];
+            // the decide pass leaves the sums zero; a slot of unknown contents (first use, a failed launch,
+            // adjacency scratch) is cleared whole
+            if (!ctx->tstats_zero[ri] && slot > 0) e = cudaMemsetAsync(r.stats, 0, slot * sizeof(int64_t), s);
+            ctx->tstats_zero[ri] = 0;
+        }
+        if (e == cudaSuccess)
+            e = launch_temporal_refs(refs, m, ctx->sample_bytes, mode, d_iframe != nullptr, t_p, t_i, ctx->d_status, s,
+                                     &ctx->launches);
+        if (e == cudaSuccess)
+            for (int j = 0; j < m; ++j) ctx->tstats_zero[ref_indices[k0 + j]] = 1;
+    }
+    return e == cudaSuccess ? FTV_OK : FTV_ERR_CUDA;
+}
+
 ftv_status ftv_temporal_mask(ftv_ctx* ctx, int32_t ref_index, const void* const* d_cur, const int64_t* cur_pitch,
                              const void* const* d_prev, const int64_t* prev_pitch, const void* const* d_iframe,
                              const int64_t* iframe_pitch, const int32_t* d_labels, int32_t n_segments, int32_t t_p,
                              int32_t t_i, int32_t mode, uint8_t* d_mask, int32_t* d_changed_list,
                              int32_t* d_n_changed, ftv_stream stream) {
-    if (!ctx || ref_index < 0 || ref_index >= ctx->n_refs || !d_cur || !cur_pitch || !d_prev || !prev_pitch)
-        return FTV_ERR_INVALID_ARG;
-    if (!d_labels || !d_mask || !d_changed_list || !d_n_changed) return FTV_ERR_INVALID_ARG;
-    if (n_segments < 0 || n_segments > ctx->max_segments || t_p < 0 || t_i < 0) return FTV_ERR_INVALID_ARG;
-    if (mode != FTV_TM_Y_ONLY && mode != FTV_TM_ALL_YUV) return FTV_ERR_INVALID_ARG;
-    if (d_iframe && !iframe_pitch) return FTV_ERR_INVALID_ARG;
-    const RefState& r = ctx->refs[ref_index];
-    const int nch = mode == FTV_TM_ALL_YUV ? 3 : 1;
-    const int64_t row = (int64_t)r.W * ctx->sample_bytes;
-    for (int c = 0; c < nch; ++c) {
-        if (!d_cur[c] || !d_prev[c] || cur_pitch[c] < row || prev_pitch[c] < row) return FTV_ERR_INVALID_ARG;
-        if (d_iframe && (!d_iframe[c] || iframe_pitch[c] < row)) return FTV_ERR_INVALID_ARG;
-    }
-    DeviceGuard g(ctx->device);
-    NvtxRange range("ftv_temporal_mask");
-    const cudaError_t e =
-        launch_temporal(d_cur, cur_pitch, d_prev, prev_pitch, d_iframe, iframe_pitch, ctx->sample_bytes, d_labels, r.W,
-                        r.H, n_segments, t_p, t_i, mode, ctx->d_tstats, d_mask, d_changed_list, d_n_changed,
-                        ctx->d_status, (cudaStream_t)stream, &ctx->launches);
-    return e == cudaSuccess ? FTV_OK : FTV_ERR_CUDA;
+    if (!ctx || !d_cur || !cur_pitch || !d_prev || !prev_pitch) return FTV_ERR_INVALID_ARG;
+    return temporal_views(ctx, 1, &ref_index, d_cur, cur_pitch, d_prev, prev_pitch, d_iframe, iframe_pitch, &d_labels,
+                          &n_segments, t_p, t_i, mode, &d_mask, &d_changed_list, &d_n_changed, stream);
+}
+
+ftv_status ftv_temporal_mask_views(ftv_ctx* ctx, int32_t n, const int32_t* ref_indices, const void* const* d_cur,
+                                   const int64_t* cur_pitch, const void* const* d_prev, const int64_t* prev_pitch,
+                                   const void* const* d_iframe, const int64_t* iframe_pitch,
+                                   const int32_t* const* d_labels, const int32_t* n_segments, int32_t t_p,
+                                   int32_t t_i, int32_t mode, uint8_t* const* d_mask, int32_t* const* d_changed_list,
+                                   int32_t* const* d_n_changed, ftv_stream stream) {
+    return temporal_views(ctx, n, ref_indices, d_cur, cur_pitch, d_prev, prev_pitch, d_iframe, iframe_pitch, d_labels,
+                          n_segments, t_p, t_i, mode, d_mask, d_changed_list, d_n_changed, stream);
 }
 
 ftv_status ftv_wta_depth(ftv_ctx* ctx, int32_t ref_index, const int32_t* d_cost, int32_t n_segments,

@@ -496,11 +496,11 @@ int64_t stream_bytes_of(size_t packed, const std::vector<RefDims>& refs, int64_t
 }
 
 // Device bytes ftv_depth_init allocates (max_segments MS): packed views, status, unit descriptors, plan,
-// temporal and adjacency scratch, label depths, and per reference its tables, neighbour geometry, segment
+// temporal sums (one slot per reference) and adjacency scratch, label depths, and per reference its tables, neighbour geometry, segment
 // index, centres and neighbour label pointers.
 int64_t context_bytes_of(size_t packed, const std::vector<RefDims>& refs, int64_t L, int64_t MS, bool fp64) {
     int64_t b = (int64_t)packed + sizeof(uint32_t) + kMaxUnits * (int64_t)sizeof(RefJob) + sizeof(Plan);
-    b += MS * 8 * 8 + L * 4 + MS * 4 + MS * 32 * 4 + MS * 4;
+    b += std::max<int64_t>(1, (int64_t)refs.size()) * MS * 8 * 8 + L * 4 + MS * 4 + MS * 32 * 4 + MS * 4;
     for (const RefDims& r : refs) {
         b += r.N * L * 9 * 4 + (fp64 ? r.N * L * 9 * 8 : 0) + r.N * (int64_t)sizeof(NbrView);
         b += 2 * (MS + 1) * 4 + MS * 4 + r.W * r.H * 4 + MS * 8 + std::max<int64_t>(1, r.N) * 8;

@@ -83,7 +83,7 @@ extern "C" ftv_status ftv_temporal_mask_static(int32_t width, int32_t height, in
     // the accumulators are cleared on `stream` before use, so the previous call's contents do not matter
     const cudaError_t e = ftv::launch_temporal(d_cur, cur_pitch, d_prev, prev_pitch, d_iframe, iframe_pitch,
                                                sample_bytes, d_labels, width, height, n_segments, t_p, t_i, mode,
-                                               scratch, d_mask, d_changed_list, d_n_changed, status,
+                                               scratch, d_mask, d_changed_list, d_n_changed, status, true,
                                                (cudaStream_t)stream, &launches);
     return e == cudaSuccess ? FTV_OK : FTV_ERR_CUDA;
 }

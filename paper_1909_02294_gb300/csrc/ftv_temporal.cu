@@ -11,6 +11,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "ftv_internal.h"
 
@@ -27,62 +28,128 @@ __device__ __forceinline__ int sample(const void* plane, int64_t pitch, int x, i
     return reinterpret_cast<const uint16_t*>(row)[x];
 }
 
-struct Frames {
-    const void* cur[3];
-    const void* prev[3];
-    const void* ifr[3];
-    int64_t pc[3], pp[3], pi[3];
-};
-
 __device__ __forceinline__ void add64(int64_t* dst, int v) {
     atomicAdd(reinterpret_cast<unsigned long long*>(dst), (unsigned long long)(long long)v);
 }
 
-// One thread per pixel (blockIdx.y = row). Per-pixel differences cur - prev and cur - I are summed per
-// segment; lanes with the same label are reduced in the warp first (one atomic per run and quantity).
+// Per-segment sums over a tile of kAccCols x 2 kAccRows pixels per CTA of 256 threads: each thread walks one
+// column of kAccRows pixels and sums the vertical runs of equal labels in registers (a segment's pixels are
+// contiguous, so a column meets few runs). A finished run is added to the CTA's bins in shared memory,
+// indexed by label - (the tile's least label); labels beyond kBins of it go to global memory directly. At
+// the end each non-empty bin is added to the segment's 64-bit sums, once per tile. All sums are exact
+// integers, so the order of the additions does not change the result. Tile bins are 32-bit: a tile has
+// at most 2048 pixels of differences below 2^16.
+constexpr int kAccCols = 128;  // pixels per tile row, one thread each
+constexpr int kAccRows = 8;    // rows per thread; two threads per column
+constexpr int kBins = 512;
+
+// The references of one launch (kernel parameters, read in place).
+struct TemporalRefs {
+    TemporalRef r[kMaxTemporalRefs];
+};
+
 template <int SB, int NCH, bool HAS_I>
-__global__ void temporal_accumulate_kernel(Frames f, const int32_t* __restrict__ labels, int W, int S,
-                                           int64_t* __restrict__ stats, uint32_t* status) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    const int lane = threadIdx.x & 31;
-    const bool in = x < W;
-    const int l = in ? labels[(int64_t)y * W + x] : -1;
-    const bool ok = in && (unsigned)l < (unsigned)S;
-    if (in && !ok) atomicOr(status, ST_BAD_LABEL);
-    int dp[3] = {0, 0, 0}, di[3] = {0, 0, 0};
-    if (ok) {
+__global__ void __launch_bounds__(2 * kAccCols) temporal_accumulate_kernel(const __grid_constant__ TemporalRefs p,
+                                                                           uint32_t* status) {
+    constexpr int Q = 1 + NCH * (HAS_I ? 2 : 1);  // per segment: n, dP[NCH], dI[NCH]
+    __shared__ int bins[Q][kBins];
+    __shared__ int s_base;
+    const TemporalRef& f = p.r[blockIdx.z];  // blockIdx.z: the reference
+    const int W = f.W, H = f.H, S = f.S;
+    if ((int)blockIdx.x * kAccCols >= W || (int)blockIdx.y * (2 * kAccRows) >= H) return;  // past this view
+    const int32_t* __restrict__ labels = f.labels;
+    int64_t* __restrict__ stats = f.stats;
+    const int tid = threadIdx.x;
+    const int x = blockIdx.x * kAccCols + (tid & (kAccCols - 1));
+    const int y0 = blockIdx.y * (2 * kAccRows) + (tid / kAccCols) * kAccRows;
+    const bool col = x < W;
+    // every load of the column is issued before any is used (the sample loads do not wait for the labels)
+    int lab[kAccRows];
+    int d[kAccRows][Q - 1];
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-            const int a = sample<SB>(f.cur[c], f.pc[c], x, y);
-            dp[c] = a - sample<SB>(f.prev[c], f.pp[c], x, y);
-            if (HAS_I) di[c] = a - sample<SB>(f.ifr[c], f.pi[c], x, y);
-        }
-    }
-    const int key = ok ? l : -1;
-    unsigned rem = __ballot_sync(kFull, ok);
-    while (rem) {
-        const int leader = __ffs(rem) - 1;
-        const int kk = __shfl_sync(kFull, key, leader);
-        const bool mine = key == kk;
-        const unsigned grp = __ballot_sync(kFull, mine);
-        int sums[1 + 2 * NCH];
-        sums[0] = __popc(grp);
+    for (int r = 0; r < kAccRows; ++r) lab[r] = col && y0 + r < H ? __ldg(labels + (int64_t)(y0 + r) * W + x) : -1;
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-            sums[1 + c] = __reduce_add_sync(kFull, mine ? dp[c] : 0);
-            sums[1 + NCH + c] = HAS_I ? __reduce_add_sync(kFull, mine ? di[c] : 0) : 0;
-        }
-        if (lane == leader) {
-            int64_t* st = stats + (int64_t)kk * kStat;
-            add64(&st[0], sums[0]);
+    for (int r = 0; r < kAccRows; ++r) {
+        const int y = y0 + r;
+#pragma unroll
+        for (int q = 0; q < Q - 1; ++q) d[r][q] = 0;
+        if (col && y < H) {
 #pragma unroll
             for (int c = 0; c < NCH; ++c) {
-                add64(&st[1 + c], sums[1 + c]);
-                if (HAS_I) add64(&st[4 + c], sums[1 + NCH + c]);
+                const int v = sample<SB>(f.cur[c], f.pc[c], x, y);
+                d[r][c] = v - sample<SB>(f.prev[c], f.pp[c], x, y);
+                if (HAS_I) d[r][NCH + c] = v - sample<SB>(f.ifr[c], f.pi[c], x, y);
             }
         }
-        rem &= ~grp;
+    }
+    int lmin = INT_MAX;
+    bool bad = false;
+#pragma unroll
+    for (int r = 0; r < kAccRows; ++r) {
+        const bool in = col && y0 + r < H;
+        if ((unsigned)lab[r] < (unsigned)S) {
+            lmin = min(lmin, lab[r]);
+        } else {
+            bad = bad || in;
+            lab[r] = -1;
+        }
+    }
+    if (bad) atomicOr(status, ST_BAD_LABEL);
+    for (int i = tid; i < Q * kBins; i += 2 * kAccCols) (&bins[0][0])[i] = 0;
+    if (tid == 0) s_base = INT_MAX;
+    __syncthreads();
+    lmin = __reduce_min_sync(kFull, lmin);
+    if ((tid & 31) == 0 && lmin != INT_MAX) atomicMin(&s_base, lmin);
+    __syncthreads();
+    const int base = s_base;
+
+    int cur = -1;
+    int acc[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) acc[q] = 0;
+    auto flush = [&]() {
+        const unsigned bi = (unsigned)(cur - base);
+        if (bi < (unsigned)kBins) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+                if (q == 0 || acc[q] != 0) atomicAdd(&bins[q][bi], acc[q]);
+        } else {
+            int64_t* st = stats + (int64_t)cur * kStat;
+            add64(&st[0], acc[0]);
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                add64(&st[1 + c], acc[1 + c]);
+                if (HAS_I) add64(&st[4 + c], acc[1 + NCH + c]);
+            }
+        }
+    };
+#pragma unroll
+    for (int r = 0; r < kAccRows; ++r) {
+        const int l = lab[r];
+        if (l != cur) {
+            if (cur >= 0) flush();
+            cur = l;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) acc[q] = 0;
+        }
+        if (l >= 0) {
+            acc[0] += 1;
+#pragma unroll
+            for (int q = 1; q < Q; ++q) acc[q] += d[r][q - 1];
+        }
+    }
+    if (cur >= 0) flush();
+    __syncthreads();
+    for (int i = tid; i < kBins; i += 2 * kAccCols) {
+        const int n = bins[0][i];
+        if (n == 0) continue;
+        int64_t* st = stats + (int64_t)(base + i) * kStat;
+        add64(&st[0], n);
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            if (bins[1 + c][i] != 0) add64(&st[1 + c], bins[1 + c][i]);
+            if (HAS_I && bins[1 + NCH + c][i] != 0) add64(&st[4 + c], bins[1 + NCH + c][i]);
+        }
     }
 }
 
@@ -115,41 +182,63 @@ __device__ int block_exclusive_scan(int v, int* total) {
 __device__ __forceinline__ int64_t abs64(int64_t v) { return v < 0 ? -v : v; }
 
 // The masks and the ordered list of changed segments, in two passes over blocks of kChunk segments.
-// decide: one thread per segment sets its mask; each block's count of changed segments goes to the spare
-// word (index 7) of the stats of its first segment. compact: each block adds up the counts of the blocks
+// decide: one thread per segment sets its mask and clears its sums (words 0 to 6), so that the next call
+// needs no clearing pass; each block's count of changed segments goes to the spare word (index 7) of the
+// stats of its first segment. compact: each block adds up the counts of the blocks
 // before it, scans its own changed flags and writes their positions; the last block writes the total.
-constexpr int kChunk = 1024;
+constexpr int kChunk = 256;
 
+// st: the segment's 16-byte-aligned sums, read in full with three vector loads before any is tested.
 __device__ __forceinline__ int decide(const int64_t* st, int nch, bool has_i, int t_p, int t_i) {
-    const int64_t n = st[0];
+    const longlong2 a = reinterpret_cast<const longlong2*>(st)[0], b = reinterpret_cast<const longlong2*>(st)[1],
+                    c = reinterpret_cast<const longlong2*>(st)[2];
+    const int64_t w[6] = {a.x, a.y, b.x, b.y, c.x, c.y};  // n, dP[3], dI[0..1]; dI[2] is word 6
+    const int64_t n = w[0], di2 = st[6];
     int m = FTV_MASK_CHANGED;
     if (n > 0) {
         bool okp = true, oki = has_i;
-        for (int c = 0; c < nch; ++c) {
-            okp = okp && abs64(st[1 + c]) < (int64_t)t_p * n;
-            oki = oki && abs64(st[4 + c]) < (int64_t)t_i * n;
+        for (int ch = 0; ch < nch; ++ch) {
+            okp = okp && abs64(w[1 + ch]) < (int64_t)t_p * n;
+            oki = oki && abs64(ch < 2 ? w[4 + ch] : di2) < (int64_t)t_i * n;
         }
         m = okp ? FTV_MASK_REUSE_P : (oki ? FTV_MASK_REUSE_I : FTV_MASK_CHANGED);
     }
     return m;
 }
 
-__global__ void __launch_bounds__(kChunk) temporal_decide_kernel(int64_t* __restrict__ stats, int S, int nch, bool has_i,
-                                                                 int t_p, int t_i, uint8_t* __restrict__ mask) {
+// blockIdx.y: the reference; blocks past its segments return.
+__global__ void __launch_bounds__(kChunk) temporal_decide_kernel(const __grid_constant__ TemporalRefs p, int nch,
+                                                                 bool has_i, int t_p, int t_i) {
+    const TemporalRef& R = p.r[blockIdx.y];
+    const int S = R.S;
+    if ((int)blockIdx.x * kChunk >= S) return;
+    int64_t* __restrict__ stats = R.stats;
+    uint8_t* __restrict__ mask = R.mask;
     const int s = blockIdx.x * kChunk + threadIdx.x;
     int m = FTV_MASK_CHANGED;
     if (s < S) {
-        m = decide(stats + (int64_t)s * kStat, nch, has_i, t_p, t_i);
+        int64_t* st = stats + (int64_t)s * kStat;
+        m = decide(st, nch, has_i, t_p, t_i);
         mask[s] = (uint8_t)m;
+        // leave the sums zero for the next call (word 7 is not a sum)
+        reinterpret_cast<longlong2*>(st)[0] = make_longlong2(0, 0);
+        reinterpret_cast<longlong2*>(st)[1] = make_longlong2(0, 0);
+        reinterpret_cast<longlong2*>(st)[2] = make_longlong2(0, 0);
+        st[6] = 0;
     }
     const int cnt = __syncthreads_count(s < S && m == FTV_MASK_CHANGED);
     if (threadIdx.x == 0) stats[(int64_t)blockIdx.x * kChunk * kStat + 7] = cnt;
 }
 
-__global__ void __launch_bounds__(kChunk) temporal_compact_kernel(const int64_t* __restrict__ stats, int S,
-                                                                  const uint8_t* __restrict__ mask,
-                                                                  int32_t* __restrict__ changed, int32_t* n_changed) {
+// blockIdx.y: the reference; blocks past its chunks return (a reference without segments has one chunk).
+__global__ void __launch_bounds__(kChunk) temporal_compact_kernel(const __grid_constant__ TemporalRefs p) {
     __shared__ int s_base;
+    const TemporalRef& R = p.r[blockIdx.y];
+    const int S = R.S, chunks = S > 0 ? (S + kChunk - 1) / kChunk : 1;
+    if ((int)blockIdx.x >= chunks) return;
+    const int64_t* __restrict__ stats = R.stats;
+    const uint8_t* __restrict__ mask = R.mask;
+    int32_t* __restrict__ changed = R.changed;
     if (threadIdx.x == 0) s_base = 0;
     __syncthreads();
     int before = 0;  // changed segments of the blocks before this one
@@ -162,7 +251,7 @@ __global__ void __launch_bounds__(kChunk) temporal_compact_kernel(const int64_t*
     int total;
     const int pos = block_exclusive_scan(flag, &total);
     if (flag) changed[s_base + pos] = s;
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *n_changed = s_base + total;
+    if ((int)blockIdx.x == chunks - 1 && threadIdx.x == 0) *R.n_changed = s_base + total;
 }
 
 // One warp per listed segment: least-cost label, smallest on ties; masked segments adopt.
@@ -221,42 +310,70 @@ __global__ void depth_map_kernel(const int32_t* __restrict__ labels, int W, int 
 
 }  // namespace
 
+cudaError_t launch_temporal_refs(const TemporalRef* refs, int n, int sample_bytes, int mode, bool has_i, int t_p,
+                                 int t_i, uint32_t* status, cudaStream_t s, int64_t* launches) {
+    if (n <= 0) return cudaSuccess;
+    if (n > kMaxTemporalRefs) return cudaErrorInvalidValue;
+    TemporalRefs p{};
+    int tx = 0, ty = 0, chunks = 1;
+    bool any_s = false;
+    for (int k = 0; k < n; ++k) {
+        p.r[k] = refs[k];
+        tx = std::max(tx, (refs[k].W + kAccCols - 1) / kAccCols);
+        ty = std::max(ty, (refs[k].H + 2 * kAccRows - 1) / (2 * kAccRows));
+        chunks = std::max(chunks, (refs[k].S + kChunk - 1) / kChunk);
+        any_s = any_s || refs[k].S > 0;
+    }
+    const int nch = mode == FTV_TM_ALL_YUV ? 3 : 1;
+    if (tx > 0 && ty > 0) {
+        const dim3 block(2 * kAccCols), grid(tx, ty, n);
+#define FTV_T(SB, NCH, HI) temporal_accumulate_kernel<SB, NCH, HI><<<grid, block, 0, s>>>(p, status)
+        if (sample_bytes == 1) {
+            if (nch == 1) { if (has_i) FTV_T(1, 1, true); else FTV_T(1, 1, false); }
+            else { if (has_i) FTV_T(1, 3, true); else FTV_T(1, 3, false); }
+        } else {
+            if (nch == 1) { if (has_i) FTV_T(2, 1, true); else FTV_T(2, 1, false); }
+            else { if (has_i) FTV_T(2, 3, true); else FTV_T(2, 3, false); }
+        }
+#undef FTV_T
+        *launches += 1;
+    }
+    if (any_s) {
+        temporal_decide_kernel<<<dim3(chunks, n), kChunk, 0, s>>>(p, nch, has_i, t_p, t_i);
+        *launches += 1;
+    }
+    temporal_compact_kernel<<<dim3(chunks, n), kChunk, 0, s>>>(p);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_temporal(const void* const* cur, const int64_t* cur_pitch, const void* const* prev,
                             const int64_t* prev_pitch, const void* const* ifr, const int64_t* ifr_pitch,
                             int sample_bytes, const int32_t* labels, int W, int H, int S, int t_p, int t_i,
                             int mode, int64_t* stats, uint8_t* mask, int32_t* changed, int32_t* n_changed,
-                            uint32_t* status, cudaStream_t s, int64_t* launches) {
-    cudaError_t e = cudaMemsetAsync(stats, 0, sizeof(int64_t) * kStat * (size_t)(S > 0 ? S : 1), s);
-    if (e != cudaSuccess) return e;
-    Frames f{};
-    const int nch = mode == FTV_TM_ALL_YUV ? 3 : 1;
+                            uint32_t* status, bool clear, cudaStream_t s, int64_t* launches) {
+    if (clear) {
+        const cudaError_t e = cudaMemsetAsync(stats, 0, sizeof(int64_t) * kStat * (size_t)(S > 0 ? S : 1), s);
+        if (e != cudaSuccess) return e;
+    }
+    TemporalRef r{};
     for (int c = 0; c < 3; ++c) {
-        f.cur[c] = cur[c];
-        f.prev[c] = prev[c];
-        f.ifr[c] = ifr ? ifr[c] : nullptr;
-        f.pc[c] = cur_pitch[c];
-        f.pp[c] = prev_pitch[c];
-        f.pi[c] = ifr ? ifr_pitch[c] : 0;
+        r.cur[c] = cur[c];
+        r.prev[c] = prev[c];
+        r.ifr[c] = ifr ? ifr[c] : nullptr;
+        r.pc[c] = cur_pitch[c];
+        r.pp[c] = prev_pitch[c];
+        r.pi[c] = ifr ? ifr_pitch[c] : 0;
     }
-    const dim3 block(256), grid((W + 255) / 256, H);
-    const bool hi = ifr != nullptr;
-#define FTV_T(SB, NCH, HI) temporal_accumulate_kernel<SB, NCH, HI><<<grid, block, 0, s>>>(f, labels, W, S, stats, status)
-    if (W > 0 && H > 0) {
-        if (sample_bytes == 1) {
-            if (nch == 1) { if (hi) FTV_T(1, 1, true); else FTV_T(1, 1, false); }
-            else { if (hi) FTV_T(1, 3, true); else FTV_T(1, 3, false); }
-        } else {
-            if (nch == 1) { if (hi) FTV_T(2, 1, true); else FTV_T(2, 1, false); }
-            else { if (hi) FTV_T(2, 3, true); else FTV_T(2, 3, false); }
-        }
-        *launches += 1;
-    }
-#undef FTV_T
-    const int chunks = std::max(1, (S + kChunk - 1) / kChunk);
-    if (S > 0) temporal_decide_kernel<<<chunks, kChunk, 0, s>>>(stats, S, nch, hi, t_p, t_i, mask);
-    temporal_compact_kernel<<<chunks, kChunk, 0, s>>>(stats, S, mask, changed, n_changed);
-    *launches += S > 0 ? 2 : 1;
-    return cudaGetLastError();
+    r.labels = labels;
+    r.stats = stats;
+    r.mask = mask;
+    r.changed = changed;
+    r.n_changed = n_changed;
+    r.W = W;
+    r.H = H;
+    r.S = S;
+    return launch_temporal_refs(&r, 1, sample_bytes, mode, ifr != nullptr, t_p, t_i, status, s, launches);
 }
 
 cudaError_t launch_wta(const int32_t* cost, int S, int L, const uint8_t* mask, const uint16_t* prev_label,

@@ -75,6 +75,7 @@ def _load() -> ctypes.CDLL:
         "ftv_segment_index": [vp, i32, vp, i32, vp],
         "ftv_cost_volume": [vp, vp, vp, vp, vp, vp, vp, vp, vp],
         "ftv_temporal_mask": [vp, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp],
+        "ftv_temporal_mask_views": [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, vp, vp, vp, vp],
         "ftv_wta_depth": [vp, i32, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp],
         "ftv_check": [vp, vp],
         "ftv_culled_evaluations": [vp, vp, vp],
@@ -139,7 +140,7 @@ lib = _load()
 EXPORTED = ["ftv_depth_init", "ftv_depth_destroy", "ftv_compute_homographies", "ftv_get_homographies",
             "ftv_get_homographies_f64", "ftv_compute_homographies_f64", "ftv_fp64_recomputed", "ftv_set_launch_shape", "ftv_get_launch_shape",
             "ftv_autotune", "ftv_get_neighbours",
-            "ftv_get_label_depths", "ftv_segment_index", "ftv_cost_volume", "ftv_temporal_mask",
+            "ftv_get_label_depths", "ftv_segment_index", "ftv_cost_volume", "ftv_temporal_mask", "ftv_temporal_mask_views",
             "ftv_wta_depth", "ftv_check", "ftv_culled_evaluations", "ftv_launch_count", "ftv_status_str", "ftv_set_profiling",
             "ftv_last_kernel_ms", "ftv_temporal_mask_static", "ftv_stream_init", "ftv_stream_footprint",
             "ftv_stream_labels", "ftv_stream_mask", "ftv_stream_changed", "ftv_stream_state_bytes", "ftv_stream_state_save",
@@ -379,6 +380,24 @@ def ftv_temporal_mask(ctx: Context, ref_index: int, cur, prev, iframe, labels, n
     _ok(lib.ftv_temporal_mask(ctx.handle, ref_index, cp, cpi, pp, ppi, ip, ipi, _ptr(labels), n_segments, t_p, t_i,
                               mode, _ptr(mask), _ptr(changed_list), _ptr(n_changed), _stream(stream)),
         "ftv_temporal_mask")
+
+
+def ftv_temporal_mask_views(ctx: Context, ref_indices, cur, prev, iframe, labels, n_segments, t_p: int, t_i: int,
+                            mode: int, masks, changed_lists, n_changed, stream=None) -> None:
+    """ftv_temporal_mask for several references in one launch sequence: cur, prev (and iframe, or None) are
+    lists of (Y, Cb, Cr) plane triples, one per reference; labels, n_segments, masks, changed_lists and
+    n_changed are per-reference lists."""
+    n = len(ref_indices)
+    cp, cpi = _trip([t for trip in cur for t in trip])
+    pp, ppi = _trip([t for trip in prev for t in trip])
+    ip, ipi = _trip([t for trip in iframe for t in trip]) if iframe is not None else (None, None)
+    _ok(lib.ftv_temporal_mask_views(ctx.handle, n, _arr(ctypes.c_int32, ref_indices), cp, cpi, pp, ppi, ip, ipi,
+                                    _arr(ctypes.c_void_p, [_ptr(t) for t in labels]),
+                                    _arr(ctypes.c_int32, n_segments), t_p, t_i, mode,
+                                    _arr(ctypes.c_void_p, [_ptr(t) for t in masks]),
+                                    _arr(ctypes.c_void_p, [_ptr(t) for t in changed_lists]),
+                                    _arr(ctypes.c_void_p, [_ptr(t) for t in n_changed]), _stream(stream)),
+        "ftv_temporal_mask_views")
 
 
 def ftv_wta_depth(ctx: Context, ref_index: int, cost, n_segments: int, label_out, *, mask=None, prev_label=None,

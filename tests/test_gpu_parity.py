@@ -369,6 +369,96 @@ def test_temporal_mask_and_adoption_bit_exact():
     run.close()
 
 
+def test_temporal_mask_label_layouts_and_call_sequences():
+    """Label maps the kernel's per-tile bins do not cover, called in sequence on one context whose segment
+    count grows, shrinks and grows again (the decide pass leaves the sums zero for the next call): one label
+    per pixel at random (a tile's labels span far more than its bins, so runs go to global memory
+    directly), three segments of whole column bands (runs span every tile) and the workload's own map, in
+    both channel modes. A call with a label outside [0, S) reports it, and the next call is exact again.
+    Frames of the reduced temporal workload (244 x 138: ragged in both tile directions; Sec. III-E)."""
+    wl = make_workload("temporal", reduced=True)
+    run = Run(wl, max_segments=6000)
+    r = wl.ref_views[2]
+    frames = [run.planes(f)[r] for f in range(3)]
+    host = [wl.view(r, f) for f in range(3)]
+    lab0, S0 = wl.labels(r)
+    Hh, W = lab0.shape
+    rng = np.random.default_rng(11)
+    rand = rng.integers(0, 5000, size=(Hh, W), dtype=np.int32)
+    bands = np.repeat((np.arange(W, dtype=np.int32) * 3 // W)[None, :], Hh, axis=0)
+
+    def check(lab, S, mode, cur, prev, ifr):
+        mask = torch.empty(S, dtype=torch.uint8, device="cuda")
+        changed = torch.empty(S, dtype=torch.int32, device="cuda")
+        n = torch.empty(1, dtype=torch.int32, device="cuda")
+        ftv.ftv_temporal_mask(run.ctx, 2, frames[cur], frames[prev], frames[ifr] if ifr is not None else None,
+                              dev(lab), S, 12, 4, mode, mask, changed, n)
+        assert run.check() == 0
+        m_ref, ch_ref, n_ref = oracle.temporal_mask(lab, S, host[cur], host[prev],
+                                                    host[ifr] if ifr is not None else None, 2, 12, 4, mode)
+        assert np.array_equal(mask.cpu().numpy(), m_ref)
+        assert int(n.item()) == n_ref
+        assert np.array_equal(changed.cpu().numpy()[:n_ref], ch_ref)
+
+    for lab, S in [(rand, 5000), (lab0, S0), (bands, 3), (rand, 5000), (lab0, S0)]:
+        check(lab, S, 0, 1, 0, 0)
+        check(lab, S, 1, 2, 1, None)
+    bad = lab0.copy()
+    bad[Hh // 2, W // 3] = S0
+    mask = torch.empty(S0, dtype=torch.uint8, device="cuda")
+    changed = torch.empty(S0, dtype=torch.int32, device="cuda")
+    n = torch.empty(1, dtype=torch.int32, device="cuda")
+    ftv.ftv_temporal_mask(run.ctx, 2, frames[1], frames[0], None, dev(bad), S0, 12, 4, 0, mask, changed, n)
+    assert run.check() == ftv.FTV_ERR_INVALID_ARG
+    check(lab0, S0, 0, 1, 0, 0)
+    run.close()
+
+
+def test_temporal_mask_views_equals_the_oracle_per_reference():
+    """Every reference of the reduced temporal workload in one ftv_temporal_mask_views call, two of them with
+    other label maps (one label per pixel at random; five column bands), in both channel modes, with and
+    without the I frame: each reference's mask, ordered list and count equal the oracle's (Sec. III-E). A
+    repeated reference index is refused before anything runs."""
+    wl = make_workload("temporal", reduced=True)
+    run = Run(wl, max_segments=6000)
+    R = len(wl.ref_views)
+    planes = [run.planes(f) for f in range(3)]
+    rng = np.random.default_rng(12)
+    labs = []
+    for i, r in enumerate(wl.ref_views):
+        lab, S = wl.labels(r)
+        if i == 1:
+            lab, S = rng.integers(0, 4000, size=lab.shape, dtype=np.int32), 4000
+        elif i == 4:
+            lab, S = np.repeat((np.arange(lab.shape[1], dtype=np.int32) * 5 // lab.shape[1])[None, :], lab.shape[0],
+                               axis=0), 5
+        labs.append((np.ascontiguousarray(lab), S))
+    labels_d = [dev(l) for l, _ in labs]
+    Ss = [S for _, S in labs]
+    for mode in (0, 1):
+        for cur, prev, ifr in [(1, 0, 0), (2, 1, None)]:
+            masks = [torch.empty(S, dtype=torch.uint8, device="cuda") for S in Ss]
+            changed = [torch.empty(S, dtype=torch.int32, device="cuda") for S in Ss]
+            ns = [torch.empty(1, dtype=torch.int32, device="cuda") for _ in Ss]
+            ftv.ftv_temporal_mask_views(run.ctx, list(range(R)), [planes[cur][r] for r in wl.ref_views],
+                                        [planes[prev][r] for r in wl.ref_views],
+                                        [planes[ifr][r] for r in wl.ref_views] if ifr is not None else None,
+                                        labels_d, Ss, 12, 4, mode, masks, changed, ns)
+            assert run.check() == 0
+            for i, r in enumerate(wl.ref_views):
+                host = [wl.view(r, f) for f in range(3)]
+                m_ref, ch_ref, n_ref = oracle.temporal_mask(labs[i][0], Ss[i], host[cur], host[prev],
+                                                            host[ifr] if ifr is not None else None, 2, 12, 4, mode)
+                assert np.array_equal(masks[i].cpu().numpy(), m_ref), (mode, i)
+                assert int(ns[i].item()) == n_ref, (mode, i)
+                assert np.array_equal(changed[i].cpu().numpy()[:n_ref], ch_ref), (mode, i)
+    with pytest.raises(ftv.FtvError):
+        ftv.ftv_temporal_mask_views(run.ctx, [0, 0], [planes[1][wl.ref_views[0]]] * 2, [planes[0][wl.ref_views[0]]] * 2,
+                                    None, [labels_d[0]] * 2, [Ss[0]] * 2, 12, 4, 0, masks[:1] * 2, changed[:1] * 2,
+                                    ns[:1] * 2)
+    run.close()
+
+
 # ------------------------------------------------------------------------------------ full size, sampled
 
 @pytest.mark.parametrize("name", ["hd8", "uhd15"])
