@@ -518,6 +518,7 @@ static ftv_status temporal_views(ftv_ctx* ctx, int32_t n, const int32_t* ref_ind
             r.W = ctx->refs[ri].W;
             r.H = ctx->refs[ri].H;
             r.S = n_segments[k];
+            r.ms = ctx->max_segments;
             // the decide pass leaves the sums zero; a slot of unknown contents (first use, a failed launch,
             // adjacency scratch) is cleared whole
             if (!ctx->tstats_zero[ri] && slot > 0) e = cudaMemsetAsync(r.stats, 0, slot * sizeof(int64_t), s);

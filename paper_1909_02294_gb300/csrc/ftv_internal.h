@@ -160,7 +160,7 @@ struct ftv_ctx {
     uint32_t* d_status = nullptr;
     ftv::RefJob* d_jobs = nullptr;            // [n_refs]
     ftv::Plan* d_plan = nullptr;
-    int64_t* d_tstats = nullptr;              // per reference: temporal sums [max_segments][8] (adjacency scratch)
+    int64_t* d_tstats = nullptr;              // per reference: temporal sums, 8 planes of max_segments (adjacency scratch)
     std::vector<uint8_t> tstats_zero;         // per reference: its d_tstats slot holds zero sums
     float* d_label_z = nullptr;               // [L]
     int32_t* d_adj_deg = nullptr;             // [max_segments] adjacency: neighbours t > s per segment
@@ -221,8 +221,10 @@ int64_t reciprocal_mismatches();
 
 // Temporal / WTA (ftv_temporal.cu)
 // One reference of a temporal-test launch sequence: its current, previous-P and I frames (plane pointers and
-// pitches in bytes; ifr unused without an I frame), label map [H][W], per-segment sums [S][8] (16-byte
-// aligned; words 0-6 zero on entry, left zero on exit) and outputs.
+// pitches in bytes; ifr unused without an I frame), label map [H][W], per-segment sums and outputs. The sums
+// are eight planes of ms int64 words (ms >= S): word q of segment s at stats[q * ms + s], q = 0 the pixel
+// count, 1 + c and 4 + c the channel-c sums of cur - prev and cur - I, plane 7 the decide pass's per-block
+// counts. Planes 0-6 are zero on entry and left zero on exit.
 struct TemporalRef {
     const void* cur[3];
     const void* prev[3];
@@ -233,7 +235,7 @@ struct TemporalRef {
     uint8_t* mask;
     int32_t* changed;
     int32_t* n_changed;
-    int32_t W, H, S, pad;
+    int32_t W, H, S, ms;
 };
 constexpr int kMaxTemporalRefs = 16;  // references per launch sequence (they travel as kernel parameters)
 // The temporal test of refs[0..n) (n <= kMaxTemporalRefs) in three launches: accumulate, decide, compact.
@@ -242,7 +244,7 @@ cudaError_t launch_temporal_refs(const TemporalRef* refs, int n, int sample_byte
 cudaError_t launch_temporal(const void* const* cur, const int64_t* cur_pitch, const void* const* prev,
                             const int64_t* prev_pitch, const void* const* ifr, const int64_t* ifr_pitch,
                             int sample_bytes, const int32_t* labels, int W, int H, int S, int t_p, int t_i,
-                            int mode, int64_t* stats, uint8_t* mask, int32_t* changed, int32_t* n_changed,
+                            int mode, int64_t* stats, int ms, uint8_t* mask, int32_t* changed, int32_t* n_changed,
                             uint32_t* status, bool clear, cudaStream_t s, int64_t* launches);
 cudaError_t launch_wta(const int32_t* cost, int S, int L, const uint8_t* mask, const uint16_t* prev_label,
                        const uint16_t* ifr_label, const int32_t* list, const int32_t* n_listed, uint16_t* out,

@@ -11,7 +11,7 @@
 
 namespace {
 
-constexpr int kStatWords = 8;     // int64 accumulators per segment, the layout the temporal kernels use
+constexpr int kStatWords = 8;     // int64 accumulators per segment (eight planes of FTV_STATIC_MAX_SEGMENTS)
 constexpr int kSpareWords = 32;   // tail of the array: the status word when the caller passes none
 
 // Accumulators of ftv_temporal_mask_static: FTV_STATIC_MAX_SEGMENTS x 8 int64 (4 MiB for 65536
@@ -83,7 +83,8 @@ extern "C" ftv_status ftv_temporal_mask_static(int32_t width, int32_t height, in
     // the accumulators are cleared on `stream` before use, so the previous call's contents do not matter
     const cudaError_t e = ftv::launch_temporal(d_cur, cur_pitch, d_prev, prev_pitch, d_iframe, iframe_pitch,
                                                sample_bytes, d_labels, width, height, n_segments, t_p, t_i, mode,
-                                               scratch, d_mask, d_changed_list, d_n_changed, status, true,
+                                               scratch, FTV_STATIC_MAX_SEGMENTS, d_mask, d_changed_list,
+                                               d_n_changed, status, true,
                                                (cudaStream_t)stream, &launches);
     return e == cudaSuccess ? FTV_OK : FTV_ERR_CUDA;
 }

@@ -19,29 +19,30 @@ namespace ftv {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kStat = 8;  // per segment: n, dP[3], dI[3], pad
 
 template <int SB>
-__device__ __forceinline__ int sample(const void* plane, int64_t pitch, int x, int y) {
-    const char* row = static_cast<const char*>(plane) + (int64_t)y * pitch;
-    if (SB == 1) return reinterpret_cast<const uint8_t*>(row)[x];
-    return reinterpret_cast<const uint16_t*>(row)[x];
+__device__ __forceinline__ int load_sample(const char* p) {
+    if (SB == 1) return __ldg(reinterpret_cast<const uint8_t*>(p));
+    return __ldg(reinterpret_cast<const uint16_t*>(p));
 }
 
 __device__ __forceinline__ void add64(int64_t* dst, int v) {
     atomicAdd(reinterpret_cast<unsigned long long*>(dst), (unsigned long long)(long long)v);
 }
 
-// Per-segment sums over a tile of kAccCols x 2 kAccRows pixels per CTA of 256 threads: each thread walks one
-// column of kAccRows pixels and sums the vertical runs of equal labels in registers (a segment's pixels are
-// contiguous, so a column meets few runs). A finished run is added to the CTA's bins in shared memory,
-// indexed by label - (the tile's least label); labels beyond kBins of it go to global memory directly. At
-// the end each non-empty bin is added to the segment's 64-bit sums, once per tile. All sums are exact
-// integers, so the order of the additions does not change the result. Tile bins are 32-bit: a tile has
-// at most 2048 pixels of differences below 2^16.
-constexpr int kAccCols = 128;  // pixels per tile row, one thread each
-constexpr int kAccRows = 8;    // rows per thread; two threads per column
+// Per-segment sums over a tile of kAccCols x kAccGroups kAccRows pixels per CTA of 256 threads: each thread
+// walks one column of kAccRows pixels and sums the vertical runs of equal labels in registers (a segment's
+// pixels are contiguous, so a column meets few runs). A finished run is added to the CTA's bins in shared
+// memory, indexed by label - (the tile's least label); labels beyond kBins of it go to global memory
+// directly. At the end each non-empty bin is added to the segment's 64-bit sums, once per tile. All sums are
+// exact integers, so the order of the additions does not change the result. Tile bins are 32-bit: a tile
+// has at most 2048 pixels of differences below 2^16.
+constexpr int kAccCols = 128;   // pixels per tile row, one thread each
+constexpr int kAccRows = 8;     // rows per thread
+constexpr int kAccGroups = 2;   // row groups per CTA
+constexpr int kAccThreads = kAccCols * kAccGroups;
 constexpr int kBins = 512;
+static_assert(kAccThreads == 256, "one CTA of 256 threads per tile");
 
 // The references of one launch (kernel parameters, read in place).
 struct TemporalRefs {
@@ -49,106 +50,138 @@ struct TemporalRefs {
 };
 
 template <int SB, int NCH, bool HAS_I>
-__global__ void __launch_bounds__(2 * kAccCols) temporal_accumulate_kernel(const __grid_constant__ TemporalRefs p,
-                                                                           uint32_t* status) {
+__global__ void __launch_bounds__(kAccThreads) temporal_accumulate_kernel(const __grid_constant__ TemporalRefs p,
+                                                                          uint32_t* status) {
     constexpr int Q = 1 + NCH * (HAS_I ? 2 : 1);  // per segment: n, dP[NCH], dI[NCH]
-    __shared__ int bins[Q][kBins];
-    __shared__ int s_base;
+    constexpr int TR = kAccGroups * kAccRows;     // tile rows
+    __shared__ __align__(16) int bins[Q][kBins];
+    __shared__ int s_base, s_top;
     const TemporalRef& f = p.r[blockIdx.z];  // blockIdx.z: the reference
     const int W = f.W, H = f.H, S = f.S;
-    if ((int)blockIdx.x * kAccCols >= W || (int)blockIdx.y * (2 * kAccRows) >= H) return;  // past this view
-    const int32_t* __restrict__ labels = f.labels;
+    if ((int)blockIdx.x * kAccCols >= W || (int)blockIdx.y * TR >= H) return;  // past this view
     int64_t* __restrict__ stats = f.stats;
     const int tid = threadIdx.x;
-    const int x = blockIdx.x * kAccCols + (tid & (kAccCols - 1));
-    const int y0 = blockIdx.y * (2 * kAccRows) + (tid / kAccCols) * kAccRows;
-    const bool col = x < W;
-    // every load of the column is issued before any is used (the sample loads do not wait for the labels)
-    int lab[kAccRows];
-    int d[kAccRows][Q - 1];
+    const int x = blockIdx.x * kAccCols + tid % kAccCols;
+    const int y0 = blockIdx.y * TR + (tid / kAccCols) * kAccRows;
+    // Every load of the column is issued before any is used: positions past the view's edge are clamped into
+    // it (the block starts inside the view), so the loads need no branch, and those pixels are then dropped
+    // through their label. Each plane's row pointer steps down the column (no per-row multiplication) and
+    // stays on the last row of the view once it is reached.
+    const int xc = min(x, W - 1), yc0 = min(y0, H - 1);
+    const int32_t* pl = f.labels + (int64_t)yc0 * W + xc;
+    const char* pa[NCH];
+    const char* pb[NCH];
+    const char* pe[HAS_I ? NCH : 1];
 #pragma unroll
-    for (int r = 0; r < kAccRows; ++r) lab[r] = col && y0 + r < H ? __ldg(labels + (int64_t)(y0 + r) * W + x) : -1;
+    for (int c = 0; c < NCH; ++c) {
+        pa[c] = static_cast<const char*>(f.cur[c]) + (int64_t)yc0 * f.pc[c] + (int64_t)xc * SB;
+        pb[c] = static_cast<const char*>(f.prev[c]) + (int64_t)yc0 * f.pp[c] + (int64_t)xc * SB;
+        if (HAS_I) pe[c] = static_cast<const char*>(f.ifr[c]) + (int64_t)yc0 * f.pi[c] + (int64_t)xc * SB;
+    }
+    int lab[kAccRows];
+    int a[kAccRows][NCH], b[kAccRows][NCH], e[kAccRows][HAS_I ? NCH : 1];
 #pragma unroll
     for (int r = 0; r < kAccRows; ++r) {
-        const int y = y0 + r;
+        lab[r] = __ldg(pl);
 #pragma unroll
-        for (int q = 0; q < Q - 1; ++q) d[r][q] = 0;
-        if (col && y < H) {
+        for (int c = 0; c < NCH; ++c) {
+            a[r][c] = load_sample<SB>(pa[c]);
+            b[r][c] = load_sample<SB>(pb[c]);
+            if (HAS_I) e[r][c] = load_sample<SB>(pe[c]);
+        }
+        if (r + 1 < kAccRows && y0 + r + 1 < H) {  // next row, unless it lies past the view
+            pl += W;
 #pragma unroll
             for (int c = 0; c < NCH; ++c) {
-                const int v = sample<SB>(f.cur[c], f.pc[c], x, y);
-                d[r][c] = v - sample<SB>(f.prev[c], f.pp[c], x, y);
-                if (HAS_I) d[r][NCH + c] = v - sample<SB>(f.ifr[c], f.pi[c], x, y);
+                pa[c] += f.pc[c];
+                pb[c] += f.pp[c];
+                if (HAS_I) pe[c] += f.pi[c];
             }
         }
     }
-    int lmin = INT_MAX;
+    int lmin = INT_MAX, lmax = -1;
     bool bad = false;
 #pragma unroll
     for (int r = 0; r < kAccRows; ++r) {
-        const bool in = col && y0 + r < H;
-        if ((unsigned)lab[r] < (unsigned)S) {
+        const bool in = x < W && y0 + r < H;
+        if (in && (unsigned)lab[r] < (unsigned)S) {
             lmin = min(lmin, lab[r]);
+            lmax = max(lmax, lab[r]);
         } else {
             bad = bad || in;
             lab[r] = -1;
         }
     }
     if (bad) atomicOr(status, ST_BAD_LABEL);
-    for (int i = tid; i < Q * kBins; i += 2 * kAccCols) (&bins[0][0])[i] = 0;
-    if (tid == 0) s_base = INT_MAX;
+    for (int i = tid; i < Q * kBins / 4; i += kAccThreads) reinterpret_cast<int4*>(&bins[0][0])[i] = make_int4(0, 0, 0, 0);
+    if (tid == 0) {
+        s_base = INT_MAX;
+        s_top = -1;
+    }
     __syncthreads();
     lmin = __reduce_min_sync(kFull, lmin);
-    if ((tid & 31) == 0 && lmin != INT_MAX) atomicMin(&s_base, lmin);
+    lmax = __reduce_max_sync(kFull, lmax);
+    if ((tid & 31) == 0 && lmax >= 0) {
+        atomicMin(&s_base, lmin);
+        atomicMax(&s_top, lmax);
+    }
     __syncthreads();
     const int base = s_base;
 
-    int cur = -1;
-    int acc[Q];
+    // word q of segment s: stats[q * ms + s] (q = 0: n, 1 + c: dP[c], 4 + c: dI[c])
+    const int64_t ms = f.ms;
+    {
+        int cur = -1;
+        int acc[Q];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) acc[q] = 0;
-    auto flush = [&]() {
-        const unsigned bi = (unsigned)(cur - base);
-        if (bi < (unsigned)kBins) {
+        for (int q = 0; q < Q; ++q) acc[q] = 0;
+        auto flush = [&]() {
+            const unsigned bi = (unsigned)(cur - base);
+            if (bi < (unsigned)kBins) {
 #pragma unroll
-            for (int q = 0; q < Q; ++q)
-                if (q == 0 || acc[q] != 0) atomicAdd(&bins[q][bi], acc[q]);
-        } else {
-            int64_t* st = stats + (int64_t)cur * kStat;
-            add64(&st[0], acc[0]);
+                for (int q = 0; q < Q; ++q)
+                    if (q == 0 || acc[q] != 0) atomicAdd(&bins[q][bi], acc[q]);
+            } else {
+                add64(&stats[cur], acc[0]);
 #pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                add64(&st[1 + c], acc[1 + c]);
-                if (HAS_I) add64(&st[4 + c], acc[1 + NCH + c]);
+                for (int c = 0; c < NCH; ++c) {
+                    add64(&stats[(1 + c) * ms + cur], acc[1 + c]);
+                    if (HAS_I) add64(&stats[(4 + c) * ms + cur], acc[1 + NCH + c]);
+                }
+            }
+        };
+#pragma unroll
+        for (int r = 0; r < kAccRows; ++r) {
+            const int l = lab[r];
+            if (l != cur) {
+                if (cur >= 0) flush();
+                cur = l;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) acc[q] = 0;
+            }
+            if (l >= 0) {
+                acc[0] += 1;
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) {
+                    acc[1 + c] += a[r][c] - b[r][c];
+                    if (HAS_I) acc[1 + NCH + c] += a[r][c] - e[r][c];
+                }
             }
         }
-    };
-#pragma unroll
-    for (int r = 0; r < kAccRows; ++r) {
-        const int l = lab[r];
-        if (l != cur) {
-            if (cur >= 0) flush();
-            cur = l;
-#pragma unroll
-            for (int q = 0; q < Q; ++q) acc[q] = 0;
-        }
-        if (l >= 0) {
-            acc[0] += 1;
-#pragma unroll
-            for (int q = 1; q < Q; ++q) acc[q] += d[r][q - 1];
-        }
+        if (cur >= 0) flush();
     }
-    if (cur >= 0) flush();
     __syncthreads();
-    for (int i = tid; i < kBins; i += 2 * kAccCols) {
+    // the bins in use: the tile's labels from base to s_top (those beyond kBins went to global memory)
+    const int used = min(kBins, s_top - base + 1);
+    for (int i = tid; i < used; i += kAccThreads) {
         const int n = bins[0][i];
         if (n == 0) continue;
-        int64_t* st = stats + (int64_t)(base + i) * kStat;
-        add64(&st[0], n);
+        const int64_t sg = base + i;
+        add64(&stats[sg], n);
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
-            if (bins[1 + c][i] != 0) add64(&st[1 + c], bins[1 + c][i]);
-            if (HAS_I && bins[1 + NCH + c][i] != 0) add64(&st[4 + c], bins[1 + NCH + c][i]);
+            if (bins[1 + c][i] != 0) add64(&stats[(1 + c) * ms + sg], bins[1 + c][i]);
+            if (HAS_I && bins[1 + NCH + c][i] != 0) add64(&stats[(4 + c) * ms + sg], bins[1 + NCH + c][i]);
         }
     }
 }
@@ -182,52 +215,51 @@ __device__ int block_exclusive_scan(int v, int* total) {
 __device__ __forceinline__ int64_t abs64(int64_t v) { return v < 0 ? -v : v; }
 
 // The masks and the ordered list of changed segments, in two passes over blocks of kChunk segments.
-// decide: one thread per segment sets its mask and clears its sums (words 0 to 6), so that the next call
-// needs no clearing pass; each block's count of changed segments goes to the spare word (index 7) of the
-// stats of its first segment. compact: each block adds up the counts of the blocks
-// before it, scans its own changed flags and writes their positions; the last block writes the total.
+// decide: one thread per segment reads its sums (one word from each plane in use, coalesced over the block),
+// sets its mask and clears those words, so that the next call needs no clearing pass; each block's count of
+// changed segments goes to plane 7 at the block's index. compact: each block adds up the counts of the
+// blocks before it, scans its own changed flags and writes their positions; the last block writes the total.
 constexpr int kChunk = 256;
 
-// st: the segment's 16-byte-aligned sums, read in full with three vector loads before any is tested.
-__device__ __forceinline__ int decide(const int64_t* st, int nch, bool has_i, int t_p, int t_i) {
-    const longlong2 a = reinterpret_cast<const longlong2*>(st)[0], b = reinterpret_cast<const longlong2*>(st)[1],
-                    c = reinterpret_cast<const longlong2*>(st)[2];
-    const int64_t w[6] = {a.x, a.y, b.x, b.y, c.x, c.y};  // n, dP[3], dI[0..1]; dI[2] is word 6
-    const int64_t n = w[0], di2 = st[6];
-    int m = FTV_MASK_CHANGED;
-    if (n > 0) {
-        bool okp = true, oki = has_i;
-        for (int ch = 0; ch < nch; ++ch) {
-            okp = okp && abs64(w[1 + ch]) < (int64_t)t_p * n;
-            oki = oki && abs64(ch < 2 ? w[4 + ch] : di2) < (int64_t)t_i * n;
-        }
-        m = okp ? FTV_MASK_REUSE_P : (oki ? FTV_MASK_REUSE_I : FTV_MASK_CHANGED);
-    }
-    return m;
-}
-
 // blockIdx.y: the reference; blocks past its segments return.
-__global__ void __launch_bounds__(kChunk) temporal_decide_kernel(const __grid_constant__ TemporalRefs p, int nch,
-                                                                 bool has_i, int t_p, int t_i) {
+template <int NCH, bool HAS_I>
+__global__ void __launch_bounds__(kChunk) temporal_decide_kernel(const __grid_constant__ TemporalRefs p, int t_p,
+                                                                 int t_i) {
     const TemporalRef& R = p.r[blockIdx.y];
     const int S = R.S;
     if ((int)blockIdx.x * kChunk >= S) return;
     int64_t* __restrict__ stats = R.stats;
-    uint8_t* __restrict__ mask = R.mask;
+    const int64_t ms = R.ms;
     const int s = blockIdx.x * kChunk + threadIdx.x;
     int m = FTV_MASK_CHANGED;
     if (s < S) {
-        int64_t* st = stats + (int64_t)s * kStat;
-        m = decide(st, nch, has_i, t_p, t_i);
-        mask[s] = (uint8_t)m;
-        // leave the sums zero for the next call (word 7 is not a sum)
-        reinterpret_cast<longlong2*>(st)[0] = make_longlong2(0, 0);
-        reinterpret_cast<longlong2*>(st)[1] = make_longlong2(0, 0);
-        reinterpret_cast<longlong2*>(st)[2] = make_longlong2(0, 0);
-        st[6] = 0;
+        int64_t dp[NCH], di[HAS_I ? NCH : 1];
+        const int64_t n = stats[s];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            dp[c] = stats[(1 + c) * ms + s];
+            if (HAS_I) di[c] = stats[(4 + c) * ms + s];
+        }
+        if (n > 0) {
+            bool okp = true, oki = HAS_I;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                okp = okp && abs64(dp[c]) < (int64_t)t_p * n;
+                if (HAS_I) oki = oki && abs64(di[c]) < (int64_t)t_i * n;
+            }
+            m = okp ? FTV_MASK_REUSE_P : (oki ? FTV_MASK_REUSE_I : FTV_MASK_CHANGED);
+        }
+        R.mask[s] = (uint8_t)m;
+        // leave the sums zero for the next call
+        stats[s] = 0;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            stats[(1 + c) * ms + s] = 0;
+            if (HAS_I) stats[(4 + c) * ms + s] = 0;
+        }
     }
     const int cnt = __syncthreads_count(s < S && m == FTV_MASK_CHANGED);
-    if (threadIdx.x == 0) stats[(int64_t)blockIdx.x * kChunk * kStat + 7] = cnt;
+    if (threadIdx.x == 0) stats[7 * ms + blockIdx.x] = cnt;
 }
 
 // blockIdx.y: the reference; blocks past its chunks return (a reference without segments has one chunk).
@@ -236,13 +268,13 @@ __global__ void __launch_bounds__(kChunk) temporal_compact_kernel(const __grid_c
     const TemporalRef& R = p.r[blockIdx.y];
     const int S = R.S, chunks = S > 0 ? (S + kChunk - 1) / kChunk : 1;
     if ((int)blockIdx.x >= chunks) return;
-    const int64_t* __restrict__ stats = R.stats;
+    const int64_t* __restrict__ counts = R.stats + 7 * (int64_t)R.ms;
     const uint8_t* __restrict__ mask = R.mask;
     int32_t* __restrict__ changed = R.changed;
     if (threadIdx.x == 0) s_base = 0;
     __syncthreads();
     int before = 0;  // changed segments of the blocks before this one
-    for (int b = threadIdx.x; b < (int)blockIdx.x; b += kChunk) before += (int)stats[(int64_t)b * kChunk * kStat + 7];
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += kChunk) before += (int)counts[b];
     before = __reduce_add_sync(kFull, before);
     if ((threadIdx.x & 31) == 0 && before) atomicAdd(&s_base, before);
     __syncthreads();
@@ -320,13 +352,13 @@ cudaError_t launch_temporal_refs(const TemporalRef* refs, int n, int sample_byte
     for (int k = 0; k < n; ++k) {
         p.r[k] = refs[k];
         tx = std::max(tx, (refs[k].W + kAccCols - 1) / kAccCols);
-        ty = std::max(ty, (refs[k].H + 2 * kAccRows - 1) / (2 * kAccRows));
+        ty = std::max(ty, (refs[k].H + kAccGroups * kAccRows - 1) / (kAccGroups * kAccRows));
         chunks = std::max(chunks, (refs[k].S + kChunk - 1) / kChunk);
         any_s = any_s || refs[k].S > 0;
     }
     const int nch = mode == FTV_TM_ALL_YUV ? 3 : 1;
     if (tx > 0 && ty > 0) {
-        const dim3 block(2 * kAccCols), grid(tx, ty, n);
+        const dim3 block(kAccThreads), grid(tx, ty, n);
 #define FTV_T(SB, NCH, HI) temporal_accumulate_kernel<SB, NCH, HI><<<grid, block, 0, s>>>(p, status)
         if (sample_bytes == 1) {
             if (nch == 1) { if (has_i) FTV_T(1, 1, true); else FTV_T(1, 1, false); }
@@ -339,7 +371,14 @@ cudaError_t launch_temporal_refs(const TemporalRef* refs, int n, int sample_byte
         *launches += 1;
     }
     if (any_s) {
-        temporal_decide_kernel<<<dim3(chunks, n), kChunk, 0, s>>>(p, nch, has_i, t_p, t_i);
+        const dim3 grid(chunks, n);
+        if (nch == 1) {
+            if (has_i) temporal_decide_kernel<1, true><<<grid, kChunk, 0, s>>>(p, t_p, t_i);
+            else temporal_decide_kernel<1, false><<<grid, kChunk, 0, s>>>(p, t_p, t_i);
+        } else {
+            if (has_i) temporal_decide_kernel<3, true><<<grid, kChunk, 0, s>>>(p, t_p, t_i);
+            else temporal_decide_kernel<3, false><<<grid, kChunk, 0, s>>>(p, t_p, t_i);
+        }
         *launches += 1;
     }
     temporal_compact_kernel<<<dim3(chunks, n), kChunk, 0, s>>>(p);
@@ -350,10 +389,10 @@ cudaError_t launch_temporal_refs(const TemporalRef* refs, int n, int sample_byte
 cudaError_t launch_temporal(const void* const* cur, const int64_t* cur_pitch, const void* const* prev,
                             const int64_t* prev_pitch, const void* const* ifr, const int64_t* ifr_pitch,
                             int sample_bytes, const int32_t* labels, int W, int H, int S, int t_p, int t_i,
-                            int mode, int64_t* stats, uint8_t* mask, int32_t* changed, int32_t* n_changed,
+                            int mode, int64_t* stats, int ms, uint8_t* mask, int32_t* changed, int32_t* n_changed,
                             uint32_t* status, bool clear, cudaStream_t s, int64_t* launches) {
-    if (clear) {
-        const cudaError_t e = cudaMemsetAsync(stats, 0, sizeof(int64_t) * kStat * (size_t)(S > 0 ? S : 1), s);
+    if (clear) {  // planes 0 to 6 over the call's segments
+        const cudaError_t e = cudaMemsetAsync(stats, 0, sizeof(int64_t) * (6 * (size_t)ms + (size_t)S), s);
         if (e != cudaSuccess) return e;
     }
     TemporalRef r{};
@@ -373,6 +412,7 @@ cudaError_t launch_temporal(const void* const* cur, const int64_t* cur_pitch, co
     r.W = W;
     r.H = H;
     r.S = S;
+    r.ms = ms;
     return launch_temporal_refs(&r, 1, sample_bytes, mode, ifr != nullptr, t_p, t_i, status, s, launches);
 }
 

@@ -114,3 +114,38 @@ def test_static_scratch_refuses_host_memory_before_launching():
                                               None, host_labels.data_ptr(), S, 12, 4, 0, m.data_ptr(), c.data_ptr(),
                                               n.data_ptr(), None, torch.cuda.current_stream().cuda_stream)
     assert rc == ftv.FTV_ERR_INVALID_ARG
+
+
+def test_static_entry_odd_width_and_unaligned_planes_equal_the_oracle():
+    """A view 243 pixels wide (odd: the kernel loads its two columns one sample at a time and clamps the second
+    one at the right edge) whose planes start one sample past a 4-byte boundary, in both channel modes, with
+    and without the I frame: mask, ordered list and count equal the oracle's (Sec. III-E)."""
+    import types
+    import oracle
+    wl = make_workload("temporal", reduced=True)
+    r = wl.ref_views[3]
+    lab, S = wl.labels(r)
+    H, W = lab.shape[0], lab.shape[1] - 1
+    labels = torch.from_numpy(np.ascontiguousarray(lab[:, 1:])).cuda()
+    host = []
+    dev_planes = []
+    for fr in range(3):
+        v = wl.view(r, fr)
+        host.append(types.SimpleNamespace(Y=v.Y[:, 1:], U=v.U[:, 1:], V=v.V[:, 1:]))
+        # full-width device planes, sliced one column in: the base is 2 bytes past a 4-byte boundary
+        dev_planes.append(tuple(torch.from_numpy(np.ascontiguousarray(a)).cuda()[:, 1:] for a in (v.Y, v.U, v.V)))
+    assert dev_planes[0][0].data_ptr() % 4 == 2
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for cur, prev, ifr, mode in [(1, 0, 0, ftv.FTV_TM_ALL_YUV), (2, 1, None, ftv.FTV_TM_Y_ONLY),
+                                 (2, 0, 1, ftv.FTV_TM_Y_ONLY)]:
+        m, c, n = _outputs(S)
+        ftv.ftv_temporal_mask_static(W, H, 2, dev_planes[cur], dev_planes[prev],
+                                     dev_planes[ifr] if ifr is not None else None, labels, S, 12, 4, mode, m, c, n,
+                                     status=status)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        m_ref, ch_ref, n_ref = oracle.temporal_mask(np.ascontiguousarray(lab[:, 1:]), S, host[cur], host[prev],
+                                                    host[ifr] if ifr is not None else None, 2, 12, 4, mode)
+        assert np.array_equal(m.cpu().numpy(), m_ref)
+        assert int(n.item()) == n_ref
+        assert np.array_equal(c.cpu().numpy()[:n_ref], ch_ref)
