@@ -414,6 +414,37 @@ def test_temporal_mask_label_layouts_and_call_sequences():
     run.close()
 
 
+def test_temporal_mask_after_adjacency_on_the_same_reference():
+    """ftv_adjacency uses a reference's slot of the context's temporal sums as scratch: a temporal test of that
+    reference right after it (and once more after that) still equals the oracle's (Sec. III-E)."""
+    wl = make_workload("temporal", reduced=True)
+    run = Run(wl)
+    i, r = 2, wl.ref_views[2]
+    lab, S = wl.labels(r)
+    labels = dev(lab)
+    frames = [run.planes(f)[r] for f in range(3)]
+    host = [wl.view(r, f) for f in range(3)]
+    cap = 8 * S + 64
+    es = torch.zeros(cap, dtype=torch.int32, device="cuda")
+    et = torch.zeros(cap, dtype=torch.int32, device="cuda")
+    beta = torch.zeros(cap, dtype=torch.float32, device="cuda")
+    ne = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        ftv.ftv_adjacency(run.ctx, i, frames[1], labels, S, 4, 37.5, 1.5, es, et, beta, ne)
+        for cur, prev in ((1, 0), (2, 1)):
+            mask = torch.empty(S, dtype=torch.uint8, device="cuda")
+            changed = torch.empty(S, dtype=torch.int32, device="cuda")
+            n = torch.empty(1, dtype=torch.int32, device="cuda")
+            ftv.ftv_temporal_mask(run.ctx, i, frames[cur], frames[prev], frames[0], labels, S, 12, 4, 1, mask,
+                                  changed, n)
+            assert run.check() == 0
+            m_ref, ch_ref, n_ref = oracle.temporal_mask(lab, S, host[cur], host[prev], host[0], 2, 12, 4, 1)
+            assert np.array_equal(mask.cpu().numpy(), m_ref)
+            assert int(n.item()) == n_ref
+            assert np.array_equal(changed.cpu().numpy()[:n_ref], ch_ref)
+    run.close()
+
+
 def test_temporal_mask_views_equals_the_oracle_per_reference():
     """Every reference of the reduced temporal workload in one ftv_temporal_mask_views call, two of them with
     other label maps (one label per pixel at random; five column bands), in both channel modes, with and
