@@ -5,7 +5,7 @@
 // three packed frames: current, previous P, I; per-segment labels of the previous and the I frame), and
 // a batch runs the whole hot path for many jobs (frames of different streams, shapes, view, segment and
 // label counts) with one fixed sequence of launches:
-//   H2D descriptor copy -> pack (all views of all jobs) -> temporal statistics -> masks + changed lists
+//   H2D descriptor copy -> pack (all views of all jobs) -> temporal statistics -> masks -> changed lists
 //   -> zero changed cost rows -> plan -> persistent cost kernel over the flat (job, reference, tile,
 //   label block) queue -> winner-take-all with adoption and label-state update -> optional depth maps.
 // Every kernel reads its work from the descriptor block and sizes its loop from it, with grids fixed
@@ -50,8 +50,10 @@ struct TempUnit {
     uint32_t* status;              // the job's status word
     const uint32_t* stream_status; // errors of the stream's resident state (its label maps' index)
     int32_t W, H, S, t_p, t_i, nch, fmt, is_i;
-    int32_t row_base;   // rows of P-frame units, flattened (I-frame units have no rows)
+    int32_t tile_base;  // temporal tiles of P-frame units, flattened (I-frame units have none)
     int32_t stat_base;  // stats words of P-frame units, flattened
+    int32_t chunk_base; // decide/compact chunks of all units, flattened
+    int32_t pad;
 };
 
 struct WtaUnit {
@@ -71,7 +73,7 @@ struct WtaUnit {
 
 struct Header {
     int32_t n_pack, n_units, fmt, combine;
-    int32_t pack_rows, temp_rows, temp_stats, wta_segs, depth_rows, pad[3];
+    int32_t pack_rows, temp_tiles, temp_stats, wta_segs, depth_rows, temp_chunks, pad[2];
 };
 
 struct BatchLayout {
@@ -165,55 +167,112 @@ __global__ void temporal_zero_multi_kernel(const Header* __restrict__ hdr, const
     }
 }
 
-// Per-segment sums of cur - prev and cur - I (rows of P-frame units flattened; one block per row at a
-// time). Lanes with the same label are reduced in the warp first.
-__global__ void temporal_accumulate_multi_kernel(const Header* __restrict__ hdr, const TempUnit* __restrict__ units) {
-    const int rows = hdr->temp_rows, n = hdr->n_units;
-    const int lane = threadIdx.x & 31;
-    for (int g = blockIdx.x; g < rows; g += gridDim.x) {
-        const int u = find_base(&units[0].row_base, sizeof(TempUnit), n, g);
-        const TempUnit& T = units[u];
-        const int y = g - T.row_base;
-        for (int x0 = 0; x0 < T.W; x0 += blockDim.x) {
-            const int x = x0 + threadIdx.x;
-            const bool in = x < T.W;
-            const int l = in ? T.labels[(int64_t)y * T.W + x] : -1;
-            const bool ok = in && (unsigned)l < (unsigned)T.S;
-            if (in && !ok) atomicOr(T.status, ST_BAD_LABEL);
-            int dp[3] = {0, 0, 0}, di[3] = {0, 0, 0};
-            if (ok) {
-                int a[3], b[3], c[3];
-                const int64_t i = (int64_t)y * T.W + x;
-                texel_fields(T.cur, T.fmt, i, a);
-                texel_fields(T.prev, T.fmt, i, b);
-                texel_fields(T.ifr, T.fmt, i, c);
-                for (int k = 0; k < 3; ++k) {
-                    dp[k] = k < T.nch ? a[k] - b[k] : 0;
-                    di[k] = k < T.nch ? a[k] - c[k] : 0;
-                }
-            }
-            const int key = ok ? l : -1;
-            unsigned rem = __ballot_sync(kFull, ok);
-            while (rem) {
-                const int leader = __ffs(rem) - 1;
-                const int kk = __shfl_sync(kFull, key, leader);
-                const bool mine = key == kk;
-                const unsigned grp = __ballot_sync(kFull, mine);
-                int sums[7];
-                sums[0] = __popc(grp);
+// Per-segment sums of cur - prev and cur - I over the P-frame units' pixels, in tiles of kTTileW x kTTileH
+// pixels flattened over the units (tile_base). Each thread walks one column of kTRows pixels of a tile and
+// sums the vertical runs of equal labels in registers; finished runs go to the CTA's 32-bit bins in shared
+// memory, indexed by label - (the tile's least label) (labels beyond kTBins of it go to global memory
+// directly), and each non-empty bin is added to the segment's 64-bit sums once per tile. Every load of a
+// column is issued before any is used (positions past the view's edge are clamped into it and dropped
+// through their label). The sums are exact integers: the order of the additions does not matter.
+constexpr int kTTileW = 128, kTRows = 8, kTTileH = 2 * kTRows, kTBins = 512;
+
+__global__ void __launch_bounds__(256) temporal_accumulate_multi_kernel(const Header* __restrict__ hdr,
+                                                                        const TempUnit* __restrict__ units) {
+    __shared__ __align__(16) int bins[7][kTBins];  // n, dP[3], dI[3]
+    __shared__ int s_base, s_top;
+    const int tiles = hdr->temp_tiles, n_units = hdr->n_units;
+    const int tid = threadIdx.x;
+    for (int g = blockIdx.x; g < tiles; g += gridDim.x) {
+        const TempUnit& T = units[find_base(&units[0].tile_base, sizeof(TempUnit), n_units, g)];
+        const int W = T.W, H = T.H, S = T.S, nch = T.nch, fmt = T.fmt;
+        const int tx = (W + kTTileW - 1) / kTTileW, t = g - T.tile_base;
+        const int x = (t % tx) * kTTileW + (tid % kTTileW), y0 = (t / tx) * kTTileH + (tid / kTTileW) * kTRows;
+        const int xc = min(x, W - 1);
+        int lab[kTRows];
+        int d[kTRows][6];  // dP[3], dI[3]
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    sums[1 + k] = __reduce_add_sync(kFull, mine ? dp[k] : 0);
-                    sums[4 + k] = __reduce_add_sync(kFull, mine ? di[k] : 0);
-                }
-                if (lane == leader) {
-                    unsigned long long* st = reinterpret_cast<unsigned long long*>(T.stats + (int64_t)kk * kStat);
+        for (int r = 0; r < kTRows; ++r) {
+            const int64_t i = (int64_t)min(y0 + r, H - 1) * W + xc;
+            lab[r] = __ldg(T.labels + i);
+            int a[3], b[3], c[3];
+            texel_fields(T.cur, fmt, i, a);
+            texel_fields(T.prev, fmt, i, b);
+            texel_fields(T.ifr, fmt, i, c);
 #pragma unroll
-                    for (int k = 0; k < 7; ++k)
-                        if (sums[k]) atomicAdd(&st[k], (unsigned long long)(long long)sums[k]);
-                }
-                rem &= ~grp;
+            for (int k = 0; k < 3; ++k) {
+                d[r][k] = k < nch ? a[k] - b[k] : 0;
+                d[r][3 + k] = k < nch ? a[k] - c[k] : 0;
             }
+        }
+        int lmin = INT_MAX, lmax = -1;
+        bool bad = false;
+#pragma unroll
+        for (int r = 0; r < kTRows; ++r) {
+            const bool in = x < W && y0 + r < H;
+            if (in && (unsigned)lab[r] < (unsigned)S) {
+                lmin = min(lmin, lab[r]);
+                lmax = max(lmax, lab[r]);
+            } else {
+                bad = bad || in;
+                lab[r] = -1;
+            }
+        }
+        if (bad) atomicOr(T.status, ST_BAD_LABEL);
+        __syncthreads();  // the previous tile's bins are no longer read
+        for (int i = tid; i < 7 * kTBins / 4; i += blockDim.x) reinterpret_cast<int4*>(&bins[0][0])[i] = make_int4(0, 0, 0, 0);
+        if (tid == 0) {
+            s_base = INT_MAX;
+            s_top = -1;
+        }
+        __syncthreads();
+        lmin = __reduce_min_sync(kFull, lmin);
+        lmax = __reduce_max_sync(kFull, lmax);
+        if ((tid & 31) == 0 && lmax >= 0) {
+            atomicMin(&s_base, lmin);
+            atomicMax(&s_top, lmax);
+        }
+        __syncthreads();
+        const int base = s_base;
+        int cur = -1, acc[7];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) acc[q] = 0;
+        auto flush = [&]() {
+            const unsigned bi = (unsigned)(cur - base);
+            if (bi < (unsigned)kTBins) {
+#pragma unroll
+                for (int q = 0; q < 7; ++q)
+                    if (q == 0 || acc[q] != 0) atomicAdd(&bins[q][bi], acc[q]);
+            } else {
+                unsigned long long* st = reinterpret_cast<unsigned long long*>(T.stats + (int64_t)cur * kStat);
+#pragma unroll
+                for (int q = 0; q < 7; ++q)
+                    if (acc[q] != 0) atomicAdd(&st[q], (unsigned long long)(long long)acc[q]);
+            }
+        };
+#pragma unroll
+        for (int r = 0; r < kTRows; ++r) {
+            const int l = lab[r];
+            if (l != cur) {
+                if (cur >= 0) flush();
+                cur = l;
+#pragma unroll
+                for (int q = 0; q < 7; ++q) acc[q] = 0;
+            }
+            if (l >= 0) {
+                acc[0] += 1;
+#pragma unroll
+                for (int q = 1; q < 7; ++q) acc[q] += d[r][q - 1];
+            }
+        }
+        if (cur >= 0) flush();
+        __syncthreads();
+        const int used = min(kTBins, s_top - base + 1);
+        for (int i = tid; i < used; i += blockDim.x) {
+            if (bins[0][i] == 0) continue;
+            unsigned long long* st = reinterpret_cast<unsigned long long*>(T.stats + (int64_t)(base + i) * kStat);
+#pragma unroll
+            for (int q = 0; q < 7; ++q)
+                if (bins[q][i] != 0) atomicAdd(&st[q], (unsigned long long)(long long)bins[q][i]);
         }
     }
 }
@@ -245,44 +304,67 @@ __device__ int block_scan_1024(int v, int* total) {
 
 __device__ __forceinline__ int64_t iabs64(int64_t v) { return v < 0 ? -v : v; }
 
-// One block of 1024 threads per unit: masks and the ordered changed list. I-frame units list every
-// segment (Sec. III-E: all segments of an I-type frame are estimated). Errors found when the stream's
-// resident state was built (a label outside [0, S), a segment too large for int32 sums) are reported by
-// every job of that stream.
-__global__ void temporal_finalize_multi_kernel(const Header* __restrict__ hdr, const TempUnit* __restrict__ units) {
-    for (int u = blockIdx.x; u < hdr->n_units; u += gridDim.x) {
-        const TempUnit& T = units[u];
-        if (threadIdx.x == 0 && T.stream_status) {
+// Masks and ordered changed lists of every unit, in two passes over chunks of kTChunk segments flattened over
+// the units (chunk_base; a unit without segments has one chunk). decide: one thread per segment sets its mask
+// (I-frame units list every segment: Sec. III-E estimates all segments of an I-type frame) and each chunk's
+// count of changed segments goes to the spare word (index 7) of its first segment's sums; the unit's first
+// chunk also reports errors found when the stream's resident state was built (a label outside [0, S), a
+// segment too large for int32 sums), which every job of that stream carries. compact: each chunk adds the
+// counts of the unit's chunks before it, scans its own flags and writes their positions; the unit's last
+// chunk writes the total.
+constexpr int kTChunk = 256;
+
+__global__ void __launch_bounds__(kTChunk) temporal_decide_multi_kernel(const Header* __restrict__ hdr,
+                                                                        const TempUnit* __restrict__ units) {
+    const int chunks = hdr->temp_chunks, n_units = hdr->n_units;
+    for (int g = blockIdx.x; g < chunks; g += gridDim.x) {
+        const TempUnit& T = units[find_base(&units[0].chunk_base, sizeof(TempUnit), n_units, g)];
+        const int c = g - T.chunk_base, S = T.S;
+        if (c == 0 && threadIdx.x == 0 && T.stream_status) {
             const uint32_t e = *T.stream_status;
             if (e) atomicOr(T.status, e);
         }
-        const int S = T.S;
-        const int per = (S + blockDim.x - 1) / blockDim.x;
-        const int b = threadIdx.x * per, e = min(S, b + per);
-        int cnt = 0;
-        for (int s = b; s < e; ++s) {
-            int m = FTV_MASK_CHANGED;
-            if (!T.is_i) {
-                const int64_t* st = T.stats + (int64_t)s * kStat;
-                const int64_t n = st[0];
-                if (n > 0) {
-                    bool okp = true, oki = true;
-                    for (int c = 0; c < T.nch; ++c) {
-                        okp = okp && iabs64(st[1 + c]) < (int64_t)T.t_p * n;
-                        oki = oki && iabs64(st[4 + c]) < (int64_t)T.t_i * n;
-                    }
-                    m = okp ? FTV_MASK_REUSE_P : (oki ? FTV_MASK_REUSE_I : FTV_MASK_CHANGED);
+        const int s = c * kTChunk + threadIdx.x;
+        int m = FTV_MASK_CHANGED;
+        if (s < S && !T.is_i) {
+            const int64_t* st = T.stats + (int64_t)s * kStat;
+            const int64_t n = st[0];
+            if (n > 0) {
+                bool okp = true, oki = true;
+                for (int k = 0; k < T.nch; ++k) {
+                    okp = okp && iabs64(st[1 + k]) < (int64_t)T.t_p * n;
+                    oki = oki && iabs64(st[4 + k]) < (int64_t)T.t_i * n;
                 }
+                m = okp ? FTV_MASK_REUSE_P : (oki ? FTV_MASK_REUSE_I : FTV_MASK_CHANGED);
             }
-            T.mask[s] = (uint8_t)m;
-            cnt += m == FTV_MASK_CHANGED;
         }
-        int total;
-        int run = block_scan_1024(cnt, &total);
-        for (int s = b; s < e; ++s)
-            if (T.mask[s] == FTV_MASK_CHANGED) T.changed[run++] = s;
-        if (threadIdx.x == 0) *T.n_changed = total;
+        if (s < S) T.mask[s] = (uint8_t)m;
+        const int cnt = __syncthreads_count(s < S && m == FTV_MASK_CHANGED);
+        if (threadIdx.x == 0 && S > 0) T.stats[(int64_t)c * kTChunk * kStat + 7] = cnt;
+    }
+}
+
+__global__ void __launch_bounds__(kTChunk) temporal_compact_multi_kernel(const Header* __restrict__ hdr,
+                                                                         const TempUnit* __restrict__ units) {
+    __shared__ int s_before;
+    const int chunks = hdr->temp_chunks, n_units = hdr->n_units;
+    for (int g = blockIdx.x; g < chunks; g += gridDim.x) {
+        const TempUnit& T = units[find_base(&units[0].chunk_base, sizeof(TempUnit), n_units, g)];
+        const int c = g - T.chunk_base, S = T.S, nc = S > 0 ? (S + kTChunk - 1) / kTChunk : 1;
+        if (threadIdx.x == 0) s_before = 0;
         __syncthreads();
+        int before = 0;  // changed segments of the unit's chunks before this one
+        for (int b = threadIdx.x; b < c; b += kTChunk) before += (int)T.stats[(int64_t)b * kTChunk * kStat + 7];
+        before = __reduce_add_sync(kFull, before);
+        if ((threadIdx.x & 31) == 0 && before) atomicAdd(&s_before, before);
+        __syncthreads();
+        const int s = c * kTChunk + threadIdx.x;
+        const int flag = s < S && T.mask[s] == FTV_MASK_CHANGED;
+        int total;
+        const int pos = block_scan_1024(flag, &total);
+        if (flag) T.changed[s_before + pos] = s;
+        if (c == nc - 1 && threadIdx.x == 0) *T.n_changed = s_before + total;
+        __syncthreads();  // s_before is reset for the next chunk only after every thread has used it
     }
 }
 
@@ -379,6 +461,7 @@ constexpr int kTicketRing = 4096;  // completed tickets whose status ftv_batch_p
 struct ftv_batch {
     int device = 0;
     int n_sm = 0;
+    int temp_per_sm = 1;  // resident CTAs per SM of temporal_accumulate_multi_kernel
     int32_t max_jobs = 0, max_units = 0, max_views = 0;
     BatchLayout lay{};
     char* d_desc = nullptr;     // device descriptor block
@@ -789,6 +872,12 @@ ftv_status ftv_batch_create(int32_t max_jobs, int32_t max_units, int32_t max_vie
         return FTV_ERR_CUDA;
     }
     cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, b->device);
+    // the temporal accumulation strides over its tiles with as many CTAs as stay resident (a second wave
+    // would only be a tail)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->temp_per_sm, temporal_accumulate_multi_kernel, 256, 0) !=
+            cudaSuccess ||
+        b->temp_per_sm < 1)
+        b->temp_per_sm = 1;
     b->fast_rcp = fast_reciprocal_exact();
     b->max_jobs = max_jobs;
     b->max_units = max_units;
@@ -881,7 +970,7 @@ ftv_status ftv_batch_prepare(ftv_batch* b, const ftv_frame_job* jobs, int32_t n_
     RefJob* R = reinterpret_cast<RefJob*>(h + b->lay.jobs);
     WtaUnit* Wt = reinterpret_cast<WtaUnit*>(h + b->lay.wta);
     std::memset(&H, 0, sizeof(H));
-    int pv = 0, pu = 0, pack_rows = 0, temp_rows = 0, temp_stats = 0, wta_segs = 0, depth_rows = 0;
+    int pv = 0, pu = 0, pack_rows = 0, temp_tiles = 0, temp_stats = 0, temp_chunks = 0, wta_segs = 0, depth_rows = 0;
     for (int j = 0; j < n_jobs; ++j) {
         const ftv_frame_job& J = jobs[j];
         ftv_ctx* c = J.ctx;
@@ -931,12 +1020,15 @@ ftv_status ftv_batch_prepare(ftv_batch* b, const ftv_frame_job* jobs, int32_t n_
             t.nch = st.mode == FTV_TM_ALL_YUV ? 3 : 1;
             t.fmt = c->fmt;
             t.is_i = is_i;
-            t.row_base = temp_rows;
+            t.tile_base = temp_tiles;
             t.stat_base = temp_stats;
+            t.chunk_base = temp_chunks;
+            t.pad = 0;
             if (!is_i) {
-                temp_rows += r.H;
+                temp_tiles += ((r.W + kTTileW - 1) / kTTileW) * ((r.H + kTTileH - 1) / kTTileH);
                 temp_stats += S.S * kStat;
             }
+            temp_chunks += S.S > 0 ? (S.S + kTChunk - 1) / kTChunk : 1;
             RefJob& q = R[pu];
             std::memset(&q, 0, sizeof(q));
             q.ref_texels = t.cur;
@@ -998,7 +1090,8 @@ ftv_status ftv_batch_prepare(ftv_batch* b, const ftv_frame_job* jobs, int32_t n_
     H.fmt = fmt;
     H.combine = combine;
     H.pack_rows = pack_rows;
-    H.temp_rows = temp_rows;
+    H.temp_tiles = temp_tiles;
+    H.temp_chunks = temp_chunks;
     H.temp_stats = temp_stats;
     H.wta_segs = wta_segs;
     H.depth_rows = depth_rows;
@@ -1027,8 +1120,9 @@ static cudaError_t enqueue(ftv_batch* b, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     pack_multi_kernel<<<g, 256, 0, s>>>(hdr, pack);
     temporal_zero_multi_kernel<<<g, 256, 0, s>>>(hdr, temp);
-    temporal_accumulate_multi_kernel<<<g, 256, 0, s>>>(hdr, temp);
-    temporal_finalize_multi_kernel<<<std::min(b->max_units, 1024), 1024, 0, s>>>(hdr, temp);
+    temporal_accumulate_multi_kernel<<<b->n_sm * b->temp_per_sm, 256, 0, s>>>(hdr, temp);
+    temporal_decide_multi_kernel<<<g, kTChunk, 0, s>>>(hdr, temp);
+    temporal_compact_multi_kernel<<<g, kTChunk, 0, s>>>(hdr, temp);
     zero_changed_rows_kernel<<<dim3(64, std::min(b->max_units, 65535)), 256, 0, s>>>(hdr, jobs);
     e = launch_plan_device(jobs, &hdr->n_units, b->d_plan, s);
     if (e != cudaSuccess) return e;
@@ -1041,7 +1135,7 @@ static cudaError_t enqueue(ftv_batch* b, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     wta_multi_kernel<<<g, 256, 0, s>>>(hdr, wta);
     depth_multi_kernel<<<g, 256, 0, s>>>(hdr, wta);
-    b->launches += 8 + b->chunks;
+    b->launches += 9 + b->chunks;
     e = cudaGetLastError();
     // every job's status word back to pinned host memory, read by ftv_batch_wait / ftv_batch_poll once the
     // launch's completion event has fired
@@ -1084,7 +1178,7 @@ ftv_status ftv_batch_replay(ftv_batch* b, ftv_stream stream) {
             e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
                 const cudaError_t e1 = enqueue(b, cap);
-                b->launches -= 8 + b->chunks;
+                b->launches -= 9 + b->chunks;
                 e = cudaStreamEndCapture(cap, &b->graph);
                 if (e1 != cudaSuccess) e = e1;
             }
@@ -1101,7 +1195,7 @@ ftv_status ftv_batch_replay(ftv_batch* b, ftv_stream stream) {
     }
     if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, s);
     if (e == cudaSuccess) {
-        b->launches += 8 + b->chunks;
+        b->launches += 9 + b->chunks;
         e = cudaEventRecord(b->done, s);
     }
     if (e == cudaSuccess) b->launched_jobs = b->prepared_jobs;

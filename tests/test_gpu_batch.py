@@ -120,7 +120,7 @@ def test_batched_streams_match_oracle_frame_by_frame():
             lab, S = s0.wl.labels(r)
             want_d = oracle.depth_map(lab, S, refs[0].prev[r], s0.wl.n_labels, s0.wl.z_near, s0.wl.z_far)
             assert np.array_equal(s0.depth[r_i].cpu().numpy(), want_d)
-    assert ftv.ftv_batch_launch_count(batch) == 9 * len(SCHEDULE)
+    assert ftv.ftv_batch_launch_count(batch) == 10 * len(SCHEDULE)
     batch.close()
     for s in streams:
         s.ctx.close()
@@ -190,7 +190,7 @@ def test_chunked_cost_launches_give_identical_results():
         for frame, ftype in SCHEDULE:
             _run(b, [s.job(frame, ftype) for s in streams], replay=replay)
             res.append([s.labels() for s in streams])
-        assert ftv.ftv_batch_launch_count(b) == (8 + chunks) * len(SCHEDULE)
+        assert ftv.ftv_batch_launch_count(b) == (9 + chunks) * len(SCHEDULE)
         results[chunks] = res
         for bad in (0, ftv.FTV_MAX_BATCH_CHUNKS + 1):
             with pytest.raises(ftv.FtvError):
