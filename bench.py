@@ -129,8 +129,9 @@ class ClockSampler:
 
 def _traffic_for_current_kernel(workload_key: str, table: str = "cost_kernel_traffic.txt",
                                 source: str = "ftv_cost.cu", column: int = 2):
-    """Bytes per launch of a kernel from the committed ncu summary table (column 2: DRAM read + write; column
-    3, where given: L2 bytes), if it was taken on the current source of that kernel (hash match); else None."""
+    """Bytes per launch of a kernel from the committed ncu summary table (column 2: DRAM read + write; columns
+    3 and 4, where given: L2 and L1 bytes), if it was taken on the current source of that kernel (hash match);
+    else None."""
     path = os.path.join(ROOT, "profiles", table)
     src = os.path.join(ROOT, "paper_1909_02294_gb300", "csrc", source)
     if not os.path.exists(path):
@@ -819,6 +820,7 @@ def main():
         achieved = (ev_bytes + comp_bytes) / (kms / 1000.0) / 1e9
         traffic = _traffic_for_current_kernel(args.workload + ("_fp64" if fp64 else ""))
         l2_bytes = _traffic_for_current_kernel(args.workload + ("_fp64" if fp64 else ""), column=3)
+        l1_bytes = _traffic_for_current_kernel(args.workload + ("_fp64" if fp64 else ""), column=4)
         clk = clocks.summary()
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         sm_mhz = clk["sm_mhz"] if clk else 2070.0
@@ -851,6 +853,7 @@ def main():
                          "dram_fraction_of_algorithmic": (traffic / (ev_bytes + comp_bytes)) if traffic else None,
                          "ncu_dram_gbs": (traffic / (kms / 1000.0) / 1e9) if traffic else None,
                          "ncu_l2_gbs": (l2_bytes / (kms / 1000.0) / 1e9) if l2_bytes else None,
+                         "ncu_l1_gbs": (l1_bytes / (kms / 1000.0) / 1e9) if l1_bytes else None,
                          "note": "a notional gather rate: most gathers hit L1/L2, and the DRAM traffic (traffic) "
                                  "is a small fraction of the algorithmic bytes; the kernel is issue/ALU-bound"},
             "alu_roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Tops/s",
