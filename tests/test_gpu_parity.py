@@ -490,6 +490,45 @@ def test_temporal_mask_views_equals_the_oracle_per_reference():
     run.close()
 
 
+def test_temporal_mask_views_more_references_than_one_launch_holds():
+    """18 references of one context (more than the 16 one launch sequence takes, so the call makes two), each
+    64 x 48 with its own random 10-bit frames and label map, in one ftv_temporal_mask_views call against the
+    oracle per reference (Sec. III-E)."""
+    import types
+    from synth import linear_rig
+    n, W, Hh, S = 18, 64, 48, 40
+    cams = linear_rig(n, 0.02, 100.0, W, Hh)
+    ctx = ftv.ftv_depth_init(cams, list(range(n)), 4, 1.0, 10.0, sample_bytes=2, bit_depth=10, max_segments=S)
+    rng = np.random.default_rng(18)
+    labs, host, dev_frames = [], [], []
+    for r in range(n):
+        labs.append(rng.integers(0, S, size=(Hh, W), dtype=np.int32) if r % 2 else
+                    np.repeat(np.repeat(np.arange(S // 8 * 8, dtype=np.int32).reshape(S // 8, 8) % S, Hh // 5 + 1,
+                                        axis=0)[:Hh], W // 8, axis=1)[:, :W].copy())
+        frames = []
+        for f in range(3):
+            Y, U, V = (rng.integers(0, 1024, size=(Hh, W)).astype(np.uint16) for _ in range(3))
+            frames.append(types.SimpleNamespace(Y=Y, U=U, V=V))
+        host.append(frames)
+        dev_frames.append([tuple(dev(a) for a in (v.Y, v.U, v.V)) for v in frames])
+    for mode, ifr in ((0, 2), (1, None)):
+        masks = [torch.empty(S, dtype=torch.uint8, device="cuda") for _ in range(n)]
+        changed = [torch.empty(S, dtype=torch.int32, device="cuda") for _ in range(n)]
+        ns = [torch.empty(1, dtype=torch.int32, device="cuda") for _ in range(n)]
+        ftv.ftv_temporal_mask_views(ctx, list(range(n)), [dev_frames[r][1] for r in range(n)],
+                                    [dev_frames[r][0] for r in range(n)],
+                                    [dev_frames[r][ifr] for r in range(n)] if ifr is not None else None,
+                                    [dev(l) for l in labs], [S] * n, 40, 20, mode, masks, changed, ns)
+        assert ftv.ftv_check(ctx) == 0
+        for r in range(n):
+            m_ref, ch_ref, n_ref = oracle.temporal_mask(labs[r], S, host[r][1], host[r][0],
+                                                        host[r][ifr] if ifr is not None else None, 2, 40, 20, mode)
+            assert np.array_equal(masks[r].cpu().numpy(), m_ref), (mode, r)
+            assert int(ns[r].item()) == n_ref, (mode, r)
+            assert np.array_equal(changed[r].cpu().numpy()[:n_ref], ch_ref), (mode, r)
+    ctx.close()
+
+
 # ------------------------------------------------------------------------------------ full size, sampled
 
 @pytest.mark.parametrize("name", ["hd8", "uhd15"])
